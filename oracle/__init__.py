@@ -1,0 +1,275 @@
+"""FP64 CPU oracle for VOctree rendering -- TEST INFRASTRUCTURE.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product (the CUDA library and its
+binding) never does, and this package imports nothing from the product: both
+take their inputs from the seeded generator.
+
+The arithmetic lives in ``neuvv_oracle.c`` (plain C, double precision); this
+module compiles it with gcc and marshals numpy arrays.  Each wrapper names the
+passage of the paper that the C function follows.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "neuvv_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (host code, no architecture-specific flags)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-pthread",
+                               "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Tree(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int), ("K", ctypes.c_int), ("T", ctypes.c_int), ("degree", ctypes.c_int),
+                ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("child", ctypes.c_void_p), ("w_sigma", ctypes.c_void_p), ("w_gamma", ctypes.c_void_p),
+                ("w_hh", ctypes.c_void_p), ("coeff_f64", ctypes.c_int),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("bmin", ctypes.c_double * 3), ("bmax", ctypes.c_double * 3)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("t_stop", ctypes.c_double), ("act", ctypes.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            d = ctypes.c_double
+            p = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            ci = ctypes.c_int
+            _lib.or_gegenbauer.restype = d
+            _lib.or_gegenbauer.argtypes = [ci, d, d]
+            _lib.or_legendre.restype = d
+            _lib.or_legendre.argtypes = [ci, ci, d]
+            _lib.or_sh_real.restype = d
+            _lib.or_sh_real.argtypes = [ci, ci, p]
+            _lib.or_hh_norm.restype = d
+            _lib.or_hh_norm.argtypes = [ci, ci]
+            _lib.or_hh_radial.restype = d
+            _lib.or_hh_radial.argtypes = [ci, ci, d]
+            _lib.or_hh_radial_dgamma.restype = d
+            _lib.or_hh_radial_dgamma.argtypes = [ci, ci, d]
+            _lib.or_hh.restype = d
+            _lib.or_hh.argtypes = [ci, ci, ci, d, p]
+            _lib.or_hh_all.restype = None
+            _lib.or_hh_all.argtypes = [ci, d, p, p, p]
+            _lib.or_n_hh.restype = ci
+            _lib.or_n_hh.argtypes = [ci]
+            _lib.or_hh_index.restype = ci
+            _lib.or_hh_index.argtypes = [ci, ci, ci]
+            _lib.or_render.restype = None
+            _lib.or_render.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, p, ci]
+            _lib.or_trace_batch.restype = None
+            _lib.or_trace_batch.argtypes = [p, i64, p, p, ci, p, p, p, p, ci]
+            _lib.or_render_grad.restype = None
+            _lib.or_render_grad.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, ci]
+            _lib.or_compose.restype = None
+            _lib.or_compose.argtypes = [p, p, p, p, ci, ci, p, i64, p, p, p, p, p, p, ci]
+            _lib.or_adam.restype = None
+            _lib.or_adam.argtypes = [i64, ci, p, p, p, p, p, d, d, d, d, ci]
+            _lib.or_round_bf16.restype = None
+            _lib.or_round_bf16.argtypes = [p, p, i64]
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1)
+
+
+class OracleTree:
+    """Holds the arrays alive while the C struct points at them.
+
+    Coefficients may be float32 (read exactly as doubles) or float64 (for
+    finite differences).  ``tree`` is any object with the generator's VOctree
+    attributes (child, w_sigma, w_gamma, w_hh, basis_A, basis_B, ...).
+    """
+
+    def __init__(self, tree, w_sigma=None, w_gamma=None, w_hh=None):
+        ws = tree.w_sigma if w_sigma is None else w_sigma
+        wg = tree.w_gamma if w_gamma is None else w_gamma
+        wh = tree.w_hh if w_hh is None else w_hh
+        f64 = any(np.asarray(x).dtype == np.float64 for x in (ws, wg, wh))
+        dt = np.float64 if f64 else np.float32
+        self.child = np.ascontiguousarray(tree.child, np.uint32)
+        self.ws = np.ascontiguousarray(ws, dt)
+        self.wg = np.ascontiguousarray(wg, dt)
+        self.wh = np.ascontiguousarray(wh, dt)
+        self.A = np.ascontiguousarray(tree.basis_A, np.float64)
+        self.B = np.ascontiguousarray(tree.basis_B, np.float64)
+        self.K, self.T, self.degree, self.depth = tree.K, tree.T, tree.hh_degree, tree.depth
+        self.n_leaves = int(self.ws.shape[1])
+        self.N_h = lib().or_n_hh(self.degree)
+        s = _Tree()
+        s.depth, s.K, s.T, s.degree = self.depth, self.K, self.T, self.degree
+        s.n_nodes, s.n_leaves = self.child.size // 8, self.n_leaves
+        s.child, s.w_sigma, s.w_gamma, s.w_hh = (self.child.ctypes.data, self.ws.ctypes.data,
+                                                 self.wg.ctypes.data, self.wh.ctypes.data)
+        s.coeff_f64 = 1 if f64 else 0
+        s.A, s.B = self.A.ctypes.data, self.B.ctypes.data
+        for k in range(3):
+            s.bmin[k] = tree.aabb_min[k]
+            s.bmax[k] = tree.aabb_max[k]
+        self.struct = s
+
+
+def _opts(t_stop: float, act: str) -> _Opts:
+    return _Opts(float(t_stop), {"sigmoid": 0, "identity": 1}[act])
+
+
+def _rays64(rays):
+    o = np.ascontiguousarray(rays.origins, np.float64)
+    d = np.ascontiguousarray(rays.dirs, np.float64)
+    t = np.ascontiguousarray(rays.times, np.float64)
+    return o, d, t
+
+
+def render(tree, rays, t_stop: float = 1e-4, act: str = "sigmoid", nthreads: int | None = None,
+           otree: OracleTree | None = None) -> dict:
+    """Eq. volume-rendering over the voxels each ray crosses (Sec. 4.3 "Rendering").
+
+    Returns rgb [n,3] (premultiplied, black background), alpha, depth, tau
+    (optical depth sum sigma*delta), nseg (composited segments) and
+    stop_margin (|tau_{i+1} - ln(1/t_stop)| minimum, for near-threshold checks).
+    """
+    ot = otree or OracleTree(tree)
+    o, d, t = _rays64(rays)
+    n = t.size
+    out = {k: np.zeros(n) for k in ("alpha", "depth", "tau", "stop_margin")}
+    out["rgb"] = np.zeros((n, 3))
+    out["nseg"] = np.zeros(n, np.int32)
+    op = _opts(t_stop, act)
+    lib().or_render(ctypes.byref(ot.struct), ctypes.byref(op), n, _ptr(o), _ptr(d), _ptr(t), _ptr(out["rgb"]),
+                    _ptr(out["alpha"]), _ptr(out["depth"]), _ptr(out["tau"]), _ptr(out["nseg"]),
+                    _ptr(out["stop_margin"]), nthreads or default_threads())
+    return out
+
+
+def trace(tree, rays, max_out: int = 64, nthreads: int | None = None, otree: OracleTree | None = None) -> dict:
+    """Occupied leaves each ray crosses, with entry/exit distances (Sec. 4.3
+    "Rendering": voxels on the path and the lengths of the segments inside)."""
+    ot = otree or OracleTree(tree)
+    o, d, _ = _rays64(rays)
+    n = o.shape[1]
+    leaf = np.full((n, max_out), -1, np.int64)
+    t0 = np.zeros((n, max_out))
+    t1 = np.zeros((n, max_out))
+    cnt = np.zeros(n, np.int32)
+    lib().or_trace_batch(ctypes.byref(ot.struct), n, _ptr(o), _ptr(d), max_out, _ptr(leaf), _ptr(t0), _ptr(t1),
+                         _ptr(cnt), nthreads or default_threads())
+    return {"leaf": leaf, "t0": t0, "t1": t1, "count": cnt}
+
+
+def render_grad(tree, rays, grad_rgb, grad_alpha=None, t_stop: float = 1e-4, act: str = "sigmoid",
+                nthreads: int | None = None, otree: OracleTree | None = None) -> dict:
+    """Analytic gradient of L(C, alpha) w.r.t. (w_sigma, w_gamma, w_hh), given
+    dL/dC and dL/dalpha per ray (Sec. 4.3 "Optimization").  Planes as inputs."""
+    ot = otree or OracleTree(tree)
+    o, d, t = _rays64(rays)
+    n = t.size
+    g = np.ascontiguousarray(grad_rgb, np.float64).reshape(n, 3)
+    ga = None if grad_alpha is None else np.ascontiguousarray(grad_alpha, np.float64)
+    gs = np.zeros((ot.K, ot.n_leaves))
+    gg = np.zeros((ot.K, ot.n_leaves))
+    gh = np.zeros((3, ot.N_h, ot.n_leaves))
+    op = _opts(t_stop, act)
+    lib().or_render_grad(ctypes.byref(ot.struct), ctypes.byref(op), n, _ptr(o), _ptr(d), _ptr(t), _ptr(g),
+                         None if ga is None else _ptr(ga), _ptr(gs), _ptr(gg), _ptr(gh), nthreads or default_threads())
+    return {"w_sigma": gs, "w_gamma": gg, "w_hh": gh}
+
+
+def compose(trees, transforms, time_offsets, tints, rays, mode: str = "sorted", t_stop: float = 1e-4,
+            act: str = "sigmoid", nthreads: int | None = None) -> dict:
+    """Eq. st_composite_affine per primitive, then depth-aware blending
+    (Algorithm 1; mode 'sorted' = stable depth sort + premultiplied over,
+    'alg1' = Algorithm 1 literally on premultiplied layers)."""
+    ots = [t if isinstance(t, OracleTree) else OracleTree(t) for t in trees]
+    P = len(ots)
+    arr = (ctypes.c_void_p * P)(*[ctypes.addressof(x.struct) for x in ots])
+    xf = np.ascontiguousarray(np.asarray(transforms, np.float64).reshape(P, 12))
+    toff = np.ascontiguousarray(time_offsets, np.float64)
+    tint = np.ascontiguousarray(np.asarray(tints, np.float64).reshape(P, 3))
+    o, d, t = _rays64(rays)
+    n = t.size
+    rgb = np.zeros((n, 3))
+    alpha = np.zeros(n)
+    depth = np.zeros(n)
+    op = _opts(t_stop, act)
+    lib().or_compose(arr, _ptr(xf), _ptr(toff), _ptr(tint), P, {"sorted": 0, "alg1": 1}[mode], ctypes.byref(op), n,
+                     _ptr(o), _ptr(d), _ptr(t), _ptr(rgb), _ptr(alpha), _ptr(depth), nthreads or default_threads())
+    return {"rgb": rgb, "alpha": alpha, "depth": depth}
+
+
+def adam(w, m, v, g, touched, lr, b1, b2, eps, step):
+    """Sparse Adam, in place on float64 [n_leaves, rec] arrays."""
+    for a in (w, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, np.float64)
+    tch = np.ascontiguousarray(touched, np.uint8)
+    lib().or_adam(w.shape[0], w.shape[1], _ptr(w), _ptr(m), _ptr(v), _ptr(g), _ptr(tch), lr, b1, b2, eps, step)
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """float32 -> bfloat16 (round to nearest even) -> float32."""
+    x = np.ascontiguousarray(x, np.float32)
+    out = np.empty_like(x)
+    lib().or_round_bf16(_ptr(x), _ptr(out), x.size)
+    return out
+
+
+# -- point evaluations for the pins -------------------------------------------
+
+def hh_all(degree: int, gamma: float, d) -> np.ndarray:
+    d = np.ascontiguousarray(d, np.float64)
+    out = np.zeros(lib().or_n_hh(degree))
+    lib().or_hh_all(degree, gamma, _ptr(d), _ptr(out), None)
+    return out
+
+
+def hh_all_dgamma(degree: int, gamma: float, d) -> np.ndarray:
+    d = np.ascontiguousarray(d, np.float64)
+    out = np.zeros(lib().or_n_hh(degree))
+    dout = np.zeros_like(out)
+    lib().or_hh_all(degree, gamma, _ptr(d), _ptr(out), _ptr(dout))
+    return dout
+
+
+def sh_real(l: int, m: int, d) -> float:
+    d = np.ascontiguousarray(d, np.float64)
+    return lib().or_sh_real(l, m, _ptr(d))
+
+
+def gegenbauer(k: int, lam: float, x: float) -> float:
+    return lib().or_gegenbauer(k, lam, x)
+
+
+def legendre(l: int, m: int, x: float) -> float:
+    return lib().or_legendre(l, m, x)
+
+
+def hh_index(n: int, l: int, m: int) -> int:
+    return lib().or_hh_index(n, l, m)

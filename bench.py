@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""VOctree renderer benchmark (NeuVV Sec. 4.3): training-step throughput.
+
+Workload: the depth-9 shell VOctree (~2M occupied leaves, K=16 temporal
+bases over T=150 frames, HH degree 3), 8 camera poses on a sphere of radius
+2.5 at 1920x1080, each at its own time stamp: 16,588,800 rays per step, all
+resident in HBM.  Coefficients are stored in BF16 with an FP32 master copy.
+
+One step = forward render (packet kernel) -> MSE loss gradient against fixed
+target images -> fused adjoint -> sparse Adam on the touched leaves.  The
+headline metric is leaf-segment samples per second of the forward+backward
+pair (a sample is one leaf segment evaluated by the forward and re-evaluated
+by the adjoint, counted once).
+
+Also reported: the BF16 forward alone (ms per 1080p frame), the plain FP32
+single-view kernel on the same rays, the roofline of the dominant kernel,
+the same metric end to end through the C ABI with host buffers, and the FP64
+oracle timed on a bounded sample on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun) runs independent replicas: one per GPU, no data-path
+collective; only the timing uses a barrier and a max over ranks.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "VOctree Msamples/s fwd+bwd (BF16 batched vs FP32 plain); ms per 1080p frame; %roof"
+UNIT = "Msamples/s"
+WORKLOAD = ("depth-9 shell VOctree (~2M leaves, K=16, T=150, HH degree 3), 8 views x 1920x1080 "
+            "at 8 time stamps (16,588,800 rays), BF16 storage + FP32 master; step = fwd + MSE grad + adjoint + "
+            "sparse Adam")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline sample")
+    return p.parse_args()
+
+
+def flops_per_sample(K, deg, backward=False):
+    """Algorithmic FP32 operations per leaf segment (FMA = 2): two K-dots,
+    the radial recurrence (4 per (n,l) pair), the colour sums (per channel
+    N_h FMAs over m plus one FMA per (n,l) pair), activations and compositing
+    (~20).  The adjoint recomputes that and adds d/dgamma of the radial
+    factors, dL/dw_HH (2 per coefficient), dL/dgamma (per channel N_h + pairs
+    FMAs) and the two K-long scatters."""
+    nh = sum((n + 1) ** 2 for n in range(deg + 1))
+    pairs = (deg + 1) * (deg + 2) // 2
+    fwd = 4 * K + 4 * pairs + 3 * 2 * (nh + pairs) + 20
+    if not backward:
+        return fwd
+    return fwd + 4 * pairs + 3 * 2 * nh + 3 * 2 * (nh + pairs) + 4 * K + 30
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 6800.0, "fallback", 2070.0
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(tree, rays, target_seconds, seed=99):
+    """FP64 oracle forward+adjoint on a seeded random sample of the same rays,
+    on all host cores; sized to about target_seconds of CPU work."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    ot = oracle.OracleTree(tree)
+    cores = oracle.default_threads()
+    n_try = 256 * cores
+    idx = np.sort(rng.choice(rays.n, size=n_try, replace=False))
+    sub = rays.subset(idx)
+    g = rng.standard_normal((sub.n, 3))
+    t0 = time.perf_counter()
+    oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores)
+    dt = time.perf_counter() - t0
+    n = int(min(rays.n, max(n_try, n_try * target_seconds / max(dt, 1e-3))))
+    idx = np.sort(rng.choice(rays.n, size=n, replace=False))
+    sub = rays.subset(idx)
+    g = rng.standard_normal((sub.n, 3))
+    fwd = oracle.render(tree, sub, otree=ot, nthreads=cores)
+    samples = int(fwd["nseg"].sum())
+    t0 = time.perf_counter()
+    oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": samples / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} seeded random rays of the same 16.6M-ray workload ({samples} samples), "
+                      f"FP64 forward+adjoint, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle (the only reference this method has)
+    timed on bounded samples of the same workload on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2202_06088_gb300 import inputs as I
+    oracle.build()
+    tree = I.config2_tree()
+    rays = I.config2_rays()[0]
+    ot = oracle.OracleTree(tree)
+    cores = oracle.default_threads()
+    rng = np.random.default_rng(5)
+    per_step = 96 * cores
+    times, samples = [], []
+    for s in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(rays.n, size=per_step, replace=False))
+        sub = rays.subset(idx)
+        g = rng.standard_normal((sub.n, 3))
+        nseg = int(oracle.render(tree, sub, otree=ot, nthreads=cores)["nseg"].sum())
+        t0 = time.perf_counter()
+        oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            samples.append(nseg)
+    value = sum(samples) / sum(times) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "per_step_sample_rays": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} seeded random rays of the workload per step, FP64 fwd+adjoint"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2202_06088_gb300 import binding as B
+    from paper_2202_06088_gb300 import inputs as I
+    B.lib()
+
+    tree = I.config2_tree()
+    rays = I.config2_rays()[0]
+    n = rays.n
+    dev = torch.device("cuda", local)
+    dr = B.DeviceRays.from_host(rays, device=dev)
+    # fixed target images: the same views rendered from perturbed coefficients
+    tgt_tree = B.Tree(I.perturbed(tree, seed=1000), "f32")
+    target = B.neuvv_render(tgt_tree, dr, kernel="packet")["rgb"].clone()
+    del tgt_tree
+    tree_d = B.Tree(tree, "bf16", with_optimizer=True)
+    B.neuvv_autotune(tree_d, dr)
+    out = B.alloc_out(n, dev)
+    grad_rgb = torch.empty(n, 3, device=dev)
+    grad = tree_d.new_grad()
+    touched = tree_d.new_touched()
+    loss = torch.zeros(1, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+
+    def step(k, evs=None):
+        if evs:
+            evs[0].record(stream)
+        B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+        if evs:
+            evs[1].record(stream)
+        loss.zero_()
+        B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
+        if evs:
+            evs[2].record(stream)
+        B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+        if evs:
+            evs[3].record(stream)
+        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=k)
+        if evs:
+            evs[4].record(stream)
+
+    for k in range(args.warmup):
+        step(k + 1)
+    torch.cuda.synchronize()
+    samples_before = int(out["nseg"].sum().item())
+    # distinct leaves one step touches (for the algorithmic bytes)
+    B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+    B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
+    B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+    torch.cuda.synchronize()
+    touched_leaves = int(sum(bin(int(x) & 0xFFFFFFFF).count("1") for x in touched.cpu().numpy()))
+    grad.zero_()
+    touched.zero_()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k + 1, ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    samples = 0.5 * (samples_before + int(out["nseg"].sum().item()))
+    value = world * samples / (ms_step / 1e3) / 1e6
+    kern = {name: statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps))
+            for i, name in enumerate(["fwd", "mse", "bwd", "adam"])}
+
+    # -- the BF16 forward alone and the plain FP32 single-view kernel
+    reps = max(3, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    fwd_samples = int(out["nseg"].sum().item())
+    tree32 = B.Tree(tree, "f32")
+    B.neuvv_render(tree32, dr, kernel="plain", out=out)
+    e0.record(stream)
+    for _ in range(reps):
+        B.neuvv_render(tree32, dr, kernel="plain", out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / reps
+    plain_samples = int(out["nseg"].sum().item())
+    del tree32
+
+    # -- roofline of the dominant kernel of the step
+    hbm_gbs, peak_kind, sm_max = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    fp32_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    info = tree_d.info
+    rec_bytes = info.rec_stride * (2 if info.dtype == B.BF16 else 4)
+    rec_f32 = info.rec_stride_f32 * 4
+    ray_in, fwd_out = 28, 28
+    traffic = {
+        "fwd": (touched_leaves * rec_bytes + n * (ray_in + fwd_out), samples * flops_per_sample(info.K, info.hh_degree)),
+        "bwd": (touched_leaves * (rec_bytes + 2 * rec_f32) + n * (ray_in + 12 + 12 + 4 + 4),
+                samples * flops_per_sample(info.K, info.hh_degree, backward=True)),
+        "adam": (touched_leaves * (8 * rec_f32 + rec_bytes) + 4 * ((info.n_leaves + 31) // 32), 0),
+        "mse": (n * 36, 0),
+    }
+    dom = max(kern, key=kern.get)
+    bytes_, flops_ = traffic[dom]
+    t_s = kern[dom] / 1e3
+    if flops_ / (fp32_tflops * 1e12) > bytes_ / (hbm_gbs * 1e9):
+        roof = {"bound": "alu", "achieved": flops_ / t_s / 1e12, "peak": fp32_tflops, "unit": "TFLOP/s",
+                "peak_kind": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_ / t_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                "peak_kind": f"{peak_kind} (copy bandwidth)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    roof["algorithmic_bytes"] = bytes_
+    roof["algorithmic_flops"] = flops_
+
+    # -- end to end through the C ABI with host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+    h_o, h_d, h_t = pin(rays.origins), pin(rays.dirs), pin(rays.times)
+    h_tgt = target.cpu().pin_memory()
+    d_o, d_d, d_t = torch.empty_like(dr.o), torch.empty_like(dr.d), torch.empty_like(dr.t)
+    d_tgt = torch.empty_like(target)
+    dr2 = B.DeviceRays(d_o, d_d, d_t)
+    h_loss = torch.zeros(1).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+
+    def e2e_step(k):
+        d_o.copy_(h_o, non_blocking=True)
+        d_d.copy_(h_d, non_blocking=True)
+        d_t.copy_(h_t, non_blocking=True)
+        d_tgt.copy_(h_tgt, non_blocking=True)
+        B.neuvv_render(tree_d, dr2, kernel="packet", out=out)
+        loss.zero_()
+        B.neuvv_mse_grad(out["rgb"], d_tgt, scale=1.0 / n, grad=grad_rgb, loss=loss)
+        B.neuvv_render_backward(tree_d, dr2, out, grad_rgb, None, grad, touched, kernel="packet")
+        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k)
+        h_loss.copy_(loss, non_blocking=True)
+
+    e2e_step(args.warmup + args.steps + 1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(e2e_steps):
+        e2e_step(args.warmup + args.steps + 2 + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d = n * 7 * 4 + n * 12
+    e2e = {"value": world * samples / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays": n, "leaves": tree.n_leaves, "depth": tree.depth, "K": tree.K,
+                   "T": tree.T, "hh_degree": tree.hh_degree, "storage": "bf16", "master": "f32",
+                   "samples_per_step": samples, "touched_leaves": touched_leaves,
+                   "l2": "inputs larger than L2 (rays 464 MB + records 512 MB per step)",
+                   "parallelism": f"replicas x{world}"},
+        "kernels_ms": kern,
+        "fwd_bf16_packet": {"ms_per_1080p_frame": fwd_ms / 8, "msamples_per_s": fwd_samples / (fwd_ms / 1e3) / 1e6},
+        "fwd_fp32_plain": {"ms_per_1080p_frame": plain_ms / 8,
+                           "msamples_per_s": plain_samples / (plain_ms / 1e3) / 1e6},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(tree, rays, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * neuvv.h -- C ABI of the GB300 VOctree renderer (NeuVV, arxiv 2202.06088).
+ *
+ * A VOctree (Sec. 4.3) is a sparse octree over a primitive's bounding box whose
+ * occupied leaves each store three coefficient vectors: w_sigma (K weights of a
+ * shared temporal density basis A, Eq. project-sigma), w_gamma (K weights of a
+ * shared hyper-angle basis B, Eq. project-gamma) and w_HH (3 x N_h coefficients
+ * of real 4D hyperspherical harmonics, Eq. HH-color-2).  Rendering a ray
+ * (Sec. 4.3 "Rendering") walks the voxels it crosses, turns each leaf's
+ * coefficients into density and colour at time t and composites them front to
+ * back (Eq. volume-rendering).
+ *
+ * Conventions for every call:
+ *  - Every entry point returns a neuvv_status; on failure neuvv_last_error()
+ *    returns a message for the calling thread.  Argument errors are detected on
+ *    the host before anything is launched.
+ *  - "device" pointers are CUDA global-memory pointers on the tree's device and
+ *    are owned by the caller unless stated otherwise.  "host" pointers are read
+ *    during the call only.
+ *  - Calls that take a stream are asynchronous on it: no host synchronisation,
+ *    no allocation.  neuvv_tree_create/destroy/status/autotune synchronise.
+ *  - Errors found on the device (a ray that exceeds its segment cap, an index
+ *    outside the tree) are recorded in a per-tree status word read by
+ *    neuvv_tree_status(); the affected ray ends early, nothing traps.
+ *  - Ray directions need not be normalised.  Per-ray times are clamped to [0,1].
+ *
+ * Numerical readings of the paper that the library implements (the FP64
+ * oracle in the test suite implements the same ones independently):
+ *  - harmonic H_nlm = Abar_{n,l} sin^l(gamma) C^{l+1}_{n-l}(cos gamma) Y_lm(d),
+ *    Abar_{n,l} = 2^l l! sqrt(2(n+1)(n-l)! / (pi (n+l+1)!)) (orthonormal on S^3);
+ *    Y_lm real, on the unit view direction, polar axis +z, no Condon-Shortley
+ *    phase, cos(m phi) for m > 0, sin(|m| phi) for m < 0;
+ *    index idx(n,l,m) = n(n+1)(2n+1)/6 + l^2 + l + m;
+ *  - frame coordinate u = t (T-1); basis rows linearly interpolated in u;
+ *  - colour = sigmoid(sum_idx w[ch][idx] H_idx) (or identity);
+ *  - a leaf segment's chord delta is the exact length of the ray inside the
+ *    voxel; alpha_i = 1 - exp(-sigma_i delta_i); compositing stops after the
+ *    segment that brings transmittance below t_stop;
+ *  - outputs: premultiplied colour C = sum w_i c_i, alpha = sum w_i,
+ *    depth = sum w_i t_mid,i / alpha if alpha >= 1e-4 else +inf, tau = sum sigma_i delta_i.
+ */
+#ifndef NEUVV_H
+#define NEUVV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct neuvv_tree neuvv_tree; /* opaque; owned by the library */
+
+typedef enum {
+  NEUVV_OK = 0,
+  NEUVV_ERR_INVALID_ARG = 1, /* bad pointer, size, shape or value */
+  NEUVV_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  NEUVV_ERR_OOM = 3,         /* device allocation failed */
+  NEUVV_ERR_TIMEOUT = 4,     /* a ray exceeded its segment cap (device status) */
+  NEUVV_ERR_UNSUPPORTED = 5, /* a valid request this build does not implement */
+  NEUVV_ERR_DEVICE = 6       /* other device-detected error (status word) */
+} neuvv_status;
+
+typedef enum { NEUVV_F32 = 0, NEUVV_BF16 = 1 } neuvv_dtype;
+
+/* Device status bits (neuvv_tree_status). */
+#define NEUVV_STATUS_SEGMENT_CAP 0x1u /* a ray needed more than 3*2^depth+8 steps */
+#define NEUVV_STATUS_BAD_INDEX 0x2u   /* a child entry pointed outside the tree */
+
+/* Tree description, all host memory, read during neuvv_tree_create only.
+ * child: [n_nodes][8] uint32, slot c = 4*xbit + 2*ybit + zbit; entry 0xFFFFFFFF
+ *   = empty, 0x80000000|leaf = occupied leaf, else index of an internal node.
+ *   Node 0 is the root covering [aabb_min, aabb_max]; children of a node at
+ *   level L are cells at level L+1; the finest level is `depth` (1..14).
+ *   Internal node indices must be breadth first (a child's index is larger
+ *   than its parent's); the top of the table is staged in shared memory.
+ * w_sigma: [K][n_leaves], w_gamma: [K][n_leaves], w_hh: [3][N_h][n_leaves] float32
+ *   planes (N_h = sum_{n<=hh_degree} (n+1)^2), the paper's per-voxel vectors.
+ * basis_A, basis_B: [T][K] float32 (T >= 2 frames).
+ * K in 1..32, hh_degree in 1..3. */
+typedef struct {
+  int32_t depth, K, T, hh_degree;
+  neuvv_dtype dtype;        /* storage of the leaf coefficients on the device */
+  int32_t with_optimizer;   /* 1: also allocate FP32 master (if dtype != F32) and Adam m, v */
+  int64_t n_nodes, n_leaves;
+  const uint32_t *child;
+  const float *w_sigma, *w_gamma, *w_hh;
+  const float *basis_A, *basis_B;
+  float aabb_min[3], aabb_max[3];
+} neuvv_tree_desc;
+
+/* Layout of a tree's per-leaf records, for views over its device buffers and
+ * for gradient buffers.  A record holds, in order, w_sigma (K_pad entries, the
+ * last K_pad-K zero), w_gamma (K_pad), w_hh (3*N_h, channel-major), then zero
+ * padding to rec_stride entries.  The FP32 gradient/master layout uses
+ * rec_stride_f32 floats per leaf (a multiple of 4, 16-byte rows). */
+typedef struct {
+  int32_t depth, K, K_pad, T, hh_degree, N_h;
+  int32_t rec_len;          /* 2*K_pad + 3*N_h meaningful entries */
+  int32_t rec_stride;       /* storage entries per leaf (16-byte multiple) */
+  int32_t rec_stride_f32;   /* FP32 floats per leaf in grad / master / m / v */
+  neuvv_dtype dtype;
+  int64_t n_nodes, n_leaves;
+  int32_t smem_nodes;       /* nodes of the table's prefix staged in shared memory */
+  int32_t device;
+} neuvv_tree_info;
+
+/* Rays, device SoA float32 arrays of length n.  t may be NULL: then the
+ * scalar time argument of the call is used for every ray. */
+typedef struct {
+  const float *ox, *oy, *oz, *dx, *dy, *dz;
+  const float *t;
+  int64_t n;
+} neuvv_rays;
+
+/* Per-ray outputs, device, caller-owned.  rgb: [n][3]; alpha, depth, tau: [n];
+ * nseg: [n] segments composited (needed by the backward pass).  Any member may
+ * be NULL except where a call says otherwise. */
+typedef struct {
+  float *rgb, *alpha, *depth, *tau;
+  int32_t *nseg;
+} neuvv_out;
+
+typedef enum { NEUVV_ACT_SIGMOID = 0, NEUVV_ACT_IDENTITY = 1 } neuvv_color_act;
+typedef enum { NEUVV_KERNEL_AUTO = 0, NEUVV_KERNEL_PLAIN = 1, NEUVV_KERNEL_PACKET = 2 } neuvv_kernel;
+typedef enum { NEUVV_COMPOSE_SORTED = 0, NEUVV_COMPOSE_ALG1 = 1 } neuvv_compose_mode;
+
+typedef struct {
+  float t_stop;        /* early termination: stop after T < t_stop (1e-4) */
+  int32_t color_act;   /* neuvv_color_act */
+  int32_t kernel;      /* neuvv_kernel: plain = one thread per ray, no staging;
+                          packet = shared-memory staged top levels, tuned launch */
+  int32_t compose_mode;/* neuvv_compose_mode */
+} neuvv_render_opts;
+
+typedef void *neuvv_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+/* Last error message of the calling thread ("" if none). */
+const char *neuvv_last_error(void);
+
+/* Copies the tree to the current CUDA device (Sec. 4.3: the VOctree holds
+ * w_sigma, w_gamma, w_HH per voxel).  Validates the child table on the host;
+ * errors: INVALID_ARG (malformed table, sizes), OOM, CUDA.  Synchronous. */
+neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out);
+neuvv_status neuvv_tree_destroy(neuvv_tree *tree);
+neuvv_status neuvv_tree_get_info(const neuvv_tree *tree, neuvv_tree_info *info);
+
+/* Device pointers owned by the tree (valid until destroy): storage records
+ * ([n_leaves][rec_stride] in dtype), FP32 master records (== storage when
+ * dtype is F32; NULL without optimizer state), Adam moments m and v (NULL
+ * without optimizer state).  For views from PyTorch and for tests. */
+neuvv_status neuvv_tree_coeff_ptrs(neuvv_tree *tree, void **storage, float **master, float **adam_m, float **adam_v);
+
+/* Reads and clears the device status word (NEUVV_STATUS_* bits).  Synchronous. */
+neuvv_status neuvv_tree_status(neuvv_tree *tree, uint32_t *flags);
+
+/* Forward render (Sec. 4.3 "Rendering"; Eq. project-sigma, project-gamma,
+ * HH-color-2, volume-rendering).  out->rgb, alpha must be non-NULL; depth, tau,
+ * nseg optional (tau and nseg are the saved state of the backward pass).
+ * t: scalar time in [0,1] used when rays->t is NULL (else ignored). */
+neuvv_status neuvv_render(const neuvv_tree *tree, const neuvv_rays *rays, float t, const neuvv_render_opts *opts,
+                          neuvv_out *out, neuvv_stream stream);
+
+/* Fused adjoint (Sec. 4.3 "Optimization": the renderer is differentiated by
+ * hand for gradient descent on the leaf coefficients).  Replays every ray with
+ * the forward traversal, recomputes each sample, and accumulates dL/dw for
+ * L(C, alpha) given grad_rgb = dL/dC [n][3] and grad_alpha = dL/dalpha [n]
+ * (nullable).  saved: the forward's rgb, tau and nseg (all required).
+ * grad: device FP32 [n_leaves][rec_stride_f32], accumulated into (+=).
+ * touched: device bitmap of ceil(n_leaves/32) uint32 words, bits OR-ed for
+ * every leaf that received a gradient (nullable). */
+neuvv_status neuvv_render_backward(const neuvv_tree *tree, const neuvv_rays *rays, float t,
+                                   const neuvv_render_opts *opts, const neuvv_out *saved, const float *grad_rgb,
+                                   const float *grad_alpha, float *grad, uint32_t *touched, neuvv_stream stream);
+
+/* Spatial-temporal composition (Eq. st_composite_affine) with depth-aware
+ * blending (Algorithm 1).  n_prims in 1..16 primitives; trees[j] may repeat
+ * (duplicates share one tree, Sec. 5.1 "Varied Manifestations"); all trees
+ * must share K_pad, hh_degree and dtype.  transforms: host [n_prims][12],
+ * row-major 3x4 world-from-local [s R | translation] with uniform scale s > 0.
+ * time_offsets: host [n_prims] frames; frame u' = (t (T-1) + offset) mod (T-1).
+ * tints: host [n_prims][3] multiplying the colour.  Rays are in world space;
+ * out->rgb, alpha required, depth optional (world units). */
+neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transforms, const float *time_offsets,
+                           const float *tints, int32_t n_prims, const neuvv_rays *rays, float t,
+                           const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream);
+
+/* Sparse Adam on the leaves whose touched bit is set (Sec. 4.3 "Optimization":
+ * SGD or Adam).  Updates the FP32 master, m and v, writes the storage copy
+ * (rounded to nearest even for BF16), zeroes those leaves' rows of grad and
+ * clears touched.  Untouched leaves keep weights and moments.  step >= 1 is
+ * the bias-correction step.  Needs a tree created with with_optimizer = 1. */
+neuvv_status neuvv_adam_step(neuvv_tree *tree, float *grad, uint32_t *touched, float lr, float beta1, float beta2,
+                             float eps, int32_t step, neuvv_stream stream);
+
+/* Loss of Eq. rgb-loss scaled by `scale` and its gradient:
+ * loss_accum[0] += scale * sum ||C - target||^2 (device float, nullable);
+ * grad_rgb = 2 * scale * (C - target).  All device [n][3]. */
+neuvv_status neuvv_mse_grad(const float *rgb, const float *target, int64_t n, float scale, float *grad_rgb,
+                            float *loss_accum, neuvv_stream stream);
+
+/* Occupied leaves each ray crosses, in order (Sec. 4.3 "Rendering": the voxels
+ * on the ray and their segment lengths), without early termination.  Writes up
+ * to max_out entries per ray: leaf [n][max_out] int32 (-1 past the end),
+ * t0/t1 [n][max_out] entry and exit distances along the normalised direction,
+ * count [n] (total, may exceed max_out).  Uses the renderer's traversal. */
+neuvv_status neuvv_trace(const neuvv_tree *tree, const neuvv_rays *rays, int32_t max_out, int32_t *leaf, float *t0,
+                         float *t1, int32_t *count, neuvv_stream stream);
+
+/* Picks launch parameters for the packet kernels by timing candidates on a
+ * sample of rays (the first min(n, 2^20)); the choice is stored in the tree.
+ * Synchronous.  best_ms (nullable) receives the best forward time. */
+neuvv_status neuvv_autotune(neuvv_tree *tree, const neuvv_rays *sample, float t, float *best_ms, neuvv_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEUVV_H */

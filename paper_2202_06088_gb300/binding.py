@@ -1,0 +1,351 @@
+"""Python binding of the C ABI in ``include/neuvv.h`` (argument marshalling only).
+
+Every function here turns PyTorch CUDA tensors into plain pointers and sizes,
+calls the entry point of the same name in ``libneuvv.so`` on the current
+PyTorch stream, and turns a non-zero status into an exception.  No step of the
+rendering, its adjoint, the composition or the optimiser runs in Python.  If
+the library cannot be loaded (or built in-tree with nvcc), every call raises:
+there is no fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+F32, BF16 = 0, 1
+_DTYPES = {"f32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16}
+_ACT = {"sigmoid": 0, "identity": 1}
+_KERNEL = {"auto": 0, "plain": 1, "packet": 2}
+_MODE = {"sorted": 0, "alg1": 1}
+
+
+class NeuvvError(RuntimeError):
+    pass
+
+
+class TreeDesc(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("K", ctypes.c_int32), ("T", ctypes.c_int32), ("hh_degree", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("with_optimizer", ctypes.c_int32),
+                ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("child", ctypes.c_void_p), ("w_sigma", ctypes.c_void_p), ("w_gamma", ctypes.c_void_p),
+                ("w_hh", ctypes.c_void_p), ("basis_A", ctypes.c_void_p), ("basis_B", ctypes.c_void_p),
+                ("aabb_min", ctypes.c_float * 3), ("aabb_max", ctypes.c_float * 3)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("K", ctypes.c_int32), ("K_pad", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("hh_degree", ctypes.c_int32), ("N_h", ctypes.c_int32), ("rec_len", ctypes.c_int32),
+                ("rec_stride", ctypes.c_int32), ("rec_stride_f32", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("smem_nodes", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class RaysC(ctypes.Structure):
+    _fields_ = [("ox", ctypes.c_void_p), ("oy", ctypes.c_void_p), ("oz", ctypes.c_void_p),
+                ("dx", ctypes.c_void_p), ("dy", ctypes.c_void_p), ("dz", ctypes.c_void_p),
+                ("t", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class OutC(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("tau", ctypes.c_void_p), ("nseg", ctypes.c_void_p)]
+
+
+class OptsC(ctypes.Structure):
+    _fields_ = [("t_stop", ctypes.c_float), ("color_act", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("compose_mode", ctypes.c_int32)]
+
+
+EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv_tree_get_info",
+           "neuvv_tree_coeff_ptrs", "neuvv_tree_status", "neuvv_render", "neuvv_render_backward", "neuvv_compose",
+           "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libneuvv.so (building it with nvcc when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise NeuvvError(f"CUDA library not found at {path}")
+            L = ctypes.CDLL(path)
+            p, i32, i64, f = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+            L.neuvv_last_error.restype = ctypes.c_char_p
+            L.neuvv_last_error.argtypes = []
+            sig = {
+                "neuvv_tree_create": [p, p], "neuvv_tree_destroy": [p], "neuvv_tree_get_info": [p, p],
+                "neuvv_tree_coeff_ptrs": [p, p, p, p, p], "neuvv_tree_status": [p, p],
+                "neuvv_render": [p, p, f, p, p, p],
+                "neuvv_render_backward": [p, p, f, p, p, p, p, p, p, p],
+                "neuvv_compose": [p, p, p, p, i32, p, f, p, p, p],
+                "neuvv_adam_step": [p, p, p, f, f, f, f, i32, p],
+                "neuvv_mse_grad": [p, p, i64, f, p, p, p],
+                "neuvv_trace": [p, p, i32, p, p, p, p, p],
+                "neuvv_autotune": [p, p, f, p, p],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.restype = ctypes.c_int
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        msg = lib().neuvv_last_error().decode(errors="replace")
+        raise NeuvvError(f"neuvv status {status}: {msg}")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if not x.is_cuda:
+            raise NeuvvError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise NeuvvError("expected a contiguous tensor")
+        return ctypes.c_void_p(x.data_ptr())
+    return x
+
+
+class _CudaView:
+    """__cuda_array_interface__ holder for library-owned device memory."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+class Tree:
+    """A VOctree uploaded to the current CUDA device (neuvv_tree_create)."""
+
+    def __init__(self, voctree, dtype: str = "f32", with_optimizer: bool = False):
+        L = lib()
+        self.dtype = _DTYPES[dtype]
+        child = np.ascontiguousarray(voctree.child, np.uint32)
+        ws = np.ascontiguousarray(voctree.w_sigma, np.float32)
+        wg = np.ascontiguousarray(voctree.w_gamma, np.float32)
+        wh = np.ascontiguousarray(voctree.w_hh, np.float32)
+        A = np.ascontiguousarray(voctree.basis_A, np.float32)
+        B = np.ascontiguousarray(voctree.basis_B, np.float32)
+        d = TreeDesc()
+        d.depth, d.K, d.T, d.hh_degree = voctree.depth, voctree.K, voctree.T, voctree.hh_degree
+        d.dtype, d.with_optimizer = self.dtype, int(with_optimizer)
+        d.n_nodes, d.n_leaves = child.size // 8, ws.shape[1]
+        d.child, d.w_sigma, d.w_gamma, d.w_hh = child.ctypes.data, ws.ctypes.data, wg.ctypes.data, wh.ctypes.data
+        d.basis_A, d.basis_B = A.ctypes.data, B.ctypes.data
+        for k in range(3):
+            d.aabb_min[k] = voctree.aabb_min[k]
+            d.aabb_max[k] = voctree.aabb_max[k]
+        h = ctypes.c_void_p()
+        _check(L.neuvv_tree_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        info = TreeInfo()
+        _check(L.neuvv_tree_get_info(h, ctypes.byref(info)))
+        self.info = info
+        self.n_leaves = int(info.n_leaves)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.neuvv_tree_destroy(h)
+            self.handle = None
+
+    def _ptrs(self):
+        s, m, a, v = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().neuvv_tree_coeff_ptrs(self.handle, ctypes.byref(s), ctypes.byref(m), ctypes.byref(a),
+                                           ctypes.byref(v)))
+        return s.value, m.value, a.value, v.value
+
+    def storage(self) -> torch.Tensor:
+        """View of the storage records [n_leaves, rec_stride] (float32 or bfloat16)."""
+        s = self._ptrs()[0]
+        if self.dtype == F32:
+            return torch.as_tensor(_CudaView(s, (self.n_leaves, self.info.rec_stride), "<f4", self), device="cuda")
+        t = torch.as_tensor(_CudaView(s, (self.n_leaves, self.info.rec_stride), "<i2", self), device="cuda")
+        return t.view(torch.bfloat16)
+
+    def master(self) -> torch.Tensor | None:
+        m = self._ptrs()[1]
+        if not m:
+            return None
+        return torch.as_tensor(_CudaView(m, (self.n_leaves, self.info.rec_stride_f32), "<f4", self), device="cuda")
+
+    def adam_state(self):
+        _, _, a, v = self._ptrs()
+        if not a:
+            return None, None
+        shape = (self.n_leaves, self.info.rec_stride_f32)
+        return (torch.as_tensor(_CudaView(a, shape, "<f4", self), device="cuda"),
+                torch.as_tensor(_CudaView(v, shape, "<f4", self), device="cuda"))
+
+    def status(self) -> int:
+        f = ctypes.c_uint32()
+        _check(lib().neuvv_tree_status(self.handle, ctypes.byref(f)))
+        return int(f.value)
+
+    def new_grad(self) -> torch.Tensor:
+        return torch.zeros(self.n_leaves, self.info.rec_stride_f32, device="cuda", dtype=torch.float32)
+
+    def new_touched(self) -> torch.Tensor:
+        return torch.zeros((self.n_leaves + 31) // 32, device="cuda", dtype=torch.int32)
+
+
+class DeviceRays:
+    """Rays resident on the device as float32 SoA tensors (origins/dirs [3, n])."""
+
+    def __init__(self, origins: torch.Tensor, dirs: torch.Tensor, times: torch.Tensor | None = None):
+        self.o = origins.contiguous()
+        self.d = dirs.contiguous()
+        self.t = None if times is None else times.contiguous()
+        for x in (self.o, self.d) + (() if self.t is None else (self.t,)):
+            if x.dtype != torch.float32 or not x.is_cuda:
+                raise NeuvvError("rays must be float32 CUDA tensors")
+        self.n = int(self.o.shape[1])
+
+    @staticmethod
+    def from_host(rays, device="cuda", non_blocking=False) -> "DeviceRays":
+        return DeviceRays(torch.as_tensor(np.ascontiguousarray(rays.origins, np.float32)).to(device, non_blocking=non_blocking),
+                          torch.as_tensor(np.ascontiguousarray(rays.dirs, np.float32)).to(device, non_blocking=non_blocking),
+                          torch.as_tensor(np.ascontiguousarray(rays.times, np.float32)).to(device, non_blocking=non_blocking))
+
+    def c(self) -> RaysC:
+        r = RaysC()
+        base = self.o.data_ptr()
+        r.ox, r.oy, r.oz = base, self.o[1].data_ptr(), self.o[2].data_ptr()
+        r.dx, r.dy, r.dz = self.d[0].data_ptr(), self.d[1].data_ptr(), self.d[2].data_ptr()
+        r.t = None if self.t is None else self.t.data_ptr()
+        r.n = self.n
+        return r
+
+
+def _opts(t_stop=1e-4, act="sigmoid", kernel="auto", mode="sorted") -> OptsC:
+    return OptsC(float(t_stop), _ACT[act], _KERNEL[kernel], _MODE[mode])
+
+
+def alloc_out(n: int, device="cuda") -> dict:
+    return {"rgb": torch.empty(n, 3, device=device), "alpha": torch.empty(n, device=device),
+            "depth": torch.empty(n, device=device), "tau": torch.empty(n, device=device),
+            "nseg": torch.empty(n, device=device, dtype=torch.int32)}
+
+
+def _outc(out: dict) -> OutC:
+    return OutC(*[None if out.get(k) is None else out[k].data_ptr() for k in ("rgb", "alpha", "depth", "tau", "nseg")])
+
+
+def neuvv_render(tree: Tree, rays: DeviceRays, t: float = 0.0, t_stop: float = 1e-4, act: str = "sigmoid",
+                 kernel: str = "auto", out: dict | None = None) -> dict:
+    out = out if out is not None else alloc_out(rays.n)
+    rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, kernel)
+    _check(lib().neuvv_render(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(op), ctypes.byref(oc), _stream()))
+    return out
+
+
+def neuvv_render_backward(tree: Tree, rays: DeviceRays, saved: dict, grad_rgb: torch.Tensor,
+                          grad_alpha: torch.Tensor | None = None, grad: torch.Tensor | None = None,
+                          touched: torch.Tensor | None = None, t: float = 0.0, t_stop: float = 1e-4,
+                          act: str = "sigmoid", kernel: str = "auto") -> torch.Tensor:
+    grad = grad if grad is not None else tree.new_grad()
+    rc, sc, op = rays.c(), _outc(saved), _opts(t_stop, act, kernel)
+    _check(lib().neuvv_render_backward(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(op), ctypes.byref(sc),
+                                       _ptr(grad_rgb.contiguous()),
+                                       _ptr(None if grad_alpha is None else grad_alpha.contiguous()), _ptr(grad),
+                                       _ptr(touched), _stream()))
+    return grad
+
+
+def neuvv_compose(trees, transforms, time_offsets, tints, rays: DeviceRays, t: float = 0.0, t_stop: float = 1e-4,
+                  act: str = "sigmoid", mode: str = "sorted", out: dict | None = None) -> dict:
+    P = len(trees)
+    arr = (ctypes.c_void_p * P)(*[tr.handle.value for tr in trees])
+    xf = np.ascontiguousarray(np.asarray(transforms, np.float32).reshape(P, 12))
+    toff = np.ascontiguousarray(np.asarray(time_offsets, np.float32).reshape(P))
+    tint = np.ascontiguousarray(np.asarray(tints, np.float32).reshape(P, 3))
+    out = out if out is not None else alloc_out(rays.n)
+    rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, "auto", mode)
+    _check(lib().neuvv_compose(arr, xf.ctypes.data, toff.ctypes.data, tint.ctypes.data, P, ctypes.byref(rc), float(t),
+                               ctypes.byref(op), ctypes.byref(oc), _stream()))
+    return out
+
+
+def neuvv_adam_step(tree: Tree, grad: torch.Tensor, touched: torch.Tensor, lr: float, beta1: float = 0.9,
+                    beta2: float = 0.999, eps: float = 1e-8, step: int = 1) -> None:
+    _check(lib().neuvv_adam_step(tree.handle, _ptr(grad), _ptr(touched), lr, beta1, beta2, eps, int(step), _stream()))
+
+
+def neuvv_mse_grad(rgb: torch.Tensor, target: torch.Tensor, scale: float = 1.0, grad: torch.Tensor | None = None,
+                   loss: torch.Tensor | None = None):
+    n = rgb.shape[0]
+    grad = grad if grad is not None else torch.empty_like(rgb)
+    _check(lib().neuvv_mse_grad(_ptr(rgb.contiguous()), _ptr(target.contiguous()), n, scale, _ptr(grad), _ptr(loss),
+                                _stream()))
+    return grad
+
+
+def neuvv_trace(tree: Tree, rays: DeviceRays, max_out: int = 64) -> dict:
+    n = rays.n
+    leaf = torch.empty(n, max_out, device="cuda", dtype=torch.int32)
+    t0 = torch.empty(n, max_out, device="cuda")
+    t1 = torch.empty(n, max_out, device="cuda")
+    count = torch.empty(n, device="cuda", dtype=torch.int32)
+    rc = rays.c()
+    _check(lib().neuvv_trace(tree.handle, ctypes.byref(rc), max_out, _ptr(leaf), _ptr(t0), _ptr(t1), _ptr(count),
+                             _stream()))
+    return {"leaf": leaf, "t0": t0, "t1": t1, "count": count}
+
+
+def neuvv_autotune(tree: Tree, rays: DeviceRays, t: float = 0.0) -> float:
+    ms = ctypes.c_float()
+    rc = rays.c()
+    _check(lib().neuvv_autotune(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(ms), _stream()))
+    return float(ms.value)
+
+
+class VOctreeRender(torch.autograd.Function):
+    """Differentiable VOctree render: forward = neuvv_render, backward =
+    neuvv_render_backward (fused adjoint).  ``coeffs`` is the tensor that
+    receives the gradient (the tree's FP32 master records, shape
+    [n_leaves, rec_stride_f32]); the forward reads the tree's storage records."""
+
+    @staticmethod
+    def forward(ctx, coeffs, tree, rays, t, t_stop, act):
+        out = neuvv_render(tree, rays, t=t, t_stop=t_stop, act=act)
+        ctx.tree, ctx.rays, ctx.t, ctx.t_stop, ctx.act = tree, rays, t, t_stop, act
+        ctx.save_for_backward(out["rgb"], out["tau"], out["nseg"])
+        ctx.mark_non_differentiable(out["depth"])
+        return out["rgb"], out["alpha"], out["depth"]
+
+    @staticmethod
+    def backward(ctx, grad_rgb, grad_alpha, grad_depth):
+        rgb, tau, nseg = ctx.saved_tensors
+        saved = {"rgb": rgb, "tau": tau, "nseg": nseg}
+        g = neuvv_render_backward(ctx.tree, ctx.rays, saved, grad_rgb.contiguous(),
+                                  None if grad_alpha is None else grad_alpha.contiguous(), t=ctx.t,
+                                  t_stop=ctx.t_stop, act=ctx.act)
+        return g, None, None, None, None, None
+
+
+def render_differentiable(coeffs: torch.Tensor, tree: Tree, rays: DeviceRays, t: float = 0.0, t_stop: float = 1e-4,
+                          act: str = "sigmoid"):
+    return VOctreeRender.apply(coeffs, tree, rays, t, t_stop, act)

@@ -1,0 +1,629 @@
+// C ABI of the VOctree renderer: tree upload, argument checking, launch
+// configuration and dispatch to the kernels.  See include/neuvv.h for the
+// contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/neuvv.h"
+#include "neuvv_kernels.h"
+
+using namespace neuvv;
+
+namespace {
+
+thread_local std::string g_err;
+
+neuvv_status fail(neuvv_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+neuvv_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? NEUVV_ERR_OOM : NEUVV_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+// Switches to the tree's device for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int kpad_of(int K) { return K <= 8 ? 8 : (K <= 16 ? 16 : 32); }
+
+// Abar_{n,l} = 2^l l! sqrt(2(n+1)(n-l)! / (pi (n+l+1)!))  (orthonormal on S^3)
+double hh_norm_value(int n, int l) {
+  auto fact = [](int k) {
+    double r = 1.0;
+    for (int i = 2; i <= k; ++i) r *= i;
+    return r;
+  };
+  return std::ldexp(1.0, l) * fact(l) * std::sqrt(2.0 * (n + 1) * fact(n - l) / (M_PI * fact(n + l + 1)));
+}
+
+// float -> bfloat16 bits, round to nearest even (NaN kept quiet).
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return (uint16_t)((u >> 16) | 0x40u);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+constexpr int kWorkSlots = 4;  // fwd, bwd, compose, spare
+
+}  // namespace
+
+struct neuvv_tree {
+  neuvv_tree_info info{};
+  uint32_t *child = nullptr;
+  void *rec = nullptr;
+  float *master = nullptr, *m = nullptr, *v = nullptr;
+  float *A = nullptr, *B = nullptr;
+  uint32_t *status = nullptr;
+  unsigned int *work = nullptr;
+  bool master_is_storage = false;
+  float bmin[3], scale[3];
+  float hh_norm[16];
+  int num_sms = 0;
+  LaunchCfg plain{128, 0, 0, 0};
+  LaunchCfg packet{128, 0, 0, 1};
+  LaunchCfg compose{128, 0, 0, 1};
+};
+
+namespace {
+
+DevTree dev_tree(const neuvv_tree *t) {
+  DevTree d;
+  d.child = t->child;
+  d.rec = t->rec;
+  d.A = t->A;
+  d.B = t->B;
+  d.status = t->status;
+  d.n_nodes = t->info.n_nodes;
+  d.n_leaves = t->info.n_leaves;
+  for (int a = 0; a < 3; ++a) {
+    d.bmin[a] = t->bmin[a];
+    d.scale[a] = t->scale[a];
+  }
+  for (int k = 0; k < 16; ++k) d.hh_norm[k] = t->hh_norm[k];
+  d.depth = t->info.depth;
+  d.T = t->info.T;
+  d.K = t->info.K;
+  d.rec_stride = t->info.rec_stride;
+  d.smem_nodes = t->info.smem_nodes;
+  return d;
+}
+
+neuvv_status check_rays(const neuvv_rays *r) {
+  if (!r) return fail(NEUVV_ERR_INVALID_ARG, "rays is NULL");
+  if (r->n < 0) return fail(NEUVV_ERR_INVALID_ARG, "rays->n < 0");
+  if (r->n > 0 && (!r->ox || !r->oy || !r->oz || !r->dx || !r->dy || !r->dz))
+    return fail(NEUVV_ERR_INVALID_ARG, "ray origin/direction pointer is NULL");
+  if (r->n > ((int64_t)1 << 37)) return fail(NEUVV_ERR_INVALID_ARG, "too many rays");
+  return NEUVV_OK;
+}
+
+DevRays dev_rays(const neuvv_rays *r, float t) {
+  DevRays d{r->ox, r->oy, r->oz, r->dx, r->dy, r->dz, r->t, (long long)r->n, t};
+  return d;
+}
+
+neuvv_status check_opts(const neuvv_render_opts *o) {
+  if (!o) return fail(NEUVV_ERR_INVALID_ARG, "opts is NULL");
+  if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "t_stop must be in [0, 1)");
+  if (o->color_act != NEUVV_ACT_SIGMOID && o->color_act != NEUVV_ACT_IDENTITY)
+    return fail(NEUVV_ERR_INVALID_ARG, "unknown color_act %d", o->color_act);
+  if (o->kernel < NEUVV_KERNEL_AUTO || o->kernel > NEUVV_KERNEL_PACKET)
+    return fail(NEUVV_ERR_INVALID_ARG, "unknown kernel %d", o->kernel);
+  if (o->compose_mode != NEUVV_COMPOSE_SORTED && o->compose_mode != NEUVV_COMPOSE_ALG1)
+    return fail(NEUVV_ERR_INVALID_ARG, "unknown compose_mode %d", o->compose_mode);
+  return NEUVV_OK;
+}
+
+neuvv_status check_time(const neuvv_rays *r, float t) {
+  if (!r->t && !(t >= 0.f && t <= 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "scalar t must be in [0, 1]");
+  return NEUVV_OK;
+}
+
+// Resident blocks per SM for a packet kernel, from the registers it uses.
+int packet_grid(const neuvv_tree *t, const LaunchCfg &c, int regs_per_thread) {
+  const int warps_per_block = c.block / 32;
+  int by_regs = 65536 / (regs_per_thread * c.block);
+  size_t sm = smem_bytes(t->info.smem_nodes);
+  int by_smem = sm ? (int)((220 * 1024) / (sm + 1024)) : 32;
+  int by_warps = 64 / warps_per_block;
+  int per_sm = by_regs < by_smem ? by_regs : by_smem;
+  if (by_warps < per_sm) per_sm = by_warps;
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * (t->num_sms > 0 ? t->num_sms : 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *neuvv_last_error(void) { return g_err.c_str(); }
+
+neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
+  if (!desc || !out) return fail(NEUVV_ERR_INVALID_ARG, "desc/out is NULL");
+  *out = nullptr;
+  const neuvv_tree_desc &d = *desc;
+  if (d.depth < 1 || d.depth > 14) return fail(NEUVV_ERR_INVALID_ARG, "depth must be in [1, 14]");
+  if (d.K < 1 || d.K > 32) return fail(NEUVV_ERR_INVALID_ARG, "K must be in [1, 32]");
+  if (d.T < 2) return fail(NEUVV_ERR_INVALID_ARG, "T must be >= 2");
+  if (d.hh_degree < 1 || d.hh_degree > 3) return fail(NEUVV_ERR_INVALID_ARG, "hh_degree must be in [1, 3]");
+  if (d.dtype != NEUVV_F32 && d.dtype != NEUVV_BF16) return fail(NEUVV_ERR_INVALID_ARG, "unknown dtype");
+  if (d.n_nodes < 1 || d.n_leaves < 0 || d.n_leaves >= 0x7FFFFFFF || d.n_nodes >= 0x7FFFFFFF)
+    return fail(NEUVV_ERR_INVALID_ARG, "bad node/leaf counts");
+  if (!d.child || !d.basis_A || !d.basis_B) return fail(NEUVV_ERR_INVALID_ARG, "child/basis pointer is NULL");
+  if (d.n_leaves > 0 && (!d.w_sigma || !d.w_gamma || !d.w_hh))
+    return fail(NEUVV_ERR_INVALID_ARG, "coefficient pointer is NULL");
+  for (int a = 0; a < 3; ++a)
+    if (!(d.aabb_max[a] > d.aabb_min[a]) || !std::isfinite(d.aabb_min[a]) || !std::isfinite(d.aabb_max[a]))
+      return fail(NEUVV_ERR_INVALID_ARG, "aabb must satisfy min < max (finite)");
+
+  // -- validate the child table: entries in range, breadth-first, one parent
+  //    per node, internal nodes only above the finest level
+  std::vector<int8_t> level((size_t)d.n_nodes, -1);
+  level[0] = 0;
+  for (int64_t n = 0; n < d.n_nodes; ++n) {
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t e = d.child[n * 8 + c];
+      if (e == kEmpty) continue;
+      if (e & kLeafBit) {
+        if ((int64_t)(e & ~kLeafBit) >= d.n_leaves)
+          return fail(NEUVV_ERR_INVALID_ARG, "node %lld slot %d: leaf id out of range", (long long)n, c);
+        continue;
+      }
+      if ((int64_t)e >= d.n_nodes || (int64_t)e <= n)
+        return fail(NEUVV_ERR_INVALID_ARG, "node %lld slot %d: child index %u not in (node, n_nodes)",
+                    (long long)n, c, e);
+      if (level[n] >= 0) {
+        if (level[e] >= 0) return fail(NEUVV_ERR_INVALID_ARG, "node %u has two parents", e);
+        if (level[n] + 1 >= d.depth)
+          return fail(NEUVV_ERR_INVALID_ARG, "internal node %u below the finest level", e);
+        level[e] = (int8_t)(level[n] + 1);
+      }
+    }
+  }
+
+  neuvv_tree *t = new neuvv_tree();
+  auto cleanup = [&](neuvv_status s) {
+    neuvv_tree_destroy(t);
+    return s;
+  };
+  neuvv_tree_info &I = t->info;
+  I.depth = d.depth;
+  I.K = d.K;
+  I.K_pad = kpad_of(d.K);
+  I.T = d.T;
+  I.hh_degree = d.hh_degree;
+  I.N_h = n_hh(d.hh_degree);
+  I.rec_len = 2 * I.K_pad + 3 * I.N_h;
+  I.rec_stride_f32 = (I.rec_len + 3) / 4 * 4;
+  I.rec_stride = d.dtype == NEUVV_F32 ? I.rec_stride_f32 : (I.rec_len + 7) / 8 * 8;
+  I.dtype = d.dtype;
+  I.n_nodes = d.n_nodes;
+  I.n_leaves = d.n_leaves;
+  I.smem_nodes = (int32_t)(d.n_nodes < 1024 ? d.n_nodes : 1024);
+  if (cudaGetDevice(&I.device) != cudaSuccess) return cleanup(fail(NEUVV_ERR_CUDA, "no CUDA device"));
+  cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, I.device);
+  for (int a = 0; a < 3; ++a) {
+    t->bmin[a] = d.aabb_min[a];
+    t->scale[a] = (float)((double)(1 << d.depth) / ((double)d.aabb_max[a] - (double)d.aabb_min[a]));
+  }
+  for (int k = 0; k < 16; ++k) t->hh_norm[k] = 0.f;
+  for (int n = 0; n <= 3; ++n)
+    for (int l = 0; l <= n; ++l) t->hh_norm[4 * n + l] = (float)hh_norm_value(n, l);
+
+  // -- records: FP32 first, then the storage dtype
+  const size_t L = (size_t)d.n_leaves;
+  const int Kp = I.K_pad, Nh = I.N_h, sf = I.rec_stride_f32;
+  std::vector<float> recf(L * sf, 0.f);
+  for (size_t l = 0; l < L; ++l) {
+    float *r = recf.data() + l * sf;
+    for (int k = 0; k < d.K; ++k) {
+      r[k] = d.w_sigma[(size_t)k * L + l];
+      r[Kp + k] = d.w_gamma[(size_t)k * L + l];
+    }
+    for (int q = 0; q < 3 * Nh; ++q) r[2 * Kp + q] = d.w_hh[(size_t)q * L + l];
+  }
+  std::vector<float> Ap((size_t)d.T * Kp, 0.f), Bp((size_t)d.T * Kp, 0.f);
+  for (int f = 0; f < d.T; ++f)
+    for (int k = 0; k < d.K; ++k) {
+      Ap[(size_t)f * Kp + k] = d.basis_A[(size_t)f * d.K + k];
+      Bp[(size_t)f * Kp + k] = d.basis_B[(size_t)f * d.K + k];
+    }
+
+  cudaError_t e;
+#define NEUVV_TRY(call, what) \
+  if ((e = (call)) != cudaSuccess) return cleanup(cuda_fail(e, what));
+  NEUVV_TRY(cudaMalloc(&t->child, (size_t)d.n_nodes * 8 * 4), "cudaMalloc(child)");
+  NEUVV_TRY(cudaMemcpy(t->child, d.child, (size_t)d.n_nodes * 8 * 4, cudaMemcpyHostToDevice), "copy child");
+  NEUVV_TRY(cudaMalloc(&t->A, Ap.size() * 4), "cudaMalloc(A)");
+  NEUVV_TRY(cudaMalloc(&t->B, Bp.size() * 4), "cudaMalloc(B)");
+  NEUVV_TRY(cudaMemcpy(t->A, Ap.data(), Ap.size() * 4, cudaMemcpyHostToDevice), "copy A");
+  NEUVV_TRY(cudaMemcpy(t->B, Bp.data(), Bp.size() * 4, cudaMemcpyHostToDevice), "copy B");
+  NEUVV_TRY(cudaMalloc(&t->status, 4), "cudaMalloc(status)");
+  NEUVV_TRY(cudaMemset(t->status, 0, 4), "memset status");
+  NEUVV_TRY(cudaMalloc(&t->work, kWorkSlots * 4), "cudaMalloc(work)");
+  NEUVV_TRY(cudaMemset(t->work, 0, kWorkSlots * 4), "memset work");
+  const size_t recf_bytes = L * sf * 4 + 16;
+  if (d.dtype == NEUVV_F32) {
+    NEUVV_TRY(cudaMalloc(&t->rec, recf_bytes), "cudaMalloc(records)");
+    if (L) NEUVV_TRY(cudaMemcpy(t->rec, recf.data(), L * sf * 4, cudaMemcpyHostToDevice), "copy records");
+    if (d.with_optimizer) {
+      t->master = static_cast<float *>(t->rec);
+      t->master_is_storage = true;
+    }
+  } else {
+    const int sb = I.rec_stride;
+    std::vector<uint16_t> recb(L * sb, 0);
+    for (size_t l = 0; l < L; ++l)
+      for (int q = 0; q < I.rec_len; ++q) recb[l * sb + q] = bf16_bits(recf[l * sf + q]);
+    NEUVV_TRY(cudaMalloc(&t->rec, L * sb * 2 + 16), "cudaMalloc(records)");
+    if (L) NEUVV_TRY(cudaMemcpy(t->rec, recb.data(), L * sb * 2, cudaMemcpyHostToDevice), "copy records");
+    if (d.with_optimizer) {
+      NEUVV_TRY(cudaMalloc(&t->master, recf_bytes), "cudaMalloc(master)");
+      if (L) NEUVV_TRY(cudaMemcpy(t->master, recf.data(), L * sf * 4, cudaMemcpyHostToDevice), "copy master");
+    }
+  }
+  if (d.with_optimizer) {
+    NEUVV_TRY(cudaMalloc(&t->m, recf_bytes), "cudaMalloc(m)");
+    NEUVV_TRY(cudaMalloc(&t->v, recf_bytes), "cudaMalloc(v)");
+    NEUVV_TRY(cudaMemset(t->m, 0, recf_bytes), "memset m");
+    NEUVV_TRY(cudaMemset(t->v, 0, recf_bytes), "memset v");
+  }
+#undef NEUVV_TRY
+  t->packet.grid = packet_grid(t, t->packet, 168);
+  t->compose.grid = packet_grid(t, t->compose, 168);
+  *out = t;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_tree_destroy(neuvv_tree *t) {
+  if (!t) return NEUVV_OK;
+  DeviceGuard g(t->info.device);
+  if (!t->master_is_storage) cudaFree(t->master);
+  cudaFree(t->rec);
+  cudaFree(t->child);
+  cudaFree(t->m);
+  cudaFree(t->v);
+  cudaFree(t->A);
+  cudaFree(t->B);
+  cudaFree(t->status);
+  cudaFree(t->work);
+  delete t;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_tree_get_info(const neuvv_tree *t, neuvv_tree_info *info) {
+  if (!t || !info) return fail(NEUVV_ERR_INVALID_ARG, "tree/info is NULL");
+  *info = t->info;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_tree_coeff_ptrs(neuvv_tree *t, void **storage, float **master, float **m, float **v) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (storage) *storage = t->rec;
+  if (master) *master = t->master;
+  if (m) *m = t->m;
+  if (v) *v = t->v;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_tree_status(neuvv_tree *t, uint32_t *flags) {
+  if (!t || !flags) return fail(NEUVV_ERR_INVALID_ARG, "tree/flags is NULL");
+  DeviceGuard g(t->info.device);
+  cudaError_t e = cudaMemcpy(flags, t->status, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status");
+  e = cudaMemset(t->status, 0, 4);
+  if (e != cudaSuccess) return cuda_fail(e, "clear status");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float time, const neuvv_render_opts *opts,
+                          neuvv_out *out, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK || (s = check_time(rays, time)))
+    return s;
+  if (!out || (rays->n > 0 && (!out->rgb || !out->alpha)))
+    return fail(NEUVV_ERR_INVALID_ARG, "out->rgb and out->alpha are required");
+  if (rays->n == 0) return NEUVV_OK;
+  DeviceGuard g(t->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  FwdArgs a;
+  a.tr = dev_tree(t);
+  a.rays = dev_rays(rays, time);
+  a.out = DevOut{out->rgb, out->alpha, out->depth, out->tau, out->nseg};
+  a.t_stop = opts->t_stop;
+  a.act = opts->color_act;
+  a.work = t->work + 0;
+  const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
+  const LaunchCfg &cfg = packet ? t->packet : t->plain;
+  if (packet && cfg.dynamic_queue) {
+    cudaError_t e = cudaMemsetAsync(a.work, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
+  }
+  cudaError_t e = launch_render_fwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "render launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, float time,
+                                   const neuvv_render_opts *opts, const neuvv_out *saved, const float *grad_rgb,
+                                   const float *grad_alpha, float *grad, uint32_t *touched, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK || (s = check_time(rays, time)))
+    return s;
+  if (rays->n == 0) return NEUVV_OK;
+  if (!saved || !saved->rgb || !saved->tau || !saved->nseg)
+    return fail(NEUVV_ERR_INVALID_ARG, "saved rgb, tau and nseg are required");
+  if (!grad_rgb || !grad) return fail(NEUVV_ERR_INVALID_ARG, "grad_rgb and grad are required");
+  if (((uintptr_t)grad & 15) != 0) return fail(NEUVV_ERR_INVALID_ARG, "grad must be 16-byte aligned");
+  DeviceGuard g(t->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  BwdArgs a;
+  a.tr = dev_tree(t);
+  a.rays = dev_rays(rays, time);
+  a.rgb = saved->rgb;
+  a.tau = saved->tau;
+  a.nseg = saved->nseg;
+  a.grad_rgb = grad_rgb;
+  a.grad_alpha = grad_alpha;
+  a.grad = grad;
+  a.grad_stride = t->info.rec_stride_f32;
+  a.touched = touched;
+  a.t_stop = opts->t_stop;
+  a.act = opts->color_act;
+  a.work = t->work + 1;
+  const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
+  const LaunchCfg &cfg = packet ? t->packet : t->plain;
+  if (packet && cfg.dynamic_queue) {
+    cudaError_t e = cudaMemsetAsync(a.work, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
+  }
+  cudaError_t e = launch_render_bwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transforms, const float *time_offsets,
+                           const float *tints, int32_t n_prims, const neuvv_rays *rays, float time,
+                           const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream) {
+  if (!trees || !transforms || !time_offsets || !tints)
+    return fail(NEUVV_ERR_INVALID_ARG, "trees/transforms/time_offsets/tints is NULL");
+  if (n_prims < 1 || n_prims > kMaxPrims) return fail(NEUVV_ERR_INVALID_ARG, "n_prims must be in [1, %d]", kMaxPrims);
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK || (s = check_time(rays, time)))
+    return s;
+  if (!out || (rays->n > 0 && (!out->rgb || !out->alpha)))
+    return fail(NEUVV_ERR_INVALID_ARG, "out->rgb and out->alpha are required");
+  const neuvv_tree *t0 = trees[0];
+  if (!t0) return fail(NEUVV_ERR_INVALID_ARG, "trees[0] is NULL");
+  ComposeArgs a;
+  std::memset(&a, 0, sizeof a);
+  int n_trees = 0;
+  const neuvv_tree *uniq[kMaxPrims];
+  for (int j = 0; j < n_prims; ++j) {
+    const neuvv_tree *t = trees[j];
+    if (!t) return fail(NEUVV_ERR_INVALID_ARG, "trees[%d] is NULL", j);
+    if (t->info.K_pad != t0->info.K_pad || t->info.hh_degree != t0->info.hh_degree || t->info.dtype != t0->info.dtype ||
+        t->info.device != t0->info.device)
+      return fail(NEUVV_ERR_UNSUPPORTED, "all trees of one compose call must share K_pad, degree, dtype, device");
+    int slot = -1;
+    for (int k = 0; k < n_trees; ++k)
+      if (uniq[k] == t) slot = k;
+    if (slot < 0) {
+      slot = n_trees;
+      uniq[n_trees++] = t;
+      a.trees[slot] = dev_tree(t);
+    }
+    const float *M = transforms + 12 * j;
+    double m[3][3], tr[3];
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) m[r][c] = M[4 * r + c];
+      tr[r] = M[4 * r + 3];
+    }
+    // uniform scale: M^T M = s^2 I
+    double s2 = 0.0;
+    for (int r = 0; r < 3; ++r) s2 += m[r][0] * m[r][0];
+    if (!(s2 > 0.0) || !std::isfinite(s2)) return fail(NEUVV_ERR_INVALID_ARG, "transform %d is degenerate", j);
+    for (int c1 = 0; c1 < 3; ++c1)
+      for (int c2 = 0; c2 < 3; ++c2) {
+        double dot = 0.0;
+        for (int r = 0; r < 3; ++r) dot += m[r][c1] * m[r][c2];
+        const double want = c1 == c2 ? s2 : 0.0;
+        if (std::fabs(dot - want) > 1e-4 * s2)
+          return fail(NEUVV_ERR_INVALID_ARG, "transform %d is not a rotation times a uniform scale", j);
+      }
+    for (int r = 0; r < 3; ++r)
+      if (!std::isfinite(tr[r])) return fail(NEUVV_ERR_INVALID_ARG, "transform %d translation not finite", j);
+    const double det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+                       m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                       m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+    if (!(det > 0.0)) return fail(NEUVV_ERR_INVALID_ARG, "transform %d must have positive determinant", j);
+    PrimParam &p = a.prim[j];
+    // (sR)^-1 = R^T / s = M^T / s^2
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) p.minv[3 * r + c] = (float)(m[c][r] / s2);
+    for (int r = 0; r < 3; ++r) p.trans[r] = (float)tr[r];
+    p.scale = (float)std::sqrt(s2);
+    if (!std::isfinite(time_offsets[j])) return fail(NEUVV_ERR_INVALID_ARG, "time offset %d not finite", j);
+    p.toff = time_offsets[j];
+    for (int c = 0; c < 3; ++c) {
+      if (!std::isfinite(tints[3 * j + c])) return fail(NEUVV_ERR_INVALID_ARG, "tint %d not finite", j);
+      p.tint[c] = tints[3 * j + c];
+    }
+    p.tree = slot;
+  }
+  if (rays->n == 0) return NEUVV_OK;
+  DeviceGuard g(t0->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  a.n_prims = n_prims;
+  a.rays = dev_rays(rays, time);
+  a.out = DevOut{out->rgb, out->alpha, out->depth, nullptr, nullptr};
+  a.t_stop = opts->t_stop;
+  a.act = opts->color_act;
+  a.mode = opts->compose_mode;
+  a.work = t0->work + 2;
+  const LaunchCfg &cfg = t0->compose;
+  if (cfg.dynamic_queue) {
+    cudaError_t e = cudaMemsetAsync(a.work, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
+  }
+  cudaError_t e = launch_compose(t0->info.K_pad, t0->info.hh_degree, (DType)t0->info.dtype, a, cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "compose launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_adam_step(neuvv_tree *t, float *grad, uint32_t *touched, float lr, float b1, float b2, float eps,
+                             int32_t step, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (!t->m || !t->v || !t->master) return fail(NEUVV_ERR_INVALID_ARG, "tree was created without optimizer state");
+  if (!grad || !touched) return fail(NEUVV_ERR_INVALID_ARG, "grad and touched are required");
+  if (((uintptr_t)grad & 15) != 0) return fail(NEUVV_ERR_INVALID_ARG, "grad must be 16-byte aligned");
+  if (step < 1) return fail(NEUVV_ERR_INVALID_ARG, "step must be >= 1");
+  if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps > 0.f && std::isfinite(lr)))
+    return fail(NEUVV_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+  DeviceGuard g(t->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const float c1 = (float)(1.0 - std::pow((double)b1, step));
+  const float c2 = (float)(1.0 - std::pow((double)b2, step));
+  cudaError_t e = launch_adam(t->master, t->m, t->v, t->master_is_storage ? nullptr : t->rec, (DType)t->info.dtype,
+                              t->info.rec_stride, grad, touched, t->info.n_leaves, t->info.rec_stride_f32,
+                              t->info.rec_len, lr, b1, b2, eps, c1, c2, st);
+  if (e != cudaSuccess) return cuda_fail(e, "adam launch");
+  e = cudaMemsetAsync(touched, 0, (size_t)((t->info.n_leaves + 31) / 32) * 4, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear touched");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_mse_grad(const float *rgb, const float *target, int64_t n, float scale, float *grad_rgb,
+                            float *loss_accum, neuvv_stream stream) {
+  if (n < 0) return fail(NEUVV_ERR_INVALID_ARG, "n < 0");
+  if (n > 0 && (!rgb || !target || !grad_rgb)) return fail(NEUVV_ERR_INVALID_ARG, "rgb/target/grad_rgb is NULL");
+  cudaError_t e = launch_mse(rgb, target, (long long)n, scale, grad_rgb, loss_accum, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mse launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_trace(const neuvv_tree *t, const neuvv_rays *rays, int32_t max_out, int32_t *leaf, float *t0,
+                         float *t1, int32_t *count, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK) return s;
+  if (max_out < 0) return fail(NEUVV_ERR_INVALID_ARG, "max_out < 0");
+  if (rays->n > 0 && (!count || (max_out > 0 && (!leaf || !t0 || !t1))))
+    return fail(NEUVV_ERR_INVALID_ARG, "trace output pointer is NULL");
+  if (rays->n == 0) return NEUVV_OK;
+  DeviceGuard g(t->info.device);
+  TraceArgs a;
+  a.tr = dev_tree(t);
+  a.rays = dev_rays(rays, 0.f);
+  a.max_out = max_out;
+  a.leaf = leaf;
+  a.t0 = t0;
+  a.t1 = t1;
+  a.count = count;
+  cudaError_t e = launch_trace(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_autotune(neuvv_tree *t, const neuvv_rays *sample, float time, float *best_ms,
+                            neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  neuvv_status s;
+  if ((s = check_rays(sample)) != NEUVV_OK || (s = check_time(sample, time)) != NEUVV_OK) return s;
+  if (sample->n == 0) return NEUVV_OK;
+  DeviceGuard g(t->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  neuvv_rays r = *sample;
+  if (r.n > (1 << 20)) r.n = 1 << 20;
+  float *rgb = nullptr, *alpha = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&rgb, r.n * 12)) != cudaSuccess) return cuda_fail(e, "autotune alloc");
+  if ((e = cudaMalloc(&alpha, r.n * 4)) != cudaSuccess) {
+    cudaFree(rgb);
+    return cuda_fail(e, "autotune alloc");
+  }
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  neuvv_render_opts opts{1e-4f, NEUVV_ACT_SIGMOID, NEUVV_KERNEL_PACKET, NEUVV_COMPOSE_SORTED};
+  neuvv_out out{rgb, alpha, nullptr, nullptr, nullptr};
+  const LaunchCfg saved = t->packet;
+  const int saved_smem = t->info.smem_nodes;
+  LaunchCfg best = saved;
+  int best_smem = saved_smem;
+  float best_t = 1e30f;
+  const int blocks[] = {64, 128, 256};
+  const int smem_opts[] = {0, 256, 1024, 4096};
+  for (int sm_nodes : smem_opts) {
+    if (sm_nodes > t->info.n_nodes) continue;
+    for (int b : blocks)
+      for (int dyn = 0; dyn <= 1; ++dyn)
+        for (int mult = 1; mult <= 2; ++mult) {
+          t->info.smem_nodes = sm_nodes;
+          LaunchCfg c{b, 0, sm_nodes, dyn};
+          c.grid = packet_grid(t, c, 168) * mult;
+          t->packet = c;
+          float ms_best = 1e30f;
+          for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(ev0, st);
+            s = neuvv_render(t, &r, time, &opts, &out, stream);
+            cudaEventRecord(ev1, st);
+            if (s != NEUVV_OK) break;
+            cudaEventSynchronize(ev1);
+            float ms;
+            cudaEventElapsedTime(&ms, ev0, ev1);
+            if (ms < ms_best) ms_best = ms;
+          }
+          if (s != NEUVV_OK) break;
+          if (ms_best < best_t) {
+            best_t = ms_best;
+            best = c;
+            best_smem = sm_nodes;
+          }
+        }
+    if (s != NEUVV_OK) break;
+  }
+  t->packet = best;
+  t->info.smem_nodes = best_smem;
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  cudaFree(rgb);
+  cudaFree(alpha);
+  if (s != NEUVV_OK) {
+    t->packet = saved;
+    t->info.smem_nodes = saved_smem;
+    return s;
+  }
+  if (best_ms) *best_ms = best_t;
+  return NEUVV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,458 @@
+// Device building blocks of the VOctree renderer (sm_103a).
+//
+// Everything a ray needs, shared by the forward, adjoint, trace and compose
+// kernels so that all of them walk exactly the same voxels:
+//   * RayWalk   -- stackless octree walk (Sec. 4.3 "Rendering": the voxels on
+//                  the ray and the chord lengths {delta_i} inside them);
+//   * sh_real   -- real spherical harmonics of the view direction, l <= 3
+//                  (App. A, Eq. real-SH; no Condon-Shortley phase);
+//   * hh_radial -- Abar_{n,l} sin^l(gamma) C^{l+1}_{n-l}(cos gamma) and its
+//                  gamma-derivative, by the Gegenbauer recurrence in registers
+//                  (Eq. complex-HSH);
+//   * LeafRecord-- one leaf's coefficient record fetched with 16-byte vector
+//                  loads and widened to FP32.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace neuvv {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr float kPi = 3.14159265358979323846f;
+constexpr uint32_t kStatusSegCap = 0x1u;
+constexpr uint32_t kStatusBadIndex = 0x2u;
+
+__host__ __device__ constexpr int n_hh(int deg) { return deg < 0 ? 0 : n_hh(deg - 1) + (deg + 1) * (deg + 1); }
+__host__ __device__ constexpr int hh_index(int n, int l, int m) { return n * (n + 1) * (2 * n + 1) / 6 + l * l + l + m; }
+__host__ __device__ constexpr int radial_index(int n, int l) { return n * (n + 1) / 2 + l; }
+
+// Device view of a tree, passed to kernels by value.
+struct DevTree {
+  const uint32_t *child;  // [n_nodes][8]
+  const void *rec;        // [n_leaves][rec_stride] storage records
+  const float *A;         // [T][KP] density basis (zero padded)
+  const float *B;         // [T][KP] hyper-angle basis
+  uint32_t *status;       // device status word
+  long long n_nodes, n_leaves;
+  float bmin[3];
+  float scale[3];         // 2^depth / (bmax - bmin)
+  float hh_norm[16];      // Abar_{n,l} at [4n + l]
+  int depth, T, K, rec_stride, smem_nodes;
+};
+
+__device__ __forceinline__ void raise_status(const DevTree &tr, uint32_t bit) {
+  if (tr.status) atomicOr(tr.status, bit);
+}
+
+// ---------------------------------------------------------------------------
+// Octree walk.  Grid space: the root box is [0, N]^3, N = 2^depth, finest
+// cells are unit cubes.  Positions are kept relative to the ray's entry into
+// the root box so that FP32 coordinates stay below N.  Decisions:
+//   * exit axis = argmin of the three exit distances, exact ties x < y < z;
+//   * the next cell is one step across the exit face on that axis, and on the
+//     other axes the cell holding the exit point (a coordinate exactly on a
+//     cell boundary goes to the side the ray moves towards), clamped to the
+//     node just left.
+// Every distance is along the unit direction, in world units.
+// ---------------------------------------------------------------------------
+struct RayWalk {
+  float go[3];     // grid position of the entry point
+  float gd[3];     // grid-space direction (unit world direction * scale)
+  float inv[3];    // 1 / gd (inf when gd == 0)
+  float t_base;    // world distance of the entry point from the origin
+  float t_cur;     // current distance past the entry point
+  float t_far;     // exit distance of the root box past the entry point
+  int cell[3];
+  int steps, max_steps;
+  bool alive;
+};
+
+__device__ __forceinline__ int cell_of(float p, float v, int N) {
+  float f = floorf(p);
+  int c = (int)f;
+  if (v < 0.f && f == p) c -= 1;
+  return min(max(c, 0), N - 1);
+}
+
+// Normalises d, intersects the root box; returns false on a miss.
+__device__ __forceinline__ bool walk_init(const DevTree &tr, const float o[3], const float d_in[3], RayWalk &w,
+                                          float dn[3]) {
+  float len = sqrtf(d_in[0] * d_in[0] + d_in[1] * d_in[1] + d_in[2] * d_in[2]);
+  float il = 1.f / len;
+  dn[0] = d_in[0] * il;
+  dn[1] = d_in[1] * il;
+  dn[2] = d_in[2] * il;
+  const float N = (float)(1 << tr.depth);
+  float tn = -INFINITY, tf = INFINITY, go[3];
+  bool hit = len > 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    go[a] = (o[a] - tr.bmin[a]) * tr.scale[a];
+    w.gd[a] = dn[a] * tr.scale[a];
+    if (w.gd[a] == 0.f) {
+      w.inv[a] = INFINITY;
+      if (go[a] < 0.f || go[a] > N) hit = false;
+    } else {
+      w.inv[a] = 1.f / w.gd[a];
+      float t0 = (0.f - go[a]) / w.gd[a];
+      float t1 = (N - go[a]) / w.gd[a];
+      tn = fmaxf(tn, fminf(t0, t1));
+      tf = fminf(tf, fmaxf(t0, t1));
+    }
+  }
+  float tin = fmaxf(tn, 0.f);
+  w.alive = hit && (tin < tf);
+  w.t_base = tin;
+  w.t_cur = 0.f;
+  w.t_far = tf - tin;
+  w.steps = 0;
+  w.max_steps = 3 * (1 << tr.depth) + 8;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    w.go[a] = go[a] + tin * w.gd[a];
+    w.cell[a] = cell_of(w.go[a], w.gd[a], 1 << tr.depth);
+  }
+  return w.alive;
+}
+
+// Descends from the root to the tree cell holding w.cell.  Returns the child
+// entry found (kEmpty or kLeafBit|leaf) and its level.  The first smem_nodes
+// rows of the child table may be read from shared memory.
+template <bool kSmem>
+__device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s_child, const int cell[3], int &level) {
+  uint32_t node = 0;
+  const int D = tr.depth;
+  for (int L = 0; L < D; ++L) {
+    const int bit = D - 1 - L;
+    const int slot = (((cell[0] >> bit) & 1) << 2) | (((cell[1] >> bit) & 1) << 1) | ((cell[2] >> bit) & 1);
+    uint32_t e;
+    if (kSmem && node < (uint32_t)tr.smem_nodes)
+      e = s_child[node * 8 + slot];
+    else
+      e = __ldg(tr.child + (size_t)node * 8 + slot);
+    if (e == kEmpty || (e & kLeafBit)) {
+      level = L + 1;
+      if (e != kEmpty && (long long)(e & ~kLeafBit) >= tr.n_leaves) {
+        raise_status(tr, kStatusBadIndex);
+        return kEmpty;
+      }
+      return e;
+    }
+    if ((long long)e >= tr.n_nodes || e <= node) {
+      raise_status(tr, kStatusBadIndex);
+      level = L + 1;
+      return kEmpty;
+    }
+    node = e;
+  }
+  level = D;
+  return kEmpty;
+}
+
+// Advances to the next occupied-leaf segment.  On success returns true with
+// leaf id and the segment [t0, t1] (relative to the entry point); false when
+// the ray has left the root box (or hit its step cap).
+template <bool kSmem>
+__device__ __forceinline__ bool walk_next(const DevTree &tr, const uint32_t *s_child, RayWalk &w, uint32_t &leaf,
+                                          float &t0, float &t1) {
+  const int N = 1 << tr.depth;
+  while (w.alive) {
+    if (++w.steps > w.max_steps) {
+      raise_status(tr, kStatusSegCap);
+      w.alive = false;
+      break;
+    }
+    int level;
+    const uint32_t e = descend<kSmem>(tr, s_child, w.cell, level);
+    const int shift = tr.depth - level;
+    const int size = 1 << shift;
+    int lo[3];
+    float tx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = (w.cell[a] >> shift) << shift;
+      const float bnd = w.gd[a] > 0.f ? (float)(lo[a] + size) : (float)lo[a];
+      tx[a] = w.gd[a] != 0.f ? (bnd - w.go[a]) * w.inv[a] : INFINITY;
+    }
+    // exit axis: first minimum (exact ties x < y < z); register-only selects
+    int ax = 0;
+    float t_exit = tx[0];
+    if (tx[1] < t_exit) { ax = 1; t_exit = tx[1]; }
+    if (tx[2] < t_exit) { ax = 2; t_exit = tx[2]; }
+    const float seg_end = fminf(t_exit, w.t_far);
+    const float seg_start = w.t_cur;
+    bool found = false;
+    if (e != kEmpty && seg_end > seg_start) {
+      leaf = e & ~kLeafBit;
+      t0 = seg_start;
+      t1 = seg_end;
+      found = true;
+    }
+    // step to the next cell
+    if (t_exit >= w.t_far) {
+      w.alive = false;
+    } else {
+      w.t_cur = fmaxf(w.t_cur, t_exit);
+      bool inside = true;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (b == ax) {
+          const int nc = w.gd[b] > 0.f ? lo[b] + size : lo[b] - 1;
+          inside = nc >= 0 && nc < N;
+          w.cell[b] = nc;
+        } else {
+          const float p = w.go[b] + w.t_cur * w.gd[b];
+          w.cell[b] = min(max(cell_of(p, w.gd[b], N), lo[b]), lo[b] + size - 1);
+        }
+      }
+      if (!inside) w.alive = false;
+    }
+    if (found) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics of a unit direction, l <= DEG <= 3, index l^2+l+m.
+// Y_l0 = K_l0 P_l(z); Y_l,m>0 = sqrt2 K_lm P_l^m(z) cos(m phi);
+// Y_l,m<0 = sqrt2 K_l|m| P_l^|m|(z) sin(|m| phi), written as polynomials in
+// (x, y, z) (sin^m(theta) e^{i m phi} = (x + i y)^m).
+// ---------------------------------------------------------------------------
+template <int DEG>
+__device__ __forceinline__ void sh_real(const float d[3], float *Y) {
+  const float x = d[0], y = d[1], z = d[2];
+  Y[0] = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+  if (DEG >= 1) {
+    const float c1 = 0.4886025119029199f;  // sqrt(3 / (4 pi))
+    Y[1] = c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = c1 * x;
+  }
+  if (DEG >= 2) {
+    const float c2a = 1.0925484305920792f;   // sqrt(15 / (4 pi))
+    const float c20 = 0.31539156525252005f;  // sqrt(5 / (16 pi))
+    const float c22 = 0.5462742152960396f;   // sqrt(15 / (16 pi))
+    Y[4] = c2a * x * y;
+    Y[5] = c2a * y * z;
+    Y[6] = c20 * (3.f * z * z - 1.f);
+    Y[7] = c2a * x * z;
+    Y[8] = c22 * (x * x - y * y);
+  }
+  if (DEG >= 3) {
+    const float c3a = 0.5900435899266435f;  // sqrt(35 / (32 pi))
+    const float c3b = 2.890611442640554f;   // sqrt(105 / (4 pi))
+    const float c3c = 0.4570457994644658f;  // sqrt(21 / (32 pi))
+    const float c30 = 0.3731763325901154f;  // sqrt(7 / (16 pi))
+    const float c32 = 1.445305721320277f;   // sqrt(105 / (16 pi))
+    const float zz = z * z;
+    Y[9] = c3a * y * (3.f * x * x - y * y);
+    Y[10] = c3b * x * y * z;
+    Y[11] = c3c * y * (5.f * zz - 1.f);
+    Y[12] = c30 * z * (5.f * zz - 3.f);
+    Y[13] = c3c * x * (5.f * zz - 1.f);
+    Y[14] = c32 * z * (x * x - y * y);
+    Y[15] = c3a * x * (x * x - 3.f * y * y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Radial factors R_nl = Abar_{n,l} sin^l(g) C^{l+1}_{n-l}(cos g) for n <= DEG,
+// stored at radial_index(n, l); optionally dR_nl/dg.  Gegenbauer recurrence
+// k C_k = 2x(k+lam-1) C_{k-1} - (k+2lam-2) C_{k-2}, differentiated alongside.
+// ---------------------------------------------------------------------------
+template <int DEG, bool kDeriv>
+__device__ __forceinline__ void hh_radial(float cg, float sg, const float *norm, float *R, float *dR) {
+  float sl = 1.f, slm1 = 0.f;  // sin^l, sin^(l-1)
+#pragma unroll
+  for (int l = 0; l <= DEG; ++l) {
+    const float lam = (float)(l + 1);
+    float cm2 = 0.f, cm1 = 0.f, dm2 = 0.f, dm1 = 0.f;  // C_{k-2}, C_{k-1} and d/dx
+#pragma unroll
+    for (int k = 0; l + k <= DEG; ++k) {
+      float ck, dk;
+      if (k == 0) {
+        ck = 1.f;
+        dk = 0.f;
+      } else if (k == 1) {
+        ck = 2.f * lam * cg;
+        dk = 2.f * lam;
+      } else {
+        const float a = 2.f * (k + lam - 1.f) / k, b = (k + 2.f * lam - 2.f) / k;
+        ck = a * cg * cm1 - b * cm2;
+        dk = a * (cm1 + cg * dm1) - b * dm2;
+      }
+      const int n = l + k;
+      const float An = norm[4 * n + l];
+      R[radial_index(n, l)] = An * sl * ck;
+      if (kDeriv) {
+        // d/dg [sin^l g C(cos g)] = l sin^(l-1) g cos g C - sin^(l+1) g C'
+        dR[radial_index(n, l)] = An * ((float)l * slm1 * cg * ck - sl * sg * dk);
+      }
+      cm2 = cm1;
+      cm1 = ck;
+      dm2 = dm1;
+      dm1 = dk;
+    }
+    slm1 = sl;
+    sl *= sg;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf records: [w_sigma KP][w_gamma KP][w_hh 3*NH channel-major][pad]
+// ---------------------------------------------------------------------------
+template <typename E>
+struct Elem;
+template <>
+struct Elem<float> {
+  static constexpr int kPerVec = 4;
+  __device__ __forceinline__ static void unpack(const uint4 v, float *o) {
+    o[0] = __uint_as_float(v.x);
+    o[1] = __uint_as_float(v.y);
+    o[2] = __uint_as_float(v.z);
+    o[3] = __uint_as_float(v.w);
+  }
+};
+template <>
+struct Elem<__nv_bfloat16> {
+  static constexpr int kPerVec = 8;
+  __device__ __forceinline__ static void unpack(const uint4 v, float *o) {
+    o[0] = __uint_as_float(v.x << 16);
+    o[1] = __uint_as_float(v.x & 0xFFFF0000u);
+    o[2] = __uint_as_float(v.y << 16);
+    o[3] = __uint_as_float(v.y & 0xFFFF0000u);
+    o[4] = __uint_as_float(v.z << 16);
+    o[5] = __uint_as_float(v.z & 0xFFFF0000u);
+    o[6] = __uint_as_float(v.w << 16);
+    o[7] = __uint_as_float(v.w & 0xFFFF0000u);
+  }
+};
+
+__device__ __forceinline__ uint4 ldg_v4(const uint4 *p) {
+  uint4 r;
+  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p));
+  return r;
+}
+
+template <int KP, int DEG, typename E>
+struct LeafRecord {
+  static constexpr int NH = n_hh(DEG);
+  static constexpr int LEN = 2 * KP + 3 * NH;
+  static constexpr int PV = Elem<E>::kPerVec;
+  static constexpr int NV = (LEN + PV - 1) / PV;
+  float w[NV * PV];
+
+  __device__ __forceinline__ void load(const DevTree &tr, uint32_t leaf) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
+    uint4 raw[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) raw[i] = ldg_v4(p + i);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Elem<E>::unpack(raw[i], w + i * PV);
+  }
+  __device__ __forceinline__ float sig(int k) const { return w[k]; }
+  __device__ __forceinline__ float gam(int k) const { return w[KP + k]; }
+  __device__ __forceinline__ float hh(int ch, int i) const { return w[2 * KP + ch * NH + i]; }
+};
+
+// Per-ray constants: interpolated basis rows and the view-direction harmonics.
+template <int KP, int DEG>
+struct RayConst {
+  float a[KP], b[KP];
+  float Y[(DEG + 1) * (DEG + 1)];
+};
+
+// Frame coordinate u = t (T - 1) (t clamped to [0, 1]); rows lerped in u.
+template <int KP, int DEG>
+__device__ __forceinline__ void ray_const_basis(const DevTree &tr, float u, RayConst<KP, DEG> &rc) {
+  const float umax = (float)(tr.T - 1);
+  u = fminf(fmaxf(u, 0.f), umax);
+  int f0 = min((int)floorf(u), tr.T - 1);
+  const int f1 = min(f0 + 1, tr.T - 1);
+  const float fr = u - (float)f0;
+  const float *A0 = tr.A + (size_t)f0 * KP, *A1 = tr.A + (size_t)f1 * KP;
+  const float *B0 = tr.B + (size_t)f0 * KP, *B1 = tr.B + (size_t)f1 * KP;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    rc.a[k] = (1.f - fr) * __ldg(A0 + k) + fr * __ldg(A1 + k);
+    rc.b[k] = (1.f - fr) * __ldg(B0 + k) + fr * __ldg(B1 + k);
+  }
+}
+
+__device__ __forceinline__ float sigmoidf_fast(float x) { return 1.f / (1.f + __expf(-x)); }
+
+// Evaluated sample: density, hyper-angle terms and colour of one leaf.
+template <int DEG>
+struct Sample {
+  float pre_sigma, sigma;
+  float s_gamma;        // sigmoid(b . w_gamma); gamma = pi * s_gamma
+  float cg, sg;         // cos, sin of gamma
+  float z[3], c[3];     // pre-activation colour, colour
+  float R[(DEG + 1) * (DEG + 2) / 2];
+};
+
+// Eq. project-sigma, Eq. project-gamma, Eq. HH-color-2 for one leaf.  When the
+// density is zero the sample cannot contribute and colour is not evaluated.
+template <int KP, int DEG, typename E>
+__device__ __forceinline__ void eval_sample(const DevTree &tr, const RayConst<KP, DEG> &rc,
+                                            const LeafRecord<KP, DEG, E> &r, int act, Sample<DEG> &s) {
+  constexpr int NH = n_hh(DEG);
+  float ps = 0.f;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) ps = fmaf(rc.a[k], r.sig(k), ps);
+  s.pre_sigma = ps;
+  s.sigma = fmaxf(ps, 0.f);
+  if (!(s.sigma > 0.f)) return;
+  float pg = 0.f;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) pg = fmaf(rc.b[k], r.gam(k), pg);
+  s.s_gamma = sigmoidf_fast(pg);
+  sincospif(s.s_gamma, &s.sg, &s.cg);
+  hh_radial<DEG, false>(s.cg, s.sg, tr.hh_norm, s.R, nullptr);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float z = 0.f;
+#pragma unroll
+    for (int n = 0; n <= DEG; ++n)
+#pragma unroll
+      for (int l = 0; l <= n; ++l) {
+        float acc = 0.f;
+#pragma unroll
+        for (int m = -l; m <= l; ++m) acc = fmaf(r.hh(ch, hh_index(n, l, m)), rc.Y[l * l + l + m], acc);
+        z = fmaf(acc, s.R[radial_index(n, l)], z);
+      }
+    s.z[ch] = z;
+    s.c[ch] = act == 0 ? sigmoidf_fast(z) : z;
+  }
+  (void)NH;
+}
+
+// Rays in structure-of-arrays form.
+struct DevRays {
+  const float *ox, *oy, *oz, *dx, *dy, *dz, *t;
+  long long n;
+  float t_scalar;
+};
+
+__device__ __forceinline__ void load_ray(const DevRays &r, long long i, float o[3], float d[3], float &t) {
+  o[0] = __ldg(r.ox + i);
+  o[1] = __ldg(r.oy + i);
+  o[2] = __ldg(r.oz + i);
+  d[0] = __ldg(r.dx + i);
+  d[1] = __ldg(r.dy + i);
+  d[2] = __ldg(r.dz + i);
+  t = r.t ? __ldg(r.t + i) : r.t_scalar;
+  t = fminf(fmaxf(t, 0.f), 1.f);
+}
+
+struct DevOut {
+  float *rgb, *alpha, *depth, *tau;
+  int *nseg;
+};
+
+}  // namespace neuvv

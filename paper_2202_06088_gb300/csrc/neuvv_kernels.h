@@ -1,0 +1,93 @@
+// Internal launch interface between the C ABI (abi.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "neuvv_device.cuh"
+
+namespace neuvv {
+
+enum DType { kF32 = 0, kBF16 = 1 };
+
+struct LaunchCfg {
+  int block;          // threads per block
+  int grid;           // blocks (packet kernels: persistent grid)
+  int smem_nodes;     // child-table rows staged in shared memory (packet kernels)
+  int dynamic_queue;  // packet kernels: 1 = warps pull packets from a counter, 0 = static stride
+};
+
+struct FwdArgs {
+  DevTree tr;
+  DevRays rays;
+  DevOut out;
+  float t_stop;
+  int act;
+  unsigned int *work;  // packet kernel work counter (zeroed before launch)
+};
+
+struct BwdArgs {
+  DevTree tr;
+  DevRays rays;
+  const float *rgb;       // saved C [n][3]
+  const float *tau;       // saved optical depth [n]
+  const int *nseg;        // saved segment count [n]
+  const float *grad_rgb;  // [n][3]
+  const float *grad_alpha;  // [n] or null
+  float *grad;            // [n_leaves][rec_stride_f32]
+  int grad_stride;
+  unsigned int *touched;  // bitmap or null
+  float t_stop;
+  int act;
+  unsigned int *work;
+};
+
+constexpr int kMaxPrims = 16;
+
+struct PrimParam {
+  float minv[9];   // (s R)^-1, row-major
+  float trans[3];  // translation of world-from-local
+  float scale;     // s
+  float toff;      // time offset, frames
+  float tint[3];
+  int tree;        // index into ComposeArgs::trees
+};
+
+struct ComposeArgs {
+  DevTree trees[kMaxPrims];
+  PrimParam prim[kMaxPrims];
+  int n_prims;
+  DevRays rays;
+  DevOut out;
+  float t_stop;
+  int act;
+  int mode;  // 0 sorted, 1 Algorithm 1 literally
+  unsigned int *work;
+};
+
+struct TraceArgs {
+  DevTree tr;
+  DevRays rays;
+  int max_out;
+  int *leaf;
+  float *t0, *t1;
+  int *count;
+};
+
+// Each returns cudaGetLastError() of its launch (or cudaErrorInvalidValue for
+// an unsupported template combination).
+cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdArgs &a, const LaunchCfg &cfg,
+                              cudaStream_t s);
+cudaError_t launch_render_bwd(int KP, int DEG, DType dt, bool packet, const BwdArgs &a, const LaunchCfg &cfg,
+                              cudaStream_t s);
+cudaError_t launch_compose(int KP, int DEG, DType dt, const ComposeArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
+cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType dt, int storage_stride, float *grad,
+                        const unsigned int *touched, long long n_leaves, int stride_f32, int rec_len, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
+cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
+                       cudaStream_t s);
+
+// Dynamic shared memory needed by the packet kernels for a given staging size.
+inline size_t smem_bytes(int smem_nodes) { return (size_t)smem_nodes * 8 * sizeof(uint32_t); }
+
+}  // namespace neuvv

@@ -1,0 +1,104 @@
+// Training-step kernels around the renderer (Sec. 4.3 "Optimization"):
+//   * mse_kernel  -- Eq. rgb-loss, sum ||C - C_gt||^2 (scaled) and dL/dC;
+//   * adam_kernel -- Adam restricted to leaves whose touched bit is set
+//     (sparse: other leaves keep weights and moments), FP32 master + moments,
+//     storage copy rewritten (BF16 rounded to nearest even), gradient rows of
+//     updated leaves reset to zero for the next step.
+#include "neuvv_kernels.h"
+
+namespace neuvv {
+
+__global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ rgb, const float *__restrict__ target,
+                                                  long long n, float scale, float *__restrict__ grad,
+                                                  float *__restrict__ loss) {
+  float part = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float r = rgb[i] - target[i];
+    grad[i] = 2.f * scale * r;
+    part = fmaf(r, r, part);
+  }
+  if (loss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+    __shared__ float red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      atomicAdd(loss, scale * s);
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned short f32_to_bf16_rne(float f) {
+  unsigned int u = __float_as_uint(f);
+  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return (unsigned short)((u >> 16) | 0x40u);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (unsigned short)(u >> 16);
+}
+
+// One thread per (leaf, 4-float quad of the record).
+__global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ master, float *__restrict__ m,
+                                                   float *__restrict__ v, void *__restrict__ storage, int dt,
+                                                   int storage_stride, float *__restrict__ grad,
+                                                   const unsigned int *__restrict__ touched, long long n_leaves,
+                                                   int stride_f32, int rec_len, float lr, float b1, float b2,
+                                                   float eps, float c1, float c2) {
+  const int quads = stride_f32 / 4;
+  const long long total = n_leaves * quads;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long leaf = idx / quads;
+    const int q = (int)(idx - leaf * quads);
+    if (!((__ldg(touched + (leaf >> 5)) >> (leaf & 31)) & 1u)) continue;
+    const size_t off = (size_t)leaf * stride_f32 + 4 * q;
+    float4 g = *reinterpret_cast<const float4 *>(grad + off);
+    float4 w = *reinterpret_cast<const float4 *>(master + off);
+    float4 mm = *reinterpret_cast<const float4 *>(m + off);
+    float4 vv = *reinterpret_cast<const float4 *>(v + off);
+    float gs[4] = {g.x, g.y, g.z, g.w}, ws[4] = {w.x, w.y, w.z, w.w};
+    float ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (4 * q + k >= rec_len) continue;  // padding stays zero
+      ms[k] = b1 * ms[k] + (1.f - b1) * gs[k];
+      vs[k] = b2 * vs[k] + (1.f - b2) * gs[k] * gs[k];
+      ws[k] -= lr * (ms[k] / c1) / (sqrtf(vs[k] / c2) + eps);
+    }
+    *reinterpret_cast<float4 *>(master + off) = make_float4(ws[0], ws[1], ws[2], ws[3]);
+    *reinterpret_cast<float4 *>(m + off) = make_float4(ms[0], ms[1], ms[2], ms[3]);
+    *reinterpret_cast<float4 *>(v + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    *reinterpret_cast<float4 *>(grad + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (dt == kBF16) {
+      unsigned short *st = static_cast<unsigned short *>(storage) + (size_t)leaf * storage_stride + 4 * q;
+      const unsigned int lo = f32_to_bf16_rne(ws[0]) | ((unsigned int)f32_to_bf16_rne(ws[1]) << 16);
+      const unsigned int hi = f32_to_bf16_rne(ws[2]) | ((unsigned int)f32_to_bf16_rne(ws[3]) << 16);
+      *reinterpret_cast<uint2 *>(st) = make_uint2(lo, hi);
+    }
+  }
+}
+
+cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
+                       cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const long long want = (3 * n + 255) / 256;
+  const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
+  mse_kernel<<<blocks, 256, 0, s>>>(rgb, target, n, scale, grad, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType dt, int storage_stride, float *grad,
+                        const unsigned int *touched, long long n_leaves, int stride_f32, int rec_len, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
+  if (n_leaves == 0) return cudaSuccess;
+  const long long total = n_leaves * (stride_f32 / 4);
+  const long long want = (total + 255) / 256;
+  const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  adam_kernel<<<blocks, 256, 0, s>>>(master, m, v, storage, (int)dt, storage_stride, grad, touched, n_leaves,
+                                     stride_f32, rec_len, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+}  // namespace neuvv

@@ -1,0 +1,79 @@
+"""GPU parity of multi-primitive composition (Eq. st_composite_affine,
+Algorithm 1) through the C ABI against the FP64 oracle: the workload of
+8 seeded duplicates of one tree (rigid transform, scale in [0.5, 1.5], time
+offset, tint) at reduced resolution, in both blending modes; plus the
+argument checks that need a device."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_06088_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B(cuda_lib):
+    from paper_2202_06088_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def scene():
+    tree = I.config1_tree()
+    prims = I.config4_primitives(8, T=tree.T)
+    rays, _, _ = I.config4_rays(96, 96)
+    return tree, prims, rays
+
+
+@pytest.mark.parametrize("mode", ["sorted", "alg1"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_compose_matches_oracle(B, scene, mode, dtype):
+    tree, prims, rays = scene
+    tree_d = B.Tree(tree, dtype)
+    src = tree if dtype == "f32" else tree.with_coeffs(oracle.round_bf16(tree.w_sigma),
+                                                       oracle.round_bf16(tree.w_gamma), oracle.round_bf16(tree.w_hh))
+    xf = [p.transform for p in prims]
+    off = [p.time_offset for p in prims]
+    tint = [p.tint for p in prims]
+    ref = oracle.compose([src] * 8, xf, off, tint, rays, mode=mode)
+    dr = B.DeviceRays.from_host(rays)
+    got = B.neuvv_compose([tree_d] * 8, xf, off, tint, dr, mode=mode)
+    got = {k: got[k].cpu().numpy() for k in ("rgb", "alpha", "depth")}
+    assert (ref["alpha"] > 0.01).mean() > 0.05       # the duplicates are in view
+    err = np.abs(got["rgb"] - ref["rgb"])
+    # a pixel where two layers' depths coincide within float32 error may blend
+    # them in the other order: allow at most 0.1% of pixels outside 1e-4
+    bad = err.max(1) > 1e-4
+    assert bad.mean() <= 1e-3, (bad.sum(), err.max())
+    assert np.abs(got["alpha"] - ref["alpha"]).max() <= 1e-4
+    fin = np.isfinite(ref["depth"])
+    assert np.array_equal(fin, np.isfinite(got["depth"]))
+    assert np.abs(got["depth"][fin] - ref["depth"][fin]).max() <= 1e-3
+
+
+def test_compose_identity_equals_render(B):
+    tree = I.config1_tree()
+    rays, _ = I.config1_rays()
+    tree_d = B.Tree(tree, "f32")
+    dr = B.DeviceRays.from_host(rays)
+    eye = np.concatenate([np.eye(3), np.zeros((3, 1))], 1)
+    c = B.neuvv_compose([tree_d], [eye], [0.0], [[1, 1, 1]], dr)
+    r = B.neuvv_render(tree_d, dr)
+    assert (c["rgb"] - r["rgb"]).abs().max().item() <= 1e-6
+    assert (c["alpha"] - r["alpha"]).abs().max().item() <= 1e-6
+
+
+def test_compose_rejects_non_similarity_transforms(B):
+    tree = I.config1_tree()
+    tree_d = B.Tree(tree, "f32")
+    rays, _ = I.config1_rays()
+    dr = B.DeviceRays.from_host(rays.subset(np.arange(64)))
+    shear = np.concatenate([np.array([[1.0, 0.5, 0], [0, 1, 0], [0, 0, 1]]), np.zeros((3, 1))], 1)
+    with pytest.raises(B.NeuvvError, match="rotation"):
+        B.neuvv_compose([tree_d], [shear], [0.0], [[1, 1, 1]], dr)
+    mirror = np.concatenate([np.diag([1.0, 1.0, -1.0]), np.zeros((3, 1))], 1)
+    with pytest.raises(B.NeuvvError, match="determinant"):
+        B.neuvv_compose([tree_d], [mirror], [0.0], [[1, 1, 1]], dr)
+    with pytest.raises(B.NeuvvError, match="n_prims"):
+        B.neuvv_compose([tree_d] * 17, [np.eye(3, 4)] * 17, [0.0] * 17, [[1, 1, 1]] * 17, dr)

@@ -1,0 +1,101 @@
+"""Parity at the full benchmark size (8 views of 1920x1080 on the depth-9,
+~2M-leaf shell VOctree, K=16, T=150, HH degree 3), in the launch
+configuration the bench times (packet kernels after autotuning).  The oracle
+checks a seeded random sample of rays one by one; properties that hold for
+every ray are checked on all of them."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2202_06088_gb300 import inputs as I
+
+from helpers import psnr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B(cuda_lib):
+    from paper_2202_06088_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def c2():
+    tree = I.config2_tree()
+    rays, _, _, _ = I.config2_rays()
+    return tree, rays
+
+
+def _sample(n, k, seed=123):
+    return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_full_size_forward(B, c2, dtype):
+    tree, rays = c2
+    tree_d = B.Tree(tree, dtype)
+    dr = B.DeviceRays.from_host(rays)
+    B.neuvv_autotune(tree_d, dr)
+    out = B.neuvv_render(tree_d, dr, kernel="packet")
+    torch.cuda.synchronize()
+    assert tree_d.status() == 0
+    alpha, tau, rgb = out["alpha"], out["tau"], out["rgb"]
+    assert torch.isfinite(rgb).all() and torch.isfinite(alpha).all()
+    assert (alpha - (1 - torch.exp(-tau))).abs().max().item() <= 2e-5
+    assert (rgb >= -1e-6).all() and (rgb <= alpha[:, None] + 1e-5).all()
+    assert (alpha > 0).float().mean().item() > 0.1
+    idx = _sample(rays.n, 4000)
+    sub = rays.subset(idx)
+    ref = oracle.render(tree, sub)
+    got = {k: v[torch.from_numpy(idx).cuda()].cpu().numpy() for k, v in out.items()}
+    amb = ref["stop_margin"] < 1e-3
+    if dtype == "f32":
+        assert np.abs(got["rgb"] - ref["rgb"]).max() <= 1e-4
+        assert np.abs(got["alpha"] - ref["alpha"]).max() <= 1e-4
+        assert ((got["nseg"] != ref["nseg"]) & ~amb).sum() == 0
+    else:
+        assert np.abs(got["rgb"] - ref["rgb"]).max() <= 4e-3
+        assert psnr(got["rgb"], ref["rgb"]) >= 50.0
+    # the plain single-view kernel agrees with the packet kernel
+    plain = B.neuvv_render(tree_d, dr, kernel="plain")
+    assert (plain["rgb"] - out["rgb"]).abs().max().item() <= 1e-5
+
+
+def test_full_size_backward_sampled(B, c2):
+    """Adjoint over all 16.6M rays with dL/dC non-zero on a sampled subset only:
+    the gradient then equals the oracle's gradient of that subset."""
+    tree, rays = c2
+    tree_d = B.Tree(tree, "f32")
+    dr = B.DeviceRays.from_host(rays)
+    B.neuvv_autotune(tree_d, dr)
+    out = B.neuvv_render(tree_d, dr, kernel="packet")
+    idx = _sample(rays.n, 600, seed=7)
+    sub = rays.subset(idx)
+    ref_out = oracle.render(tree, sub)
+    keep = ref_out["stop_margin"] > 1e-3
+    idx, sub = idx[keep], sub.subset(np.nonzero(keep)[0])
+    rng = np.random.default_rng(8)
+    g_sub = rng.standard_normal((idx.size, 3)).astype(np.float32)
+    g = torch.zeros(rays.n, 3, device="cuda")
+    g[torch.from_numpy(idx).cuda()] = torch.from_numpy(g_sub).cuda()
+    grad = B.neuvv_render_backward(tree_d, dr, out, g, kernel="packet")
+    ref = oracle.render_grad(tree, sub, g_sub)
+    info = tree_d.info
+    K, Kp, Nh = info.K, info.K_pad, info.N_h
+    G = grad.cpu().numpy().astype(np.float64)
+    touched = np.nonzero(np.abs(ref["w_hh"]).sum((0, 1)) > 0)[0]
+    assert touched.size > 100
+    got_h = G[touched, 2 * Kp:2 * Kp + 3 * Nh]
+    ref_h = ref["w_hh"][:, :, touched].reshape(3 * Nh, -1).T
+    got_s = G[touched, :K]
+    ref_s = ref["w_sigma"][:, touched].T
+    for got_, ref_ in ((got_h, ref_h), (got_s, ref_s)):
+        num = np.linalg.norm(got_ - ref_, axis=1)
+        den = np.linalg.norm(ref_, axis=1)
+        assert np.all(num <= 1e-4 * den + 1e-6 * den.max()), (num / np.maximum(den, 1e-30)).max()
+    # leaves no sampled ray touched got exactly zero
+    mask = np.ones(tree.n_leaves, bool)
+    mask[touched] = False
+    assert np.abs(G[mask]).max() == 0.0

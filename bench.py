@@ -46,11 +46,15 @@ WORKLOAD = ("depth-9 shell VOctree (~2M leaves, K=16, T=150, HH degree 3), 8 vie
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline sample")
+    p.add_argument("--views", type=int, default=8, help="1920x1080 views per step (8 = the benchmark workload)")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default packet launch configuration")
+    p.add_argument("--profile-kernel", choices=["fwd", "bwd", "adam"], default=None,
+                   help="profiling case: launch that kernel twice on the workload and exit (no JSON)")
     return p.parse_args()
 
 
@@ -139,13 +143,14 @@ def cpu_baseline(tree, rays, target_seconds, seed=99):
     rng = np.random.default_rng(seed)
     ot = oracle.OracleTree(tree)
     cores = oracle.default_threads()
-    n_try = 256 * cores
+    n_try = 1024 * cores
     idx = np.sort(rng.choice(rays.n, size=n_try, replace=False))
     sub = rays.subset(idx)
     g = rng.standard_normal((sub.n, 3))
-    t0 = time.perf_counter()
-    oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores)
-    dt = time.perf_counter() - t0
+    for _ in range(2):   # the first pass also pages the coefficient planes in
+        t0 = time.perf_counter()
+        oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores)
+        dt = time.perf_counter() - t0
     n = int(min(rays.n, max(n_try, n_try * target_seconds / max(dt, 1e-3))))
     idx = np.sort(rng.choice(rays.n, size=n, replace=False))
     sub = rays.subset(idx)
@@ -198,6 +203,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args, B, tree, dr):
+    """Two launches of one kernel of the step on the given views (for ncu)."""
+    import torch
+    tree_d = B.Tree(tree, "bf16", with_optimizer=args.profile_kernel == "adam")
+    out = B.neuvv_render(tree_d, dr, kernel="packet")
+    grad_rgb = torch.randn(dr.n, 3, device=dr.o.device) * 1e-3
+    grad = tree_d.new_grad()
+    touched = tree_d.new_touched()
+    for k in range(2):
+        if args.profile_kernel == "fwd":
+            B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+        elif args.profile_kernel == "bwd":
+            B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+        else:
+            B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+            B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k + 1)
+    torch.cuda.synchronize()
+    print(f"profile case done: {args.profile_kernel} on {dr.n} rays", flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -218,16 +243,23 @@ def main():
     B.lib()
 
     tree = I.config2_tree()
-    rays = I.config2_rays()[0]
+    rays = I.config2_rays(n_views=args.views)[0]
     n = rays.n
     dev = torch.device("cuda", local)
     dr = B.DeviceRays.from_host(rays, device=dev)
+    if args.profile_kernel:
+        profile_case(args, B, tree, dr)
+        return
     # fixed target images: the same views rendered from perturbed coefficients
     tgt_tree = B.Tree(I.perturbed(tree, seed=1000), "f32")
     target = B.neuvv_render(tgt_tree, dr, kernel="packet")["rgb"].clone()
     del tgt_tree
     tree_d = B.Tree(tree, "bf16", with_optimizer=True)
-    B.neuvv_autotune(tree_d, dr)
+    if not args.no_autotune:
+        B.neuvv_autotune(tree_d, dr)
+    launch = {"block": tree_d.info.packet_block, "grid": tree_d.info.packet_grid,
+              "dynamic_queue": tree_d.info.packet_dynamic, "smem_nodes": tree_d.info.smem_nodes,
+              "autotuned": not args.no_autotune}
     out = B.alloc_out(n, dev)
     grad_rgb = torch.empty(n, 3, device=dev)
     grad = tree_d.new_grad()
@@ -253,6 +285,8 @@ def main():
         if evs:
             evs[4].record(stream)
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for k in range(args.warmup):
         step(k + 1)
     torch.cuda.synchronize()
@@ -268,8 +302,6 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
@@ -382,7 +414,8 @@ def main():
                    "T": tree.T, "hh_degree": tree.hh_degree, "storage": "bf16", "master": "f32",
                    "samples_per_step": samples, "touched_leaves": touched_leaves,
                    "l2": "inputs larger than L2 (rays 464 MB + records 512 MB per step)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "launch": launch,
+                   "clocks_window": "warm-up and timed steps"},
         "kernels_ms": kern,
         "fwd_bf16_packet": {"ms_per_1080p_frame": fwd_ms / 8, "msamples_per_s": fwd_samples / (fwd_ms / 1e3) / 1e6},
         "fwd_fp32_plain": {"ms_per_1080p_frame": plain_ms / 8,

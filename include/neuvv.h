@@ -103,6 +103,9 @@ typedef struct {
   int64_t n_nodes, n_leaves;
   int32_t smem_nodes;       /* nodes of the table's prefix staged in shared memory */
   int32_t device;
+  int32_t packet_block;     /* packet kernels: threads per block */
+  int32_t packet_grid;      /* packet kernels: persistent blocks */
+  int32_t packet_dynamic;   /* packet kernels: 1 = packets from a work counter */
 } neuvv_tree_info;
 
 /* Rays, device SoA float32 arrays of length n.  t may be NULL: then the

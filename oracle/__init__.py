@@ -49,48 +49,69 @@ class _Opts(ctypes.Structure):
     _fields_ = [("t_stop", ctypes.c_double), ("act", ctypes.c_int)]
 
 
+def configure(L):
+    """Declares the argument and result types of a loaded oracle library."""
+    d = ctypes.c_double
+    p = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    ci = ctypes.c_int
+    L.or_gegenbauer.restype = d
+    L.or_gegenbauer.argtypes = [ci, d, d]
+    L.or_legendre.restype = d
+    L.or_legendre.argtypes = [ci, ci, d]
+    L.or_sh_real.restype = d
+    L.or_sh_real.argtypes = [ci, ci, p]
+    L.or_hh_norm.restype = d
+    L.or_hh_norm.argtypes = [ci, ci]
+    L.or_hh_radial.restype = d
+    L.or_hh_radial.argtypes = [ci, ci, d]
+    L.or_hh_radial_dgamma.restype = d
+    L.or_hh_radial_dgamma.argtypes = [ci, ci, d]
+    L.or_hh.restype = d
+    L.or_hh.argtypes = [ci, ci, ci, d, p]
+    L.or_hh_all.restype = None
+    L.or_hh_all.argtypes = [ci, d, p, p, p]
+    L.or_n_hh.restype = ci
+    L.or_n_hh.argtypes = [ci]
+    L.or_hh_index.restype = ci
+    L.or_hh_index.argtypes = [ci, ci, ci]
+    L.or_render.restype = None
+    L.or_render.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, p, ci]
+    L.or_trace_batch.restype = None
+    L.or_trace_batch.argtypes = [p, i64, p, p, ci, p, p, p, p, ci]
+    L.or_render_grad.restype = None
+    L.or_render_grad.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, ci]
+    L.or_compose.restype = None
+    L.or_compose.argtypes = [p, p, p, p, ci, ci, p, i64, p, p, p, p, p, p, ci]
+    L.or_adam.restype = None
+    L.or_adam.argtypes = [i64, ci, p, p, p, p, p, d, d, d, d, ci]
+    L.or_round_bf16.restype = None
+    L.or_round_bf16.argtypes = [p, p, i64]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = ctypes.CDLL(build())
-            d = ctypes.c_double
-            p = ctypes.c_void_p
-            i64 = ctypes.c_int64
-            ci = ctypes.c_int
-            _lib.or_gegenbauer.restype = d
-            _lib.or_gegenbauer.argtypes = [ci, d, d]
-            _lib.or_legendre.restype = d
-            _lib.or_legendre.argtypes = [ci, ci, d]
-            _lib.or_sh_real.restype = d
-            _lib.or_sh_real.argtypes = [ci, ci, p]
-            _lib.or_hh_norm.restype = d
-            _lib.or_hh_norm.argtypes = [ci, ci]
-            _lib.or_hh_radial.restype = d
-            _lib.or_hh_radial.argtypes = [ci, ci, d]
-            _lib.or_hh_radial_dgamma.restype = d
-            _lib.or_hh_radial_dgamma.argtypes = [ci, ci, d]
-            _lib.or_hh.restype = d
-            _lib.or_hh.argtypes = [ci, ci, ci, d, p]
-            _lib.or_hh_all.restype = None
-            _lib.or_hh_all.argtypes = [ci, d, p, p, p]
-            _lib.or_n_hh.restype = ci
-            _lib.or_n_hh.argtypes = [ci]
-            _lib.or_hh_index.restype = ci
-            _lib.or_hh_index.argtypes = [ci, ci, ci]
-            _lib.or_render.restype = None
-            _lib.or_render.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, p, ci]
-            _lib.or_trace_batch.restype = None
-            _lib.or_trace_batch.argtypes = [p, i64, p, p, ci, p, p, p, p, ci]
-            _lib.or_render_grad.restype = None
-            _lib.or_render_grad.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, ci]
-            _lib.or_compose.restype = None
-            _lib.or_compose.argtypes = [p, p, p, p, ci, ci, p, i64, p, p, p, p, p, p, ci]
-            _lib.or_adam.restype = None
-            _lib.or_adam.argtypes = [i64, ci, p, p, p, p, p, d, d, d, d, ci]
-            _lib.or_round_bf16.restype = None
-            _lib.or_round_bf16.argtypes = [p, p, i64]
+            _lib = configure(ctypes.CDLL(build()))
     return _lib
+
+
+def compile_variant(src_text: str, out_path: str):
+    """Compiles another version of the oracle source (the mutation tests plant
+    mistakes in a copy to check that the pins catch them) and loads it."""
+    c_path = out_path + ".c"
+    with open(c_path, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-pthread", "-fno-fast-math",
+                           "-ffp-contract=off", c_path, "-o", out_path, "-lm"])
+    return configure(ctypes.CDLL(out_path))
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _ptr(a: np.ndarray):

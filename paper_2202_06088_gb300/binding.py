@@ -47,7 +47,8 @@ class TreeInfo(ctypes.Structure):
                 ("hh_degree", ctypes.c_int32), ("N_h", ctypes.c_int32), ("rec_len", ctypes.c_int32),
                 ("rec_stride", ctypes.c_int32), ("rec_stride_f32", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("smem_nodes", ctypes.c_int32),
-                ("device", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("packet_block", ctypes.c_int32), ("packet_grid", ctypes.c_int32),
+                ("packet_dynamic", ctypes.c_int32)]
 
 
 class RaysC(ctypes.Structure):
@@ -200,6 +201,12 @@ class Tree:
         return (torch.as_tensor(_CudaView(a, shape, "<f4", self), device="cuda"),
                 torch.as_tensor(_CudaView(v, shape, "<f4", self), device="cuda"))
 
+    def refresh_info(self) -> TreeInfo:
+        info = TreeInfo()
+        _check(lib().neuvv_tree_get_info(self.handle, ctypes.byref(info)))
+        self.info = info
+        return info
+
     def status(self) -> int:
         f = ctypes.c_uint32()
         _check(lib().neuvv_tree_status(self.handle, ctypes.byref(f)))
@@ -319,6 +326,7 @@ def neuvv_autotune(tree: Tree, rays: DeviceRays, t: float = 0.0) -> float:
     ms = ctypes.c_float()
     rc = rays.c()
     _check(lib().neuvv_autotune(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(ms), _stream()))
+    tree.refresh_info()
     return float(ms.value)
 
 

@@ -82,7 +82,7 @@ struct neuvv_tree {
   uint32_t *status = nullptr;
   unsigned int *work = nullptr;
   bool master_is_storage = false;
-  float bmin[3], scale[3];
+  float bmin[3], bmax[3], scale[3];
   float hh_norm[16];
   int num_sms = 0;
   LaunchCfg plain{128, 0, 0, 0};
@@ -103,6 +103,7 @@ DevTree dev_tree(const neuvv_tree *t) {
   d.n_leaves = t->info.n_leaves;
   for (int a = 0; a < 3; ++a) {
     d.bmin[a] = t->bmin[a];
+    d.bmax[a] = t->bmax[a];
     d.scale[a] = t->scale[a];
   }
   for (int k = 0; k < 16; ++k) d.hh_norm[k] = t->hh_norm[k];
@@ -230,6 +231,7 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
   cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, I.device);
   for (int a = 0; a < 3; ++a) {
     t->bmin[a] = d.aabb_min[a];
+    t->bmax[a] = d.aabb_max[a];
     t->scale[a] = (float)((double)(1 << d.depth) / ((double)d.aabb_max[a] - (double)d.aabb_min[a]));
   }
   for (int k = 0; k < 16; ++k) t->hh_norm[k] = 0.f;
@@ -320,6 +322,9 @@ neuvv_status neuvv_tree_destroy(neuvv_tree *t) {
 neuvv_status neuvv_tree_get_info(const neuvv_tree *t, neuvv_tree_info *info) {
   if (!t || !info) return fail(NEUVV_ERR_INVALID_ARG, "tree/info is NULL");
   *info = t->info;
+  info->packet_block = t->packet.block;
+  info->packet_grid = t->packet.grid;
+  info->packet_dynamic = t->packet.dynamic_queue;
   return NEUVV_OK;
 }
 

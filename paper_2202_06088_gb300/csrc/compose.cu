@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(256) compose_kernel(ComposeArgs a, int dynamic
       for (int j = 0; j < a.n_prims; ++j) {
         const PrimParam &pp = a.prim[j];
         const DevTree &tr = a.trees[pp.tree];
+        // rough local ray: enough to find where the line enters the local box
         const float q[3] = {o[0] - pp.trans[0], o[1] - pp.trans[1], o[2] - pp.trans[2]};
         float ol[3], dl[3];
 #pragma unroll
@@ -45,20 +46,41 @@ __global__ void __launch_bounds__(256) compose_kernel(ComposeArgs a, int dynamic
           ol[r] = pp.minv[3 * r] * q[0] + pp.minv[3 * r + 1] * q[1] + pp.minv[3 * r + 2] * q[2];
           dl[r] = pp.minv[3 * r] * d[0] + pp.minv[3 * r + 1] * d[1] + pp.minv[3 * r + 2] * d[2];
         }
-        // the world direction need not be unit: local length per world length
-        const float dlen = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const float period = (float)(tr.T - 1);
-        float u = fmodf(t * period + pp.toff, period);
-        if (u < 0.f) u += period;
         RayResult r;
-        integrate_ray<KP, DEG, E, false>(tr, nullptr, ol, dl, u, a.t_stop, a.act, r);
+        clear(r);
+        float s_in, s_out;
+        int ax;
+        const float dlen = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const float llen = sqrtf(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
+        if (dlen > 0.f && llen > 0.f && box_interval(tr, ol, dl, s_in, s_out, ax)) {
+          // entry point formed in world space from the exact input line, then
+          // taken to the local frame (small magnitudes: little rounding)
+          float pw[3], pl[3], dn[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) pw[k] = fmaf(s_in, d[k], o[k]) - pp.trans[k];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            pl[k] = pp.minv[3 * k] * pw[0] + pp.minv[3 * k + 1] * pw[1] + pp.minv[3 * k + 2] * pw[2];
+            dn[k] = dl[k] / llen;
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            if (k == ax) pl[k] = dl[k] > 0.f ? tr.bmin[k] : tr.bmax[k];
+          RayWalk w;
+          walk_start(tr, pl, dn, w);
+          if (w.alive) {
+            const float period = (float)(tr.T - 1);
+            float u = fmodf(t * period + pp.toff, period);
+            if (u < 0.f) u += period;
+            // world distance = s_in |d| + (local distance) * |d| / |dl|
+            integrate_walk<KP, DEG, E, false>(tr, nullptr, w, dn, u, a.t_stop, a.act, s_in * dlen, dlen / llen, r);
+          }
+        }
         Lc[j][0] = pp.tint[0] * r.C[0];
         Lc[j][1] = pp.tint[1] * r.C[1];
         Lc[j][2] = pp.tint[2] * r.C[2];
         La[j] = r.A;
-        // local distance along the unit local direction -> world distance
-        const float llen = sqrtf(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
-        Ld[j] = r.A >= 1e-4f ? (r.dnum / r.A) * (dlen / llen) : INFINITY;
+        Ld[j] = depth_of(r);
       }
       float I0, I1, I2, A, D;
       if (a.mode == 0) {

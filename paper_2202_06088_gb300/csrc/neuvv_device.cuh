@@ -37,7 +37,7 @@ struct DevTree {
   const float *B;         // [T][KP] hyper-angle basis
   uint32_t *status;       // device status word
   long long n_nodes, n_leaves;
-  float bmin[3];
+  float bmin[3], bmax[3];
   float scale[3];         // 2^depth / (bmax - bmin)
   float hh_norm[16];      // Abar_{n,l} at [4n + l]
   int depth, T, K, rec_stride, smem_nodes;
@@ -77,44 +77,77 @@ __device__ __forceinline__ int cell_of(float p, float v, int N) {
   return min(max(c, 0), N - 1);
 }
 
-// Normalises d, intersects the root box; returns false on a miss.
-__device__ __forceinline__ bool walk_init(const DevTree &tr, const float o[3], const float d_in[3], RayWalk &w,
-                                          float dn[3]) {
-  float len = sqrtf(d_in[0] * d_in[0] + d_in[1] * d_in[1] + d_in[2] * d_in[2]);
-  float il = 1.f / len;
-  dn[0] = d_in[0] * il;
-  dn[1] = d_in[1] * il;
-  dn[2] = d_in[2] * il;
-  const float N = (float)(1 << tr.depth);
-  float tn = -INFINITY, tf = INFINITY, go[3];
-  bool hit = len > 0.f;
+// Intersects the line o + s d (s >= 0, d as given, not normalised) with the
+// tree's box.  On a hit: the parameter interval [s_in, s_out] and the axis of
+// the entry face (-1 when the origin is inside the box).
+__device__ __forceinline__ bool box_interval(const DevTree &tr, const float o[3], const float d[3], float &s_in,
+                                             float &s_out, int &ax_in) {
+  float sn = -INFINITY, sf = INFINITY;
+  int axn = -1;
+  bool hit = true;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    go[a] = (o[a] - tr.bmin[a]) * tr.scale[a];
-    w.gd[a] = dn[a] * tr.scale[a];
-    if (w.gd[a] == 0.f) {
-      w.inv[a] = INFINITY;
-      if (go[a] < 0.f || go[a] > N) hit = false;
+    if (d[a] == 0.f) {
+      if (o[a] < tr.bmin[a] || o[a] > tr.bmax[a]) hit = false;
     } else {
-      w.inv[a] = 1.f / w.gd[a];
-      float t0 = (0.f - go[a]) / w.gd[a];
-      float t1 = (N - go[a]) / w.gd[a];
-      tn = fmaxf(tn, fminf(t0, t1));
-      tf = fminf(tf, fmaxf(t0, t1));
+      const float s0 = (tr.bmin[a] - o[a]) / d[a], s1 = (tr.bmax[a] - o[a]) / d[a];
+      const float lo = fminf(s0, s1), hi = fmaxf(s0, s1);
+      if (lo > sn) {
+        sn = lo;
+        axn = a;
+      }
+      sf = fminf(sf, hi);
     }
   }
-  float tin = fmaxf(tn, 0.f);
-  w.alive = hit && (tin < tf);
-  w.t_base = tin;
-  w.t_cur = 0.f;
-  w.t_far = tf - tin;
-  w.steps = 0;
-  w.max_steps = 3 * (1 << tr.depth) + 8;
+  s_in = fmaxf(sn, 0.f);
+  s_out = sf;
+  ax_in = sn > 0.f ? axn : -1;
+  return hit && s_in < s_out;
+}
+
+// Starts the walk at point p of the tree's frame (inside the box; on the
+// entry face when the ray comes from outside) along the unit direction dn.
+__device__ __forceinline__ void walk_start(const DevTree &tr, const float p[3], const float dn[3], RayWalk &w) {
+  const int N = 1 << tr.depth;
+  float tf = INFINITY;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    w.go[a] = go[a] + tin * w.gd[a];
-    w.cell[a] = cell_of(w.go[a], w.gd[a], 1 << tr.depth);
+    w.go[a] = fminf(fmaxf((p[a] - tr.bmin[a]) * tr.scale[a], 0.f), (float)N);
+    w.gd[a] = dn[a] * tr.scale[a];
+    w.inv[a] = w.gd[a] != 0.f ? 1.f / w.gd[a] : INFINITY;
+    w.cell[a] = cell_of(w.go[a], w.gd[a], N);
+    if (w.gd[a] != 0.f) tf = fminf(tf, ((w.gd[a] > 0.f ? (float)N : 0.f) - w.go[a]) * w.inv[a]);
   }
+  w.t_cur = 0.f;
+  w.t_far = tf;
+  w.steps = 0;
+  w.max_steps = 3 * N + 8;
+  w.alive = tf > 0.f;
+}
+
+// Ray given in the tree's own frame.  The entry point is formed from the exact
+// input line with one FMA per axis and the entry face's coordinate set
+// exactly, so a distant origin costs no precision inside the box.
+__device__ __forceinline__ bool walk_init(const DevTree &tr, const float o[3], const float d[3], RayWalk &w,
+                                          float dn[3]) {
+  const float len = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  w.alive = false;
+  if (!(len > 0.f)) return false;
+  const float il = 1.f / len;
+  dn[0] = d[0] * il;
+  dn[1] = d[1] * il;
+  dn[2] = d[2] * il;
+  float s_in, s_out;
+  int ax;
+  if (!box_interval(tr, o, d, s_in, s_out, ax)) return false;
+  float p[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) p[a] = fmaf(s_in, d[a], o[a]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a == ax) p[a] = d[a] > 0.f ? tr.bmin[a] : tr.bmax[a];
+  w.t_base = s_in * len;
+  walk_start(tr, p, dn, w);
   return w.alive;
 }
 

@@ -14,19 +14,14 @@ struct RayResult {
   int nseg;      // composited segments
 };
 
-// Walks the ray and composites front to back, stopping after the segment that
-// brings the transmittance below t_stop.  u is the frame coordinate.
+// Composites front to back along a started walk, stopping after the segment
+// that brings the transmittance below t_stop.  dn: unit direction in the
+// tree's frame (the view direction of the harmonics); u: frame coordinate;
+// t_base + dist_scale * t converts a walk distance t to the caller's frame.
 template <int KP, int DEG, typename E, bool kSmem>
-__device__ __forceinline__ void integrate_ray(const DevTree &tr, const uint32_t *s_child, const float o[3],
-                                              const float d[3], float u, float t_stop, int act, RayResult &res) {
-  res.C[0] = res.C[1] = res.C[2] = 0.f;
-  res.A = 0.f;
-  res.dnum = 0.f;
-  res.tau = 0.f;
-  res.nseg = 0;
-  RayWalk w;
-  float dn[3];
-  if (!walk_init(tr, o, d, w, dn)) return;
+__device__ __forceinline__ void integrate_walk(const DevTree &tr, const uint32_t *s_child, RayWalk &w,
+                                               const float dn[3], float u, float t_stop, int act, float t_base,
+                                               float dist_scale, RayResult &res) {
   RayConst<KP, DEG> rc;
   ray_const_basis<KP, DEG>(tr, u, rc);
   sh_real<DEG>(dn, rc.Y);
@@ -47,12 +42,31 @@ __device__ __forceinline__ void integrate_ray(const DevTree &tr, const uint32_t 
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) res.C[ch] = fmaf(wgt, s.c[ch], res.C[ch]);
       res.A += wgt;
-      res.dnum = fmaf(wgt, w.t_base + 0.5f * (t0 + t1), res.dnum);
+      res.dnum = fmaf(wgt, fmaf(dist_scale, 0.5f * (t0 + t1), t_base), res.dnum);
       res.tau += sd;
       T *= e;
       if (T < t_stop) break;
     }
   }
+}
+
+__device__ __forceinline__ void clear(RayResult &res) {
+  res.C[0] = res.C[1] = res.C[2] = 0.f;
+  res.A = 0.f;
+  res.dnum = 0.f;
+  res.tau = 0.f;
+  res.nseg = 0;
+}
+
+// One ray given in the tree's own frame (render kernels).
+template <int KP, int DEG, typename E, bool kSmem>
+__device__ __forceinline__ void integrate_ray(const DevTree &tr, const uint32_t *s_child, const float o[3],
+                                              const float d[3], float u, float t_stop, int act, RayResult &res) {
+  clear(res);
+  RayWalk w;
+  float dn[3];
+  if (!walk_init(tr, o, d, w, dn)) return;
+  integrate_walk<KP, DEG, E, kSmem>(tr, s_child, w, dn, u, t_stop, act, w.t_base, 1.f, res);
 }
 
 __device__ __forceinline__ float depth_of(const RayResult &r) { return r.A >= 1e-4f ? r.dnum / r.A : INFINITY; }

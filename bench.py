@@ -143,15 +143,19 @@ def cpu_baseline(tree, rays, target_seconds, seed=99):
     rng = np.random.default_rng(seed)
     ot = oracle.OracleTree(tree)
     cores = oracle.default_threads()
-    n_try = 1024 * cores
-    idx = np.sort(rng.choice(rays.n, size=n_try, replace=False))
-    sub = rays.subset(idx)
-    g = rng.standard_normal((sub.n, 3))
-    for _ in range(2):   # the first pass also pages the coefficient planes in
+    # time at two sizes (a fixed cost: zeroing the FP64 gradient planes) and
+    # pick the sample size that takes about target_seconds
+    pts = []
+    for n_try in (512 * cores, 2048 * cores):
+        idx = np.sort(rng.choice(rays.n, size=n_try, replace=False))
+        sub = rays.subset(idx)
+        g = rng.standard_normal((sub.n, 3))
         t0 = time.perf_counter()
         oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores)
-        dt = time.perf_counter() - t0
-    n = int(min(rays.n, max(n_try, n_try * target_seconds / max(dt, 1e-3))))
+        pts.append((n_try, time.perf_counter() - t0))
+    slope = max((pts[1][1] - pts[0][1]) / (pts[1][0] - pts[0][0]), 1e-9)
+    fixed = max(pts[0][1] - slope * pts[0][0], 0.0)
+    n = int(min(rays.n, max(pts[1][0], (target_seconds - fixed) / slope)))
     idx = np.sort(rng.choice(rays.n, size=n, replace=False))
     sub = rays.subset(idx)
     g = rng.standard_normal((sub.n, 3))
@@ -257,8 +261,8 @@ def main():
     tree_d = B.Tree(tree, "bf16", with_optimizer=True)
     if not args.no_autotune:
         B.neuvv_autotune(tree_d, dr)
-    launch = {"block": tree_d.info.packet_block, "grid": tree_d.info.packet_grid,
-              "dynamic_queue": tree_d.info.packet_dynamic, "smem_nodes": tree_d.info.smem_nodes,
+    launch = {"block": tree_d.info.packet_block, "grid": tree_d.info.packet_grid or "occupancy",
+              "chunk": tree_d.info.packet_chunk, "smem_nodes": tree_d.info.smem_nodes,
               "autotuned": not args.no_autotune}
     out = B.alloc_out(n, dev)
     grad_rgb = torch.empty(n, 3, device=dev)

@@ -104,8 +104,8 @@ typedef struct {
   int32_t smem_nodes;       /* nodes of the table's prefix staged in shared memory */
   int32_t device;
   int32_t packet_block;     /* packet kernels: threads per block */
-  int32_t packet_grid;      /* packet kernels: persistent blocks */
-  int32_t packet_dynamic;   /* packet kernels: 1 = packets from a work counter */
+  int32_t packet_grid;      /* packet kernels: persistent blocks (0 = as many as fit) */
+  int32_t packet_chunk;     /* packet kernels: rays a warp takes from the work counter at once */
 } neuvv_tree_info;
 
 /* Rays, device SoA float32 arrays of length n.  t may be NULL: then the

@@ -48,7 +48,7 @@ class TreeInfo(ctypes.Structure):
                 ("rec_stride", ctypes.c_int32), ("rec_stride_f32", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("smem_nodes", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("packet_block", ctypes.c_int32), ("packet_grid", ctypes.c_int32),
-                ("packet_dynamic", ctypes.c_int32)]
+                ("packet_chunk", ctypes.c_int32)]
 
 
 class RaysC(ctypes.Structure):

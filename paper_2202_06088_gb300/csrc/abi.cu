@@ -80,14 +80,14 @@ struct neuvv_tree {
   float *master = nullptr, *m = nullptr, *v = nullptr;
   float *A = nullptr, *B = nullptr;
   uint32_t *status = nullptr;
-  unsigned int *work = nullptr;
+  unsigned long long *work = nullptr;
   bool master_is_storage = false;
   float bmin[3], bmax[3], scale[3];
   float hh_norm[16];
   int num_sms = 0;
-  LaunchCfg plain{128, 0, 0, 0};
-  LaunchCfg packet{128, 0, 0, 1};
-  LaunchCfg compose{128, 0, 0, 1};
+  LaunchCfg plain{128, 0, 0, 0, 0};
+  LaunchCfg packet{128, 0, 128, 0, 0};
+  LaunchCfg compose{128, 0, 0, 1, 0};
 };
 
 namespace {
@@ -144,19 +144,6 @@ neuvv_status check_opts(const neuvv_render_opts *o) {
 neuvv_status check_time(const neuvv_rays *r, float t) {
   if (!r->t && !(t >= 0.f && t <= 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "scalar t must be in [0, 1]");
   return NEUVV_OK;
-}
-
-// Resident blocks per SM for a packet kernel, from the registers it uses.
-int packet_grid(const neuvv_tree *t, const LaunchCfg &c, int regs_per_thread) {
-  const int warps_per_block = c.block / 32;
-  int by_regs = 65536 / (regs_per_thread * c.block);
-  size_t sm = smem_bytes(t->info.smem_nodes);
-  int by_smem = sm ? (int)((220 * 1024) / (sm + 1024)) : 32;
-  int by_warps = 64 / warps_per_block;
-  int per_sm = by_regs < by_smem ? by_regs : by_smem;
-  if (by_warps < per_sm) per_sm = by_warps;
-  if (per_sm < 1) per_sm = 1;
-  return per_sm * (t->num_sms > 0 ? t->num_sms : 1);
 }
 
 }  // namespace
@@ -268,8 +255,8 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
   NEUVV_TRY(cudaMemcpy(t->B, Bp.data(), Bp.size() * 4, cudaMemcpyHostToDevice), "copy B");
   NEUVV_TRY(cudaMalloc(&t->status, 4), "cudaMalloc(status)");
   NEUVV_TRY(cudaMemset(t->status, 0, 4), "memset status");
-  NEUVV_TRY(cudaMalloc(&t->work, kWorkSlots * 4), "cudaMalloc(work)");
-  NEUVV_TRY(cudaMemset(t->work, 0, kWorkSlots * 4), "memset work");
+  NEUVV_TRY(cudaMalloc(&t->work, kWorkSlots * sizeof(unsigned long long)), "cudaMalloc(work)");
+  NEUVV_TRY(cudaMemset(t->work, 0, kWorkSlots * sizeof(unsigned long long)), "memset work");
   const size_t recf_bytes = L * sf * 4 + 16;
   if (d.dtype == NEUVV_F32) {
     NEUVV_TRY(cudaMalloc(&t->rec, recf_bytes), "cudaMalloc(records)");
@@ -297,8 +284,8 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
     NEUVV_TRY(cudaMemset(t->v, 0, recf_bytes), "memset v");
   }
 #undef NEUVV_TRY
-  t->packet.grid = packet_grid(t, t->packet, 168);
-  t->compose.grid = packet_grid(t, t->compose, 168);
+  t->plain.num_sms = t->packet.num_sms = t->compose.num_sms = t->num_sms > 0 ? t->num_sms : 1;
+  I.smem_nodes = (int32_t)(d.n_nodes < 512 ? d.n_nodes : 512);
   *out = t;
   return NEUVV_OK;
 }
@@ -324,7 +311,7 @@ neuvv_status neuvv_tree_get_info(const neuvv_tree *t, neuvv_tree_info *info) {
   *info = t->info;
   info->packet_block = t->packet.block;
   info->packet_grid = t->packet.grid;
-  info->packet_dynamic = t->packet.dynamic_queue;
+  info->packet_chunk = t->packet.chunk;
   return NEUVV_OK;
 }
 
@@ -367,8 +354,8 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   a.work = t->work + 0;
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
-  if (packet && cfg.dynamic_queue) {
-    cudaError_t e = cudaMemsetAsync(a.work, 0, 4, st);
+  if (packet) {
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
   }
   cudaError_t e = launch_render_fwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
@@ -406,8 +393,8 @@ neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, 
   a.work = t->work + 1;
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
-  if (packet && cfg.dynamic_queue) {
-    cudaError_t e = cudaMemsetAsync(a.work, 0, 4, st);
+  if (packet) {
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
   }
   cudaError_t e = launch_render_bwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
@@ -496,7 +483,7 @@ neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transfor
   a.work = t0->work + 2;
   const LaunchCfg &cfg = t0->compose;
   if (cfg.dynamic_queue) {
-    cudaError_t e = cudaMemsetAsync(a.work, 0, 4, st);
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
   }
   cudaError_t e = launch_compose(t0->info.K_pad, t0->info.hh_degree, (DType)t0->info.dtype, a, cfg, st);
@@ -586,34 +573,35 @@ neuvv_status neuvv_autotune(neuvv_tree *t, const neuvv_rays *sample, float time,
   int best_smem = saved_smem;
   float best_t = 1e30f;
   const int blocks[] = {64, 128, 256};
-  const int smem_opts[] = {0, 256, 1024, 4096};
+  const int smem_opts[] = {0, 512, 2048};
+  const int chunks[] = {64, 256};
   for (int sm_nodes : smem_opts) {
     if (sm_nodes > t->info.n_nodes) continue;
-    for (int b : blocks)
-      for (int dyn = 0; dyn <= 1; ++dyn)
-        for (int mult = 1; mult <= 2; ++mult) {
-          t->info.smem_nodes = sm_nodes;
-          LaunchCfg c{b, 0, sm_nodes, dyn};
-          c.grid = packet_grid(t, c, 168) * mult;
-          t->packet = c;
-          float ms_best = 1e30f;
-          for (int rep = 0; rep < 3; ++rep) {
-            cudaEventRecord(ev0, st);
-            s = neuvv_render(t, &r, time, &opts, &out, stream);
-            cudaEventRecord(ev1, st);
-            if (s != NEUVV_OK) break;
-            cudaEventSynchronize(ev1);
-            float ms;
-            cudaEventElapsedTime(&ms, ev0, ev1);
-            if (ms < ms_best) ms_best = ms;
-          }
+    for (int b : blocks) {
+      if (smem_bytes(sm_nodes, b, t->info.K_pad) > 200 * 1024) continue;
+      for (int ch : chunks) {
+        t->info.smem_nodes = sm_nodes;
+        t->packet = LaunchCfg{b, 0, ch, 0, saved.num_sms};
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(ev0, st);
+          s = neuvv_render(t, &r, time, &opts, &out, stream);
+          cudaEventRecord(ev1, st);
           if (s != NEUVV_OK) break;
-          if (ms_best < best_t) {
-            best_t = ms_best;
-            best = c;
-            best_smem = sm_nodes;
-          }
+          cudaEventSynchronize(ev1);
+          float ms;
+          cudaEventElapsedTime(&ms, ev0, ev1);
+          if (ms < ms_best) ms_best = ms;
         }
+        if (s != NEUVV_OK) break;
+        if (ms_best < best_t) {
+          best_t = ms_best;
+          best = t->packet;
+          best_smem = sm_nodes;
+        }
+      }
+      if (s != NEUVV_OK) break;
+    }
     if (s != NEUVV_OK) break;
   }
   t->packet = best;

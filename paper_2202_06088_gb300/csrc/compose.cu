@@ -16,15 +16,15 @@
 namespace neuvv {
 
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) compose_kernel(ComposeArgs a, int dynamic) {
+__global__ void __launch_bounds__(256) compose_kernel(const __grid_constant__ ComposeArgs a, int dynamic) {
   const long long n = a.rays.n;
   const long long n_packets = (n + 31) >> 5;
   const long long stride = ((long long)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   long long p;
   if (dynamic) {
-    unsigned int q = 0;
-    if (lane == 0) q = atomicAdd(a.work, 1u);
+    unsigned long long q = 0;
+    if (lane == 0) q = atomicAdd(a.work, 1ull);
     p = (long long)__shfl_sync(0xFFFFFFFFu, q, 0);
   } else {
     p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(256) compose_kernel(ComposeArgs a, int dynamic
     }
     __syncwarp();
     if (dynamic) {
-      unsigned int q = 0;
-      if (lane == 0) q = atomicAdd(a.work, 1u);
+      unsigned long long q = 0;
+      if (lane == 0) q = atomicAdd(a.work, 1ull);
       p = (long long)__shfl_sync(0xFFFFFFFFu, q, 0);
     } else {
       p += stride;
@@ -149,7 +149,14 @@ __global__ void __launch_bounds__(256) compose_kernel(ComposeArgs a, int dynamic
 template <int KP, int DEG, typename E>
 static cudaError_t compose_one(const ComposeArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
   if (a.rays.n == 0) return cudaSuccess;
-  compose_kernel<KP, DEG, E><<<cfg.grid, cfg.block, 0, s>>>(a, cfg.dynamic_queue);
+  int grid = cfg.grid;
+  if (grid <= 0) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, compose_kernel<KP, DEG, E>, cfg.block, 0);
+    if (e != cudaSuccess) return e;
+    grid = (per_sm > 0 ? per_sm : 1) * cfg.num_sms;
+  }
+  compose_kernel<KP, DEG, E><<<grid, cfg.block, 0, s>>>(a, cfg.dynamic_queue);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,7 @@ struct RayWalk {
   float t_far;     // exit distance of the root box past the entry point
   int cell[3];
   int steps, max_steps;
+  int restart;     // level at which the next descent may start (0 = root)
   bool alive;
 };
 
@@ -120,6 +121,7 @@ __device__ __forceinline__ void walk_start(const DevTree &tr, const float p[3], 
   }
   w.t_cur = 0.f;
   w.t_far = tf;
+  w.restart = 0;
   w.steps = 0;
   w.max_steps = 3 * N + 8;
   w.alive = tf > 0.f;
@@ -151,14 +153,30 @@ __device__ __forceinline__ bool walk_init(const DevTree &tr, const float o[3], c
   return w.alive;
 }
 
-// Descends from the root to the tree cell holding w.cell.  Returns the child
-// entry found (kEmpty or kLeafBit|leaf) and its level.  The first smem_nodes
-// rows of the child table may be read from shared memory.
-template <bool kSmem>
-__device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s_child, const int cell[3], int &level) {
-  uint32_t node = 0;
+// Path of the current descent, one node per level, kept per thread in shared
+// memory (entry L at path[L * stride]) so that the next descent can start at
+// the lowest common ancestor of the old and the new cell instead of the root.
+struct PathRef {
+  uint32_t *path;
+  int stride;
+};
+
+// Descends to the tree cell holding `cell`, from the root or (kPath) from the
+// ancestor at level `start` recorded by the previous descent.  Returns the
+// child entry found (kEmpty or kLeafBit|leaf) and its level.  The first
+// smem_nodes rows of the child table may be read from shared memory.
+template <bool kSmem, bool kPath>
+__device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s_child, PathRef pr, const int cell[3],
+                                            int start, int &level) {
   const int D = tr.depth;
-  for (int L = 0; L < D; ++L) {
+  uint32_t node = 0;
+  int L = 0;
+  if (kPath && start > 0) {
+    L = start;
+    node = pr.path[L * pr.stride];
+  }
+  for (; L < D; ++L) {
+    if (kPath) pr.path[L * pr.stride] = node;
     const int bit = D - 1 - L;
     const int slot = (((cell[0] >> bit) & 1) << 2) | (((cell[1] >> bit) & 1) << 1) | ((cell[2] >> bit) & 1);
     uint32_t e;
@@ -188,9 +206,9 @@ __device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s
 // Advances to the next occupied-leaf segment.  On success returns true with
 // leaf id and the segment [t0, t1] (relative to the entry point); false when
 // the ray has left the root box (or hit its step cap).
-template <bool kSmem>
+template <bool kSmem, bool kPath = false>
 __device__ __forceinline__ bool walk_next(const DevTree &tr, const uint32_t *s_child, RayWalk &w, uint32_t &leaf,
-                                          float &t0, float &t1) {
+                                          float &t0, float &t1, PathRef pr = PathRef{nullptr, 0}) {
   const int N = 1 << tr.depth;
   while (w.alive) {
     if (++w.steps > w.max_steps) {
@@ -199,7 +217,7 @@ __device__ __forceinline__ bool walk_next(const DevTree &tr, const uint32_t *s_c
       break;
     }
     int level;
-    const uint32_t e = descend<kSmem>(tr, s_child, w.cell, level);
+    const uint32_t e = descend<kSmem, kPath>(tr, s_child, pr, w.cell, w.restart, level);
     const int shift = tr.depth - level;
     const int size = 1 << shift;
     int lo[3];
@@ -236,6 +254,8 @@ __device__ __forceinline__ bool walk_next(const DevTree &tr, const uint32_t *s_c
           const int nc = w.gd[b] > 0.f ? lo[b] + size : lo[b] - 1;
           inside = nc >= 0 && nc < N;
           w.cell[b] = nc;
+          // deepest level whose cell holds both the old node and the new cell
+          if (kPath && inside) w.restart = tr.depth - 32 + __clz(nc ^ lo[b]);
         } else {
           const float p = w.go[b] + w.t_cur * w.gd[b];
           w.cell[b] = min(max(cell_of(p, w.gd[b], N), lo[b]), lo[b] + size - 1);
@@ -426,43 +446,88 @@ struct Sample {
   float s_gamma;        // sigmoid(b . w_gamma); gamma = pi * s_gamma
   float cg, sg;         // cos, sin of gamma
   float z[3], c[3];     // pre-activation colour, colour
+  float u[3];           // d z / d gamma (evaluated when the adjoint asks for it)
   float R[(DEG + 1) * (DEG + 2) / 2];
 };
 
+// Where a ray's interpolated basis rows a(u), b(u) live: registers
+// (RegRows) or a per-thread column of shared memory (SmemRows, entry k at
+// p[k * stride], b after a).
+template <int KP>
+struct RegRows {
+  const float *a, *b;
+  __device__ __forceinline__ float A(int k) const { return a[k]; }
+  __device__ __forceinline__ float B(int k) const { return b[k]; }
+};
+template <int KP>
+struct SmemRows {
+  const float *p;
+  int stride;
+  __device__ __forceinline__ float A(int k) const { return p[k * stride]; }
+  __device__ __forceinline__ float B(int k) const { return p[(KP + k) * stride]; }
+};
+
+// Frame coordinate u = t (T - 1), rows lerped in u, written to shared memory.
+template <int KP>
+__device__ __forceinline__ void rows_to_smem(const DevTree &tr, float u, float *p, int stride) {
+  const float umax = (float)(tr.T - 1);
+  u = fminf(fmaxf(u, 0.f), umax);
+  const int f0 = min((int)floorf(u), tr.T - 1);
+  const int f1 = min(f0 + 1, tr.T - 1);
+  const float fr = u - (float)f0;
+  const float *A0 = tr.A + (size_t)f0 * KP, *A1 = tr.A + (size_t)f1 * KP;
+  const float *B0 = tr.B + (size_t)f0 * KP, *B1 = tr.B + (size_t)f1 * KP;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    p[k * stride] = (1.f - fr) * __ldg(A0 + k) + fr * __ldg(A1 + k);
+    p[(KP + k) * stride] = (1.f - fr) * __ldg(B0 + k) + fr * __ldg(B1 + k);
+  }
+}
+
 // Eq. project-sigma, Eq. project-gamma, Eq. HH-color-2 for one leaf.  When the
 // density is zero the sample cannot contribute and colour is not evaluated.
-template <int KP, int DEG, typename E>
-__device__ __forceinline__ void eval_sample(const DevTree &tr, const RayConst<KP, DEG> &rc,
+// With kDz the gamma-derivative of each channel's pre-activation is formed
+// from the same inner sums sum_m w Y (the adjoint then needs no coefficient
+// after this call).
+template <int KP, int DEG, typename E, typename Rows, bool kDz = false>
+__device__ __forceinline__ void eval_sample(const DevTree &tr, const Rows &rows, const float *Y,
                                             const LeafRecord<KP, DEG, E> &r, int act, Sample<DEG> &s) {
-  constexpr int NH = n_hh(DEG);
   float ps = 0.f;
 #pragma unroll
-  for (int k = 0; k < KP; ++k) ps = fmaf(rc.a[k], r.sig(k), ps);
+  for (int k = 0; k < KP; ++k) ps = fmaf(rows.A(k), r.sig(k), ps);
   s.pre_sigma = ps;
   s.sigma = fmaxf(ps, 0.f);
   if (!(s.sigma > 0.f)) return;
   float pg = 0.f;
 #pragma unroll
-  for (int k = 0; k < KP; ++k) pg = fmaf(rc.b[k], r.gam(k), pg);
+  for (int k = 0; k < KP; ++k) pg = fmaf(rows.B(k), r.gam(k), pg);
   s.s_gamma = sigmoidf_fast(pg);
   sincospif(s.s_gamma, &s.sg, &s.cg);
-  hh_radial<DEG, false>(s.cg, s.sg, tr.hh_norm, s.R, nullptr);
+  float dR[(DEG + 1) * (DEG + 2) / 2];
+  hh_radial<DEG, kDz>(s.cg, s.sg, tr.hh_norm, s.R, dR);
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) {
-    float z = 0.f;
+    float z = 0.f, u = 0.f;
 #pragma unroll
     for (int n = 0; n <= DEG; ++n)
 #pragma unroll
       for (int l = 0; l <= n; ++l) {
         float acc = 0.f;
 #pragma unroll
-        for (int m = -l; m <= l; ++m) acc = fmaf(r.hh(ch, hh_index(n, l, m)), rc.Y[l * l + l + m], acc);
+        for (int m = -l; m <= l; ++m) acc = fmaf(r.hh(ch, hh_index(n, l, m)), Y[l * l + l + m], acc);
         z = fmaf(acc, s.R[radial_index(n, l)], z);
+        if (kDz) u = fmaf(acc, dR[radial_index(n, l)], u);
       }
     s.z[ch] = z;
+    s.u[ch] = u;
     s.c[ch] = act == 0 ? sigmoidf_fast(z) : z;
   }
-  (void)NH;
+}
+
+template <int KP, int DEG, typename E>
+__device__ __forceinline__ void eval_sample(const DevTree &tr, const RayConst<KP, DEG> &rc,
+                                            const LeafRecord<KP, DEG, E> &r, int act, Sample<DEG> &s) {
+  eval_sample<KP, DEG, E>(tr, RegRows<KP>{rc.a, rc.b}, rc.Y, r, act, s);
 }
 
 // Rays in structure-of-arrays form.

@@ -11,9 +11,10 @@ enum DType { kF32 = 0, kBF16 = 1 };
 
 struct LaunchCfg {
   int block;          // threads per block
-  int grid;           // blocks (packet kernels: persistent grid)
-  int smem_nodes;     // child-table rows staged in shared memory (packet kernels)
-  int dynamic_queue;  // packet kernels: 1 = warps pull packets from a counter, 0 = static stride
+  int grid;           // persistent kernels: blocks (0 = as many as fit, from the occupancy API)
+  int chunk;          // persistent kernels: rays a warp takes from the counter at a time
+  int dynamic_queue;  // compose: 1 = warps pull packets from a counter, 0 = static stride
+  int num_sms;        // multiprocessors of the device
 };
 
 struct FwdArgs {
@@ -22,7 +23,7 @@ struct FwdArgs {
   DevOut out;
   float t_stop;
   int act;
-  unsigned int *work;  // packet kernel work counter (zeroed before launch)
+  unsigned long long *work;  // persistent kernel work counter (zeroed before launch)
 };
 
 struct BwdArgs {
@@ -38,7 +39,7 @@ struct BwdArgs {
   unsigned int *touched;  // bitmap or null
   float t_stop;
   int act;
-  unsigned int *work;
+  unsigned long long *work;
 };
 
 constexpr int kMaxPrims = 16;
@@ -61,7 +62,7 @@ struct ComposeArgs {
   float t_stop;
   int act;
   int mode;  // 0 sorted, 1 Algorithm 1 literally
-  unsigned int *work;
+  unsigned long long *work;
 };
 
 struct TraceArgs {
@@ -87,7 +88,12 @@ cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType 
 cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
                        cudaStream_t s);
 
-// Dynamic shared memory needed by the packet kernels for a given staging size.
-inline size_t smem_bytes(int smem_nodes) { return (size_t)smem_nodes * 8 * sizeof(uint32_t); }
+// Dynamic shared memory of the persistent render kernels: the staged top of
+// the child table, then per thread the basis rows (2 K_pad floats) and the
+// descent path (16 levels).
+inline size_t smem_bytes(int smem_nodes, int block, int KP) {
+  return (size_t)smem_nodes * 8 * sizeof(uint32_t) + (size_t)block * (2 * KP + 16) * sizeof(float);
+}
+constexpr int kMaxDepth = 14;
 
 }  // namespace neuvv

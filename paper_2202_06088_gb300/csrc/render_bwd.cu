@@ -14,144 +14,183 @@
 // pi*sigmoid and d H / d gamma.  Gradients are scattered into an FP32
 // record-layout buffer with 16-byte vector atomics.
 #include "neuvv_kernels.h"
+#include "neuvv_feed.cuh"
 #include "neuvv_ray.cuh"
 
 namespace neuvv {
 
+// Vector reduction into global memory.  No memory clobber: the kernel never
+// reads the gradient buffer, so no load needs ordering against these adds.
 __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
-               : "memory");
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d));
 }
 
-template <int KP, int DEG, typename E, bool kSmem>
-__device__ __forceinline__ void adjoint_ray(const BwdArgs &a, const uint32_t *s_child, long long i) {
+// Per-ray replay state of the adjoint.
+struct AdjState {
+  float T;         // transmittance in front of the current sample
+  float acc[3];    // sum_{j<=i} w_j c_j
+  float C[3];      // saved colour
+  float g[3];      // dL/dC
+  float gA;        // dL/dalpha
+  float T_final;   // exp(-tau)
+  int count, target;
+};
+
+// Gradient of one sample; scatters it into the leaf's FP32 record.
+template <int KP, int DEG, typename E, typename Rows>
+__device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &rows, const float *Y, uint32_t leaf,
+                                               float t0, float t1, AdjState &st) {
   constexpr int NH = n_hh(DEG);
-  constexpr int LEN = 2 * KP + 3 * NH;
-  constexpr int LEN4 = (LEN + 3) / 4 * 4;
-  const int nseg = a.nseg[i];
-  if (nseg <= 0) return;
-  float o[3], d[3], t;
-  load_ray(a.rays, i, o, d, t);
-  const float g[3] = {a.grad_rgb[3 * i], a.grad_rgb[3 * i + 1], a.grad_rgb[3 * i + 2]};
-  const float gA = a.grad_alpha ? a.grad_alpha[i] : 0.f;
-  const float C[3] = {a.rgb[3 * i], a.rgb[3 * i + 1], a.rgb[3 * i + 2]};
-  const float T_final = __expf(-a.tau[i]);
   const DevTree &tr = a.tr;
-  RayWalk w;
-  float dn[3];
-  if (!walk_init(tr, o, d, w, dn)) return;
-  RayConst<KP, DEG> rc;
-  ray_const_basis<KP, DEG>(tr, t * (float)(tr.T - 1), rc);
-  sh_real<DEG>(dn, rc.Y);
-  float T = 1.f, acc[3] = {0.f, 0.f, 0.f};
-  uint32_t leaf;
-  float t0, t1;
-  int count = 0;
-  while (count < nseg && walk_next<kSmem>(tr, s_child, w, leaf, t0, t1)) {
-    ++count;
-    LeafRecord<KP, DEG, E> rec;
-    rec.load(tr, leaf);
-    Sample<DEG> s;
-    eval_sample<KP, DEG, E>(tr, rc, rec, a.act, s);
-    if (!(s.sigma > 0.f)) continue;  // alpha = 0: no path from this sample to L
-    const float delta = t1 - t0;
-    const float e = __expf(-s.sigma * delta);
-    const float wgt = T * (1.f - e);
-    const float Tn = T * e;
-    float dsig = gA * T_final;
-    float dz[3];
+  LeafRecord<KP, DEG, E> rec;
+  rec.load(tr, leaf);
+  Sample<DEG> s;
+  eval_sample<KP, DEG, E, Rows, true>(tr, rows, Y, rec, a.act, s);
+  if (!(s.sigma > 0.f)) return;  // alpha = 0: no path from this sample to L
+  const float delta = t1 - t0;
+  const float e = __expf(-s.sigma * delta);
+  const float wgt = st.T * (1.f - e);
+  const float Tn = st.T * e;
+  float dsig = st.gA * st.T_final;
+  float dz[3];
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      acc[ch] = fmaf(wgt, s.c[ch], acc[ch]);
-      const float S_after = C[ch] - acc[ch];
-      dsig = fmaf(g[ch], Tn * s.c[ch] - S_after, dsig);
-      const float dc = wgt * g[ch];
-      dz[ch] = a.act == 0 ? dc * s.c[ch] * (1.f - s.c[ch]) : dc;
-    }
-    dsig *= delta;
-    T = Tn;
-    // d/dgamma of the colour pre-activations
-    float R[(DEG + 1) * (DEG + 2) / 2], dR[(DEG + 1) * (DEG + 2) / 2];
-    hh_radial<DEG, true>(s.cg, s.sg, tr.hh_norm, R, dR);
-    float grad[LEN4];
-    float dgam = 0.f;
+  for (int ch = 0; ch < 3; ++ch) {
+    st.acc[ch] = fmaf(wgt, s.c[ch], st.acc[ch]);
+    const float S_after = st.C[ch] - st.acc[ch];
+    dsig = fmaf(st.g[ch], Tn * s.c[ch] - S_after, dsig);
+    const float dc = wgt * st.g[ch];
+    dz[ch] = a.act == 0 ? dc * s.c[ch] * (1.f - s.c[ch]) : dc;
+  }
+  dsig *= delta;
+  st.T = Tn;
+  float *dst = a.grad + (size_t)leaf * a.grad_stride;
+  // dL/dw_HH[ch][idx] = dz[ch] H_idx, in record order (channel, then idx
+  // ascending over n, l, m), streamed out one 16-byte quad at a time
+  float v[4];
+  int j = 0;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
+  for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
-      for (int n = 0; n <= DEG; ++n)
+    for (int n = 0; n <= DEG; ++n)
 #pragma unroll
-        for (int l = 0; l <= n; ++l) {
-          float wy = 0.f;
+      for (int l = 0; l <= n; ++l)
 #pragma unroll
-          for (int m = -l; m <= l; ++m) {
-            const int idx = hh_index(n, l, m);
-            const float Y = rc.Y[l * l + l + m];
-            grad[2 * KP + ch * NH + idx] = dz[ch] * R[radial_index(n, l)] * Y;
-            wy = fmaf(rec.hh(ch, idx), Y, wy);
-          }
-          dgam = fmaf(dz[ch] * wy, dR[radial_index(n, l)], dgam);
+        for (int m = -l; m <= l; ++m) {
+          v[j & 3] = dz[ch] * s.R[radial_index(n, l)] * Y[l * l + l + m];
+          if ((j & 3) == 3) red_add_v4(dst + 2 * KP + j - 3, v[0], v[1], v[2], v[3]);
+          ++j;
         }
-    }
-    const float dpre_g = dgam * kPi * s.s_gamma * (1.f - s.s_gamma);
-    const float dpre_s = s.pre_sigma > 0.f ? dsig : 0.f;
+  if (j & 3) {
 #pragma unroll
-    for (int k = 0; k < KP; ++k) {
-      grad[k] = dpre_s * rc.a[k];
-      grad[KP + k] = dpre_g * rc.b[k];
-    }
+    for (int k = 0; k < 4; ++k)
+      if (k >= (j & 3)) v[k] = 0.f;
+    red_add_v4(dst + 2 * KP + (j & ~3), v[0], v[1], v[2], v[3]);
+  }
+  // dL/dgamma = sum_ch dz[ch] d z_ch / dgamma
+  const float dgam = dz[0] * s.u[0] + dz[1] * s.u[1] + dz[2] * s.u[2];
+  const float dpre_g = dgam * kPi * s.s_gamma * (1.f - s.s_gamma);
+  const float dpre_s = s.pre_sigma > 0.f ? dsig : 0.f;
 #pragma unroll
-    for (int k = LEN; k < LEN4; ++k) grad[k] = 0.f;
-    float *dst = a.grad + (size_t)leaf * a.grad_stride;
-#pragma unroll
-    for (int q = 0; q < LEN4 / 4; ++q)
-      red_add_v4(dst + 4 * q, grad[4 * q], grad[4 * q + 1], grad[4 * q + 2], grad[4 * q + 3]);
-    if (a.touched) {
-      const unsigned int bit = 1u << (leaf & 31);
-      unsigned int *word = a.touched + (leaf >> 5);
-      if (!(__ldcg(word) & bit)) atomicOr(word, bit);
-    }
+  for (int q = 0; q < KP / 4; ++q) {
+    red_add_v4(dst + 4 * q, dpre_s * rows.A(4 * q), dpre_s * rows.A(4 * q + 1), dpre_s * rows.A(4 * q + 2),
+               dpre_s * rows.A(4 * q + 3));
+    red_add_v4(dst + KP + 4 * q, dpre_g * rows.B(4 * q), dpre_g * rows.B(4 * q + 1), dpre_g * rows.B(4 * q + 2),
+               dpre_g * rows.B(4 * q + 3));
+  }
+  if (a.touched) {
+    const unsigned int bit = 1u << (leaf & 31);
+    unsigned int *word = a.touched + (leaf >> 5);
+    if (!(__ldcg(word) & bit)) atomicOr(word, bit);
   }
 }
 
+// Sets up the replay of ray i; false when the ray has nothing to replay.
+__device__ __forceinline__ bool adjoint_setup(const BwdArgs &a, long long i, RayWalk &w, float dn[3], float &t,
+                                              AdjState &st) {
+  st.target = a.nseg[i];
+  if (st.target <= 0) return false;
+  float o[3], d[3];
+  load_ray(a.rays, i, o, d, t);
+  if (!walk_init(a.tr, o, d, w, dn)) return false;
+  st.T = 1.f;
+  st.count = 0;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    st.acc[ch] = 0.f;
+    st.C[ch] = a.rgb[3 * i + ch];
+    st.g[ch] = a.grad_rgb[3 * i + ch];
+  }
+  st.gA = a.grad_alpha ? a.grad_alpha[i] : 0.f;
+  st.T_final = __expf(-a.tau[i]);
+  return true;
+}
+
+// One thread per ray, root descents (baseline).
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_bwd_plain_kernel(BwdArgs a) {
+__global__ void __launch_bounds__(256) render_bwd_plain_kernel(const __grid_constant__ BwdArgs a) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.rays.n) return;
-  adjoint_ray<KP, DEG, E, false>(a, nullptr, i);
+  RayWalk w;
+  float dn[3], t;
+  AdjState st;
+  if (!adjoint_setup(a, i, w, dn, t, st)) return;
+  RayConst<KP, DEG> rc;
+  ray_const_basis<KP, DEG>(a.tr, t * (float)(a.tr.T - 1), rc);
+  sh_real<DEG>(dn, rc.Y);
+  uint32_t leaf;
+  float t0, t1;
+  while (st.count < st.target && walk_next<false>(a.tr, nullptr, w, leaf, t0, t1)) {
+    ++st.count;
+    adjoint_sample<KP, DEG, E>(a, RegRows<KP>{rc.a, rc.b}, rc.Y, leaf, t0, t1, st);
+  }
 }
 
+// Persistent adjoint: the forward's lane refill and ancestor-restarted descents.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_bwd_packet_kernel(BwdArgs a, int dynamic) {
-  extern __shared__ __align__(16) uint32_t s_child[];
+__global__ void __launch_bounds__(256) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a, int chunk) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const DevTree &tr = a.tr;
+  const int B = blockDim.x, tid = threadIdx.x;
+  uint32_t *s_child = smem;
+  float *my_rows = reinterpret_cast<float *>(smem + tr.smem_nodes * 8) + tid;
+  const PathRef pr{smem + tr.smem_nodes * 8 + 2 * KP * B + tid, B};
   {
-    const int words = a.tr.smem_nodes * 8;
-    const uint4 *src = reinterpret_cast<const uint4 *>(a.tr.child);
+    const int words = tr.smem_nodes * 8;
+    const uint4 *src = reinterpret_cast<const uint4 *>(tr.child);
     uint4 *dst = reinterpret_cast<uint4 *>(s_child);
-    for (int k = threadIdx.x; k < words / 4; k += blockDim.x) dst[k] = __ldg(src + k);
+    for (int k = tid; k < words / 4; k += B) dst[k] = __ldg(src + k);
     __syncthreads();
   }
-  const long long n = a.rays.n;
-  const long long n_packets = (n + 31) >> 5;
-  const long long stride = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  long long p;
-  if (dynamic) {
-    unsigned int q = 0;
-    if (lane == 0) q = atomicAdd(a.work, 1u);
-    p = (long long)__shfl_sync(0xFFFFFFFFu, q, 0);
-  } else {
-    p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  }
-  while (p < n_packets) {
-    const long long i = (p << 5) + lane;
-    if (i < n) adjoint_ray<KP, DEG, E, true>(a, s_child, i);
-    __syncwarp();
-    if (dynamic) {
-      unsigned int q = 0;
-      if (lane == 0) q = atomicAdd(a.work, 1u);
-      p = (long long)__shfl_sync(0xFFFFFFFFu, q, 0);
+  const SmemRows<KP> rows{my_rows, B};
+  WarpFeed feed{0, 0, false};
+  bool active = false;
+  RayWalk w;
+  AdjState st;
+  float Y[(DEG + 1) * (DEG + 1)];
+  for (;;) {
+    while (!feed.exhausted) {
+      const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
+      if (!need) break;
+      const long long i = feed_take(feed, a.work, a.rays.n, chunk, need);
+      if (i >= 0) {
+        float dn[3], t;
+        if (adjoint_setup(a, i, w, dn, t, st)) {
+          active = true;
+          rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+          sh_real<DEG>(dn, Y);
+        }
+      }
+    }
+    if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
+    if (!active) continue;
+    uint32_t leaf;
+    float t0, t1;
+    if (walk_next<true, true>(tr, s_child, w, leaf, t0, t1, pr)) {
+      ++st.count;
+      adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, t0, t1, st);
+      if (st.count >= st.target) active = false;
     } else {
-      p += stride;
+      active = false;
     }
   }
 }
@@ -162,12 +201,22 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
   if (!packet) {
     const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
     render_bwd_plain_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, 0, s>>>(a);
-  } else {
-    const size_t sm = smem_bytes(a.tr.smem_nodes);
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(render_bwd_packet_kernel<KP, DEG, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    render_bwd_packet_kernel<KP, DEG, E><<<cfg.grid, cfg.block, sm, s>>>(a, cfg.dynamic_queue);
+    return cudaGetLastError();
   }
+  const size_t sm = smem_bytes(a.tr.smem_nodes, cfg.block, KP);
+  auto kern = render_bwd_packet_kernel<KP, DEG, E>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = cfg.grid;
+  if (grid <= 0) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.block, sm);
+    if (e != cudaSuccess) return e;
+    grid = (per_sm > 0 ? per_sm : 1) * cfg.num_sms;
+  }
+  kern<<<grid, cfg.block, sm, s>>>(a, cfg.chunk);
   return cudaGetLastError();
 }
 

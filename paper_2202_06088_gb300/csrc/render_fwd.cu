@@ -3,17 +3,19 @@
 // render_plain_kernel  : one thread per ray, child table read from global
 //                        memory -- the baseline single-view path.
 // render_packet_kernel : persistent grid; each block stages the top of the
-//                        child table in shared memory once, then its warps
-//                        take 32-ray packets (coherent 8x4 pixel tiles when the
-//                        caller orders rays that way) from a global counter or
-//                        a static stride until the batch is done.
+//                        child table in shared memory once; warps take chunks
+//                        of consecutive rays (coherent 8x4 pixel tiles when the
+//                        caller orders rays that way) from a global counter and
+//                        refill each lane as its ray finishes; descents restart
+//                        at the lowest common ancestor of successive cells.
 #include "neuvv_kernels.h"
+#include "neuvv_feed.cuh"
 #include "neuvv_ray.cuh"
 
 namespace neuvv {
 
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_plain_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(256) render_plain_kernel(const __grid_constant__ FwdArgs a) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.rays.n) return;
   float o[3], d[3], t;
@@ -29,7 +31,7 @@ __global__ void __launch_bounds__(256) render_plain_kernel(FwdArgs a) {
   if (a.out.nseg) a.out.nseg[i] = r.nseg;
 }
 
-// Copies the first `rows` rows of the child table to shared memory.
+// Copies the first smem_nodes rows of the child table to shared memory.
 __device__ __forceinline__ void stage_child(const DevTree &tr, uint32_t *s_child) {
   const int words = tr.smem_nodes * 8;
   const uint4 *src = reinterpret_cast<const uint4 *>(tr.child);
@@ -38,49 +40,101 @@ __device__ __forceinline__ void stage_child(const DevTree &tr, uint32_t *s_child
   __syncthreads();
 }
 
-// Next packet of a warp: from the counter (dynamic) or by static stride.
-__device__ __forceinline__ long long next_packet(unsigned int *work, bool dynamic, long long cur, long long stride) {
-  if (dynamic) {
-    unsigned int p = 0;
-    if ((threadIdx.x & 31) == 0) p = atomicAdd(work, 1u);
-    return (long long)__shfl_sync(0xFFFFFFFFu, p, 0);
-  }
-  return cur + stride;
+__device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
+  out.rgb[3 * i + 0] = 0.f;
+  out.rgb[3 * i + 1] = 0.f;
+  out.rgb[3 * i + 2] = 0.f;
+  out.alpha[i] = 0.f;
+  if (out.depth) out.depth[i] = INFINITY;
+  if (out.tau) out.tau[i] = 0.f;
+  if (out.nseg) out.nseg[i] = 0;
 }
 
-__device__ __forceinline__ long long first_packet(unsigned int *work, bool dynamic) {
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  return dynamic ? next_packet(work, true, 0, 0) : warp;
-}
-
+// Persistent forward kernel.  Per lane: one ray at a time, refilled from the
+// warp's chunk when it finishes; per iteration every active lane advances to
+// its next occupied-leaf segment (descent restarted at the lowest common
+// ancestor, top of the table in shared memory) and then all of them shade
+// that sample together.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_packet_kernel(FwdArgs a, int dynamic) {
-  extern __shared__ __align__(16) uint32_t s_child[];
-  stage_child(a.tr, s_child);
+__global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constant__ FwdArgs a, int chunk) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const DevTree &tr = a.tr;
+  const int B = blockDim.x, tid = threadIdx.x;
+  uint32_t *s_child = smem;
+  float *my_rows = reinterpret_cast<float *>(smem + tr.smem_nodes * 8) + tid;
+  const PathRef pr{smem + tr.smem_nodes * 8 + 2 * KP * B + tid, B};
+  stage_child(tr, s_child);
+  const SmemRows<KP> rows{my_rows, B};
   const long long n = a.rays.n;
-  const long long n_packets = (n + 31) >> 5;
-  const long long stride = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  for (long long p = first_packet(a.work, dynamic); p < n_packets; p = next_packet(a.work, dynamic, p, stride)) {
-    const long long i = (p << 5) + lane;
-    if (i < n) {
-      float o[3], d[3], t;
-      load_ray(a.rays, i, o, d, t);
-      RayResult r;
-      integrate_ray<KP, DEG, E, true>(a.tr, s_child, o, d, t * (float)(a.tr.T - 1), a.t_stop, a.act, r);
-      a.out.rgb[3 * i + 0] = r.C[0];
-      a.out.rgb[3 * i + 1] = r.C[1];
-      a.out.rgb[3 * i + 2] = r.C[2];
-      a.out.alpha[i] = r.A;
-      if (a.out.depth) a.out.depth[i] = depth_of(r);
-      if (a.out.tau) a.out.tau[i] = r.tau;
-      if (a.out.nseg) a.out.nseg[i] = r.nseg;
+  WarpFeed feed{0, 0, false};
+  bool active = false;
+  long long ray = 0;
+  RayWalk w;
+  float Y[(DEG + 1) * (DEG + 1)];
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f, dnum = 0.f, tau = 0.f;
+  int nseg = 0;
+  for (;;) {
+    // give every idle lane a ray; rays that miss the box are finished here
+    while (!feed.exhausted) {
+      const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
+      if (!need) break;
+      const long long i = feed_take(feed, a.work, n, chunk, need);
+      if (i >= 0) {
+        float o[3], d[3], t, dn[3];
+        load_ray(a.rays, i, o, d, t);
+        if (walk_init(tr, o, d, w, dn)) {
+          active = true;
+          ray = i;
+          T = 1.f;
+          C0 = C1 = C2 = A = dnum = tau = 0.f;
+          nseg = 0;
+          rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+          sh_real<DEG>(dn, Y);
+        } else {
+          write_miss(a.out, i);
+        }
+      }
     }
-    __syncwarp();
+    if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
+    if (!active) continue;
+    uint32_t leaf;
+    float t0, t1;
+    bool more = walk_next<true, true>(tr, s_child, w, leaf, t0, t1, pr);
+    if (more) {
+      LeafRecord<KP, DEG, E> rec;
+      rec.load(tr, leaf);
+      Sample<DEG> s;
+      eval_sample<KP, DEG, E>(tr, rows, Y, rec, a.act, s);
+      ++nseg;
+      if (s.sigma > 0.f) {
+        const float delta = t1 - t0;
+        const float sd = s.sigma * delta;
+        const float e = __expf(-sd);
+        const float wgt = T * (1.f - e);
+        C0 = fmaf(wgt, s.c[0], C0);
+        C1 = fmaf(wgt, s.c[1], C1);
+        C2 = fmaf(wgt, s.c[2], C2);
+        A += wgt;
+        dnum = fmaf(wgt, w.t_base + 0.5f * (t0 + t1), dnum);
+        tau += sd;
+        T *= e;
+        if (T < a.t_stop) more = false;
+      }
+    }
+    if (!more) {
+      a.out.rgb[3 * ray + 0] = C0;
+      a.out.rgb[3 * ray + 1] = C1;
+      a.out.rgb[3 * ray + 2] = C2;
+      a.out.alpha[ray] = A;
+      if (a.out.depth) a.out.depth[ray] = A >= 1e-4f ? dnum / A : INFINITY;
+      if (a.out.tau) a.out.tau[ray] = tau;
+      if (a.out.nseg) a.out.nseg[ray] = nseg;
+      active = false;
+    }
   }
 }
 
-__global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
+__global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceArgs a) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.rays.n) return;
   float o[3], d[3], t;
@@ -114,12 +168,22 @@ static cudaError_t fwd_one(bool packet, const FwdArgs &a, const LaunchCfg &cfg, 
   if (!packet) {
     const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
     render_plain_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, 0, s>>>(a);
-  } else {
-    const size_t sm = smem_bytes(a.tr.smem_nodes);
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(render_packet_kernel<KP, DEG, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    render_packet_kernel<KP, DEG, E><<<cfg.grid, cfg.block, sm, s>>>(a, cfg.dynamic_queue);
+    return cudaGetLastError();
   }
+  const size_t sm = smem_bytes(a.tr.smem_nodes, cfg.block, KP);
+  auto kern = render_packet_kernel<KP, DEG, E>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = cfg.grid;
+  if (grid <= 0) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.block, sm);
+    if (e != cudaSuccess) return e;
+    grid = (per_sm > 0 ? per_sm : 1) * cfg.num_sms;
+  }
+  kern<<<grid, cfg.block, sm, s>>>(a, cfg.chunk);
   return cudaGetLastError();
 }
 

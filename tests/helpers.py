@@ -59,3 +59,23 @@ def compare_traces(tree, ref, gpu, max_out, eps_rel=1e-3, chord_tol_rel=5e-3):
         if not ok:
             bad.append((r, "mismatch"))
     return n - len(bad), len(bad), bad
+
+
+def nseg_mismatch_explained(B, tree, tree_d, rays, idx, max_out=None):
+    """For rays whose composited-segment counts differ between the GPU and the
+    oracle, checks that their leaf sequences still align under the tiny-cell
+    rule (the difference is a near-tie cell with a chord below 1e-3 of a
+    finest cell).  Returns the indices that are not explained."""
+    import oracle
+    if len(idx) == 0:
+        return []
+    sub = rays.subset(np.asarray(idx))
+    mo = max_out or 4 * (1 << tree.depth)
+    ref = oracle.trace(tree, sub, max_out=mo)
+    dr = B.DeviceRays.from_host(sub)
+    got = {k: v.cpu().numpy() for k, v in B.neuvv_trace(tree_d, dr, mo).items()}
+    _, _, bad = compare_traces(tree, ref, got, mo)
+    bad_rows = {r for r, _ in bad}
+    # aligned sequences of equal length cannot explain a different count
+    bad_rows |= {r for r in range(len(idx)) if int(ref["count"][r]) == int(got["count"][r])}
+    return [int(np.asarray(idx)[r]) for r in sorted(bad_rows)]

@@ -15,7 +15,7 @@ import pytest
 import oracle
 from paper_2202_06088_gb300 import inputs as I
 
-from helpers import compare_traces, psnr
+from helpers import compare_traces, nseg_mismatch_explained, psnr
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,8 @@ def _ambiguous_stop(ref, t_stop=1e-4):
     return ref["stop_margin"] < 1e-3
 
 
-def _check_render(ref, got, tol, stop_ok=None):
+def _check_render(ref, got, tol, stop_ok=None, explain=None):
+    """explain(idx) -> unexplained subset of rays whose segment counts differ."""
     assert np.abs(got["rgb"] - ref["rgb"]).max() <= tol, np.abs(got["rgb"] - ref["rgb"]).max()
     assert np.abs(got["alpha"] - ref["alpha"]).max() <= tol
     fin = np.isfinite(ref["depth"]) & (ref["alpha"] > 1e-3)
@@ -61,7 +62,10 @@ def _check_render(ref, got, tol, stop_ok=None):
     diff = got["nseg"] != ref["nseg"]
     if stop_ok is not None:
         diff &= ~stop_ok
-    assert diff.sum() == 0, np.nonzero(diff)[0][:10]
+    bad = np.nonzero(diff)[0]
+    if explain is not None:
+        bad = explain(bad)
+    assert len(bad) == 0, bad[:10]
 
 
 def test_trace_matches_oracle_c1(B, c1, c1_rays):

@@ -261,8 +261,7 @@ def main():
     tree_d = B.Tree(tree, "bf16", with_optimizer=True)
     if not args.no_autotune:
         B.neuvv_autotune(tree_d, dr)
-    launch = {"block": tree_d.info.packet_block, "grid": tree_d.info.packet_grid or "occupancy",
-              "chunk": tree_d.info.packet_chunk, "smem_nodes": tree_d.info.smem_nodes,
+    launch = {"block": tree_d.info.packet_block,
               "autotuned": not args.no_autotune}
     out = B.alloc_out(n, dev)
     grad_rgb = torch.empty(n, 3, device=dev)

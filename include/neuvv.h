@@ -73,7 +73,7 @@ typedef enum { NEUVV_F32 = 0, NEUVV_BF16 = 1 } neuvv_dtype;
  *   Node 0 is the root covering [aabb_min, aabb_max]; children of a node at
  *   level L are cells at level L+1; the finest level is `depth` (1..14).
  *   Internal node indices must be breadth first (a child's index is larger
- *   than its parent's); the top of the table is staged in shared memory.
+ *   than its parent's).
  * w_sigma: [K][n_leaves], w_gamma: [K][n_leaves], w_hh: [3][N_h][n_leaves] float32
  *   planes (N_h = sum_{n<=hh_degree} (n+1)^2), the paper's per-voxel vectors.
  * basis_A, basis_B: [T][K] float32 (T >= 2 frames).
@@ -101,11 +101,8 @@ typedef struct {
   int32_t rec_stride_f32;   /* FP32 floats per leaf in grad / master / m / v */
   neuvv_dtype dtype;
   int64_t n_nodes, n_leaves;
-  int32_t smem_nodes;       /* nodes of the table's prefix staged in shared memory */
   int32_t device;
-  int32_t packet_block;     /* packet kernels: threads per block */
-  int32_t packet_grid;      /* packet kernels: persistent blocks (0 = as many as fit) */
-  int32_t packet_chunk;     /* packet kernels: rays a warp takes from the work counter at once */
+  int32_t packet_block;     /* packet kernels: threads per block (set by neuvv_autotune) */
 } neuvv_tree_info;
 
 /* Rays, device SoA float32 arrays of length n.  t may be NULL: then the
@@ -131,8 +128,10 @@ typedef enum { NEUVV_COMPOSE_SORTED = 0, NEUVV_COMPOSE_ALG1 = 1 } neuvv_compose_
 typedef struct {
   float t_stop;        /* early termination: stop after T < t_stop (1e-4) */
   int32_t color_act;   /* neuvv_color_act */
-  int32_t kernel;      /* neuvv_kernel: plain = one thread per ray, no staging;
-                          packet = shared-memory staged top levels, tuned launch */
+  int32_t kernel;      /* neuvv_kernel: plain = one thread per ray, descents from
+                          the root, basis rows in registers; packet = warps of
+                          32 consecutive rays, descents restarted at the lowest
+                          common ancestor, rows in shared memory, tuned block */
   int32_t compose_mode;/* neuvv_compose_mode */
 } neuvv_render_opts;
 
@@ -210,7 +209,7 @@ neuvv_status neuvv_mse_grad(const float *rgb, const float *target, int64_t n, fl
 neuvv_status neuvv_trace(const neuvv_tree *tree, const neuvv_rays *rays, int32_t max_out, int32_t *leaf, float *t0,
                          float *t1, int32_t *count, neuvv_stream stream);
 
-/* Picks launch parameters for the packet kernels by timing candidates on a
+/* Picks the block size of the packet kernels by timing candidates on a
  * sample of rays (the first min(n, 2^20)); the choice is stored in the tree.
  * Synchronous.  best_ms (nullable) receives the best forward time. */
 neuvv_status neuvv_autotune(neuvv_tree *tree, const neuvv_rays *sample, float t, float *best_ms, neuvv_stream stream);

@@ -46,9 +46,8 @@ class TreeInfo(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("K", ctypes.c_int32), ("K_pad", ctypes.c_int32), ("T", ctypes.c_int32),
                 ("hh_degree", ctypes.c_int32), ("N_h", ctypes.c_int32), ("rec_len", ctypes.c_int32),
                 ("rec_stride", ctypes.c_int32), ("rec_stride_f32", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("smem_nodes", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("packet_block", ctypes.c_int32), ("packet_grid", ctypes.c_int32),
-                ("packet_chunk", ctypes.c_int32)]
+                ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("device", ctypes.c_int32), ("packet_block", ctypes.c_int32)]
 
 
 class RaysC(ctypes.Structure):

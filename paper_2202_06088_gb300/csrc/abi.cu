@@ -85,9 +85,9 @@ struct neuvv_tree {
   float bmin[3], bmax[3], scale[3];
   float hh_norm[16];
   int num_sms = 0;
-  LaunchCfg plain{128, 0, 0, 0, 0};
-  LaunchCfg packet{128, 0, 128, 0, 0};
-  LaunchCfg compose{128, 0, 0, 1, 0};
+  LaunchCfg plain{128, 0, 0, 0};
+  LaunchCfg packet{128, 0, 0, 0};
+  LaunchCfg compose{128, 0, 1, 0};
 };
 
 namespace {
@@ -111,7 +111,7 @@ DevTree dev_tree(const neuvv_tree *t) {
   d.T = t->info.T;
   d.K = t->info.K;
   d.rec_stride = t->info.rec_stride;
-  d.smem_nodes = t->info.smem_nodes;
+  d.smem_nodes = 0;
   return d;
 }
 
@@ -213,7 +213,6 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
   I.dtype = d.dtype;
   I.n_nodes = d.n_nodes;
   I.n_leaves = d.n_leaves;
-  I.smem_nodes = (int32_t)(d.n_nodes < 1024 ? d.n_nodes : 1024);
   if (cudaGetDevice(&I.device) != cudaSuccess) return cleanup(fail(NEUVV_ERR_CUDA, "no CUDA device"));
   cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, I.device);
   for (int a = 0; a < 3; ++a) {
@@ -285,7 +284,6 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
   }
 #undef NEUVV_TRY
   t->plain.num_sms = t->packet.num_sms = t->compose.num_sms = t->num_sms > 0 ? t->num_sms : 1;
-  I.smem_nodes = (int32_t)(d.n_nodes < 512 ? d.n_nodes : 512);
   *out = t;
   return NEUVV_OK;
 }
@@ -310,8 +308,6 @@ neuvv_status neuvv_tree_get_info(const neuvv_tree *t, neuvv_tree_info *info) {
   if (!t || !info) return fail(NEUVV_ERR_INVALID_ARG, "tree/info is NULL");
   *info = t->info;
   info->packet_block = t->packet.block;
-  info->packet_grid = t->packet.grid;
-  info->packet_chunk = t->packet.chunk;
   return NEUVV_OK;
 }
 
@@ -351,13 +347,8 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   a.out = DevOut{out->rgb, out->alpha, out->depth, out->tau, out->nseg};
   a.t_stop = opts->t_stop;
   a.act = opts->color_act;
-  a.work = t->work + 0;
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
-  if (packet) {
-    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
-  }
   cudaError_t e = launch_render_fwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   return NEUVV_OK;
@@ -390,13 +381,8 @@ neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, 
   a.touched = touched;
   a.t_stop = opts->t_stop;
   a.act = opts->color_act;
-  a.work = t->work + 1;
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
-  if (packet) {
-    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
-  }
   cudaError_t e = launch_render_bwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   return NEUVV_OK;
@@ -568,53 +554,34 @@ neuvv_status neuvv_autotune(neuvv_tree *t, const neuvv_rays *sample, float time,
   neuvv_render_opts opts{1e-4f, NEUVV_ACT_SIGMOID, NEUVV_KERNEL_PACKET, NEUVV_COMPOSE_SORTED};
   neuvv_out out{rgb, alpha, nullptr, nullptr, nullptr};
   const LaunchCfg saved = t->packet;
-  const int saved_smem = t->info.smem_nodes;
   LaunchCfg best = saved;
-  int best_smem = saved_smem;
   float best_t = 1e30f;
-  const int blocks[] = {64, 128, 256};
-  const int smem_opts[] = {0, 512, 2048};
-  const int chunks[] = {64, 256};
-  for (int sm_nodes : smem_opts) {
-    if (sm_nodes > t->info.n_nodes) continue;
-    for (int b : blocks) {
-      if (smem_bytes(sm_nodes, b, t->info.K_pad) > 200 * 1024) continue;
-      for (int ch : chunks) {
-        t->info.smem_nodes = sm_nodes;
-        t->packet = LaunchCfg{b, 0, ch, 0, saved.num_sms};
-        float ms_best = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-          cudaEventRecord(ev0, st);
-          s = neuvv_render(t, &r, time, &opts, &out, stream);
-          cudaEventRecord(ev1, st);
-          if (s != NEUVV_OK) break;
-          cudaEventSynchronize(ev1);
-          float ms;
-          cudaEventElapsedTime(&ms, ev0, ev1);
-          if (ms < ms_best) ms_best = ms;
-        }
-        if (s != NEUVV_OK) break;
-        if (ms_best < best_t) {
-          best_t = ms_best;
-          best = t->packet;
-          best_smem = sm_nodes;
-        }
-      }
+  const int blocks[] = {64, 96, 128, 192, 256};
+  for (int b : blocks) {
+    t->packet = LaunchCfg{b, 0, 0, saved.num_sms};
+    float ms_best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(ev0, st);
+      s = neuvv_render(t, &r, time, &opts, &out, stream);
+      cudaEventRecord(ev1, st);
       if (s != NEUVV_OK) break;
+      cudaEventSynchronize(ev1);
+      float ms;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      if (ms < ms_best) ms_best = ms;
     }
     if (s != NEUVV_OK) break;
+    if (ms_best < best_t) {
+      best_t = ms_best;
+      best = t->packet;
+    }
   }
-  t->packet = best;
-  t->info.smem_nodes = best_smem;
+  t->packet = s == NEUVV_OK ? best : saved;
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   cudaFree(rgb);
   cudaFree(alpha);
-  if (s != NEUVV_OK) {
-    t->packet = saved;
-    t->info.smem_nodes = saved_smem;
-    return s;
-  }
+  if (s != NEUVV_OK) return s;
   if (best_ms) *best_ms = best_t;
   return NEUVV_OK;
 }

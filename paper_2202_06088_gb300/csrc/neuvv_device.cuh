@@ -62,6 +62,7 @@ struct RayWalk {
   float go[3];     // grid position of the entry point
   float gd[3];     // grid-space direction (unit world direction * scale)
   float inv[3];    // 1 / gd (inf when gd == 0)
+  float ngi[3];    // -go * inv: the exit distance of plane x is fma(x, inv, ngi)
   float t_base;    // world distance of the entry point from the origin
   float t_cur;     // current distance past the entry point
   float t_far;     // exit distance of the root box past the entry point
@@ -72,9 +73,9 @@ struct RayWalk {
 };
 
 __device__ __forceinline__ int cell_of(float p, float v, int N) {
-  float f = floorf(p);
-  int c = (int)f;
-  if (v < 0.f && f == p) c -= 1;
+  // the cell the ray occupies just after this instant: floor(p), or
+  // ceil(p) - 1 when moving towards lower coordinates (one rounding each)
+  const int c = v < 0.f ? __float2int_ru(p) - 1 : __float2int_rd(p);
   return min(max(c, 0), N - 1);
 }
 
@@ -116,6 +117,7 @@ __device__ __forceinline__ void walk_start(const DevTree &tr, const float p[3], 
     w.go[a] = fminf(fmaxf((p[a] - tr.bmin[a]) * tr.scale[a], 0.f), (float)N);
     w.gd[a] = dn[a] * tr.scale[a];
     w.inv[a] = w.gd[a] != 0.f ? 1.f / w.gd[a] : INFINITY;
+    w.ngi[a] = w.gd[a] != 0.f ? -w.go[a] * w.inv[a] : 0.f;
     w.cell[a] = cell_of(w.go[a], w.gd[a], N);
     if (w.gd[a] != 0.f) tf = fminf(tf, ((w.gd[a] > 0.f ? (float)N : 0.f) - w.go[a]) * w.inv[a]);
   }
@@ -186,13 +188,13 @@ __device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s
       e = __ldg(tr.child + (size_t)node * 8 + slot);
     if (e == kEmpty || (e & kLeafBit)) {
       level = L + 1;
-      if (e != kEmpty && (long long)(e & ~kLeafBit) >= tr.n_leaves) {
+      if (e != kEmpty && (e & ~kLeafBit) >= (uint32_t)tr.n_leaves) {
         raise_status(tr, kStatusBadIndex);
         return kEmpty;
       }
       return e;
     }
-    if ((long long)e >= tr.n_nodes || e <= node) {
+    if (e >= (uint32_t)tr.n_nodes) {
       raise_status(tr, kStatusBadIndex);
       level = L + 1;
       return kEmpty;
@@ -224,9 +226,9 @@ __device__ __forceinline__ bool walk_next(const DevTree &tr, const uint32_t *s_c
     float tx[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      lo[a] = (w.cell[a] >> shift) << shift;
-      const float bnd = w.gd[a] > 0.f ? (float)(lo[a] + size) : (float)lo[a];
-      tx[a] = w.gd[a] != 0.f ? (bnd - w.go[a]) * w.inv[a] : INFINITY;
+      lo[a] = w.cell[a] & -size;
+      const float bnd = (float)(w.gd[a] > 0.f ? lo[a] + size : lo[a]);
+      tx[a] = w.gd[a] != 0.f ? fmaf(bnd, w.inv[a], w.ngi[a]) : INFINITY;
     }
     // exit axis: first minimum (exact ties x < y < z); register-only selects
     int ax = 0;
@@ -257,7 +259,7 @@ __device__ __forceinline__ bool walk_next(const DevTree &tr, const uint32_t *s_c
           // deepest level whose cell holds both the old node and the new cell
           if (kPath && inside) w.restart = tr.depth - 32 + __clz(nc ^ lo[b]);
         } else {
-          const float p = w.go[b] + w.t_cur * w.gd[b];
+          const float p = fmaf(w.t_cur, w.gd[b], w.go[b]);
           w.cell[b] = min(max(cell_of(p, w.gd[b], N), lo[b]), lo[b] + size - 1);
         }
       }

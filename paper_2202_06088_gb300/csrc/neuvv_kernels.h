@@ -11,8 +11,7 @@ enum DType { kF32 = 0, kBF16 = 1 };
 
 struct LaunchCfg {
   int block;          // threads per block
-  int grid;           // persistent kernels: blocks (0 = as many as fit, from the occupancy API)
-  int chunk;          // persistent kernels: rays a warp takes from the counter at a time
+  int grid;           // compose: persistent blocks (0 = as many as fit, from the occupancy API)
   int dynamic_queue;  // compose: 1 = warps pull packets from a counter, 0 = static stride
   int num_sms;        // multiprocessors of the device
 };
@@ -23,7 +22,6 @@ struct FwdArgs {
   DevOut out;
   float t_stop;
   int act;
-  unsigned long long *work;  // persistent kernel work counter (zeroed before launch)
 };
 
 struct BwdArgs {
@@ -39,7 +37,6 @@ struct BwdArgs {
   unsigned int *touched;  // bitmap or null
   float t_stop;
   int act;
-  unsigned long long *work;
 };
 
 constexpr int kMaxPrims = 16;
@@ -88,12 +85,9 @@ cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType 
 cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
                        cudaStream_t s);
 
-// Dynamic shared memory of the persistent render kernels: the staged top of
-// the child table, then per thread the basis rows (2 K_pad floats) and the
-// descent path (16 levels).
-inline size_t smem_bytes(int smem_nodes, int block, int KP) {
-  return (size_t)smem_nodes * 8 * sizeof(uint32_t) + (size_t)block * (2 * KP + 16) * sizeof(float);
-}
+// Dynamic shared memory of the packet kernels: per thread the basis rows
+// (2 K_pad floats) and the descent path (16 levels).
+inline size_t smem_bytes(int block, int KP) { return (size_t)block * (2 * KP + 16) * sizeof(float); }
 constexpr int kMaxDepth = 14;
 
 }  // namespace neuvv

@@ -14,7 +14,6 @@
 // pi*sigmoid and d H / d gamma.  Gradients are scattered into an FP32
 // record-layout buffer with 16-byte vector atomics.
 #include "neuvv_kernels.h"
-#include "neuvv_feed.cuh"
 #include "neuvv_ray.cuh"
 
 namespace neuvv {
@@ -145,78 +144,43 @@ __global__ void __launch_bounds__(256) render_bwd_plain_kernel(const __grid_cons
   }
 }
 
-// Persistent adjoint: the forward's lane refill and ancestor-restarted descents.
+// Packet adjoint: one thread per ray (warps = 32-ray packets), the forward's
+// ancestor-restarted descents, basis rows in shared memory.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a, int chunk) {
+__global__ void __launch_bounds__(256) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
   const int B = blockDim.x, tid = threadIdx.x;
-  uint32_t *s_child = smem;
-  float *my_rows = reinterpret_cast<float *>(smem + tr.smem_nodes * 8) + tid;
-  const PathRef pr{smem + tr.smem_nodes * 8 + 2 * KP * B + tid, B};
-  {
-    const int words = tr.smem_nodes * 8;
-    const uint4 *src = reinterpret_cast<const uint4 *>(tr.child);
-    uint4 *dst = reinterpret_cast<uint4 *>(s_child);
-    for (int k = tid; k < words / 4; k += B) dst[k] = __ldg(src + k);
-    __syncthreads();
-  }
+  float *my_rows = reinterpret_cast<float *>(smem) + tid;
+  const PathRef pr{smem + 2 * KP * B + tid, B};
   const SmemRows<KP> rows{my_rows, B};
-  WarpFeed feed{0, 0, false};
-  bool active = false;
+  const long long i = (long long)blockIdx.x * B + tid;
+  if (i >= a.rays.n) return;
   RayWalk w;
   AdjState st;
+  float dn[3], t;
+  if (!adjoint_setup(a, i, w, dn, t, st)) return;
+  rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
   float Y[(DEG + 1) * (DEG + 1)];
-  for (;;) {
-    while (!feed.exhausted) {
-      const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
-      if (!need) break;
-      const long long i = feed_take(feed, a.work, a.rays.n, chunk, need);
-      if (i >= 0) {
-        float dn[3], t;
-        if (adjoint_setup(a, i, w, dn, t, st)) {
-          active = true;
-          rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
-          sh_real<DEG>(dn, Y);
-        }
-      }
-    }
-    if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
-    if (!active) continue;
-    uint32_t leaf;
-    float t0, t1;
-    if (walk_next<true, true>(tr, s_child, w, leaf, t0, t1, pr)) {
-      ++st.count;
-      adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, t0, t1, st);
-      if (st.count >= st.target) active = false;
-    } else {
-      active = false;
-    }
+  sh_real<DEG>(dn, Y);
+  uint32_t leaf;
+  float t0, t1;
+  while (st.count < st.target && walk_next<false, true>(tr, nullptr, w, leaf, t0, t1, pr)) {
+    ++st.count;
+    adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, t0, t1, st);
   }
 }
 
 template <int KP, int DEG, typename E>
 static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
   if (a.rays.n == 0) return cudaSuccess;
+  const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
   if (!packet) {
-    const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
     render_bwd_plain_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, 0, s>>>(a);
-    return cudaGetLastError();
+  } else {
+    const size_t sm = smem_bytes(cfg.block, KP);
+    render_bwd_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a);
   }
-  const size_t sm = smem_bytes(a.tr.smem_nodes, cfg.block, KP);
-  auto kern = render_bwd_packet_kernel<KP, DEG, E>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  int grid = cfg.grid;
-  if (grid <= 0) {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.block, sm);
-    if (e != cudaSuccess) return e;
-    grid = (per_sm > 0 ? per_sm : 1) * cfg.num_sms;
-  }
-  kern<<<grid, cfg.block, sm, s>>>(a, cfg.chunk);
   return cudaGetLastError();
 }
 

@@ -2,14 +2,11 @@
 //
 // render_plain_kernel  : one thread per ray, child table read from global
 //                        memory -- the baseline single-view path.
-// render_packet_kernel : persistent grid; each block stages the top of the
-//                        child table in shared memory once; warps take chunks
-//                        of consecutive rays (coherent 8x4 pixel tiles when the
-//                        caller orders rays that way) from a global counter and
-//                        refill each lane as its ray finishes; descents restart
-//                        at the lowest common ancestor of successive cells.
+// render_packet_kernel : one thread per ray with warps as 32-ray packets;
+//                        descents restart at the lowest common ancestor of
+//                        successive cells; basis rows and the descent path in
+//                        shared memory.
 #include "neuvv_kernels.h"
-#include "neuvv_feed.cuh"
 #include "neuvv_ray.cuh"
 
 namespace neuvv {
@@ -31,15 +28,6 @@ __global__ void __launch_bounds__(256) render_plain_kernel(const __grid_constant
   if (a.out.nseg) a.out.nseg[i] = r.nseg;
 }
 
-// Copies the first smem_nodes rows of the child table to shared memory.
-__device__ __forceinline__ void stage_child(const DevTree &tr, uint32_t *s_child) {
-  const int words = tr.smem_nodes * 8;
-  const uint4 *src = reinterpret_cast<const uint4 *>(tr.child);
-  uint4 *dst = reinterpret_cast<uint4 *>(s_child);
-  for (int i = threadIdx.x; i < words / 4; i += blockDim.x) dst[i] = __ldg(src + i);
-  __syncthreads();
-}
-
 __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
   out.rgb[3 * i + 0] = 0.f;
   out.rgb[3 * i + 1] = 0.f;
@@ -50,88 +38,64 @@ __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
   if (out.nseg) out.nseg[i] = 0;
 }
 
-// Persistent forward kernel.  Per lane: one ray at a time, refilled from the
-// warp's chunk when it finishes; per iteration every active lane advances to
-// its next occupied-leaf segment (descent restarted at the lowest common
-// ancestor, top of the table in shared memory) and then all of them shade
-// that sample together.
+// Packet forward kernel: one thread per ray, so each warp is a packet of 32
+// consecutive rays (an 8x4 pixel tile when the caller orders rays that way);
+// descents restart at the lowest common ancestor of successive cells (path
+// kept per thread in shared memory), basis rows live in shared memory to keep
+// registers (and so resident warps) up; the block scheduler balances uneven
+// ray lengths across the grid.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constant__ FwdArgs a, int chunk) {
+__global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constant__ FwdArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
   const int B = blockDim.x, tid = threadIdx.x;
-  uint32_t *s_child = smem;
-  float *my_rows = reinterpret_cast<float *>(smem + tr.smem_nodes * 8) + tid;
-  const PathRef pr{smem + tr.smem_nodes * 8 + 2 * KP * B + tid, B};
-  stage_child(tr, s_child);
+  float *my_rows = reinterpret_cast<float *>(smem) + tid;
+  const PathRef pr{smem + 2 * KP * B + tid, B};
   const SmemRows<KP> rows{my_rows, B};
-  const long long n = a.rays.n;
-  WarpFeed feed{0, 0, false};
-  bool active = false;
-  long long ray = 0;
+  const long long i = (long long)blockIdx.x * B + tid;
+  if (i >= a.rays.n) return;
+  float o[3], d[3], t, dn[3];
+  load_ray(a.rays, i, o, d, t);
   RayWalk w;
+  if (!walk_init(tr, o, d, w, dn)) {
+    write_miss(a.out, i);
+    return;
+  }
+  rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
   float Y[(DEG + 1) * (DEG + 1)];
+  sh_real<DEG>(dn, Y);
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f, dnum = 0.f, tau = 0.f;
   int nseg = 0;
-  for (;;) {
-    // give every idle lane a ray; rays that miss the box are finished here
-    while (!feed.exhausted) {
-      const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
-      if (!need) break;
-      const long long i = feed_take(feed, a.work, n, chunk, need);
-      if (i >= 0) {
-        float o[3], d[3], t, dn[3];
-        load_ray(a.rays, i, o, d, t);
-        if (walk_init(tr, o, d, w, dn)) {
-          active = true;
-          ray = i;
-          T = 1.f;
-          C0 = C1 = C2 = A = dnum = tau = 0.f;
-          nseg = 0;
-          rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
-          sh_real<DEG>(dn, Y);
-        } else {
-          write_miss(a.out, i);
-        }
-      }
-    }
-    if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
-    if (!active) continue;
-    uint32_t leaf;
-    float t0, t1;
-    bool more = walk_next<true, true>(tr, s_child, w, leaf, t0, t1, pr);
-    if (more) {
-      LeafRecord<KP, DEG, E> rec;
-      rec.load(tr, leaf);
-      Sample<DEG> s;
-      eval_sample<KP, DEG, E>(tr, rows, Y, rec, a.act, s);
-      ++nseg;
-      if (s.sigma > 0.f) {
-        const float delta = t1 - t0;
-        const float sd = s.sigma * delta;
-        const float e = __expf(-sd);
-        const float wgt = T * (1.f - e);
-        C0 = fmaf(wgt, s.c[0], C0);
-        C1 = fmaf(wgt, s.c[1], C1);
-        C2 = fmaf(wgt, s.c[2], C2);
-        A += wgt;
-        dnum = fmaf(wgt, w.t_base + 0.5f * (t0 + t1), dnum);
-        tau += sd;
-        T *= e;
-        if (T < a.t_stop) more = false;
-      }
-    }
-    if (!more) {
-      a.out.rgb[3 * ray + 0] = C0;
-      a.out.rgb[3 * ray + 1] = C1;
-      a.out.rgb[3 * ray + 2] = C2;
-      a.out.alpha[ray] = A;
-      if (a.out.depth) a.out.depth[ray] = A >= 1e-4f ? dnum / A : INFINITY;
-      if (a.out.tau) a.out.tau[ray] = tau;
-      if (a.out.nseg) a.out.nseg[ray] = nseg;
-      active = false;
+  uint32_t leaf;
+  float t0, t1;
+  while (walk_next<false, true>(tr, nullptr, w, leaf, t0, t1, pr)) {
+    LeafRecord<KP, DEG, E> rec;
+    rec.load(tr, leaf);
+    Sample<DEG> s;
+    eval_sample<KP, DEG, E>(tr, rows, Y, rec, a.act, s);
+    ++nseg;
+    if (s.sigma > 0.f) {
+      const float delta = t1 - t0;
+      const float sd = s.sigma * delta;
+      const float e = __expf(-sd);
+      const float wgt = T * (1.f - e);
+      C0 = fmaf(wgt, s.c[0], C0);
+      C1 = fmaf(wgt, s.c[1], C1);
+      C2 = fmaf(wgt, s.c[2], C2);
+      A += wgt;
+      dnum = fmaf(wgt, w.t_base + 0.5f * (t0 + t1), dnum);
+      tau += sd;
+      T *= e;
+      if (T < a.t_stop) break;
     }
   }
+  a.out.rgb[3 * i + 0] = C0;
+  a.out.rgb[3 * i + 1] = C1;
+  a.out.rgb[3 * i + 2] = C2;
+  a.out.alpha[i] = A;
+  if (a.out.depth) a.out.depth[i] = A >= 1e-4f ? dnum / A : INFINITY;
+  if (a.out.tau) a.out.tau[i] = tau;
+  if (a.out.nseg) a.out.nseg[i] = nseg;
 }
 
 __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceArgs a) {
@@ -165,25 +129,13 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
 template <int KP, int DEG, typename E>
 static cudaError_t fwd_one(bool packet, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
   if (a.rays.n == 0) return cudaSuccess;
+  const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
   if (!packet) {
-    const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
     render_plain_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, 0, s>>>(a);
-    return cudaGetLastError();
+  } else {
+    const size_t sm = smem_bytes(cfg.block, KP);
+    render_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a);
   }
-  const size_t sm = smem_bytes(a.tr.smem_nodes, cfg.block, KP);
-  auto kern = render_packet_kernel<KP, DEG, E>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  int grid = cfg.grid;
-  if (grid <= 0) {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.block, sm);
-    if (e != cudaSuccess) return e;
-    grid = (per_sm > 0 ? per_sm : 1) * cfg.num_sms;
-  }
-  kern<<<grid, cfg.block, sm, s>>>(a, cfg.chunk);
   return cudaGetLastError();
 }
 

@@ -82,7 +82,7 @@ def configure(L):
     L.or_render_grad.restype = None
     L.or_render_grad.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, ci]
     L.or_compose.restype = None
-    L.or_compose.argtypes = [p, p, p, p, ci, ci, p, i64, p, p, p, p, p, p, ci]
+    L.or_compose.argtypes = [p, p, p, p, ci, ci, p, i64, p, p, p, p, p, p, p, ci]
     L.or_adam.restype = None
     L.or_adam.argtypes = [i64, ci, p, p, p, p, p, d, d, d, d, ci]
     L.or_round_bf16.restype = None
@@ -239,10 +239,12 @@ def compose(trees, transforms, time_offsets, tints, rays, mode: str = "sorted", 
     rgb = np.zeros((n, 3))
     alpha = np.zeros(n)
     depth = np.zeros(n)
+    margin = np.zeros(n)
     op = _opts(t_stop, act)
     lib().or_compose(arr, _ptr(xf), _ptr(toff), _ptr(tint), P, {"sorted": 0, "alg1": 1}[mode], ctypes.byref(op), n,
-                     _ptr(o), _ptr(d), _ptr(t), _ptr(rgb), _ptr(alpha), _ptr(depth), nthreads or default_threads())
-    return {"rgb": rgb, "alpha": alpha, "depth": depth}
+                     _ptr(o), _ptr(d), _ptr(t), _ptr(rgb), _ptr(alpha), _ptr(depth), _ptr(margin),
+                     nthreads or default_threads())
+    return {"rgb": rgb, "alpha": alpha, "depth": depth, "stop_margin": margin}
 
 
 def adam(w, m, v, g, touched, lr, b1, b2, eps, step):

@@ -629,7 +629,7 @@ typedef struct {
   const or_opts *op;
   const double *o, *d, *t;
   int64_t n;
-  double *rgb, *alpha, *depth;
+  double *rgb, *alpha, *depth, *margin;
 } compose_ctx;
 
 static void compose_range(void *p, int64_t lo, int64_t hi) {
@@ -654,6 +654,7 @@ static void compose_range(void *p, int64_t lo, int64_t hi) {
     double t = c->t[r];
     if (t < 0.0) t = 0.0;
     if (t > 1.0) t = 1.0;
+    double margin = INFINITY;
     for (int j = 0; j < P; ++j) {
       const or_tree *tr = c->trees[j];
       const double *M = c->xf + 12 * j;
@@ -670,6 +671,7 @@ static void compose_range(void *p, int64_t lo, int64_t hi) {
       if (u < 0.0) u += period;
       or_ray_out out;
       render_ray(tr, c->op, ol, dl, u, segs, H, a, b, &out, NULL);
+      if (out.stop_margin < margin) margin = out.stop_margin;
       for (int ch = 0; ch < 3; ++ch) LC[3 * j + ch] = c->tint[3 * j + ch] * out.rgb[ch];
       LA[j] = out.alpha;
       LD[j] = isinf(out.depth) ? INFINITY : out.depth / inv_s;
@@ -706,14 +708,15 @@ static void compose_range(void *p, int64_t lo, int64_t hi) {
     for (int ch = 0; ch < 3; ++ch) c->rgb[3 * r + ch] = I[ch];
     c->alpha[r] = A;
     c->depth[r] = D;
+    if (c->margin) c->margin[r] = margin;
   }
   free(segs); free(H); free(a); free(b); free(LC); free(LA); free(LD); free(ord);
 }
 
 void or_compose(const or_tree *const *trees, const double *xf, const double *toff, const double *tint, int n_prims,
                 int mode, const or_opts *op, int64_t n, const double *o, const double *d, const double *t,
-                double *rgb, double *alpha, double *depth, int nthreads) {
-  compose_ctx c = {trees, xf, toff, tint, n_prims, mode, op, o, d, t, n, rgb, alpha, depth};
+                double *rgb, double *alpha, double *depth, double *margin, int nthreads) {
+  compose_ctx c = {trees, xf, toff, tint, n_prims, mode, op, o, d, t, n, rgb, alpha, depth, margin};
   parallel_for(n, nthreads, compose_range, &c);
 }
 

@@ -41,12 +41,16 @@ def test_compose_matches_oracle(B, scene, mode, dtype):
     got = B.neuvv_compose([tree_d] * 8, xf, off, tint, dr, mode=mode)
     got = {k: got[k].cpu().numpy() for k in ("rgb", "alpha", "depth")}
     assert (ref["alpha"] > 0.01).mean() > 0.05       # the duplicates are in view
-    err = np.abs(got["rgb"] - ref["rgb"])
+    # pixels where a layer's early-stop decision sits at the threshold are
+    # exempt (as in the render tests)
+    ok = ref["stop_margin"] > 1e-3
+    assert ok.mean() > 0.99
+    err = np.abs(got["rgb"] - ref["rgb"])[ok]
     # a pixel where two layers' depths coincide within float32 error may blend
     # them in the other order: allow at most 0.1% of pixels outside 1e-4
     bad = err.max(1) > 1e-4
     assert bad.mean() <= 1e-3, (bad.sum(), err.max())
-    assert np.abs(got["alpha"] - ref["alpha"]).max() <= 1e-4
+    assert np.abs(got["alpha"] - ref["alpha"])[ok].max() <= 1e-4
     fin = np.isfinite(ref["depth"])
     assert np.array_equal(fin, np.isfinite(got["depth"]))
     assert np.abs(got["depth"][fin] - ref["depth"][fin]).max() <= 1e-3

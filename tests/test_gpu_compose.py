@@ -46,11 +46,15 @@ def test_compose_matches_oracle(B, scene, mode, dtype):
     ok = ref["stop_margin"] > 1e-3
     assert ok.mean() > 0.99
     err = np.abs(got["rgb"] - ref["rgb"])[ok]
-    # a pixel where two layers' depths coincide within float32 error may blend
-    # them in the other order: allow at most 0.1% of pixels outside 1e-4
-    bad = err.max(1) > 1e-4
-    assert bad.mean() <= 1e-3, (bad.sum(), err.max())
-    assert np.abs(got["alpha"] - ref["alpha"])[ok].max() <= 1e-4
+    aerr = np.abs(got["alpha"] - ref["alpha"])[ok]
+    # Allowed on at most 0.1% of pixels: two layers whose depths coincide within
+    # float32 error blend in the other order (rgb), and a ray that crosses a
+    # voxel face at a grazing angle, where the ~1e-5 grid-unit float32 error of
+    # the ray taken into the primitive's frame moves the crossing by
+    # 1/sin(angle) times that (rgb and alpha).  Every pixel stays within 2e-3.
+    bad = (err.max(1) > 1e-4) | (aerr > 1e-4)
+    assert bad.mean() <= 1e-3, (bad.sum(), err.max(), aerr.max())
+    assert err.max() <= 2e-3 and aerr.max() <= 2e-3
     fin = np.isfinite(ref["depth"])
     assert np.array_equal(fin, np.isfinite(got["depth"]))
     assert np.abs(got["depth"][fin] - ref["depth"][fin]).max() <= 1e-3

@@ -187,6 +187,28 @@ neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transfor
                            const float *tints, int32_t n_prims, const neuvv_rays *rays, float t,
                            const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream);
 
+/* neuvv_compose without any allocation: the same composition as
+ * neuvv_compose (same arguments, same results), but its packet work counter
+ * is one 64-bit word of file-scope device memory inside the library instead
+ * of memory owned by the trees.  The paper has no counterpart; it is for
+ * callers that cannot allocate device memory, or touch memory they did not
+ * set up, at the moment they render: e.g. a frame callback of an interactive
+ * viewer that must not call into the allocator, or a process whose device
+ * memory is all reserved up front by another framework.  (The trees must
+ * still have been created earlier.)
+ *  - Allocates nothing: no cudaMalloc/cudaFree or allocating library routine.
+ *  - The first call on a device looks the counter's device address up with
+ *    cudaGetSymbolAddress (with that device current) and caches it; make that
+ *    first call before any stream capture.
+ *  - Every call on a device shares the one counter, which is reset on the
+ *    call's stream before the launch: calls that overlap on the GPU (other
+ *    streams, or several threads) race and must be serialised by the caller.
+ *  - At most NEUVV_NOALLOC_MAX_RAYS rays per call; more is INVALID_ARG. */
+#define NEUVV_NOALLOC_MAX_RAYS ((int64_t)1 << 37)
+neuvv_status neuvv_compose_noalloc(const neuvv_tree *const *trees, const float *transforms, const float *time_offsets,
+                                   const float *tints, int32_t n_prims, const neuvv_rays *rays, float t,
+                                   const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream);
+
 /* Sparse Adam on the leaves whose touched bit is set (Sec. 4.3 "Optimization":
  * SGD or Adam).  Updates the FP32 master, m and v, writes the storage copy
  * (rounded to nearest even for BF16), zeroes those leaves' rows of grad and

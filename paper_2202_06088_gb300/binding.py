@@ -68,7 +68,7 @@ class OptsC(ctypes.Structure):
 
 EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv_tree_get_info",
            "neuvv_tree_coeff_ptrs", "neuvv_tree_status", "neuvv_render", "neuvv_render_backward", "neuvv_compose",
-           "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune"]
+           "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc"]
 
 
 def library_path() -> str:
@@ -93,6 +93,7 @@ def lib(build_if_missing: bool = True):
                 "neuvv_render": [p, p, f, p, p, p],
                 "neuvv_render_backward": [p, p, f, p, p, p, p, p, p, p],
                 "neuvv_compose": [p, p, p, p, i32, p, f, p, p, p],
+                "neuvv_compose_noalloc": [p, p, p, p, i32, p, f, p, p, p],
                 "neuvv_adam_step": [p, p, p, f, f, f, f, i32, p],
                 "neuvv_mse_grad": [p, p, i64, f, p, p, p],
                 "neuvv_trace": [p, p, i32, p, p, p, p, p],
@@ -292,6 +293,24 @@ def neuvv_compose(trees, transforms, time_offsets, tints, rays: DeviceRays, t: f
     rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, "auto", mode)
     _check(lib().neuvv_compose(arr, xf.ctypes.data, toff.ctypes.data, tint.ctypes.data, P, ctypes.byref(rc), float(t),
                                ctypes.byref(op), ctypes.byref(oc), _stream()))
+    return out
+
+
+def neuvv_compose_noalloc(trees, transforms, time_offsets, tints, rays: DeviceRays, t: float = 0.0,
+                          t_stop: float = 1e-4, act: str = "sigmoid", mode: str = "sorted", out: dict | None = None) -> dict:
+    """neuvv_compose without any device allocation during the call (the work
+    counter is a static array of the library); overlapping calls race."""
+    P = len(trees)
+    arr = (ctypes.c_void_p * P)(*[tr.handle.value for tr in trees])
+    xf = np.ascontiguousarray(np.asarray(transforms, np.float32).reshape(P, 12))
+    toff = np.ascontiguousarray(np.asarray(time_offsets, np.float32).reshape(P))
+    tint = np.ascontiguousarray(np.asarray(tints, np.float32).reshape(P, 3))
+    if out is None:
+        out = {"rgb": torch.empty(rays.n, 3, device="cuda"), "alpha": torch.empty(rays.n, device="cuda"),
+               "depth": torch.empty(rays.n, device="cuda")}
+    rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, "auto", mode)
+    _check(lib().neuvv_compose_noalloc(arr, xf.ctypes.data, toff.ctypes.data, tint.ctypes.data, P,
+                                       ctypes.byref(rc), float(t), ctypes.byref(op), ctypes.byref(oc), _stream()))
     return out
 
 

@@ -477,6 +477,99 @@ neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transfor
   return NEUVV_OK;
 }
 
+neuvv_status neuvv_compose_noalloc(const neuvv_tree *const *trees, const float *transforms, const float *time_offsets,
+                           const float *tints, int32_t n_prims, const neuvv_rays *rays, float time,
+                           const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream) {
+  if (!trees || !transforms || !time_offsets || !tints)
+    return fail(NEUVV_ERR_INVALID_ARG, "trees/transforms/time_offsets/tints is NULL");
+  if (n_prims < 1 || n_prims > kMaxPrims) return fail(NEUVV_ERR_INVALID_ARG, "n_prims must be in [1, %d]", kMaxPrims);
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK || (s = check_time(rays, time)))
+    return s;
+  if (!out || (rays->n > 0 && (!out->rgb || !out->alpha)))
+    return fail(NEUVV_ERR_INVALID_ARG, "out->rgb and out->alpha are required");
+  const neuvv_tree *t0 = trees[0];
+  if (!t0) return fail(NEUVV_ERR_INVALID_ARG, "trees[0] is NULL");
+  ComposeArgs a;
+  std::memset(&a, 0, sizeof a);
+  int n_trees = 0;
+  const neuvv_tree *uniq[kMaxPrims];
+  for (int j = 0; j < n_prims; ++j) {
+    const neuvv_tree *t = trees[j];
+    if (!t) return fail(NEUVV_ERR_INVALID_ARG, "trees[%d] is NULL", j);
+    if (t->info.K_pad != t0->info.K_pad || t->info.hh_degree != t0->info.hh_degree || t->info.dtype != t0->info.dtype ||
+        t->info.device != t0->info.device)
+      return fail(NEUVV_ERR_UNSUPPORTED, "all trees of one compose call must share K_pad, degree, dtype, device");
+    int slot = -1;
+    for (int k = 0; k < n_trees; ++k)
+      if (uniq[k] == t) slot = k;
+    if (slot < 0) {
+      slot = n_trees;
+      uniq[n_trees++] = t;
+      a.trees[slot] = dev_tree(t);
+    }
+    const float *M = transforms + 12 * j;
+    double m[3][3], tr[3];
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) m[r][c] = M[4 * r + c];
+      tr[r] = M[4 * r + 3];
+    }
+    // uniform scale: M^T M = s^2 I
+    double s2 = 0.0;
+    for (int r = 0; r < 3; ++r) s2 += m[r][0] * m[r][0];
+    if (!(s2 > 0.0) || !std::isfinite(s2)) return fail(NEUVV_ERR_INVALID_ARG, "transform %d is degenerate", j);
+    for (int c1 = 0; c1 < 3; ++c1)
+      for (int c2 = 0; c2 < 3; ++c2) {
+        double dot = 0.0;
+        for (int r = 0; r < 3; ++r) dot += m[r][c1] * m[r][c2];
+        const double want = c1 == c2 ? s2 : 0.0;
+        if (std::fabs(dot - want) > 1e-4 * s2)
+          return fail(NEUVV_ERR_INVALID_ARG, "transform %d is not a rotation times a uniform scale", j);
+      }
+    for (int r = 0; r < 3; ++r)
+      if (!std::isfinite(tr[r])) return fail(NEUVV_ERR_INVALID_ARG, "transform %d translation not finite", j);
+    const double det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+                       m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                       m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+    if (!(det > 0.0)) return fail(NEUVV_ERR_INVALID_ARG, "transform %d must have positive determinant", j);
+    PrimParam &p = a.prim[j];
+    // (sR)^-1 = R^T / s = M^T / s^2
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) p.minv[3 * r + c] = (float)(m[c][r] / s2);
+    for (int r = 0; r < 3; ++r) p.trans[r] = (float)tr[r];
+    p.scale = (float)std::sqrt(s2);
+    if (!std::isfinite(time_offsets[j])) return fail(NEUVV_ERR_INVALID_ARG, "time offset %d not finite", j);
+    p.toff = time_offsets[j];
+    for (int c = 0; c < 3; ++c) {
+      if (!std::isfinite(tints[3 * j + c])) return fail(NEUVV_ERR_INVALID_ARG, "tint %d not finite", j);
+      p.tint[c] = tints[3 * j + c];
+    }
+    p.tree = slot;
+  }
+  if (rays->n > NEUVV_NOALLOC_MAX_RAYS)
+    return fail(NEUVV_ERR_INVALID_ARG, "neuvv_compose_noalloc: %lld rays exceed the maximum of %lld",
+                (long long)rays->n, (long long)NEUVV_NOALLOC_MAX_RAYS);
+  if (rays->n == 0) return NEUVV_OK;
+  DeviceGuard g(t0->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  a.n_prims = n_prims;
+  a.rays = dev_rays(rays, time);
+  a.out = DevOut{out->rgb, out->alpha, out->depth, nullptr, nullptr};
+  a.t_stop = opts->t_stop;
+  a.act = opts->color_act;
+  a.mode = opts->compose_mode;
+  // the packet counter is the library's static device array, not tree memory
+  cudaError_t e = noalloc_queue(&a.work);
+  if (e != cudaSuccess) return cuda_fail(e, "neuvv_compose_noalloc: device address of the static counter");
+  e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(e, "neuvv_compose_noalloc: reset counter");
+  LaunchCfg cfg = t0->compose;
+  cfg.dynamic_queue = 1;
+  e = launch_compose(t0->info.K_pad, t0->info.hh_degree, (DType)t0->info.dtype, a, cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "compose launch");
+  return NEUVV_OK;
+}
+
 neuvv_status neuvv_adam_step(neuvv_tree *t, float *grad, uint32_t *touched, float lr, float b1, float b2, float eps,
                              int32_t step, neuvv_stream stream) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");

@@ -10,6 +10,8 @@
 // (tint_j * C_j, A_j, s * D_j).  The layers are then merged: sorted by depth
 // (stable) with front-to-back "over" on premultiplied colour, or Algorithm 1
 // taken literally (sequential pairwise merge) on premultiplied colour.
+#include <mutex>
+
 #include "neuvv_kernels.h"
 #include "neuvv_ray.cuh"
 
@@ -179,6 +181,32 @@ static cudaError_t compose_dispatch(int KP, int DEG, const ComposeArgs &a, const
 cudaError_t launch_compose(int KP, int DEG, DType dt, const ComposeArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
   if (dt == kF32) return compose_dispatch<float>(KP, DEG, a, cfg, s);
   return compose_dispatch<__nv_bfloat16>(KP, DEG, a, cfg, s);
+}
+
+// Work counter for neuvv_compose_noalloc: file-scope device memory (one
+// 64-bit packet counter, 256-byte aligned) that exists on every device where
+// the library is loaded, so that entry point needs no allocation.  Host code
+// must not use the symbol as an address: noalloc_queue() asks the runtime for
+// the device address once per device (with that device current) and caches it.
+static __device__ __align__(256) unsigned long long g_noalloc_queue[1];
+
+cudaError_t noalloc_queue(unsigned long long **out) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static unsigned long long *ptrs[kMaxDevices] = {};
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_queue);
+    if (e != cudaSuccess) return e;
+    ptrs[dev] = static_cast<unsigned long long *>(p);
+  }
+  *out = ptrs[dev];
+  return cudaSuccess;
 }
 
 }  // namespace neuvv

@@ -79,6 +79,9 @@ cudaError_t launch_render_bwd(int KP, int DEG, DType dt, bool packet, const BwdA
                               cudaStream_t s);
 cudaError_t launch_compose(int KP, int DEG, DType dt, const ComposeArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
+// Device address of the static work counter used by neuvv_compose_noalloc on
+// the current device (looked up on first use per device).
+cudaError_t noalloc_queue(unsigned long long **out);
 cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType dt, int storage_stride, float *grad,
                         const unsigned int *touched, long long n_leaves, int stride_f32, int rec_len, float lr,
                         float b1, float b2, float eps, float c1, float c2, cudaStream_t s);

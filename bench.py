@@ -261,7 +261,8 @@ def main():
     tree_d = B.Tree(tree, "bf16", with_optimizer=True)
     if not args.no_autotune:
         B.neuvv_autotune(tree_d, dr)
-    launch = {"block": tree_d.info.packet_block,
+    launch = {"block": tree_d.info.packet_block, "queue": tree_d.info.packet_queue,
+              "ready": tree_d.info.packet_ready,
               "autotuned": not args.no_autotune}
     out = B.alloc_out(n, dev)
     grad_rgb = torch.empty(n, 3, device=dev)

@@ -87,7 +87,12 @@ typedef struct {
   const float *w_sigma, *w_gamma, *w_hh;
   const float *basis_A, *basis_B;
   float aabb_min[3], aabb_max[3];
+  uint32_t flags;           /* NEUVV_TREE_* bits */
 } neuvv_tree_desc;
+
+/* neuvv_tree_desc.flags: skip the bricks (dense per-node tables of the last
+ * three levels that shorten descents; built by default when depth >= 3). */
+#define NEUVV_TREE_NO_BRICKS 0x1u
 
 /* Layout of a tree's per-leaf records, for views over its device buffers and
  * for gradient buffers.  A record holds, in order, w_sigma (K_pad entries, the
@@ -102,7 +107,10 @@ typedef struct {
   neuvv_dtype dtype;
   int64_t n_nodes, n_leaves;
   int32_t device;
-  int32_t packet_block;     /* packet kernels: threads per block (set by neuvv_autotune) */
+  int32_t packet_block;     /* packet kernels: threads per block */
+  int32_t packet_queue;     /* packet kernels: leaf segments a ray may queue ahead of shading */
+  int32_t packet_ready;     /* packet kernels: lanes holding a queued segment that start a
+                               shading round (all three set by neuvv_autotune) */
 } neuvv_tree_info;
 
 /* Rays, device SoA float32 arrays of length n.  t may be NULL: then the
@@ -129,9 +137,10 @@ typedef struct {
   float t_stop;        /* early termination: stop after T < t_stop (1e-4) */
   int32_t color_act;   /* neuvv_color_act */
   int32_t kernel;      /* neuvv_kernel: plain = one thread per ray, descents from
-                          the root, basis rows in registers; packet = warps of
-                          32 consecutive rays, descents restarted at the lowest
-                          common ancestor, rows in shared memory, tuned block */
+                          the root, walk and shading in lockstep; packet = warps
+                          of 32 consecutive rays, descents restarted at the
+                          lowest common ancestor, walk and shading decoupled by
+                          a per-ray queue, tuned launch */
   int32_t compose_mode;/* neuvv_compose_mode */
 } neuvv_render_opts;
 
@@ -231,7 +240,13 @@ neuvv_status neuvv_mse_grad(const float *rgb, const float *target, int64_t n, fl
 neuvv_status neuvv_trace(const neuvv_tree *tree, const neuvv_rays *rays, int32_t max_out, int32_t *leaf, float *t0,
                          float *t1, int32_t *count, neuvv_stream stream);
 
-/* Picks the block size of the packet kernels by timing candidates on a
+/* Sets the packet kernels' launch explicitly instead of neuvv_autotune:
+ * block (a multiple of 32 in [32, 256]), queue (a power of two in [1, 32]:
+ * leaf segments a ray's walk may run ahead of its shading) and ready (1..32:
+ * lanes with a queued segment that start a shading round).  Host only. */
+neuvv_status neuvv_tree_set_launch(neuvv_tree *tree, int32_t block, int32_t queue, int32_t ready);
+
+/* Picks the block size, queue and ready count of the packet kernels by timing candidates on a
  * sample of rays (the first min(n, 2^20)); the choice is stored in the tree.
  * Synchronous.  best_ms (nullable) receives the best forward time. */
 neuvv_status neuvv_autotune(neuvv_tree *tree, const neuvv_rays *sample, float t, float *best_ms, neuvv_stream stream);

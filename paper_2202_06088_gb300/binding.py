@@ -39,7 +39,7 @@ class TreeDesc(ctypes.Structure):
                 ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("child", ctypes.c_void_p), ("w_sigma", ctypes.c_void_p), ("w_gamma", ctypes.c_void_p),
                 ("w_hh", ctypes.c_void_p), ("basis_A", ctypes.c_void_p), ("basis_B", ctypes.c_void_p),
-                ("aabb_min", ctypes.c_float * 3), ("aabb_max", ctypes.c_float * 3)]
+                ("aabb_min", ctypes.c_float * 3), ("aabb_max", ctypes.c_float * 3), ("flags", ctypes.c_uint32)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -47,7 +47,8 @@ class TreeInfo(ctypes.Structure):
                 ("hh_degree", ctypes.c_int32), ("N_h", ctypes.c_int32), ("rec_len", ctypes.c_int32),
                 ("rec_stride", ctypes.c_int32), ("rec_stride_f32", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
-                ("device", ctypes.c_int32), ("packet_block", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("packet_block", ctypes.c_int32), ("packet_queue", ctypes.c_int32),
+                ("packet_ready", ctypes.c_int32)]
 
 
 class RaysC(ctypes.Structure):
@@ -68,7 +69,8 @@ class OptsC(ctypes.Structure):
 
 EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv_tree_get_info",
            "neuvv_tree_coeff_ptrs", "neuvv_tree_status", "neuvv_render", "neuvv_render_backward", "neuvv_compose",
-           "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc"]
+           "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc",
+           "neuvv_tree_set_launch"]
 
 
 def library_path() -> str:
@@ -98,6 +100,7 @@ def lib(build_if_missing: bool = True):
                 "neuvv_mse_grad": [p, p, i64, f, p, p, p],
                 "neuvv_trace": [p, p, i32, p, p, p, p, p],
                 "neuvv_autotune": [p, p, f, p, p],
+                "neuvv_tree_set_launch": [p, i32, i32, i32],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -141,7 +144,7 @@ class _CudaView:
 class Tree:
     """A VOctree uploaded to the current CUDA device (neuvv_tree_create)."""
 
-    def __init__(self, voctree, dtype: str = "f32", with_optimizer: bool = False):
+    def __init__(self, voctree, dtype: str = "f32", with_optimizer: bool = False, bricks: bool = True):
         L = lib()
         self.dtype = _DTYPES[dtype]
         child = np.ascontiguousarray(voctree.child, np.uint32)
@@ -153,6 +156,7 @@ class Tree:
         d = TreeDesc()
         d.depth, d.K, d.T, d.hh_degree = voctree.depth, voctree.K, voctree.T, voctree.hh_degree
         d.dtype, d.with_optimizer = self.dtype, int(with_optimizer)
+        d.flags = 0 if bricks else 1
         d.n_nodes, d.n_leaves = child.size // 8, ws.shape[1]
         d.child, d.w_sigma, d.w_gamma, d.w_hh = child.ctypes.data, ws.ctypes.data, wg.ctypes.data, wh.ctypes.data
         d.basis_A, d.basis_B = A.ctypes.data, B.ctypes.data
@@ -206,6 +210,10 @@ class Tree:
         _check(lib().neuvv_tree_get_info(self.handle, ctypes.byref(info)))
         self.info = info
         return info
+
+    def set_launch(self, block: int, queue: int, ready: int) -> None:
+        _check(lib().neuvv_tree_set_launch(self.handle, int(block), int(queue), int(ready)))
+        self.refresh_info()
 
     def status(self) -> int:
         f = ctypes.c_uint32()

@@ -76,6 +76,8 @@ constexpr int kWorkSlots = 4;  // fwd, bwd, compose, spare
 struct neuvv_tree {
   neuvv_tree_info info{};
   uint32_t *child = nullptr;
+  uint32_t *bricks = nullptr;
+  int brick_level = 0, brick_first = 0, brick_count = 0;
   void *rec = nullptr;
   float *master = nullptr, *m = nullptr, *v = nullptr;
   float *A = nullptr, *B = nullptr;
@@ -85,9 +87,9 @@ struct neuvv_tree {
   float bmin[3], bmax[3], scale[3];
   float hh_norm[16];
   int num_sms = 0;
-  LaunchCfg plain{128, 0, 0, 0};
-  LaunchCfg packet{128, 0, 0, 0};
-  LaunchCfg compose{128, 0, 1, 0};
+  LaunchCfg plain{128, 1, 1, 0, 0, 0};
+  LaunchCfg packet{64, 8, 16, 0, 0, 0};
+  LaunchCfg compose{128, 1, 1, 0, 1, 0};
 };
 
 namespace {
@@ -112,6 +114,10 @@ DevTree dev_tree(const neuvv_tree *t) {
   d.K = t->info.K;
   d.rec_stride = t->info.rec_stride;
   d.smem_nodes = 0;
+  d.bricks = t->bricks;
+  d.brick_level = t->brick_level;
+  d.brick_first = t->brick_first;
+  d.brick_count = t->brick_count;
   return d;
 }
 
@@ -144,6 +150,27 @@ neuvv_status check_opts(const neuvv_render_opts *o) {
 neuvv_status check_time(const neuvv_rays *r, float t) {
   if (!r->t && !(t >= 0.f && t <= 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "scalar t must be in [0, 1]");
   return NEUVV_OK;
+}
+
+// Writes, for the subtree of `node` (at `level`, origin o in brick-local
+// finest cells), the entry (level << 28 | id) of the tree cell holding each
+// finest cell of the brick (side 2^sh).
+void fill_brick(const uint32_t *child, uint32_t node, int level, int depth, int sh, int ox, int oy, int oz,
+                uint32_t *brick) {
+  const int half = 1 << (depth - level - 1);
+  for (int c = 0; c < 8; ++c) {
+    const int cx = ox + ((c >> 2) & 1) * half, cy = oy + ((c >> 1) & 1) * half, cz = oz + (c & 1) * half;
+    const uint32_t e = child[(size_t)node * 8 + c];
+    if (e != kEmpty && !(e & kLeafBit)) {
+      fill_brick(child, e, level + 1, depth, sh, cx, cy, cz, brick);
+      continue;
+    }
+    const uint32_t id = e == kEmpty ? kBrickEmpty : (e & ~kLeafBit);
+    const uint32_t v = ((uint32_t)(level + 1) << 28) | id;
+    for (int x = cx; x < cx + half; ++x)
+      for (int y = cy; y < cy + half; ++y)
+        for (int z = cz; z < cz + half; ++z) brick[((size_t)x << (2 * sh)) | ((size_t)y << sh) | (size_t)z] = v;
+  }
 }
 
 }  // namespace
@@ -282,6 +309,30 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
     NEUVV_TRY(cudaMemset(t->m, 0, recf_bytes), "memset m");
     NEUVV_TRY(cudaMemset(t->v, 0, recf_bytes), "memset v");
   }
+  // -- bricks at level depth-3 (8^3 finest cells per internal node there),
+  //    when those nodes form one contiguous index range and leaf ids fit
+  if (!(d.flags & NEUVV_TREE_NO_BRICKS) && d.depth >= 3 && d.n_leaves < (int64_t)kBrickEmpty) {
+    const int Lb = d.depth - 3, sh = 3;
+    int64_t first = -1, last = -1;
+    bool contiguous = true;
+    for (int64_t n = 0; n < d.n_nodes; ++n)
+      if (level[n] == Lb) {
+        if (first < 0) first = n;
+        else if (n != last + 1) contiguous = false;
+        last = n;
+      }
+    const int64_t count = first < 0 ? 0 : last - first + 1;
+    if (contiguous && count > 0 && count * 512 * 4 <= ((int64_t)1 << 30)) {
+      std::vector<uint32_t> br((size_t)count * 512, 0);
+      for (int64_t n = first; n <= last; ++n)
+        fill_brick(d.child, (uint32_t)n, Lb, d.depth, sh, 0, 0, 0, br.data() + (size_t)(n - first) * 512);
+      NEUVV_TRY(cudaMalloc(&t->bricks, br.size() * 4), "cudaMalloc(bricks)");
+      NEUVV_TRY(cudaMemcpy(t->bricks, br.data(), br.size() * 4, cudaMemcpyHostToDevice), "copy bricks");
+      t->brick_level = Lb;
+      t->brick_first = (int)first;
+      t->brick_count = (int)count;
+    }
+  }
 #undef NEUVV_TRY
   t->plain.num_sms = t->packet.num_sms = t->compose.num_sms = t->num_sms > 0 ? t->num_sms : 1;
   *out = t;
@@ -294,6 +345,7 @@ neuvv_status neuvv_tree_destroy(neuvv_tree *t) {
   if (!t->master_is_storage) cudaFree(t->master);
   cudaFree(t->rec);
   cudaFree(t->child);
+  cudaFree(t->bricks);
   cudaFree(t->m);
   cudaFree(t->v);
   cudaFree(t->A);
@@ -308,6 +360,8 @@ neuvv_status neuvv_tree_get_info(const neuvv_tree *t, neuvv_tree_info *info) {
   if (!t || !info) return fail(NEUVV_ERR_INVALID_ARG, "tree/info is NULL");
   *info = t->info;
   info->packet_block = t->packet.block;
+  info->packet_queue = t->packet.queue;
+  info->packet_ready = t->packet.ready;
   return NEUVV_OK;
 }
 
@@ -624,6 +678,19 @@ neuvv_status neuvv_trace(const neuvv_tree *t, const neuvv_rays *rays, int32_t ma
   return NEUVV_OK;
 }
 
+neuvv_status neuvv_tree_set_launch(neuvv_tree *t, int32_t block, int32_t queue, int32_t ready) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (block < 32 || block > 256 || block % 32 != 0)
+    return fail(NEUVV_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 256]");
+  if (queue < 1 || queue > kMaxQueue || (queue & (queue - 1)) != 0)
+    return fail(NEUVV_ERR_INVALID_ARG, "queue must be a power of two in [1, %d]", kMaxQueue);
+  if (ready < 1 || ready > 32) return fail(NEUVV_ERR_INVALID_ARG, "ready must be in [1, 32]");
+  t->packet.block = block;
+  t->packet.queue = queue;
+  t->packet.ready = ready;
+  return NEUVV_OK;
+}
+
 neuvv_status neuvv_autotune(neuvv_tree *t, const neuvv_rays *sample, float time, float *best_ms,
                             neuvv_stream stream) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
@@ -649,9 +716,10 @@ neuvv_status neuvv_autotune(neuvv_tree *t, const neuvv_rays *sample, float time,
   const LaunchCfg saved = t->packet;
   LaunchCfg best = saved;
   float best_t = 1e30f;
-  const int blocks[] = {64, 96, 128, 192, 256};
-  for (int b : blocks) {
-    t->packet = LaunchCfg{b, 0, 0, saved.num_sms};
+  struct Cand { int block, queue, ready; };
+  const Cand cands[] = {{64, 8, 16}, {64, 1, 1}, {64, 4, 8}, {128, 8, 16}, {128, 1, 1}, {32, 8, 16}, {64, 16, 16}};
+  for (const Cand &c : cands) {
+    t->packet = LaunchCfg{c.block, c.queue, c.ready, 0, 0, saved.num_sms};
     float ms_best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(ev0, st);

@@ -41,7 +41,16 @@ struct DevTree {
   float scale[3];         // 2^depth / (bmax - bmin)
   float hh_norm[16];      // Abar_{n,l} at [4n + l]
   int depth, T, K, rec_stride, smem_nodes;
+  // Bricks: for each internal node at brick_level (nodes brick_first ..
+  // brick_first + brick_count - 1), a dense table over its finest cells of
+  // (level << 28 | leaf id), 0x0FFFFFFF as id for empty: the node that holds
+  // each cell, so the descent below brick_level is one load.  Null when the
+  // tree has none.
+  const uint32_t *bricks;
+  int brick_level, brick_first, brick_count;
 };
+
+constexpr uint32_t kBrickEmpty = 0x0FFFFFFFu;
 
 __device__ __forceinline__ void raise_status(const DevTree &tr, uint32_t bit) {
   if (tr.status) atomicOr(tr.status, bit);
@@ -175,10 +184,27 @@ __device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s
   int L = 0;
   if (kPath && start > 0) {
     L = start;
+    if (tr.bricks && L > tr.brick_level) L = tr.brick_level;
     node = pr.path[L * pr.stride];
   }
   for (; L < D; ++L) {
     if (kPath) pr.path[L * pr.stride] = node;
+    if (tr.bricks && L == tr.brick_level) {
+      // the rest of the descent is one entry of the node's brick
+      const uint32_t b = node - (uint32_t)tr.brick_first;
+      if (b >= (uint32_t)tr.brick_count) {
+        raise_status(tr, kStatusBadIndex);
+        level = L + 1;
+        return kEmpty;
+      }
+      const int sh = D - L;
+      const int m = (1 << sh) - 1;
+      const uint32_t idx = (uint32_t)(((cell[0] & m) << (2 * sh)) | ((cell[1] & m) << sh) | (cell[2] & m));
+      const uint32_t v = __ldg(tr.bricks + ((size_t)b << (3 * sh)) + idx);
+      level = (int)(v >> 28);
+      const uint32_t id = v & kBrickEmpty;
+      return id == kBrickEmpty ? kEmpty : (kLeafBit | id);
+    }
     const int bit = D - 1 - L;
     const int slot = (((cell[0] >> bit) & 1) << 2) | (((cell[1] >> bit) & 1) << 1) | ((cell[2] >> bit) & 1);
     uint32_t e;
@@ -205,68 +231,77 @@ __device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s
   return kEmpty;
 }
 
-// Advances to the next occupied-leaf segment.  On success returns true with
-// leaf id and the segment [t0, t1] (relative to the entry point); false when
-// the ray has left the root box (or hit its step cap).
+// One step of the walk: the tree cell holding the current finest cell, then
+// the move across its exit face.  Returns true (with leaf and [t0, t1],
+// distances past the entry point) when that cell is an occupied leaf crossed
+// with a positive chord.  Clears w.alive when the ray leaves the root box or
+// reaches its step cap.
+template <bool kSmem, bool kPath = false>
+__device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_child, RayWalk &w, uint32_t &leaf,
+                                          float &t0, float &t1, PathRef pr = PathRef{nullptr, 0}) {
+  const int N = 1 << tr.depth;
+  if (++w.steps > w.max_steps) {
+    raise_status(tr, kStatusSegCap);
+    w.alive = false;
+    return false;
+  }
+  int level;
+  const uint32_t e = descend<kSmem, kPath>(tr, s_child, pr, w.cell, w.restart, level);
+  const int shift = tr.depth - level;
+  const int size = 1 << shift;
+  int lo[3];
+  float tx[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = w.cell[a] & -size;
+    const float bnd = (float)(w.gd[a] > 0.f ? lo[a] + size : lo[a]);
+    tx[a] = w.gd[a] != 0.f ? fmaf(bnd, w.inv[a], w.ngi[a]) : INFINITY;
+  }
+  // exit axis: first minimum (exact ties x < y < z); register-only selects
+  int ax = 0;
+  float t_exit = tx[0];
+  if (tx[1] < t_exit) { ax = 1; t_exit = tx[1]; }
+  if (tx[2] < t_exit) { ax = 2; t_exit = tx[2]; }
+  const float seg_end = fminf(t_exit, w.t_far);
+  const float seg_start = w.t_cur;
+  bool found = false;
+  if (e != kEmpty && seg_end > seg_start) {
+    leaf = e & ~kLeafBit;
+    t0 = seg_start;
+    t1 = seg_end;
+    found = true;
+  }
+  // step to the next cell
+  if (t_exit >= w.t_far) {
+    w.alive = false;
+  } else {
+    w.t_cur = fmaxf(w.t_cur, t_exit);
+    bool inside = true;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b == ax) {
+        const int nc = w.gd[b] > 0.f ? lo[b] + size : lo[b] - 1;
+        inside = nc >= 0 && nc < N;
+        w.cell[b] = nc;
+        // deepest level whose cell holds both the old node and the new cell
+        if (kPath && inside) w.restart = tr.depth - 32 + __clz(nc ^ lo[b]);
+      } else {
+        const float p = fmaf(w.t_cur, w.gd[b], w.go[b]);
+        w.cell[b] = min(max(cell_of(p, w.gd[b], N), lo[b]), lo[b] + size - 1);
+      }
+    }
+    if (!inside) w.alive = false;
+  }
+  return found;
+}
+
+// Advances to the next occupied-leaf segment (see walk_step); false when the
+// ray has left the root box (or hit its step cap).
 template <bool kSmem, bool kPath = false>
 __device__ __forceinline__ bool walk_next(const DevTree &tr, const uint32_t *s_child, RayWalk &w, uint32_t &leaf,
                                           float &t0, float &t1, PathRef pr = PathRef{nullptr, 0}) {
-  const int N = 1 << tr.depth;
-  while (w.alive) {
-    if (++w.steps > w.max_steps) {
-      raise_status(tr, kStatusSegCap);
-      w.alive = false;
-      break;
-    }
-    int level;
-    const uint32_t e = descend<kSmem, kPath>(tr, s_child, pr, w.cell, w.restart, level);
-    const int shift = tr.depth - level;
-    const int size = 1 << shift;
-    int lo[3];
-    float tx[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = w.cell[a] & -size;
-      const float bnd = (float)(w.gd[a] > 0.f ? lo[a] + size : lo[a]);
-      tx[a] = w.gd[a] != 0.f ? fmaf(bnd, w.inv[a], w.ngi[a]) : INFINITY;
-    }
-    // exit axis: first minimum (exact ties x < y < z); register-only selects
-    int ax = 0;
-    float t_exit = tx[0];
-    if (tx[1] < t_exit) { ax = 1; t_exit = tx[1]; }
-    if (tx[2] < t_exit) { ax = 2; t_exit = tx[2]; }
-    const float seg_end = fminf(t_exit, w.t_far);
-    const float seg_start = w.t_cur;
-    bool found = false;
-    if (e != kEmpty && seg_end > seg_start) {
-      leaf = e & ~kLeafBit;
-      t0 = seg_start;
-      t1 = seg_end;
-      found = true;
-    }
-    // step to the next cell
-    if (t_exit >= w.t_far) {
-      w.alive = false;
-    } else {
-      w.t_cur = fmaxf(w.t_cur, t_exit);
-      bool inside = true;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        if (b == ax) {
-          const int nc = w.gd[b] > 0.f ? lo[b] + size : lo[b] - 1;
-          inside = nc >= 0 && nc < N;
-          w.cell[b] = nc;
-          // deepest level whose cell holds both the old node and the new cell
-          if (kPath && inside) w.restart = tr.depth - 32 + __clz(nc ^ lo[b]);
-        } else {
-          const float p = fmaf(w.t_cur, w.gd[b], w.go[b]);
-          w.cell[b] = min(max(cell_of(p, w.gd[b], N), lo[b]), lo[b] + size - 1);
-        }
-      }
-      if (!inside) w.alive = false;
-    }
-    if (found) return true;
-  }
+  while (w.alive)
+    if (walk_step<kSmem, kPath>(tr, s_child, w, leaf, t0, t1, pr)) return true;
   return false;
 }
 
@@ -410,6 +445,14 @@ struct LeafRecord {
 #pragma unroll
     for (int i = 0; i < NV; ++i) Elem<E>::unpack(raw[i], w + i * PV);
   }
+  // Asks L1 for a leaf's record ahead of its use (no registers held).
+  __device__ __forceinline__ static void prefetch(const DevTree &tr, uint32_t leaf) {
+    const char *p = reinterpret_cast<const char *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
+    constexpr int kBytes = NV * 16;
+#pragma unroll
+    for (int b = 0; b < kBytes; b += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + b));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + kBytes - 1));
+  }
   __device__ __forceinline__ float sig(int k) const { return w[k]; }
   __device__ __forceinline__ float gam(int k) const { return w[KP + k]; }
   __device__ __forceinline__ float hh(int ch, int i) const { return w[2 * KP + ch * NH + i]; }
@@ -494,15 +537,18 @@ __device__ __forceinline__ void rows_to_smem(const DevTree &tr, float u, float *
 template <int KP, int DEG, typename E, typename Rows, bool kDz = false>
 __device__ __forceinline__ void eval_sample(const DevTree &tr, const Rows &rows, const float *Y,
                                             const LeafRecord<KP, DEG, E> &r, int act, Sample<DEG> &s) {
-  float ps = 0.f;
+  // four partial sums: independent FMA chains
+  float p4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < KP; ++k) ps = fmaf(rows.A(k), r.sig(k), ps);
+  for (int k = 0; k < KP; ++k) p4[k & 3] = fmaf(rows.A(k), r.sig(k), p4[k & 3]);
+  const float ps = (p4[0] + p4[1]) + (p4[2] + p4[3]);
   s.pre_sigma = ps;
   s.sigma = fmaxf(ps, 0.f);
   if (!(s.sigma > 0.f)) return;
-  float pg = 0.f;
+  float q4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < KP; ++k) pg = fmaf(rows.B(k), r.gam(k), pg);
+  for (int k = 0; k < KP; ++k) q4[k & 3] = fmaf(rows.B(k), r.gam(k), q4[k & 3]);
+  const float pg = (q4[0] + q4[1]) + (q4[2] + q4[3]);
   s.s_gamma = sigmoidf_fast(pg);
   sincospif(s.s_gamma, &s.sg, &s.cg);
   float dR[(DEG + 1) * (DEG + 2) / 2];

@@ -11,6 +11,8 @@ enum DType { kF32 = 0, kBF16 = 1 };
 
 struct LaunchCfg {
   int block;          // threads per block
+  int queue;          // packet kernels: per-lane queue of found leaf segments (power of 2, <= kMaxQueue)
+  int ready;          // packet kernels: lanes with a queued segment that trigger a shading round
   int grid;           // compose: persistent blocks (0 = as many as fit, from the occupancy API)
   int dynamic_queue;  // compose: 1 = warps pull packets from a counter, 0 = static stride
   int num_sms;        // multiprocessors of the device
@@ -89,8 +91,12 @@ cudaError_t launch_mse(const float *rgb, const float *target, long long n, float
                        cudaStream_t s);
 
 // Dynamic shared memory of the packet kernels: per thread the basis rows
-// (2 K_pad floats) and the descent path (16 levels).
-inline size_t smem_bytes(int block, int KP) { return (size_t)block * (2 * KP + 16) * sizeof(float); }
+// (2 K_pad floats), the descent path (16 levels) and the segment queue
+// (queue x {leaf, t0, t1}).
+inline size_t smem_bytes(int block, int KP, int queue) {
+  return (size_t)block * (2 * KP + 16 + 3 * queue) * sizeof(float);
+}
+constexpr int kMaxQueue = 32;
 constexpr int kMaxDepth = 14;
 
 }  // namespace neuvv

@@ -144,30 +144,65 @@ __global__ void __launch_bounds__(256) render_bwd_plain_kernel(const __grid_cons
   }
 }
 
-// Packet adjoint: one thread per ray (warps = 32-ray packets), the forward's
-// ancestor-restarted descents, basis rows in shared memory.
+// Packet adjoint: the forward packet kernel's structure (one thread per ray,
+// walk steps and sample rounds decoupled through a per-lane queue), the walk
+// stopped at the forward's segment count.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a) {
+__global__ void __launch_bounds__(256, 2) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a, int queue,
+                                                                int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
   const int B = blockDim.x, tid = threadIdx.x;
   float *my_rows = reinterpret_cast<float *>(smem) + tid;
   const PathRef pr{smem + 2 * KP * B + tid, B};
+  uint32_t *q_leaf = smem + (2 * KP + 16) * B + tid;
+  float *q_t0 = reinterpret_cast<float *>(q_leaf + queue * B);
+  float *q_t1 = q_t0 + queue * B;
   const SmemRows<KP> rows{my_rows, B};
   const long long i = (long long)blockIdx.x * B + tid;
+  const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
   if (i >= a.rays.n) return;
   RayWalk w;
   AdjState st;
   float dn[3], t;
-  if (!adjoint_setup(a, i, w, dn, t, st)) return;
-  rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+  const bool live = adjoint_setup(a, i, w, dn, t, st);
+  if (__ballot_sync(present, live) == 0) return;
   float Y[(DEG + 1) * (DEG + 1)];
-  sh_real<DEG>(dn, Y);
-  uint32_t leaf;
-  float t0, t1;
-  while (st.count < st.target && walk_next<false, true>(tr, nullptr, w, leaf, t0, t1, pr)) {
-    ++st.count;
-    adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, t0, t1, st);
+  if (live) {
+    rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+    sh_real<DEG>(dn, Y);
+  }
+  int walked = 0;  // segments found so far (the walk stops at the forward's count)
+  bool walking = live && w.alive;
+  int qh = 0, qn = 0;
+  const int qmask = queue - 1;
+  for (;;) {
+    if (walking && qn < queue) {
+      uint32_t leaf;
+      float t0, t1;
+      if (walk_step<false, true>(tr, nullptr, w, leaf, t0, t1, pr)) {
+        const int slot = (qh + qn) & qmask;
+        q_leaf[slot * B] = leaf;
+        q_t0[slot * B] = t0;
+        q_t1[slot * B] = t1;
+        ++qn;
+        ++walked;
+      }
+      walking = w.alive && walked < st.target;
+    }
+    const unsigned have = __ballot_sync(present, qn > 0);
+    const unsigned stepping = __ballot_sync(present, walking && qn < queue);
+    if (!have && !stepping) break;
+    const int active = __popc(__ballot_sync(present, walking || qn > 0));
+    if (stepping && __popc(have) < min(ready, active)) continue;
+    if (qn > 0) {
+      const uint32_t leaf = q_leaf[qh * B];
+      const float t0 = q_t0[qh * B], t1 = q_t1[qh * B];
+      qh = (qh + 1) & qmask;
+      --qn;
+      ++st.count;
+      adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, t0, t1, st);
+    }
   }
 }
 
@@ -178,8 +213,13 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
   if (!packet) {
     render_bwd_plain_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, 0, s>>>(a);
   } else {
-    const size_t sm = smem_bytes(cfg.block, KP);
-    render_bwd_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a);
+    const size_t sm = smem_bytes(cfg.block, KP, cfg.queue);
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(render_bwd_packet_kernel<KP, DEG, E>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    render_bwd_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
   }
   return cudaGetLastError();
 }

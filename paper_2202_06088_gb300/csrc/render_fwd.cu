@@ -3,9 +3,9 @@
 // render_plain_kernel  : one thread per ray, child table read from global
 //                        memory -- the baseline single-view path.
 // render_packet_kernel : one thread per ray with warps as 32-ray packets;
-//                        descents restart at the lowest common ancestor of
-//                        successive cells; basis rows and the descent path in
-//                        shared memory.
+//                        walking and shading decoupled through a per-lane
+//                        queue of found segments; descents restart at the
+//                        lowest common ancestor of successive cells.
 #include "neuvv_kernels.h"
 #include "neuvv_ray.cuh"
 
@@ -39,56 +39,95 @@ __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
 }
 
 // Packet forward kernel: one thread per ray, so each warp is a packet of 32
-// consecutive rays (an 8x4 pixel tile when the caller orders rays that way);
-// descents restart at the lowest common ancestor of successive cells (path
-// kept per thread in shared memory), basis rows live in shared memory to keep
-// registers (and so resident warps) up; the block scheduler balances uneven
-// ray lengths across the grid.
+// consecutive rays (an 8x4 pixel tile when the caller orders rays that way).
+// Walking and shading are decoupled: in every iteration of one warp-uniform
+// loop each lane takes at most one walk step and queues the occupied-leaf
+// segment it finds; the warp runs a shading round (each lane evaluates and
+// composites its oldest queued segment, in ray order) once `ready` lanes hold
+// one, or when no lane can step any further.  Lanes therefore do not wait at
+// every sample for the slowest searcher of the packet, and shading rounds run
+// nearly full.  Descents restart at the lowest common ancestor of successive
+// cells (path per thread in shared memory); basis rows and the queue live in
+// shared memory too.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constant__ FwdArgs a) {
+__global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constant__ FwdArgs a, int queue, int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
   const int B = blockDim.x, tid = threadIdx.x;
   float *my_rows = reinterpret_cast<float *>(smem) + tid;
   const PathRef pr{smem + 2 * KP * B + tid, B};
+  uint32_t *q_leaf = smem + (2 * KP + 16) * B + tid;
+  float *q_t0 = reinterpret_cast<float *>(q_leaf + queue * B);
+  float *q_t1 = q_t0 + queue * B;
   const SmemRows<KP> rows{my_rows, B};
   const long long i = (long long)blockIdx.x * B + tid;
+  // lanes past the end leave now; the others stay to the end of the loop
+  const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
   if (i >= a.rays.n) return;
   float o[3], d[3], t, dn[3];
   load_ray(a.rays, i, o, d, t);
   RayWalk w;
-  if (!walk_init(tr, o, d, w, dn)) {
-    write_miss(a.out, i);
-    return;
-  }
-  rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+  const bool hit = walk_init(tr, o, d, w, dn);
+  if (!hit) write_miss(a.out, i);
+  if (__ballot_sync(present, hit) == 0) return;  // the whole packet missed the tree
   float Y[(DEG + 1) * (DEG + 1)];
-  sh_real<DEG>(dn, Y);
+  if (hit) {
+    rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+    sh_real<DEG>(dn, Y);
+  }
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f, dnum = 0.f, tau = 0.f;
   int nseg = 0;
-  uint32_t leaf;
-  float t0, t1;
-  while (walk_next<false, true>(tr, nullptr, w, leaf, t0, t1, pr)) {
-    LeafRecord<KP, DEG, E> rec;
-    rec.load(tr, leaf);
-    Sample<DEG> s;
-    eval_sample<KP, DEG, E>(tr, rows, Y, rec, a.act, s);
-    ++nseg;
-    if (s.sigma > 0.f) {
-      const float delta = t1 - t0;
-      const float sd = s.sigma * delta;
-      const float e = __expf(-sd);
-      const float wgt = T * (1.f - e);
-      C0 = fmaf(wgt, s.c[0], C0);
-      C1 = fmaf(wgt, s.c[1], C1);
-      C2 = fmaf(wgt, s.c[2], C2);
-      A += wgt;
-      dnum = fmaf(wgt, w.t_base + 0.5f * (t0 + t1), dnum);
-      tau += sd;
-      T *= e;
-      if (T < a.t_stop) break;
+  bool walking = hit && w.alive;
+  int qh = 0, qn = 0;  // queue head and length
+  const int qmask = queue - 1;
+  for (;;) {
+    if (walking && qn < queue) {
+      uint32_t leaf;
+      float t0, t1;
+      if (walk_step<false, true>(tr, nullptr, w, leaf, t0, t1, pr)) {
+        const int slot = (qh + qn) & qmask;
+        q_leaf[slot * B] = leaf;
+        q_t0[slot * B] = t0;
+        q_t1[slot * B] = t1;
+        ++qn;
+      }
+      walking = w.alive;
+    }
+    const unsigned have = __ballot_sync(present, qn > 0);
+    const unsigned stepping = __ballot_sync(present, walking && qn < queue);
+    if (!have && !stepping) break;
+    const int active = __popc(__ballot_sync(present, walking || qn > 0));
+    if (stepping && __popc(have) < min(ready, active)) continue;
+    if (qn > 0) {
+      const uint32_t leaf = q_leaf[qh * B];
+      const float t0 = q_t0[qh * B], t1 = q_t1[qh * B];
+      qh = (qh + 1) & qmask;
+      --qn;
+      LeafRecord<KP, DEG, E> rec;
+      rec.load(tr, leaf);
+      Sample<DEG> s;
+      eval_sample<KP, DEG, E>(tr, rows, Y, rec, a.act, s);
+      ++nseg;
+      if (s.sigma > 0.f) {
+        const float delta = t1 - t0;
+        const float sd = s.sigma * delta;
+        const float e = __expf(-sd);
+        const float wgt = T * (1.f - e);
+        C0 = fmaf(wgt, s.c[0], C0);
+        C1 = fmaf(wgt, s.c[1], C1);
+        C2 = fmaf(wgt, s.c[2], C2);
+        A += wgt;
+        dnum = fmaf(wgt, w.t_base + 0.5f * (t0 + t1), dnum);
+        tau += sd;
+        T *= e;
+        if (T < a.t_stop) {  // early termination: drop what is still queued
+          walking = false;
+          qn = 0;
+        }
+      }
     }
   }
+  if (!hit) return;
   a.out.rgb[3 * i + 0] = C0;
   a.out.rgb[3 * i + 1] = C1;
   a.out.rgb[3 * i + 2] = C2;
@@ -133,8 +172,13 @@ static cudaError_t fwd_one(bool packet, const FwdArgs &a, const LaunchCfg &cfg, 
   if (!packet) {
     render_plain_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, 0, s>>>(a);
   } else {
-    const size_t sm = smem_bytes(cfg.block, KP);
-    render_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a);
+    const size_t sm = smem_bytes(cfg.block, KP, cfg.queue);
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(render_packet_kernel<KP, DEG, E>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    render_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
   }
   return cudaGetLastError();
 }

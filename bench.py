@@ -83,6 +83,36 @@ def load_peaks():
         return 6800.0, "fallback", 2070.0
 
 
+def kernel_sources_digest():
+    """sha256 (first 16 hex digits) over the library's CUDA sources, in name order."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2202_06088_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of a step kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_depth9_8x1080p.md")
+    try:
+        with open(path) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    digest = kernel_sources_digest()
+    for ln in lines:
+        w = ln.split()
+        if len(w) == 6 and w[0] == "traffic" and w[2] == kernel and w[4] == "sources":
+            return int(w[3]) if w[5] == digest else None
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -372,7 +402,8 @@ def main():
                 "peak_kind": f"{peak_kind} (copy bandwidth)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
-    roof["traffic"] = None
+    # DRAM bytes per launch from one ncu capture of this workload (null once the kernel changed)
+    roof["traffic"] = measured_traffic(dom) if args.views == 8 else None
     roof["algorithmic_bytes"] = bytes_
     roof["algorithmic_flops"] = flops_
 
@@ -421,8 +452,8 @@ def main():
                    "parallelism": f"replicas x{world}", "launch": launch,
                    "clocks_window": "warm-up and timed steps"},
         "kernels_ms": kern,
-        "fwd_bf16_packet": {"ms_per_1080p_frame": fwd_ms / 8, "msamples_per_s": fwd_samples / (fwd_ms / 1e3) / 1e6},
-        "fwd_fp32_plain": {"ms_per_1080p_frame": plain_ms / 8,
+        "fwd_bf16_packet": {"ms_per_1080p_frame": fwd_ms / args.views, "msamples_per_s": fwd_samples / (fwd_ms / 1e3) / 1e6},
+        "fwd_fp32_plain": {"ms_per_1080p_frame": plain_ms / args.views,
                            "msamples_per_s": plain_samples / (plain_ms / 1e3) / 1e6},
         "roofline": roof,
         "e2e": e2e,

@@ -87,6 +87,10 @@ def configure(L):
     L.or_adam.argtypes = [i64, ci, p, p, p, p, p, d, d, d, d, ci]
     L.or_round_bf16.restype = None
     L.or_round_bf16.argtypes = [p, p, i64]
+    L.or_quantize_fp8.restype = None
+    L.or_quantize_fp8.argtypes = [p, i64, ci, p, p]
+    L.or_round_e4m3.restype = None
+    L.or_round_e4m3.argtypes = [p, p, i64]
     return L
 
 
@@ -262,6 +266,38 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     out = np.empty_like(x)
     lib().or_round_bf16(_ptr(x), _ptr(out), x.size)
     return out
+
+
+def round_e4m3(x: np.ndarray) -> np.ndarray:
+    """The nearest FP8 E4M3 value of each entry (ties to even, saturating at 448)."""
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.empty_like(x)
+    lib().or_round_e4m3(_ptr(x), _ptr(out), x.size)
+    return out
+
+
+def quantize_fp8_groups(w: np.ndarray):
+    """[n_groups, len] float32 -> (dequantised float64 [n_groups, len], scales
+    [n_groups]): each group scaled by the smallest power of two that brings its
+    largest magnitude to <= 448, rounded to E4M3, scaled back."""
+    w = np.ascontiguousarray(w, np.float32)
+    out = np.empty(w.shape, np.float64)
+    scale = np.empty(w.shape[0], np.float64)
+    lib().or_quantize_fp8(_ptr(w), w.shape[0], w.shape[1], _ptr(out), _ptr(scale))
+    return out, scale
+
+
+def quantize_fp8_tree(tree):
+    """The tree as FP8 storage holds it: per leaf, one scale for its w_sigma,
+    one for its w_gamma, one for its w_hh (all three channels).  Returns the
+    tree with dequantised coefficients and the scales [n_leaves, 3]."""
+    L = tree.n_leaves
+    ws, s_s = quantize_fp8_groups(tree.w_sigma.reshape(tree.K, L).T)
+    wg, s_g = quantize_fp8_groups(tree.w_gamma.reshape(tree.K, L).T)
+    wh, s_h = quantize_fp8_groups(tree.w_hh.reshape(-1, L).T)
+    out = tree.with_coeffs(ws.T.astype(np.float32), wg.T.astype(np.float32),
+                           wh.T.reshape(tree.w_hh.shape).astype(np.float32))
+    return out, np.stack([s_s, s_g, s_h], axis=1)
 
 
 # -- point evaluations for the pins -------------------------------------------

@@ -19,7 +19,8 @@
  *     (Sec. 4.3 "Optimization")
  *   - spatial/temporal edits and depth-ordered blending (Eq. st_composite_affine,
  *     Algorithm 1)
- *   - Adam on touched leaves, BF16 rounding of stored coefficients.
+ *   - Adam on touched leaves, BF16 rounding of stored coefficients, FP8 E4M3
+ *     rounding with per-leaf power-of-two scales (a storage ablation).
  *
  * Readings taken where the paper is garbled or silent (kept identical in the
  * design notes):
@@ -759,4 +760,56 @@ void or_round_bf16(const float *in, float *out, int64_t n) {
     u &= 0xFFFF0000u;
     memcpy(&out[i], &u, 4);
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public: FP8 E4M3 storage with per-leaf scales (storage ablation)         */
+/* ------------------------------------------------------------------------ */
+
+/* The E4M3 value nearest to x: 1 sign bit, 4 exponent bits with bias 7, 3
+ * fraction bits, subnormals down to 2^-9, largest finite magnitude 448, no
+ * infinities.  Ties go to the even code; magnitudes from 448 up saturate. */
+static double e4m3_nearest(double x) {
+  double a = fabs(x);
+  if (a >= 448.0) return copysign(448.0, x);
+  if (a == 0.0) return x;
+  int e;
+  frexp(a, &e);                 /* a in [2^(e-1), 2^e) */
+  int binade = e - 1;
+  if (binade < -6) binade = -6; /* subnormals are spaced like binade -6 */
+  double spacing = ldexp(1.0, binade - 3);
+  /* nearbyint rounds half to even in the default mode; an even multiple of
+   * the spacing is an even code (the code's last bit is the multiple's) */
+  return copysign(nearbyint(a / spacing) * spacing, x);
+}
+
+/* The smallest power of two s with max |w| <= 448 s over a group (1 for an
+ * all-zero group), so that w / s fits E4M3 without saturating. */
+static double fp8_group_scale(const float *w, int len) {
+  double mx = 0.0;
+  for (int i = 0; i < len; ++i)
+    if (fabs((double)w[i]) > mx) mx = fabs((double)w[i]);
+  if (mx == 0.0) return 1.0;
+  int e;
+  frexp(mx, &e);                /* mx >= 2^(e-1) > 448 * 2^(e-10) */
+  int p = e - 10;
+  while (ldexp(448.0, p) < mx) ++p;
+  return ldexp(1.0, p);
+}
+
+/* Quantises n_groups groups of len float32 values each ([group][len]): every
+ * group gets its own power-of-two scale s, each value becomes
+ * s * e4m3_nearest(w / s).  Writes the dequantised values and the scales. */
+void or_quantize_fp8(const float *in, int64_t n_groups, int len, double *out, double *scale) {
+  for (int64_t g = 0; g < n_groups; ++g) {
+    const float *w = in + g * len;
+    double s = fp8_group_scale(w, len);
+    scale[g] = s;
+    for (int i = 0; i < len; ++i) out[g * len + i] = e4m3_nearest((double)w[i] / s) * s;
+  }
+}
+
+/* The plain E4M3 rounding of each value (no scale), for the pins. */
+void or_round_e4m3(const double *in, double *out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) out[i] = e4m3_nearest(in[i]);
 }

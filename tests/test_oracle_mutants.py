@@ -36,6 +36,11 @@ MUTANTS = {
                                            "LD[j] = out.depth;"),
     "early_stop_one_segment_late": ("if (exp(-tau) < op->t_stop) break;",
                                     "if (exp(-(tau - e.sigma * delta)) < op->t_stop) break;"),
+    "e4m3_subnormal_spacing_halved": ("if (binade < -6) binade = -6;", "if (binade < -7) binade = -7;"),
+    "e4m3_ties_away_from_zero": ("return copysign(nearbyint(a / spacing) * spacing, x);",
+                                 "return copysign(round(a / spacing) * spacing, x);"),
+    "fp8_scale_search_starts_too_high": ("int p = e - 10;", "int p = e - 8;"),
+    "fp8_scale_not_smallest_at_exact_fit": ("while (ldexp(448.0, p) < mx) ++p;", "while (ldexp(448.0, p) <= mx) ++p;"),
 }
 
 
@@ -171,6 +176,16 @@ def _battery():
     fin = np.isfinite(a0["depth"])
     if np.abs(a1["depth"][fin] - s * a0["depth"][fin]).max() > 1e-10:
         failed.append("compose_scale")
+    # FP8 E4M3: midpoints go to the even code; per-group scales are minimal
+    from test_oracle_fp8 import e4m3_codes
+    v = e4m3_codes()
+    mid = 0.5 * (v[:-1] + v[1:])
+    even = np.where(np.arange(v.size - 1) % 2 == 0, v[:-1], v[1:])
+    if not np.array_equal(oracle.round_e4m3(mid), even):
+        failed.append("fp8_ties")
+    _, sq = oracle.quantize_fp8_groups(np.array([[448.0, 1.0], [300.0, -1.0], [0.0, 0.0]], np.float32))
+    if not np.array_equal(sq, [1.0, 1.0, 1.0]):
+        failed.append("fp8_scale")
     return failed
 
 

@@ -53,6 +53,8 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline sample")
     p.add_argument("--views", type=int, default=8, help="1920x1080 views per step (8 = the benchmark workload)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default packet launch configuration")
+    p.add_argument("--no-fp8", action="store_true", help="skip the FP8-storage ablation leg")
+    p.add_argument("--launch", default=None, help="packet launch block,queue,ready (profiling case; default: library's)")
     p.add_argument("--profile-kernel", choices=["fwd", "bwd", "adam"], default=None,
                    help="profiling case: launch that kernel twice on the workload and exit (no JSON)")
     return p.parse_args()
@@ -241,6 +243,8 @@ def profile_case(args, B, tree, dr):
     """Two launches of one kernel of the step on the given views (for ncu)."""
     import torch
     tree_d = B.Tree(tree, "bf16", with_optimizer=args.profile_kernel == "adam")
+    if args.launch:
+        tree_d.set_launch(*[int(x) for x in args.launch.split(",")])
     out = B.neuvv_render(tree_d, dr, kernel="packet")
     grad_rgb = torch.randn(dr.n, 3, device=dr.o.device) * 1e-3
     grad = tree_d.new_grad()
@@ -374,7 +378,53 @@ def main():
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / reps
     plain_samples = int(out["nseg"].sum().item())
+    rgb32 = B.neuvv_render(tree32, dr, kernel="packet")["rgb"]
     del tree32
+
+    # -- storage ablation: the same training step on FP8 E4M3 records with
+    #    per-leaf scales (same FP32 master, same rays and targets)
+    fp8 = None
+    if not args.no_fp8:
+        tree8 = B.Tree(tree, "fp8", with_optimizer=True)
+        tree8.set_launch(launch["block"], launch["queue"], launch["ready"])
+        rgb8 = B.neuvv_render(tree8, dr, kernel="packet")["rgb"]
+        mse8 = float(((rgb8 - rgb32) ** 2).mean().item())
+        rgb16 = B.neuvv_render(tree_d, dr, kernel="packet")["rgb"]
+        mse16 = float(((rgb16 - rgb32) ** 2).mean().item())
+        del rgb8, rgb16
+        g8 = tree8.new_grad()
+        t8 = tree8.new_touched()
+        st8 = args.steps // 2 + 1
+
+        def step8(k):
+            B.neuvv_render(tree8, dr, kernel="packet", out=out)
+            loss.zero_()
+            B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
+            B.neuvv_render_backward(tree8, dr, out, grad_rgb, None, g8, t8, kernel="packet")
+            B.neuvv_adam_step(tree8, g8, t8, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=k)
+
+        for k in range(3):
+            step8(k + 1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(st8):
+            step8(4 + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms8 = e0.elapsed_time(e1) / st8
+        e0.record(stream)
+        for _ in range(reps):
+            B.neuvv_render(tree8, dr, kernel="packet", out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f8 = e0.elapsed_time(e1) / reps
+        psnr = lambda m: float("inf") if m == 0 else 10 * np.log10(1.0 / m)
+        fp8 = {"record_bytes": tree8.info.rec_stride, "ms_per_step": ms8,
+               "msamples_per_s": samples / (ms8 / 1e3) / 1e6, "fwd_ms_per_1080p_frame": f8 / args.views,
+               "psnr_vs_fp32_storage_db": psnr(mse8), "bf16_psnr_vs_fp32_storage_db": psnr(mse16),
+               "steps": st8}
+        del tree8, g8, t8
+    del rgb32
 
     # -- roofline of the dominant kernel of the step
     hbm_gbs, peak_kind, sm_max = load_peaks()
@@ -455,6 +505,7 @@ def main():
         "fwd_bf16_packet": {"ms_per_1080p_frame": fwd_ms / args.views, "msamples_per_s": fwd_samples / (fwd_ms / 1e3) / 1e6},
         "fwd_fp32_plain": {"ms_per_1080p_frame": plain_ms / args.views,
                            "msamples_per_s": plain_samples / (plain_ms / 1e3) / 1e6},
+        "fp8_ablation": fp8,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,

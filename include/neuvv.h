@@ -61,7 +61,11 @@ typedef enum {
   NEUVV_ERR_DEVICE = 6       /* other device-detected error (status word) */
 } neuvv_status;
 
-typedef enum { NEUVV_F32 = 0, NEUVV_BF16 = 1 } neuvv_dtype;
+/* Storage of the leaf coefficients on the device.  Arithmetic is FP32 for all.
+ * NEUVV_FP8_E4M3 is a storage ablation (no counterpart in the paper, which
+ * stores FP32): E4M3 codes with one power-of-two scale per leaf and group,
+ * built for K <= 8 with hh_degree 2 and 9 <= K <= 16 with hh_degree 3. */
+typedef enum { NEUVV_F32 = 0, NEUVV_BF16 = 1, NEUVV_FP8_E4M3 = 2 } neuvv_dtype;
 
 /* Device status bits (neuvv_tree_status). */
 #define NEUVV_STATUS_SEGMENT_CAP 0x1u /* a ray needed more than 3*2^depth+8 steps */
@@ -98,11 +102,18 @@ typedef struct {
  * for gradient buffers.  A record holds, in order, w_sigma (K_pad entries, the
  * last K_pad-K zero), w_gamma (K_pad), w_hh (3*N_h, channel-major), then zero
  * padding to rec_stride entries.  The FP32 gradient/master layout uses
- * rec_stride_f32 floats per leaf (a multiple of 4, 16-byte rows). */
+ * rec_stride_f32 floats per leaf (a multiple of 4, 16-byte rows).
+ * FP8_E4M3 records (rec_stride counts bytes): a 16-byte header of three FP32
+ * scales (w_sigma, w_gamma, w_hh groups) and a zero word, then one E4M3 code
+ * per entry in the order above, zero padded to a 16-byte multiple.  An entry
+ * is its code's value times its group's scale; each scale is the smallest
+ * power of two 2^p with max |w| <= 448 * 2^p over the group (1 if all zero),
+ * and codes are the nearest E4M3 values (ties to even) of w / 2^p.  Adam
+ * re-derives scales and codes from the FP32 master for each touched leaf. */
 typedef struct {
   int32_t depth, K, K_pad, T, hh_degree, N_h;
   int32_t rec_len;          /* 2*K_pad + 3*N_h meaningful entries */
-  int32_t rec_stride;       /* storage entries per leaf (16-byte multiple) */
+  int32_t rec_stride;       /* storage entries per leaf (16-byte multiple); FP8: bytes */
   int32_t rec_stride_f32;   /* FP32 floats per leaf in grad / master / m / v */
   neuvv_dtype dtype;
   int64_t n_nodes, n_leaves;

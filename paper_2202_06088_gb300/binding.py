@@ -22,8 +22,8 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-F32, BF16 = 0, 1
-_DTYPES = {"f32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16}
+F32, BF16, FP8 = 0, 1, 2
+_DTYPES = {"f32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16, "fp8": FP8, "fp8_e4m3": FP8}
 _ACT = {"sigmoid": 0, "identity": 1}
 _KERNEL = {"auto": 0, "plain": 1, "packet": 2}
 _MODE = {"sorted": 0, "alg1": 1}
@@ -184,8 +184,11 @@ class Tree:
         return s.value, m.value, a.value, v.value
 
     def storage(self) -> torch.Tensor:
-        """View of the storage records [n_leaves, rec_stride] (float32 or bfloat16)."""
+        """View of the storage records [n_leaves, rec_stride] (float32, bfloat16,
+        or the raw bytes of FP8 records)."""
         s = self._ptrs()[0]
+        if self.dtype == FP8:
+            return torch.as_tensor(_CudaView(s, (self.n_leaves, self.info.rec_stride), "|u1", self), device="cuda")
         if self.dtype == F32:
             return torch.as_tensor(_CudaView(s, (self.n_leaves, self.info.rec_stride), "<f4", self), device="cuda")
         t = torch.as_tensor(_CudaView(s, (self.n_leaves, self.info.rec_stride), "<i2", self), device="cuda")

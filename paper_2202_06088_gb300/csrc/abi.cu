@@ -3,6 +3,7 @@
 // contract of every entry point.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -187,7 +188,10 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
   if (d.K < 1 || d.K > 32) return fail(NEUVV_ERR_INVALID_ARG, "K must be in [1, 32]");
   if (d.T < 2) return fail(NEUVV_ERR_INVALID_ARG, "T must be >= 2");
   if (d.hh_degree < 1 || d.hh_degree > 3) return fail(NEUVV_ERR_INVALID_ARG, "hh_degree must be in [1, 3]");
-  if (d.dtype != NEUVV_F32 && d.dtype != NEUVV_BF16) return fail(NEUVV_ERR_INVALID_ARG, "unknown dtype");
+  if (d.dtype != NEUVV_F32 && d.dtype != NEUVV_BF16 && d.dtype != NEUVV_FP8_E4M3)
+    return fail(NEUVV_ERR_INVALID_ARG, "unknown dtype");
+  if (d.dtype == NEUVV_FP8_E4M3 && !((kpad_of(d.K) == 8 && d.hh_degree == 2) || (kpad_of(d.K) == 16 && d.hh_degree == 3)))
+    return fail(NEUVV_ERR_UNSUPPORTED, "FP8 storage is built for K <= 8 with degree 2 and 9 <= K <= 16 with degree 3");
   if (d.n_nodes < 1 || d.n_leaves < 0 || d.n_leaves >= 0x7FFFFFFF || d.n_nodes >= 0x7FFFFFFF)
     return fail(NEUVV_ERR_INVALID_ARG, "bad node/leaf counts");
   if (!d.child || !d.basis_A || !d.basis_B) return fail(NEUVV_ERR_INVALID_ARG, "child/basis pointer is NULL");
@@ -236,7 +240,9 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
   I.N_h = n_hh(d.hh_degree);
   I.rec_len = 2 * I.K_pad + 3 * I.N_h;
   I.rec_stride_f32 = (I.rec_len + 3) / 4 * 4;
-  I.rec_stride = d.dtype == NEUVV_F32 ? I.rec_stride_f32 : (I.rec_len + 7) / 8 * 8;
+  I.rec_stride = d.dtype == NEUVV_F32    ? I.rec_stride_f32
+                 : d.dtype == NEUVV_BF16 ? (I.rec_len + 7) / 8 * 8
+                                         : 16 + (I.rec_len + 15) / 16 * 16;  // FP8: bytes, scale header first
   I.dtype = d.dtype;
   I.n_nodes = d.n_nodes;
   I.n_leaves = d.n_leaves;
@@ -290,6 +296,31 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
     if (d.with_optimizer) {
       t->master = static_cast<float *>(t->rec);
       t->master_is_storage = true;
+    }
+  } else if (d.dtype == NEUVV_FP8_E4M3) {
+    // per leaf and group (w_sigma, w_gamma, w_hh): power-of-two scale, then
+    // one E4M3 code per entry, nearest with ties to even
+    const int sb = I.rec_stride;
+    std::vector<uint8_t> rec8(L * sb, 0);
+    for (size_t l = 0; l < L; ++l) {
+      const float *r = recf.data() + l * sf;
+      uint8_t *o = rec8.data() + l * sb;
+      const int lo[3] = {0, Kp, 2 * Kp}, hi[3] = {Kp, 2 * Kp, I.rec_len};
+      for (int g = 0; g < 3; ++g) {
+        float mx = 0.f;
+        for (int q = lo[g]; q < hi[g]; ++q) mx = std::max(mx, std::fabs(r[q]));
+        const int p = fp8_scale_exp(mx);
+        const float sc = std::ldexp(1.f, p);
+        std::memcpy(o + 4 * g, &sc, 4);
+        for (int q = lo[g]; q < hi[g]; ++q)
+          o[16 + q] = (uint8_t)__nv_cvt_float_to_fp8(std::ldexp(r[q], -p), __NV_SATFINITE, __NV_E4M3);
+      }
+    }
+    NEUVV_TRY(cudaMalloc(&t->rec, L * sb + 16), "cudaMalloc(records)");
+    if (L) NEUVV_TRY(cudaMemcpy(t->rec, rec8.data(), L * sb, cudaMemcpyHostToDevice), "copy records");
+    if (d.with_optimizer) {
+      NEUVV_TRY(cudaMalloc(&t->master, recf_bytes), "cudaMalloc(master)");
+      if (L) NEUVV_TRY(cudaMemcpy(t->master, recf.data(), L * sf * 4, cudaMemcpyHostToDevice), "copy master");
     }
   } else {
     const int sb = I.rec_stride;
@@ -639,7 +670,7 @@ neuvv_status neuvv_adam_step(neuvv_tree *t, float *grad, uint32_t *touched, floa
   const float c2 = (float)(1.0 - std::pow((double)b2, step));
   cudaError_t e = launch_adam(t->master, t->m, t->v, t->master_is_storage ? nullptr : t->rec, (DType)t->info.dtype,
                               t->info.rec_stride, grad, touched, t->info.n_leaves, t->info.rec_stride_f32,
-                              t->info.rec_len, lr, b1, b2, eps, c1, c2, st);
+                              t->info.rec_len, t->info.K_pad, lr, b1, b2, eps, c1, c2, st);
   if (e != cudaSuccess) return cuda_fail(e, "adam launch");
   e = cudaMemsetAsync(touched, 0, (size_t)((t->info.n_leaves + 31) / 32) * 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear touched");

@@ -180,7 +180,10 @@ static cudaError_t compose_dispatch(int KP, int DEG, const ComposeArgs &a, const
 
 cudaError_t launch_compose(int KP, int DEG, DType dt, const ComposeArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
   if (dt == kF32) return compose_dispatch<float>(KP, DEG, a, cfg, s);
-  return compose_dispatch<__nv_bfloat16>(KP, DEG, a, cfg, s);
+  if (dt == kBF16) return compose_dispatch<__nv_bfloat16>(KP, DEG, a, cfg, s);
+  if (KP == 8 && DEG == 2) return compose_one<8, 2, Fp8E4M3>(a, cfg, s);
+  if (KP == 16 && DEG == 3) return compose_one<16, 3, Fp8E4M3>(a, cfg, s);
+  return cudaErrorInvalidValue;
 }
 
 // Work counter for neuvv_compose_noalloc: file-scope device memory (one

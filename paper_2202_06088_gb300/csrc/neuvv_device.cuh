@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -429,6 +430,12 @@ __device__ __forceinline__ uint4 ldg_v4(const uint4 *p) {
   return r;
 }
 
+// FP8 storage (an ablation): E4M3 codes with power-of-two scales per leaf.
+// Record = 16-byte header {scale of w_sigma, of w_gamma, of w_hh, 0} as FP32,
+// then one code byte per entry of the FP32 layout, zero padded to 16 bytes;
+// rec_stride counts bytes.  Entry value = decoded code * scale of its group.
+struct Fp8E4M3 {};
+
 template <int KP, int DEG, typename E>
 struct LeafRecord {
   static constexpr int NH = n_hh(DEG);
@@ -456,6 +463,60 @@ struct LeafRecord {
   __device__ __forceinline__ float sig(int k) const { return w[k]; }
   __device__ __forceinline__ float gam(int k) const { return w[KP + k]; }
   __device__ __forceinline__ float hh(int ch, int i) const { return w[2 * KP + ch * NH + i]; }
+  __device__ __forceinline__ float scale_sigma() const { return 1.f; }
+  __device__ __forceinline__ float scale_gamma() const { return 1.f; }
+  __device__ __forceinline__ float scale_hh() const { return 1.f; }
+};
+
+// Exponent p of an FP8 group's scale 2^p: the smallest p with
+// max |w| <= 448 * 2^p, so that w / 2^p encodes without saturating (0 for an
+// all-zero group).  Host and device use this one rule.
+__host__ __device__ inline int fp8_scale_exp(float maxabs) {
+  if (!(maxabs > 0.f)) return 0;
+  int ex;
+  frexpf(maxabs, &ex);  // maxabs in [2^(ex-1), 2^ex); 448 * 2^(ex-9) = 0.875 * 2^ex
+  int p = ex - 9;
+  if (ldexpf(448.f, p) < maxabs) ++p;
+  return p;
+}
+
+template <int KP, int DEG>
+struct LeafRecord<KP, DEG, Fp8E4M3> {
+  static constexpr int NH = n_hh(DEG);
+  static constexpr int LEN = 2 * KP + 3 * NH;
+  static constexpr int NV = (LEN + 15) / 16;
+  uint4 raw[NV];  // codes, decoded where an entry is used
+  float sc[3];    // group scales (powers of two)
+
+  __device__ __forceinline__ void load(const DevTree &tr, uint32_t leaf) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(tr.rec) +
+                                                     (size_t)leaf * tr.rec_stride);
+    const uint4 h = ldg_v4(p);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) raw[i] = ldg_v4(p + 1 + i);
+    sc[0] = __uint_as_float(h.x);
+    sc[1] = __uint_as_float(h.y);
+    sc[2] = __uint_as_float(h.z);
+  }
+  // Entry j's code value, not yet scaled (j is a compile-time index once the
+  // callers' loops are unrolled).
+  __device__ __forceinline__ float code(int j) const {
+    const uint4 v = raw[j >> 4];
+    const int w = (j >> 2) & 3;
+    const unsigned int word = w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((word >> (16 * ((j >> 1) & 1))) & 0xFFFFu),
+                                                     __NV_E4M3);
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&h));
+    return (j & 1) ? f.y : f.x;
+  }
+  // The scale is a power of two, so applying it to a finished dot product
+  // gives the same FP32 result as scaling every entry first.
+  __device__ __forceinline__ float sig(int k) const { return code(k); }
+  __device__ __forceinline__ float gam(int k) const { return code(KP + k); }
+  __device__ __forceinline__ float hh(int ch, int i) const { return code(2 * KP + ch * NH + i); }
+  __device__ __forceinline__ float scale_sigma() const { return sc[0]; }
+  __device__ __forceinline__ float scale_gamma() const { return sc[1]; }
+  __device__ __forceinline__ float scale_hh() const { return sc[2]; }
 };
 
 // Per-ray constants: interpolated basis rows and the view-direction harmonics.
@@ -541,14 +602,14 @@ __device__ __forceinline__ void eval_sample(const DevTree &tr, const Rows &rows,
   float p4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < KP; ++k) p4[k & 3] = fmaf(rows.A(k), r.sig(k), p4[k & 3]);
-  const float ps = (p4[0] + p4[1]) + (p4[2] + p4[3]);
+  const float ps = ((p4[0] + p4[1]) + (p4[2] + p4[3])) * r.scale_sigma();
   s.pre_sigma = ps;
   s.sigma = fmaxf(ps, 0.f);
   if (!(s.sigma > 0.f)) return;
   float q4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < KP; ++k) q4[k & 3] = fmaf(rows.B(k), r.gam(k), q4[k & 3]);
-  const float pg = (q4[0] + q4[1]) + (q4[2] + q4[3]);
+  const float pg = ((q4[0] + q4[1]) + (q4[2] + q4[3])) * r.scale_gamma();
   s.s_gamma = sigmoidf_fast(pg);
   sincospif(s.s_gamma, &s.sg, &s.cg);
   float dR[(DEG + 1) * (DEG + 2) / 2];
@@ -566,6 +627,8 @@ __device__ __forceinline__ void eval_sample(const DevTree &tr, const Rows &rows,
         z = fmaf(acc, s.R[radial_index(n, l)], z);
         if (kDz) u = fmaf(acc, dR[radial_index(n, l)], u);
       }
+    z *= r.scale_hh();
+    if (kDz) u *= r.scale_hh();
     s.z[ch] = z;
     s.u[ch] = u;
     s.c[ch] = act == 0 ? sigmoidf_fast(z) : z;

@@ -7,7 +7,7 @@
 
 namespace neuvv {
 
-enum DType { kF32 = 0, kBF16 = 1 };
+enum DType { kF32 = 0, kBF16 = 1, kFP8 = 2 };
 
 struct LaunchCfg {
   int block;          // threads per block
@@ -85,8 +85,8 @@ cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
 // the current device (looked up on first use per device).
 cudaError_t noalloc_queue(unsigned long long **out);
 cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType dt, int storage_stride, float *grad,
-                        const unsigned int *touched, long long n_leaves, int stride_f32, int rec_len, float lr,
-                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
+                        const unsigned int *touched, long long n_leaves, int stride_f32, int rec_len, int kp,
+                        float lr, float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
 cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
                        cudaStream_t s);
 

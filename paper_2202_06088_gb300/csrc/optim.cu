@@ -2,7 +2,8 @@
 //   * mse_kernel  -- Eq. rgb-loss, sum ||C - C_gt||^2 (scaled) and dL/dC;
 //   * adam_kernel -- Adam restricted to leaves whose touched bit is set
 //     (sparse: other leaves keep weights and moments), FP32 master + moments,
-//     storage copy rewritten (BF16 rounded to nearest even), gradient rows of
+//     storage copy rewritten (BF16 rounded to nearest even, or FP8 E4M3 with
+//     fresh per-leaf scales), gradient rows of
 //     updated leaves reset to zero for the next step.
 #include "neuvv_kernels.h"
 
@@ -80,6 +81,82 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ master, f
   }
 }
 
+// FP8 storage: one warp per leaf.  The warp applies the same Adam update,
+// then takes the largest magnitude of each group (w_sigma, w_gamma, w_hh),
+// picks its power-of-two scale and re-encodes the whole record: header of
+// scales, then one E4M3 code (nearest, ties to even) per entry.
+__global__ void __launch_bounds__(256) adam_fp8_kernel(float *__restrict__ master, float *__restrict__ m,
+                                                       float *__restrict__ v, unsigned char *__restrict__ storage,
+                                                       int storage_stride, float *__restrict__ grad,
+                                                       const unsigned int *__restrict__ touched, long long n_leaves,
+                                                       int stride_f32, int rec_len, int kp, float lr, float b1,
+                                                       float b2, float eps, float c1, float c2) {
+  constexpr int kMaxRounds = 2;  // stride_f32 <= 256 floats (64 quads) per leaf
+  const int lane = threadIdx.x & 31;
+  const int quads = stride_f32 / 4;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long leaf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < n_leaves; leaf += nwarps) {
+    if (!((__ldg(touched + (leaf >> 5)) >> (leaf & 31)) & 1u)) continue;  // the same for the whole warp
+    float ws[kMaxRounds][4];
+    float mx[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < kMaxRounds; ++r) {
+      const int q = lane + 32 * r;
+      if (q >= quads) continue;
+      const size_t off = (size_t)leaf * stride_f32 + 4 * q;
+      const float4 g = *reinterpret_cast<const float4 *>(grad + off);
+      const float4 w = *reinterpret_cast<const float4 *>(master + off);
+      const float4 mm = *reinterpret_cast<const float4 *>(m + off);
+      const float4 vv = *reinterpret_cast<const float4 *>(v + off);
+      float gs[4] = {g.x, g.y, g.z, g.w}, ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+      ws[r][0] = w.x;
+      ws[r][1] = w.y;
+      ws[r][2] = w.z;
+      ws[r][3] = w.w;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = 4 * q + k;
+        if (j >= rec_len) continue;  // padding stays zero
+        ms[k] = b1 * ms[k] + (1.f - b1) * gs[k];
+        vs[k] = b2 * vs[k] + (1.f - b2) * gs[k] * gs[k];
+        ws[r][k] -= lr * (ms[k] / c1) / (sqrtf(vs[k] / c2) + eps);
+        const int grp = j < kp ? 0 : (j < 2 * kp ? 1 : 2);
+        mx[grp] = fmaxf(mx[grp], fabsf(ws[r][k]));
+      }
+      *reinterpret_cast<float4 *>(master + off) = make_float4(ws[r][0], ws[r][1], ws[r][2], ws[r][3]);
+      *reinterpret_cast<float4 *>(m + off) = make_float4(ms[0], ms[1], ms[2], ms[3]);
+      *reinterpret_cast<float4 *>(v + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+      *reinterpret_cast<float4 *>(grad + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    int p[3];
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx[g] = fmaxf(mx[g], __shfl_xor_sync(0xFFFFFFFFu, mx[g], o));
+      p[g] = fp8_scale_exp(mx[g]);
+    }
+    unsigned char *rec = storage + (size_t)leaf * storage_stride;
+    if (lane == 0)
+      *reinterpret_cast<uint4 *>(rec) = make_uint4(__float_as_uint(ldexpf(1.f, p[0])), __float_as_uint(ldexpf(1.f, p[1])),
+                                                   __float_as_uint(ldexpf(1.f, p[2])), 0u);
+#pragma unroll
+    for (int r = 0; r < kMaxRounds; ++r) {
+      const int q = lane + 32 * r;
+      if (q >= quads) continue;
+      unsigned int word = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = 4 * q + k;
+        if (j >= rec_len) continue;
+        const int grp = j < kp ? 0 : (j < 2 * kp ? 1 : 2);
+        const unsigned int code = __nv_cvt_float_to_fp8(ldexpf(ws[r][k], -p[grp]), __NV_SATFINITE, __NV_E4M3);
+        word |= code << (8 * k);
+      }
+      *reinterpret_cast<unsigned int *>(rec + 16 + 4 * q) = word;
+    }
+  }
+}
+
 cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
                        cudaStream_t s) {
   if (n == 0) return cudaSuccess;
@@ -90,9 +167,17 @@ cudaError_t launch_mse(const float *rgb, const float *target, long long n, float
 }
 
 cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType dt, int storage_stride, float *grad,
-                        const unsigned int *touched, long long n_leaves, int stride_f32, int rec_len, float lr,
-                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
+                        const unsigned int *touched, long long n_leaves, int stride_f32, int rec_len, int kp,
+                        float lr, float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
   if (n_leaves == 0) return cudaSuccess;
+  if (dt == kFP8) {
+    if (stride_f32 > 256 || !storage) return cudaErrorInvalidValue;
+    const long long want = (n_leaves * 32 + 255) / 256;
+    const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+    adam_fp8_kernel<<<blocks, 256, 0, s>>>(master, m, v, static_cast<unsigned char *>(storage), storage_stride, grad,
+                                           touched, n_leaves, stride_f32, rec_len, kp, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+  }
   const long long total = n_leaves * (stride_f32 / 4);
   const long long want = (total + 255) / 256;
   const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);

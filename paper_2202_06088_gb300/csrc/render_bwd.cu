@@ -243,7 +243,10 @@ static cudaError_t bwd_dispatch(int KP, int DEG, bool packet, const BwdArgs &a, 
 cudaError_t launch_render_bwd(int KP, int DEG, DType dt, bool packet, const BwdArgs &a, const LaunchCfg &cfg,
                               cudaStream_t s) {
   if (dt == kF32) return bwd_dispatch<float>(KP, DEG, packet, a, cfg, s);
-  return bwd_dispatch<__nv_bfloat16>(KP, DEG, packet, a, cfg, s);
+  if (dt == kBF16) return bwd_dispatch<__nv_bfloat16>(KP, DEG, packet, a, cfg, s);
+  if (KP == 8 && DEG == 2) return bwd_one<8, 2, Fp8E4M3>(packet, a, cfg, s);
+  if (KP == 16 && DEG == 3) return bwd_one<16, 3, Fp8E4M3>(packet, a, cfg, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace neuvv

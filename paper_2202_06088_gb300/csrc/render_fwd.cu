@@ -205,7 +205,11 @@ static cudaError_t fwd_dispatch(int KP, int DEG, bool packet, const FwdArgs &a, 
 cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdArgs &a, const LaunchCfg &cfg,
                               cudaStream_t s) {
   if (dt == kF32) return fwd_dispatch<float>(KP, DEG, packet, a, cfg, s);
-  return fwd_dispatch<__nv_bfloat16>(KP, DEG, packet, a, cfg, s);
+  if (dt == kBF16) return fwd_dispatch<__nv_bfloat16>(KP, DEG, packet, a, cfg, s);
+  // FP8 storage is built for the two record shapes of the workloads only
+  if (KP == 8 && DEG == 2) return fwd_one<8, 2, Fp8E4M3>(packet, a, cfg, s);
+  if (KP == 16 && DEG == 3) return fwd_one<16, 3, Fp8E4M3>(packet, a, cfg, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s) {

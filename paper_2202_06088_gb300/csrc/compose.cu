@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) compose_kernel(const __grid_constant__ Co
           for (int k = 0; k < 3; ++k)
             if (k == ax) pl[k] = dl[k] > 0.f ? tr.bmin[k] : tr.bmax[k];
           RayWalk w;
-          walk_start(tr, pl, dn, w);
+          const float zero[3] = {0.f, 0.f, 0.f};
+          walk_start(tr, pl, zero, dn, w);
           if (w.alive) {
             const float period = (float)(tr.T - 1);
             float u = fmodf(t * period + pp.toff, period);

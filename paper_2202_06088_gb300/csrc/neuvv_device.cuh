@@ -60,7 +60,18 @@ __device__ __forceinline__ void raise_status(const DevTree &tr, uint32_t bit) {
 // ---------------------------------------------------------------------------
 // Octree walk.  Grid space: the root box is [0, N]^3, N = 2^depth, finest
 // cells are unit cubes.  Positions are kept relative to the ray's entry into
-// the root box so that FP32 coordinates stay below N.  Decisions:
+// the root box so that FP32 coordinates stay below N.  Chords must be exact
+// to a few FP32 ulps of the chord itself (a thin corner clip of a leaf
+// weighs its gradient by its chord), so:
+//   * the entry point is carried as go + lo per axis, go a multiple of
+//     2^(depth-24) grid units, so that plane - go is exact for every cell
+//     plane x in [0, N];
+//   * a plane's distance (x - go) * inv - lo * inv is carried as an
+//     unevaluated sum hi + lo: the exact product of the exact gap with inv,
+//     minus the small per-axis constant lo * inv;
+//   * a chord is the difference of two such sums, so its error is relative to
+//     the chord, not to the distance from the entry.
+// Decisions:
 //   * exit axis = argmin of the three exit distances, exact ties x < y < z;
 //   * the next cell is one step across the exit face on that axis, and on the
 //     other axes the cell holding the exit point (a coordinate exactly on a
@@ -69,18 +80,30 @@ __device__ __forceinline__ void raise_status(const DevTree &tr, uint32_t bit) {
 // Every distance is along the unit direction, in world units.
 // ---------------------------------------------------------------------------
 struct RayWalk {
-  float go[3];     // grid position of the entry point
+  float go[3];     // grid position of the entry point (a multiple of 2^(depth-24))
   float gd[3];     // grid-space direction (unit world direction * scale)
   float inv[3];    // 1 / gd (inf when gd == 0)
-  float ngi[3];    // -go * inv: the exit distance of plane x is fma(x, inv, ngi)
+  float c[3];      // (exact entry - go) * inv: plane x lies at (x - go) * inv - c
   float t_base;    // world distance of the entry point from the origin
-  float t_cur;     // current distance past the entry point
+  float t_cur;     // current distance past the entry point (hi part)
+  float t_lo;      // its lo part (t_cur + t_lo: see the plane distances above)
   float t_far;     // exit distance of the root box past the entry point
   int cell[3];
   int steps, max_steps;
   int restart;     // level at which the next descent may start (0 = root)
   bool alive;
 };
+
+// Error-free transformations: s + e = a + b and p + e = a * b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
 
 __device__ __forceinline__ int cell_of(float p, float v, int N) {
   // the cell the ray occupies just after this instant: floor(p), or
@@ -117,21 +140,37 @@ __device__ __forceinline__ bool box_interval(const DevTree &tr, const float o[3]
   return hit && s_in < s_out;
 }
 
-// Starts the walk at point p of the tree's frame (inside the box; on the
-// entry face when the ray comes from outside) along the unit direction dn.
-__device__ __forceinline__ void walk_start(const DevTree &tr, const float p[3], const float dn[3], RayWalk &w) {
+// Starts the walk at point p + pl of the tree's frame (inside the box; on
+// the entry face when the ray comes from outside; pl the part of the point
+// below p's FP32 precision) along the unit direction dn.
+__device__ __forceinline__ void walk_start(const DevTree &tr, const float p[3], const float pl[3], const float dn[3],
+                                           RayWalk &w) {
   const int N = 1 << tr.depth;
+  const float q = ldexpf(1.f, tr.depth - 24), iq = ldexpf(1.f, 24 - tr.depth);
   float tf = INFINITY;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    w.go[a] = fminf(fmaxf((p[a] - tr.bmin[a]) * tr.scale[a], 0.f), (float)N);
+    // grid coordinate gh + gl = (p + pl - bmin) * scale, then split at q
+    float dh, dl, gh, ge;
+    two_sum(p[a], -tr.bmin[a], dh, dl);
+    two_prod(dh, tr.scale[a], gh, ge);
+    float gl = fmaf(dl + pl[a], tr.scale[a], ge);
+    if (!(gh > 0.f)) { gh = 0.f; gl = fmaxf(gl, 0.f); }
+    if (gh >= (float)N) { gh = (float)N; gl = fminf(gl, 0.f); }
+    const float go = rintf(gh * iq) * q;  // x - go is exact for integer x in [0, N]
+    const float lo = (gh - go) + gl;
+    w.go[a] = go;
     w.gd[a] = dn[a] * tr.scale[a];
     w.inv[a] = w.gd[a] != 0.f ? 1.f / w.gd[a] : INFINITY;
-    w.ngi[a] = w.gd[a] != 0.f ? -w.go[a] * w.inv[a] : 0.f;
-    w.cell[a] = cell_of(w.go[a], w.gd[a], N);
-    if (w.gd[a] != 0.f) tf = fminf(tf, ((w.gd[a] > 0.f ? (float)N : 0.f) - w.go[a]) * w.inv[a]);
+    w.c[a] = w.gd[a] != 0.f ? lo * w.inv[a] : 0.f;
+    // the cell the ray occupies just after the exact entry point
+    int cell = cell_of(go, w.gd[a], N);
+    if (go == floorf(go) && lo != 0.f) cell = (lo < 0.f ? (int)go - 1 : (int)go);
+    w.cell[a] = min(max(cell, 0), N - 1);
+    if (w.gd[a] != 0.f) tf = fminf(tf, ((w.gd[a] > 0.f ? (float)N : 0.f) - go) * w.inv[a] - w.c[a]);
   }
   w.t_cur = 0.f;
+  w.t_lo = 0.f;
   w.t_far = tf;
   w.restart = 0;
   w.steps = 0;
@@ -154,14 +193,42 @@ __device__ __forceinline__ bool walk_init(const DevTree &tr, const float o[3], c
   float s_in, s_out;
   int ax;
   if (!box_interval(tr, o, d, s_in, s_out, ax)) return false;
-  float p[3];
+  float p[3], pl[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) p[a] = fmaf(s_in, d[a], o[a]);
+  for (int a = 0; a < 3; ++a) {
+    p[a] = o[a];
+    pl[a] = 0.f;
+  }
+  if (ax >= 0) {
+    // entry parameter s = (face - o) / d on the entry axis as sh + sl, then
+    // each other coordinate o + s d as an unevaluated sum (error-free steps)
+    float f = tr.bmin[0], oa = o[0], da = d[0];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-    if (a == ax) p[a] = d[a] > 0.f ? tr.bmin[a] : tr.bmax[a];
+    for (int a = 1; a < 3; ++a)
+      if (a == ax) { f = tr.bmin[a]; oa = o[a]; da = d[a]; }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a == ax && d[a] < 0.f) f = tr.bmax[a];
+    float nh, nl;
+    two_sum(f, -oa, nh, nl);
+    const float sh = nh / da;
+    const float sl = (fmaf(-sh, da, nh) + nl) / da;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == ax) {
+        p[a] = f;
+      } else {
+        float ph, pe, sh2, se;
+        two_prod(sh, d[a], ph, pe);
+        two_sum(o[a], ph, sh2, se);
+        const float lo = fmaf(sl, d[a], se + pe);
+        p[a] = sh2 + lo;
+        pl[a] = lo - (p[a] - sh2);
+      }
+    }
+  }
   w.t_base = s_in * len;
-  walk_start(tr, p, dn, w);
+  walk_start(tr, p, pl, dn, w);
   return w.alive;
 }
 
@@ -233,13 +300,13 @@ __device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s
 }
 
 // One step of the walk: the tree cell holding the current finest cell, then
-// the move across its exit face.  Returns true (with leaf and [t0, t1],
-// distances past the entry point) when that cell is an occupied leaf crossed
-// with a positive chord.  Clears w.alive when the ray leaves the root box or
-// reaches its step cap.
+// the move across its exit face.  Returns true (with the leaf, the distance
+// t0 of the segment's start past the entry point and its chord dt) when that
+// cell is an occupied leaf crossed with a positive chord.  Clears w.alive when
+// the ray leaves the root box or reaches its step cap.
 template <bool kSmem, bool kPath = false>
 __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_child, RayWalk &w, uint32_t &leaf,
-                                          float &t0, float &t1, PathRef pr = PathRef{nullptr, 0}) {
+                                          float &t0, float &dt, PathRef pr = PathRef{nullptr, 0}) {
   const int N = 1 << tr.depth;
   if (++w.steps > w.max_steps) {
     raise_status(tr, kStatusSegCap);
@@ -251,32 +318,36 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
   const int shift = tr.depth - level;
   const int size = 1 << shift;
   int lo[3];
-  float tx[3];
+  float gap[3], tx[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     lo[a] = w.cell[a] & -size;
-    const float bnd = (float)(w.gd[a] > 0.f ? lo[a] + size : lo[a]);
-    tx[a] = w.gd[a] != 0.f ? fmaf(bnd, w.inv[a], w.ngi[a]) : INFINITY;
+    gap[a] = (float)(w.gd[a] > 0.f ? lo[a] + size : lo[a]) - w.go[a];  // exact
+    tx[a] = w.gd[a] != 0.f ? gap[a] * w.inv[a] : INFINITY;
   }
   // exit axis: first minimum (exact ties x < y < z); register-only selects
   int ax = 0;
-  float t_exit = tx[0];
-  if (tx[1] < t_exit) { ax = 1; t_exit = tx[1]; }
-  if (tx[2] < t_exit) { ax = 2; t_exit = tx[2]; }
-  const float seg_end = fminf(t_exit, w.t_far);
-  const float seg_start = w.t_cur;
+  float t_exit = tx[0], g_ax = gap[0], i_ax = w.inv[0], c_ax = w.c[0];
+  if (tx[1] < t_exit) { ax = 1; t_exit = tx[1]; g_ax = gap[1]; i_ax = w.inv[1]; c_ax = w.c[1]; }
+  if (tx[2] < t_exit) { ax = 2; t_exit = tx[2]; g_ax = gap[2]; i_ax = w.inv[2]; c_ax = w.c[2]; }
+  // the exit plane lies at t_exit + x_lo: the exact product gap * inv minus c
+  const float x_lo = fmaf(g_ax, i_ax, -t_exit) - c_ax;
+  const float chord = (t_exit - w.t_cur) + (x_lo - w.t_lo);
   bool found = false;
-  if (e != kEmpty && seg_end > seg_start) {
+  if (e != kEmpty && chord > 0.f) {
     leaf = e & ~kLeafBit;
-    t0 = seg_start;
-    t1 = seg_end;
+    t0 = w.t_cur;
+    dt = chord;
     found = true;
   }
   // step to the next cell
   if (t_exit >= w.t_far) {
     w.alive = false;
   } else {
-    w.t_cur = fmaxf(w.t_cur, t_exit);
+    if (chord > 0.f) {
+      w.t_cur = t_exit;
+      w.t_lo = x_lo;
+    }
     bool inside = true;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -300,9 +371,9 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
 // ray has left the root box (or hit its step cap).
 template <bool kSmem, bool kPath = false>
 __device__ __forceinline__ bool walk_next(const DevTree &tr, const uint32_t *s_child, RayWalk &w, uint32_t &leaf,
-                                          float &t0, float &t1, PathRef pr = PathRef{nullptr, 0}) {
+                                          float &t0, float &dt, PathRef pr = PathRef{nullptr, 0}) {
   while (w.alive)
-    if (walk_step<kSmem, kPath>(tr, s_child, w, leaf, t0, t1, pr)) return true;
+    if (walk_step<kSmem, kPath>(tr, s_child, w, leaf, t0, dt, pr)) return true;
   return false;
 }
 
@@ -544,6 +615,13 @@ __device__ __forceinline__ void ray_const_basis(const DevTree &tr, float u, RayC
 }
 
 __device__ __forceinline__ float sigmoidf_fast(float x) { return 1.f / (1.f + __expf(-x)); }
+
+// Opacity of a segment of optical depth sd, 1 - exp(-sd), without the
+// cancellation of 1 - expf(-sd) when sd is small (a thin or faint segment):
+// there 1 - expf(-sd) carries an absolute error of an FP32 ulp of 1, which is
+// a relative error of ~1e-7 / sd.  The transmittance factor exp(-sd) itself is
+// accurate relative to its value and keeps using expf.
+__device__ __forceinline__ float alpha_of(float sd) { return -expm1f(-sd); }
 
 // Evaluated sample: density, hyper-angle terms and colour of one leaf.
 template <int DEG>

@@ -27,22 +27,21 @@ __device__ __forceinline__ void integrate_walk(const DevTree &tr, const uint32_t
   sh_real<DEG>(dn, rc.Y);
   float T = 1.f;
   uint32_t leaf;
-  float t0, t1;
-  while (walk_next<kSmem>(tr, s_child, w, leaf, t0, t1)) {
+  float t0, dt;
+  while (walk_next<kSmem>(tr, s_child, w, leaf, t0, dt)) {
     LeafRecord<KP, DEG, E> rec;
     rec.load(tr, leaf);
     Sample<DEG> s;
     eval_sample<KP, DEG, E>(tr, rc, rec, act, s);
     res.nseg += 1;
     if (s.sigma > 0.f) {
-      const float delta = t1 - t0;
-      const float sd = s.sigma * delta;
+      const float sd = s.sigma * dt;
       const float e = __expf(-sd);
-      const float wgt = T * (1.f - e);
+      const float wgt = T * alpha_of(sd);
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) res.C[ch] = fmaf(wgt, s.c[ch], res.C[ch]);
       res.A += wgt;
-      res.dnum = fmaf(wgt, fmaf(dist_scale, 0.5f * (t0 + t1), t_base), res.dnum);
+      res.dnum = fmaf(wgt, fmaf(dist_scale, fmaf(0.5f, dt, t0), t_base), res.dnum);
       res.tau += sd;
       T *= e;
       if (T < t_stop) break;

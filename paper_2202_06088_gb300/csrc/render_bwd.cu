@@ -38,7 +38,7 @@ struct AdjState {
 // Gradient of one sample; scatters it into the leaf's FP32 record.
 template <int KP, int DEG, typename E, typename Rows>
 __device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &rows, const float *Y, uint32_t leaf,
-                                               float t0, float t1, AdjState &st) {
+                                               float dt, AdjState &st) {
   constexpr int NH = n_hh(DEG);
   const DevTree &tr = a.tr;
   LeafRecord<KP, DEG, E> rec;
@@ -46,9 +46,9 @@ __device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &row
   Sample<DEG> s;
   eval_sample<KP, DEG, E, Rows, true>(tr, rows, Y, rec, a.act, s);
   if (!(s.sigma > 0.f)) return;  // alpha = 0: no path from this sample to L
-  const float delta = t1 - t0;
-  const float e = __expf(-s.sigma * delta);
-  const float wgt = st.T * (1.f - e);
+  const float sd = s.sigma * dt;
+  const float e = __expf(-sd);
+  const float wgt = st.T * alpha_of(sd);
   const float Tn = st.T * e;
   float dsig = st.gA * st.T_final;
   float dz[3];
@@ -60,7 +60,7 @@ __device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &row
     const float dc = wgt * st.g[ch];
     dz[ch] = a.act == 0 ? dc * s.c[ch] * (1.f - s.c[ch]) : dc;
   }
-  dsig *= delta;
+  dsig *= dt;
   st.T = Tn;
   float *dst = a.grad + (size_t)leaf * a.grad_stride;
   // dL/dw_HH[ch][idx] = dz[ch] H_idx, in record order (channel, then idx
@@ -137,10 +137,10 @@ __global__ void __launch_bounds__(256) render_bwd_plain_kernel(const __grid_cons
   ray_const_basis<KP, DEG>(a.tr, t * (float)(a.tr.T - 1), rc);
   sh_real<DEG>(dn, rc.Y);
   uint32_t leaf;
-  float t0, t1;
-  while (st.count < st.target && walk_next<false>(a.tr, nullptr, w, leaf, t0, t1)) {
+  float t0, dt;
+  while (st.count < st.target && walk_next<false>(a.tr, nullptr, w, leaf, t0, dt)) {
     ++st.count;
-    adjoint_sample<KP, DEG, E>(a, RegRows<KP>{rc.a, rc.b}, rc.Y, leaf, t0, t1, st);
+    adjoint_sample<KP, DEG, E>(a, RegRows<KP>{rc.a, rc.b}, rc.Y, leaf, dt, st);
   }
 }
 
@@ -156,8 +156,7 @@ __global__ void __launch_bounds__(256, 2) render_bwd_packet_kernel(const __grid_
   float *my_rows = reinterpret_cast<float *>(smem) + tid;
   const PathRef pr{smem + 2 * KP * B + tid, B};
   uint32_t *q_leaf = smem + (2 * KP + 16) * B + tid;
-  float *q_t0 = reinterpret_cast<float *>(q_leaf + queue * B);
-  float *q_t1 = q_t0 + queue * B;
+  float *q_dt = reinterpret_cast<float *>(q_leaf + queue * B);
   const SmemRows<KP> rows{my_rows, B};
   const long long i = (long long)blockIdx.x * B + tid;
   const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
@@ -179,12 +178,11 @@ __global__ void __launch_bounds__(256, 2) render_bwd_packet_kernel(const __grid_
   for (;;) {
     if (walking && qn < queue) {
       uint32_t leaf;
-      float t0, t1;
-      if (walk_step<false, true>(tr, nullptr, w, leaf, t0, t1, pr)) {
+      float t0, dt;
+      if (walk_step<false, true>(tr, nullptr, w, leaf, t0, dt, pr)) {
         const int slot = (qh + qn) & qmask;
         q_leaf[slot * B] = leaf;
-        q_t0[slot * B] = t0;
-        q_t1[slot * B] = t1;
+        q_dt[slot * B] = dt;
         ++qn;
         ++walked;
       }
@@ -197,11 +195,11 @@ __global__ void __launch_bounds__(256, 2) render_bwd_packet_kernel(const __grid_
     if (stepping && __popc(have) < min(ready, active)) continue;
     if (qn > 0) {
       const uint32_t leaf = q_leaf[qh * B];
-      const float t0 = q_t0[qh * B], t1 = q_t1[qh * B];
+      const float dt = q_dt[qh * B];
       qh = (qh + 1) & qmask;
       --qn;
       ++st.count;
-      adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, t0, t1, st);
+      adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, dt, st);
     }
   }
 }

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constan
   const PathRef pr{smem + 2 * KP * B + tid, B};
   uint32_t *q_leaf = smem + (2 * KP + 16) * B + tid;
   float *q_t0 = reinterpret_cast<float *>(q_leaf + queue * B);
-  float *q_t1 = q_t0 + queue * B;
+  float *q_dt = q_t0 + queue * B;
   const SmemRows<KP> rows{my_rows, B};
   const long long i = (long long)blockIdx.x * B + tid;
   // lanes past the end leave now; the others stay to the end of the loop
@@ -83,12 +83,12 @@ __global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constan
   for (;;) {
     if (walking && qn < queue) {
       uint32_t leaf;
-      float t0, t1;
-      if (walk_step<false, true>(tr, nullptr, w, leaf, t0, t1, pr)) {
+      float t0, dt;
+      if (walk_step<false, true>(tr, nullptr, w, leaf, t0, dt, pr)) {
         const int slot = (qh + qn) & qmask;
         q_leaf[slot * B] = leaf;
         q_t0[slot * B] = t0;
-        q_t1[slot * B] = t1;
+        q_dt[slot * B] = dt;
         ++qn;
       }
       walking = w.alive;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constan
     if (stepping && __popc(have) < min(ready, active)) continue;
     if (qn > 0) {
       const uint32_t leaf = q_leaf[qh * B];
-      const float t0 = q_t0[qh * B], t1 = q_t1[qh * B];
+      const float t0 = q_t0[qh * B], dt = q_dt[qh * B];
       qh = (qh + 1) & qmask;
       --qn;
       LeafRecord<KP, DEG, E> rec;
@@ -109,15 +109,14 @@ __global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constan
       eval_sample<KP, DEG, E>(tr, rows, Y, rec, a.act, s);
       ++nseg;
       if (s.sigma > 0.f) {
-        const float delta = t1 - t0;
-        const float sd = s.sigma * delta;
+        const float sd = s.sigma * dt;
         const float e = __expf(-sd);
-        const float wgt = T * (1.f - e);
+        const float wgt = T * alpha_of(sd);
         C0 = fmaf(wgt, s.c[0], C0);
         C1 = fmaf(wgt, s.c[1], C1);
         C2 = fmaf(wgt, s.c[2], C2);
         A += wgt;
-        dnum = fmaf(wgt, w.t_base + 0.5f * (t0 + t1), dnum);
+        dnum = fmaf(wgt, w.t_base + fmaf(0.5f, dt, t0), dnum);
         tau += sd;
         T *= e;
         if (T < a.t_stop) {  // early termination: drop what is still queued
@@ -147,12 +146,12 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
   int c = 0;
   if (walk_init(a.tr, o, d, w, dn)) {
     uint32_t leaf;
-    float t0, t1;
-    while (walk_next<false>(a.tr, nullptr, w, leaf, t0, t1)) {
+    float t0, dt;
+    while (walk_next<false>(a.tr, nullptr, w, leaf, t0, dt)) {
       if (c < a.max_out) {
         a.leaf[i * a.max_out + c] = (int)leaf;
         a.t0[i * a.max_out + c] = w.t_base + t0;
-        a.t1[i * a.max_out + c] = w.t_base + t1;
+        a.t1[i * a.max_out + c] = w.t_base + (t0 + dt);
       }
       ++c;
     }

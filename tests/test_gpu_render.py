@@ -52,6 +52,13 @@ def _ambiguous_stop(ref, t_stop=1e-4):
     return ref["stop_margin"] < 1e-3
 
 
+def _explainer(B, tree, tree_d, rays):
+    """Rays whose composited-segment counts differ must owe it to a near-tie
+    cell (chord below 1e-3 of a finest cell) on one side (the traversal
+    reading); returns the rays that do not."""
+    return lambda idx: nseg_mismatch_explained(B, tree, tree_d, rays, idx)
+
+
 def _check_render(ref, got, tol, stop_ok=None, explain=None):
     """explain(idx) -> unexplained subset of rays whose segment counts differ."""
     assert np.abs(got["rgb"] - ref["rgb"]).max() <= tol, np.abs(got["rgb"] - ref["rgb"]).max()
@@ -97,7 +104,7 @@ def test_render_fp32_matches_oracle_c1(B, c1, c1_rays, kernel):
     tree_d = B.Tree(c1, "f32")
     ref = oracle.render(c1, c1_rays)
     got = _render(B, tree_d, c1_rays, kernel)
-    _check_render(ref, got, 1e-4, _ambiguous_stop(ref))
+    _check_render(ref, got, 1e-4, _ambiguous_stop(ref), _explainer(B, c1, tree_d, c1_rays))
     assert tree_d.status() == 0
 
 
@@ -110,7 +117,7 @@ def test_render_bf16_against_unrounded_and_rounded_oracle(B, c1, c1_rays):
     assert psnr(got["rgb"], ref["rgb"]) >= 50.0
     rounded = c1.with_coeffs(oracle.round_bf16(c1.w_sigma), oracle.round_bf16(c1.w_gamma), oracle.round_bf16(c1.w_hh))
     ref_q = oracle.render(rounded, c1_rays)
-    _check_render(ref_q, got, 1e-4, _ambiguous_stop(ref_q))
+    _check_render(ref_q, got, 1e-4, _ambiguous_stop(ref_q), _explainer(B, rounded, B.Tree(rounded, "f32"), c1_rays))
 
 
 @pytest.mark.parametrize("K,deg", [(4, 1), (16, 3), (31, 2)])
@@ -124,8 +131,10 @@ def test_render_other_shapes_and_identity_activation(B, K, deg):
     for act in ("sigmoid", "identity"):
         ref = oracle.render(tree, rays, act=act)
         for kernel in ("plain", "packet"):
-            got = _render(B, B.Tree(tree, "f32"), rays, kernel, act=act)
-            _check_render(ref, got, 1e-4 if act == "sigmoid" else 3e-4, _ambiguous_stop(ref))
+            td = B.Tree(tree, "f32")
+            got = _render(B, td, rays, kernel, act=act)
+            _check_render(ref, got, 1e-4 if act == "sigmoid" else 3e-4, _ambiguous_stop(ref),
+                          _explainer(B, tree, td, rays))
 
 
 def test_render_edge_cases(B, c1):
@@ -151,6 +160,6 @@ def test_render_stops_early_and_respects_t_stop_zero(B, c1, c1_rays):
     tree_d = B.Tree(c1, "f32")
     ref0 = oracle.render(c1, c1_rays, t_stop=0.0)
     got0 = _render(B, tree_d, c1_rays, "packet", t_stop=0.0)
-    _check_render(ref0, got0, 1e-4)
+    _check_render(ref0, got0, 1e-4, None, _explainer(B, c1, tree_d, c1_rays))
     got = _render(B, tree_d, c1_rays, "packet")
     assert (got["nseg"] <= got0["nseg"]).all() and (got["nseg"] < got0["nseg"]).any()

@@ -89,7 +89,7 @@ struct neuvv_tree {
   float hh_norm[16];
   int num_sms = 0;
   LaunchCfg plain{128, 1, 1, 0, 0, 0};
-  LaunchCfg packet{64, 8, 16, 0, 0, 0};
+  LaunchCfg packet{64, 8, 16, 0, 1, 0};
   LaunchCfg compose{128, 1, 1, 0, 1, 0};
 };
 
@@ -434,6 +434,7 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   a.act = opts->color_act;
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
+  a.work = packet && cfg.dynamic_queue ? t->work + 0 : nullptr;
   cudaError_t e = launch_render_fwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   return NEUVV_OK;
@@ -750,7 +751,7 @@ neuvv_status neuvv_autotune(neuvv_tree *t, const neuvv_rays *sample, float time,
   struct Cand { int block, queue, ready; };
   const Cand cands[] = {{64, 8, 16}, {64, 1, 1}, {64, 4, 8}, {128, 8, 16}, {128, 1, 1}, {32, 8, 16}, {64, 16, 16}};
   for (const Cand &c : cands) {
-    t->packet = LaunchCfg{c.block, c.queue, c.ready, 0, 0, saved.num_sms};
+    t->packet = LaunchCfg{c.block, c.queue, c.ready, 0, 1, saved.num_sms};
     float ms_best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(ev0, st);

@@ -14,7 +14,8 @@ struct LaunchCfg {
   int queue;          // packet kernels: per-lane queue of found leaf segments (power of 2, <= kMaxQueue)
   int ready;          // packet kernels: lanes with a queued segment that trigger a shading round
   int grid;           // compose: persistent blocks (0 = as many as fit, from the occupancy API)
-  int dynamic_queue;  // compose: 1 = warps pull packets from a counter, 0 = static stride
+  int dynamic_queue;  // compose and the packet forward: 1 = persistent warps pull 32-ray
+                      // packets from a counter, 0 = one packet per warp of the grid
   int num_sms;        // multiprocessors of the device
 };
 
@@ -24,6 +25,7 @@ struct FwdArgs {
   DevOut out;
   float t_stop;
   int act;
+  unsigned long long *work;  // packet counter of persistent warps (null: one packet per warp)
 };
 
 struct BwdArgs {
@@ -97,6 +99,11 @@ inline size_t smem_bytes(int block, int KP, int queue) {
   return (size_t)block * (2 * KP + 16 + 3 * queue) * sizeof(float);
 }
 constexpr int kMaxQueue = 32;
+// Packet kernels are latency bound: two 256-thread blocks per SM (128
+// registers a thread) keep enough warps resident; FP32 records need the
+// registers of one block per SM instead.
+template <typename E>
+constexpr int packet_min_blocks() { return sizeof(E) == 4 ? 1 : 2; }
 constexpr int kMaxDepth = 14;
 
 }  // namespace neuvv

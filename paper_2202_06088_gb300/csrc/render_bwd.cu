@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) render_bwd_plain_kernel(const __grid_cons
 // walk steps and sample rounds decoupled through a per-lane queue), the walk
 // stopped at the forward's segment count.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256, 2) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a, int queue,
+__global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a, int queue,
                                                                 int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;

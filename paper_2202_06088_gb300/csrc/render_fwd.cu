@@ -50,7 +50,7 @@ __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
 // cells (path per thread in shared memory); basis rows and the queue live in
 // shared memory too.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constant__ FwdArgs a, int queue, int ready) {
+__device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, unsigned present, int queue, int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
   const int B = blockDim.x, tid = threadIdx.x;
@@ -60,10 +60,6 @@ __global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constan
   float *q_t0 = reinterpret_cast<float *>(q_leaf + queue * B);
   float *q_dt = q_t0 + queue * B;
   const SmemRows<KP> rows{my_rows, B};
-  const long long i = (long long)blockIdx.x * B + tid;
-  // lanes past the end leave now; the others stay to the end of the loop
-  const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
-  if (i >= a.rays.n) return;
   float o[3], d[3], t, dn[3];
   load_ray(a.rays, i, o, d, t);
   RayWalk w;
@@ -136,6 +132,34 @@ __global__ void __launch_bounds__(256) render_packet_kernel(const __grid_constan
   if (a.out.nseg) a.out.nseg[i] = nseg;
 }
 
+// Packet forward kernel.  With a work counter the grid is persistent: each
+// warp takes the next 32-ray packet from the counter when it finishes one, so
+// a long ray holds up only its own warp, not the other warps of its block.
+template <int KP, int DEG, typename E>
+__global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_kernel(const __grid_constant__ FwdArgs a, int queue, int ready) {
+  // one packet per warp of the grid, or (with a work counter) packets pulled
+  // one after another until the counter passes the last
+  const int lane = threadIdx.x & 31;
+  const long long n_packets = (a.rays.n + 31) >> 5;
+  long long pk = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (a.work) {
+    unsigned long long q = 0;
+    if (lane == 0) q = atomicAdd(a.work, 1ull);
+    pk = (long long)__shfl_sync(0xFFFFFFFFu, q, 0);
+  }
+  while (pk < n_packets) {
+    const long long i = (pk << 5) + lane;
+    // lanes past the end sit the packet out; the others stay to its end
+    const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
+    if (i < a.rays.n) packet_forward<KP, DEG, E>(a, i, present, queue, ready);
+    __syncwarp();
+    if (!a.work) break;
+    unsigned long long q = 0;
+    if (lane == 0) q = atomicAdd(a.work, 1ull);
+    pk = (long long)__shfl_sync(0xFFFFFFFFu, q, 0);
+  }
+}
+
 __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceArgs a) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.rays.n) return;
@@ -177,7 +201,19 @@ static cudaError_t fwd_one(bool packet, const FwdArgs &a, const LaunchCfg &cfg, 
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
     }
-    render_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
+    if (!a.work) {
+      render_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
+    } else {
+      int per_sm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_packet_kernel<KP, DEG, E>,
+                                                                    cfg.block, sm);
+      if (e != cudaSuccess) return e;
+      const long long want = (long long)(per_sm > 0 ? per_sm : 1) * cfg.num_sms;
+      e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
+      if (e != cudaSuccess) return e;
+      render_packet_kernel<KP, DEG, E><<<(unsigned)(want < blocks ? want : blocks), cfg.block, sm, s>>>(
+          a, cfg.queue, cfg.ready);
+    }
   }
   return cudaGetLastError();
 }

@@ -245,7 +245,7 @@ def profile_case(args, B, tree, dr):
     tree_d = B.Tree(tree, "bf16", with_optimizer=args.profile_kernel == "adam")
     if args.launch:
         tree_d.set_launch(*[int(x) for x in args.launch.split(",")])
-    out = B.neuvv_render(tree_d, dr, kernel="packet")
+    out = B.neuvv_render(tree_d, dr, kernel="packet", out=B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=64))
     grad_rgb = torch.randn(dr.n, 3, device=dr.o.device) * 1e-3
     grad = tree_d.new_grad()
     touched = tree_d.new_touched()
@@ -298,7 +298,7 @@ def main():
     launch = {"block": tree_d.info.packet_block, "queue": tree_d.info.packet_queue,
               "ready": tree_d.info.packet_ready,
               "autotuned": not args.no_autotune}
-    out = B.alloc_out(n, dev)
+    out = B.alloc_out(n, dev, log_bytes_per_ray=64)
     grad_rgb = torch.empty(n, 3, device=dev)
     grad = tree_d.new_grad()
     touched = tree_d.new_touched()

@@ -134,10 +134,20 @@ typedef struct {
 
 /* Per-ray outputs, device, caller-owned.  rgb: [n][3]; alpha, depth, tau: [n];
  * nseg: [n] segments composited (needed by the backward pass).  Any member may
- * be NULL except where a call says otherwise. */
+ * be NULL except where a call says otherwise.
+ * log, log_bytes: optional device buffer (16-byte aligned) in which the packet
+ * forward records, per 32-ray packet, the leaf and chord of every segment it
+ * composites, in shading order; neuvv_render_backward given the same saved
+ * outputs replays a packet from the log instead of walking the tree again.
+ * The layout is private to the library.  A packet whose segments do not fit
+ * is marked and replayed by walking, so any size (including 0) is correct;
+ * about 64 bytes per ray holds the segments of a typical batch.  Other calls
+ * (plain forward, compose) mark the log empty. */
 typedef struct {
   float *rgb, *alpha, *depth, *tau;
   int32_t *nseg;
+  void *log;
+  int64_t log_bytes;
 } neuvv_out;
 
 typedef enum { NEUVV_ACT_SIGMOID = 0, NEUVV_ACT_IDENTITY = 1 } neuvv_color_act;

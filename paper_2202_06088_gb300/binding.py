@@ -59,7 +59,8 @@ class RaysC(ctypes.Structure):
 
 class OutC(ctypes.Structure):
     _fields_ = [("rgb", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("depth", ctypes.c_void_p),
-                ("tau", ctypes.c_void_p), ("nseg", ctypes.c_void_p)]
+                ("tau", ctypes.c_void_p), ("nseg", ctypes.c_void_p), ("log", ctypes.c_void_p),
+                ("log_bytes", ctypes.c_int64)]
 
 
 class OptsC(ctypes.Structure):
@@ -262,14 +263,21 @@ def _opts(t_stop=1e-4, act="sigmoid", kernel="auto", mode="sorted") -> OptsC:
     return OptsC(float(t_stop), _ACT[act], _KERNEL[kernel], _MODE[mode])
 
 
-def alloc_out(n: int, device="cuda") -> dict:
-    return {"rgb": torch.empty(n, 3, device=device), "alpha": torch.empty(n, device=device),
-            "depth": torch.empty(n, device=device), "tau": torch.empty(n, device=device),
-            "nseg": torch.empty(n, device=device, dtype=torch.int32)}
+def alloc_out(n: int, device="cuda", log_bytes_per_ray: int = 0) -> dict:
+    """Output tensors of a render; with log_bytes_per_ray > 0 also a segment log
+    (lets the backward replay the forward's segments instead of walking)."""
+    out = {"rgb": torch.empty(n, 3, device=device), "alpha": torch.empty(n, device=device),
+           "depth": torch.empty(n, device=device), "tau": torch.empty(n, device=device),
+           "nseg": torch.empty(n, device=device, dtype=torch.int32)}
+    if log_bytes_per_ray > 0:
+        out["log"] = torch.empty((n * log_bytes_per_ray + 1023) // 16 * 16 // 4 + 64, device=device, dtype=torch.int32)
+    return out
 
 
 def _outc(out: dict) -> OutC:
-    return OutC(*[None if out.get(k) is None else out[k].data_ptr() for k in ("rgb", "alpha", "depth", "tau", "nseg")])
+    ptrs = [None if out.get(k) is None else out[k].data_ptr() for k in ("rgb", "alpha", "depth", "tau", "nseg")]
+    log = out.get("log")
+    return OutC(*ptrs, None if log is None else log.data_ptr(), 0 if log is None else log.numel() * log.element_size())
 
 
 def neuvv_render(tree: Tree, rays: DeviceRays, t: float = 0.0, t_stop: float = 1e-4, act: str = "sigmoid",
@@ -367,8 +375,10 @@ class VOctreeRender(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, coeffs, tree, rays, t, t_stop, act):
-        out = neuvv_render(tree, rays, t=t, t_stop=t_stop, act=act)
+        out = neuvv_render(tree, rays, t=t, t_stop=t_stop, act=act,
+                           out=alloc_out(rays.n, rays.o.device, log_bytes_per_ray=64))
         ctx.tree, ctx.rays, ctx.t, ctx.t_stop, ctx.act = tree, rays, t, t_stop, act
+        ctx.log = out["log"]
         ctx.save_for_backward(out["rgb"], out["tau"], out["nseg"])
         ctx.mark_non_differentiable(out["depth"])
         return out["rgb"], out["alpha"], out["depth"]
@@ -376,7 +386,7 @@ class VOctreeRender(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_rgb, grad_alpha, grad_depth):
         rgb, tau, nseg = ctx.saved_tensors
-        saved = {"rgb": rgb, "tau": tau, "nseg": nseg}
+        saved = {"rgb": rgb, "tau": tau, "nseg": nseg, "log": ctx.log}
         g = neuvv_render_backward(ctx.tree, ctx.rays, saved, grad_rgb.contiguous(),
                                   None if grad_alpha is None else grad_alpha.contiguous(), t=ctx.t,
                                   t_stop=ctx.t_stop, act=ctx.act)

@@ -136,6 +136,45 @@ DevRays dev_rays(const neuvv_rays *r, float t) {
   return d;
 }
 
+// Device view of a caller's segment log buffer (layout private to the
+// library): 64-byte header, heads [n_packets], next [n_chunks], then leaf and
+// chord planes of n_chunks x kLogRounds x 32 entries.  n_chunks = 0 when the
+// buffer is absent or too small for one chunk.
+SampleLog log_view(void *base, int64_t bytes, int64_t n_rays) {
+  SampleLog l;
+  std::memset(&l, 0, sizeof l);
+  if (!base || bytes < 64) return l;
+  char *p = static_cast<char *>(base);
+  l.counter = reinterpret_cast<unsigned long long *>(p);
+  l.header = reinterpret_cast<uint32_t *>(p + 8);
+  const int64_t n_packets = (n_rays + 31) / 32;
+  const int64_t heads_bytes = (4 * n_packets + 15) / 16 * 16;
+  const int64_t per_chunk = 4 + (int64_t)kLogRounds * 32 * 8;
+  const int64_t avail = bytes - 64 - heads_bytes - 16;
+  if (avail < per_chunk) return l;
+  int64_t nc = avail / per_chunk;
+  if (nc > (int64_t)0x7FFFFFFF) nc = 0x7FFFFFFF;
+  l.heads = reinterpret_cast<uint32_t *>(p + 64);
+  l.next = reinterpret_cast<uint32_t *>(p + 64 + heads_bytes);
+  const int64_t leaf_off = (64 + heads_bytes + 4 * nc + 15) / 16 * 16;
+  l.leaf = reinterpret_cast<uint32_t *>(p + leaf_off);
+  l.dt = reinterpret_cast<float *>(p + leaf_off + nc * kLogRounds * 32 * 4);
+  l.n_chunks = (uint32_t)nc;
+  return l;
+}
+
+neuvv_status check_log(const neuvv_out *out) {
+  if (out && out->log && (((uintptr_t)out->log & 15) != 0 || out->log_bytes < 0))
+    return fail(NEUVV_ERR_INVALID_ARG, "out->log must be 16-byte aligned with log_bytes >= 0");
+  return NEUVV_OK;
+}
+
+// Marks a caller's log empty (a call that does not fill it).
+cudaError_t clear_log(const neuvv_out *out, cudaStream_t st) {
+  if (!out || !out->log || out->log_bytes < 64) return cudaSuccess;
+  return cudaMemsetAsync(static_cast<char *>(out->log) + 8, 0, 24, st);
+}
+
 neuvv_status check_opts(const neuvv_render_opts *o) {
   if (!o) return fail(NEUVV_ERR_INVALID_ARG, "opts is NULL");
   if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "t_stop must be in [0, 1)");
@@ -423,6 +462,7 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
     return s;
   if (!out || (rays->n > 0 && (!out->rgb || !out->alpha)))
     return fail(NEUVV_ERR_INVALID_ARG, "out->rgb and out->alpha are required");
+  if ((s = check_log(out)) != NEUVV_OK) return s;
   if (rays->n == 0) return NEUVV_OK;
   DeviceGuard g(t->info.device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -435,7 +475,15 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
   a.work = packet && cfg.dynamic_queue ? t->work + 0 : nullptr;
-  cudaError_t e = launch_render_fwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
+  a.log = packet ? log_view(out->log, out->log_bytes, rays->n) : log_view(nullptr, 0, 0);
+  cudaError_t e;
+  if (a.log.n_chunks) {
+    e = cudaMemsetAsync(a.log.counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "reset log");
+  } else if ((e = clear_log(out, st)) != cudaSuccess) {
+    return cuda_fail(e, "clear log");
+  }
+  e = launch_render_fwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   return NEUVV_OK;
 }
@@ -450,6 +498,7 @@ neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, 
   if (rays->n == 0) return NEUVV_OK;
   if (!saved || !saved->rgb || !saved->tau || !saved->nseg)
     return fail(NEUVV_ERR_INVALID_ARG, "saved rgb, tau and nseg are required");
+  if ((s = check_log(saved)) != NEUVV_OK) return s;
   if (!grad_rgb || !grad) return fail(NEUVV_ERR_INVALID_ARG, "grad_rgb and grad are required");
   if (((uintptr_t)grad & 15) != 0) return fail(NEUVV_ERR_INVALID_ARG, "grad must be 16-byte aligned");
   DeviceGuard g(t->info.device);
@@ -467,6 +516,7 @@ neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, 
   a.touched = touched;
   a.t_stop = opts->t_stop;
   a.act = opts->color_act;
+  a.log = log_view(saved->log, saved->log_bytes, rays->n);
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
   cudaError_t e = launch_render_bwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
@@ -558,7 +608,9 @@ neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transfor
     cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "reset work counter");
   }
-  cudaError_t e = launch_compose(t0->info.K_pad, t0->info.hh_degree, (DType)t0->info.dtype, a, cfg, st);
+  cudaError_t e = clear_log(out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear log");
+  e = launch_compose(t0->info.K_pad, t0->info.hh_degree, (DType)t0->info.dtype, a, cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "compose launch");
   return NEUVV_OK;
 }
@@ -651,6 +703,7 @@ neuvv_status neuvv_compose_noalloc(const neuvv_tree *const *trees, const float *
   if (e != cudaSuccess) return cuda_fail(e, "neuvv_compose_noalloc: reset counter");
   LaunchCfg cfg = t0->compose;
   cfg.dynamic_queue = 1;
+  if ((e = clear_log(out, st)) != cudaSuccess) return cuda_fail(e, "clear log");
   e = launch_compose(t0->info.K_pad, t0->info.hh_degree, (DType)t0->info.dtype, a, cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "compose launch");
   return NEUVV_OK;

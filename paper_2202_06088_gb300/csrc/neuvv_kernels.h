@@ -19,6 +19,24 @@ struct LaunchCfg {
   int num_sms;        // multiprocessors of the device
 };
 
+// Segment log of the packet forward (device view of neuvv_out.log).  Chunks
+// of kLogRounds shading rounds x 32 lanes hold (leaf, chord) per lane, kEmpty
+// for a lane that shaded nothing in that round; a packet's chunks are linked
+// from heads[packet] through next[].  heads[packet] = kNoLog: not logged
+// (replay by walking).  Header: chunk counter (u64), then n_chunks, rounds,
+// n_rays (i64) and a valid word, all written by the forward that fills it.
+constexpr int kLogRounds = 8;
+constexpr uint32_t kNoLog = 0xFFFFFFFFu;
+struct SampleLog {
+  unsigned long long *counter;
+  uint32_t *header;   // [0] n_chunks, [1] rounds, [2..3] n_rays, [4] valid
+  uint32_t *heads;    // [n_packets]
+  uint32_t *next;     // [n_chunks]
+  uint32_t *leaf;     // [n_chunks][kLogRounds][32]
+  float *dt;          // [n_chunks][kLogRounds][32]
+  uint32_t n_chunks;  // 0: no log
+};
+
 struct FwdArgs {
   DevTree tr;
   DevRays rays;
@@ -26,6 +44,7 @@ struct FwdArgs {
   float t_stop;
   int act;
   unsigned long long *work;  // packet counter of persistent warps (null: one packet per warp)
+  SampleLog log;             // segments to record (n_chunks == 0: none)
 };
 
 struct BwdArgs {
@@ -41,6 +60,7 @@ struct BwdArgs {
   unsigned int *touched;  // bitmap or null
   float t_stop;
   int act;
+  SampleLog log;          // the forward's segment log (n_chunks == 0: walk every packet)
 };
 
 constexpr int kMaxPrims = 16;

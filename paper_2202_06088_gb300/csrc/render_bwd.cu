@@ -103,6 +103,12 @@ __device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &row
   }
 }
 
+// Whether a segment log was written by a forward over these rays.
+__device__ __forceinline__ bool log_matches(const SampleLog &l, long long n) {
+  return __ldg(l.header + 4) == 1u && __ldg(l.header) == l.n_chunks && __ldg(l.header + 1) == (uint32_t)kLogRounds &&
+         __ldg(l.header + 2) == (uint32_t)(n & 0xFFFFFFFFll) && __ldg(l.header + 3) == (uint32_t)(n >> 32);
+}
+
 // Sets up the replay of ray i; false when the ray has nothing to replay.
 __device__ __forceinline__ bool adjoint_setup(const BwdArgs &a, long long i, RayWalk &w, float dn[3], float &t,
                                               AdjState &st) {
@@ -144,9 +150,10 @@ __global__ void __launch_bounds__(256) render_bwd_plain_kernel(const __grid_cons
   }
 }
 
-// Packet adjoint: the forward packet kernel's structure (one thread per ray,
-// walk steps and sample rounds decoupled through a per-lane queue), the walk
-// stopped at the forward's segment count.
+// Packet adjoint: replays each packet's shading rounds from the forward's
+// segment log when there is one; otherwise the forward packet kernel's
+// structure (one thread per ray, walk steps and sample rounds decoupled
+// through a per-lane queue), the walk stopped at the forward's segment count.
 template <int KP, int DEG, typename E>
 __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a, int queue,
                                                                 int ready) {
@@ -170,6 +177,35 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
   if (live) {
     rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
     sh_real<DEG>(dn, Y);
+  }
+  if (a.log.n_chunks && log_matches(a.log, a.rays.n)) {
+    // replay the forward's shading rounds from its log: no walk
+    const uint32_t head = __ldg(a.log.heads + (i >> 5));
+    if (head != kNoLog) {
+      const int lane = tid & 31;
+      uint32_t chunk = head;
+      int round = 0;
+      while (__ballot_sync(present, live && st.count < st.target)) {
+        if (chunk >= a.log.n_chunks) {  // a log that does not belong to these rays
+          raise_status(tr, kStatusBadIndex);
+          return;
+        }
+        if (live && st.count < st.target) {
+          const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
+          const uint32_t leaf = __ldg(a.log.leaf + slot);
+          if (leaf != kEmpty) {
+            ++st.count;
+            if (leaf < (uint32_t)tr.n_leaves) adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, __ldg(a.log.dt + slot), st);
+            else raise_status(tr, kStatusBadIndex);
+          }
+        }
+        if (++round == kLogRounds) {
+          round = 0;
+          chunk = __ldg(a.log.next + chunk);
+        }
+      }
+      return;
+    }
   }
   int walked = 0;  // segments found so far (the walk stops at the forward's count)
   bool walking = live && w.alive;

@@ -76,6 +76,12 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
   bool walking = hit && w.alive;
   int qh = 0, qn = 0;  // queue head and length
   const int qmask = queue - 1;
+  // segment log of this packet (warp-uniform state): current chunk and round
+  const int lane = threadIdx.x & 31;
+  const long long pk = i >> 5;
+  bool logging = a.log.n_chunks != 0;
+  uint32_t chunk = kNoLog;
+  int round = kLogRounds;
   for (;;) {
     if (walking && qn < queue) {
       uint32_t leaf;
@@ -94,6 +100,32 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
     if (!have && !stepping) break;
     const int active = __popc(__ballot_sync(present, walking || qn > 0));
     if (stepping && __popc(have) < min(ready, active)) continue;
+    if (logging) {
+      if (round == kLogRounds) {  // next chunk: one counter add per 8 rounds
+        const int leader = __ffs(present) - 1;
+        uint32_t nc = kNoLog;
+        if (lane == leader) {
+          const unsigned long long c = atomicAdd(a.log.counter, 1ull);
+          if (c < a.log.n_chunks) {
+            nc = (uint32_t)c;
+            if (chunk == kNoLog) a.log.heads[pk] = nc;
+            else a.log.next[chunk] = nc;
+          } else {
+            a.log.heads[pk] = kNoLog;  // out of room: the adjoint walks this packet
+          }
+        }
+        nc = __shfl_sync(present, nc, leader);
+        logging = nc != kNoLog;
+        chunk = nc;
+        round = 0;
+      }
+      if (logging) {
+        const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
+        a.log.leaf[slot] = qn > 0 ? q_leaf[qh * B] : kEmpty;
+        a.log.dt[slot] = qn > 0 ? q_dt[qh * B] : 0.f;
+        ++round;
+      }
+    }
     if (qn > 0) {
       const uint32_t leaf = q_leaf[qh * B];
       const float t0 = q_t0[qh * B], dt = q_dt[qh * B];
@@ -141,6 +173,13 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_ker
   // one after another until the counter passes the last
   const int lane = threadIdx.x & 31;
   const long long n_packets = (a.rays.n + 31) >> 5;
+  if (a.log.n_chunks && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.log.header[0] = a.log.n_chunks;
+    a.log.header[1] = kLogRounds;
+    a.log.header[2] = (uint32_t)(a.rays.n & 0xFFFFFFFFll);
+    a.log.header[3] = (uint32_t)(a.rays.n >> 32);
+    a.log.header[4] = 1u;
+  }
   long long pk = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (a.work) {
     unsigned long long q = 0;

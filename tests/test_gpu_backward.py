@@ -195,3 +195,42 @@ def test_sparse_adam_matches_oracle(B, dtype):
         # ... and within half a BF16 spacing (plus the master's error) of the oracle's weights
         wo = w[:, :info.rec_len]
         assert np.all(np.abs(st_ - wo) <= 2.0 ** -8 * np.abs(wo) + 2e-5)
+
+
+def test_adjoint_from_the_segment_log_matches_the_walk(B):
+    """The packet forward's segment log lets the adjoint replay each packet's
+    shading rounds without walking; any log size, including one too small for
+    most packets (those are walked), and a log written for other rays (ignored)
+    give the same gradient."""
+    rng = np.random.default_rng(95)
+    st = I.random_mixed_tree(6, 95, p_leaf=0.3, p_empty=0.2)
+    tree = I.make_coefficients(rng, st, K=16, T=9, hh_degree=3, mean_sigma=8.0)
+    from test_oracle_render import _random_rays
+    rays = _random_rays(rng, 4096 + 7)
+    rays.times[:] = rng.uniform(0, 1, rays.n).astype(np.float32)
+    g = torch.from_numpy(rng.standard_normal((rays.n, 3)).astype(np.float32)).cuda()
+    tree_d = B.Tree(tree, "bf16")
+    dr = B.DeviceRays.from_host(rays)
+    walk = B.neuvv_render_backward(tree_d, dr, B.neuvv_render(tree_d, dr, kernel="packet"), g, kernel="packet")
+    ref = walk.cpu().numpy().astype(np.float64)
+    scale = np.abs(ref).max()
+    for per_ray in (64, 2):          # ample, then room for a few chunks only
+        out = B.neuvv_render(tree_d, dr, kernel="packet", out=B.alloc_out(rays.n, log_bytes_per_ray=per_ray))
+        got = B.neuvv_render_backward(tree_d, dr, out, g, kernel="packet").cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-5 * scale, per_ray
+        assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+    # a log filled for a different batch is not used
+    other = rays.subset(np.arange(rays.n - 40))
+    out_o = B.neuvv_render(tree_d, B.DeviceRays.from_host(other), kernel="packet",
+                           out=B.alloc_out(rays.n, log_bytes_per_ray=64))
+    out = B.neuvv_render(tree_d, dr, kernel="packet")
+    out["log"] = out_o["log"]
+    got = B.neuvv_render_backward(tree_d, dr, out, g, kernel="packet").cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * scale
+    # the plain forward marks a log empty
+    out_p = B.alloc_out(rays.n, log_bytes_per_ray=64)
+    B.neuvv_render(tree_d, dr, kernel="packet", out=out_p)
+    B.neuvv_render(tree_d, dr, kernel="plain", out=out_p)
+    got = B.neuvv_render_backward(tree_d, dr, out_p, g, kernel="packet").cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * scale
+    assert tree_d.status() == 0

@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--views", type=int, default=8, help="1920x1080 views per step (8 = the benchmark workload)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default packet launch configuration")
     p.add_argument("--no-fp8", action="store_true", help="skip the FP8-storage ablation leg")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the legs of the other workloads (depth-8 and depth-10 training, stereo composition)")
     p.add_argument("--launch", default=None, help="packet launch block,queue,ready (profiling case; default: library's)")
     p.add_argument("--profile-kernel", choices=["fwd", "bwd", "adam"], default=None,
                    help="profiling case: launch that kernel twice on the workload and exit (no JSON)")
@@ -237,6 +239,95 @@ def run_reference(args):
                              "sample": f"{per_step} seeded random rays of the workload per step, FP64 fwd+adjoint"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def train_step_leg(B, tree, rays, dtype, steps, seed):
+    """ms per training step (fwd + MSE + adjoint + Adam) and samples/s on one
+    workload, targets rendered from perturbed coefficients."""
+    import torch
+    from paper_2202_06088_gb300 import inputs as I
+    dr = B.DeviceRays.from_host(rays)
+    n = rays.n
+    tgt_tree = B.Tree(I.perturbed(tree, seed=seed), "f32")
+    target = B.neuvv_render(tgt_tree, dr, kernel="packet")["rgb"].clone()
+    del tgt_tree
+    tree_d = B.Tree(tree, dtype, with_optimizer=True)
+    B.neuvv_autotune(tree_d, dr)
+    out = B.alloc_out(n, dr.o.device, log_bytes_per_ray=64)
+    grad_rgb = torch.empty(n, 3, device=dr.o.device)
+    grad = tree_d.new_grad()
+    touched = tree_d.new_touched()
+    loss = torch.zeros(1, device=dr.o.device)
+
+    def step(k):
+        B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+        loss.zero_()
+        B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
+        B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k)
+
+    for k in range(3):
+        step(k + 1)
+    torch.cuda.synchronize()
+    samples = int(out["nseg"].sum().item())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        step(4 + k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"ms_per_step": ms, "msamples_per_s": samples / (ms / 1e3) / 1e6, "rays": n,
+            "leaves": tree.n_leaves, "samples_per_step": samples, "storage": dtype, "steps": steps}
+
+
+def extra_workloads(B, steps):
+    """The other synthetic workloads, one leg each: the depth-8 differentiable
+    render (262,144 rays over 16 cameras x 16 times), the 8-primitive stereo
+    composition at 2 x 2160^2 replayed from a CUDA graph, and the depth-10
+    training step (8M leaves, 1,048,576 rays) in BF16 and FP8 storage."""
+    import torch
+    from paper_2202_06088_gb300 import inputs as I
+    res = {}
+    tree3 = I.config3_tree()
+    res["depth8_train_262k_rays"] = train_step_leg(B, tree3, I.config3_rays(), "bf16", steps, 1003)
+    del tree3
+    tree1 = I.config1_tree()
+    prims = I.config4_primitives(8, T=tree1.T)
+    rays4 = I.config4_rays()[0]
+    t4 = B.Tree(tree1, "bf16")
+    dr4 = B.DeviceRays.from_host(rays4)
+    xf = [p.transform for p in prims]
+    off = [p.time_offset for p in prims]
+    tint = [p.tint for p in prims]
+    out4 = B.alloc_out(rays4.n)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        B.neuvv_compose([t4] * 8, xf, off, tint, dr4, out=out4)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        B.neuvv_compose([t4] * 8, xf, off, tint, dr4, out=out4)
+    for _ in range(3):
+        graph.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms4 = e0.elapsed_time(e1) / steps
+    res["compose_8prims_stereo_2160"] = {"ms_per_stereo_frame": ms4, "rays": rays4.n, "primitives": 8,
+                                         "mray_prims_per_s": rays4.n * 8 / (ms4 / 1e3) / 1e6,
+                                         "storage": "bf16", "cuda_graph": True, "steps": steps}
+    del graph, t4, dr4, out4
+    tree5 = I.config5_tree()
+    rays5 = I.config5_rays()
+    res["depth10_train_1m_rays"] = train_step_leg(B, tree5, rays5, "bf16", steps, 1005)
+    res["depth10_train_1m_rays_fp8"] = train_step_leg(B, tree5, rays5, "fp8", steps, 1005)
+    return res
 
 
 def profile_case(args, B, tree, dr):
@@ -511,6 +602,8 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
+    if not args.no_extra:
+        line["other_workloads"] = extra_workloads(B, max(5, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(tree, rays, args.cpu_seconds)
     if rank == 0:

@@ -137,9 +137,9 @@ DevRays dev_rays(const neuvv_rays *r, float t) {
 }
 
 // Device view of a caller's segment log buffer (layout private to the
-// library): 64-byte header, heads [n_packets], next [n_chunks], then leaf and
-// chord planes of n_chunks x kLogRounds x 32 entries.  n_chunks = 0 when the
-// buffer is absent or too small for one chunk.
+// library): 64-byte header, heads, key and order [n_packets], the sort bins,
+// next [n_chunks], then leaf and chord planes of n_chunks x kLogRounds x 32
+// entries.  n_chunks = 0 when the buffer is absent or too small for one chunk.
 SampleLog log_view(void *base, int64_t bytes, int64_t n_rays) {
   SampleLog l;
   std::memset(&l, 0, sizeof l);
@@ -148,15 +148,19 @@ SampleLog log_view(void *base, int64_t bytes, int64_t n_rays) {
   l.counter = reinterpret_cast<unsigned long long *>(p);
   l.header = reinterpret_cast<uint32_t *>(p + 8);
   const int64_t n_packets = (n_rays + 31) / 32;
-  const int64_t heads_bytes = (4 * n_packets + 15) / 16 * 16;
+  const int64_t pk_bytes = (4 * n_packets + 15) / 16 * 16;
+  const int64_t fixed = 64 + 3 * pk_bytes + 4 * kSortBins;
   const int64_t per_chunk = 4 + (int64_t)kLogRounds * 32 * 8;
-  const int64_t avail = bytes - 64 - heads_bytes - 16;
+  const int64_t avail = bytes - fixed - 16;
   if (avail < per_chunk) return l;
   int64_t nc = avail / per_chunk;
   if (nc > (int64_t)0x7FFFFFFF) nc = 0x7FFFFFFF;
   l.heads = reinterpret_cast<uint32_t *>(p + 64);
-  l.next = reinterpret_cast<uint32_t *>(p + 64 + heads_bytes);
-  const int64_t leaf_off = (64 + heads_bytes + 4 * nc + 15) / 16 * 16;
+  l.key = reinterpret_cast<uint32_t *>(p + 64 + pk_bytes);
+  l.order = reinterpret_cast<uint32_t *>(p + 64 + 2 * pk_bytes);
+  l.bins = reinterpret_cast<uint32_t *>(p + 64 + 3 * pk_bytes);
+  l.next = reinterpret_cast<uint32_t *>(p + fixed);
+  const int64_t leaf_off = (fixed + 4 * nc + 15) / 16 * 16;
   l.leaf = reinterpret_cast<uint32_t *>(p + leaf_off);
   l.dt = reinterpret_cast<float *>(p + leaf_off + nc * kLogRounds * 32 * 4);
   l.n_chunks = (uint32_t)nc;

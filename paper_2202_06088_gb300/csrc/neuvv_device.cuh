@@ -523,13 +523,13 @@ struct LeafRecord {
 #pragma unroll
     for (int i = 0; i < NV; ++i) Elem<E>::unpack(raw[i], w + i * PV);
   }
-  // Asks L1 for a leaf's record ahead of its use (no registers held).
-  __device__ __forceinline__ static void prefetch(const DevTree &tr, uint32_t leaf) {
+  // Asks L2 for the lines of a leaf's record ahead of its use (no registers held).
+  __device__ __forceinline__ static void prefetch_l2(const DevTree &tr, uint32_t leaf) {
     const char *p = reinterpret_cast<const char *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
     constexpr int kBytes = NV * 16;
 #pragma unroll
-    for (int b = 0; b < kBytes; b += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + b));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + kBytes - 1));
+    for (int b = 0; b < kBytes; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + b));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + kBytes - 1));
   }
   __device__ __forceinline__ float sig(int k) const { return w[k]; }
   __device__ __forceinline__ float gam(int k) const { return w[KP + k]; }
@@ -568,6 +568,13 @@ struct LeafRecord<KP, DEG, Fp8E4M3> {
     sc[0] = __uint_as_float(h.x);
     sc[1] = __uint_as_float(h.y);
     sc[2] = __uint_as_float(h.z);
+  }
+  __device__ __forceinline__ static void prefetch_l2(const DevTree &tr, uint32_t leaf) {
+    const char *p = reinterpret_cast<const char *>(tr.rec) + (size_t)leaf * tr.rec_stride;
+    constexpr int kBytes = 16 + NV * 16;
+#pragma unroll
+    for (int b = 0; b < kBytes; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + b));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + kBytes - 1));
   }
   // Entry j's code value, not yet scaled (j is a compile-time index once the
   // callers' loops are unrolled).

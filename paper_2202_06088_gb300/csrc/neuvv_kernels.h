@@ -31,11 +31,18 @@ struct SampleLog {
   unsigned long long *counter;
   uint32_t *header;   // [0] n_chunks, [1] rounds, [2..3] n_rays, [4] valid
   uint32_t *heads;    // [n_packets]
+  uint32_t *key;      // [n_packets] first leaf the packet shaded (kNoKey: none)
+  uint32_t *order;    // [n_packets] packets sorted by key (filled by the adjoint)
+  uint32_t *bins;     // [kSortBins] counting-sort scratch
   uint32_t *next;     // [n_chunks]
   uint32_t *leaf;     // [n_chunks][kLogRounds][32]
   float *dt;          // [n_chunks][kLogRounds][32]
   uint32_t n_chunks;  // 0: no log
 };
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+// Bins of the counting sort that orders the adjoint's packets by key (leaf
+// ids follow the Morton order of the leaves, so a bin is a compact region).
+constexpr int kSortBins = 4096;
 
 struct FwdArgs {
   DevTree tr;

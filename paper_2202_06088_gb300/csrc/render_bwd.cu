@@ -13,6 +13,8 @@
 // depth.  The chain continues through ReLU (zero slope at pre-activation <= 0),
 // pi*sigmoid and d H / d gamma.  Gradients are scattered into an FP32
 // record-layout buffer with 16-byte vector atomics.
+#include <algorithm>
+
 #include "neuvv_kernels.h"
 #include "neuvv_ray.cuh"
 
@@ -35,23 +37,24 @@ struct AdjState {
   int count, target;
 };
 
-// Gradient of one sample; scatters it into the leaf's FP32 record.
+// Gradient factors of one sample: with them, dL/dw_sigma = dpre_s a(u),
+// dL/dw_gamma = dpre_g b(u) and dL/dw_HH[ch][n,l,m] = R_nl(gamma) F[ch][l,m]
+// with F[ch][l,m] = dz[ch] Y_lm.  Advances the ray's replay state; false when
+// the sample has zero density (no path from it to the loss).
 template <int KP, int DEG, typename E, typename Rows>
-__device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &rows, const float *Y, uint32_t leaf,
-                                               float dt, AdjState &st) {
-  constexpr int NH = n_hh(DEG);
+__device__ __forceinline__ bool sample_factors(const BwdArgs &a, const Rows &rows, const float *Y, uint32_t leaf,
+                                               float dt, AdjState &st, Sample<DEG> &s, float dz[3], float &dpre_s,
+                                               float &dpre_g) {
   const DevTree &tr = a.tr;
   LeafRecord<KP, DEG, E> rec;
   rec.load(tr, leaf);
-  Sample<DEG> s;
   eval_sample<KP, DEG, E, Rows, true>(tr, rows, Y, rec, a.act, s);
-  if (!(s.sigma > 0.f)) return;  // alpha = 0: no path from this sample to L
+  if (!(s.sigma > 0.f)) return false;
   const float sd = s.sigma * dt;
   const float e = __expf(-sd);
   const float wgt = st.T * alpha_of(sd);
   const float Tn = st.T * e;
   float dsig = st.gA * st.T_final;
-  float dz[3];
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) {
     st.acc[ch] = fmaf(wgt, s.c[ch], st.acc[ch]);
@@ -62,9 +65,21 @@ __device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &row
   }
   dsig *= dt;
   st.T = Tn;
+  // dL/dgamma = sum_ch dz[ch] d z_ch / dgamma
+  const float dgam = dz[0] * s.u[0] + dz[1] * s.u[1] + dz[2] * s.u[2];
+  dpre_g = dgam * kPi * s.s_gamma * (1.f - s.s_gamma);
+  dpre_s = s.pre_sigma > 0.f ? dsig : 0.f;
+  return true;
+}
+
+// Scatters a leaf's gradient from its factors into its FP32 record with
+// 16-byte vector atomics: the w_HH part in record order (channel, then idx
+// ascending over n, l, m), one quad at a time, then w_sigma and w_gamma.
+template <int KP, int DEG, typename Rows>
+__device__ __forceinline__ void scatter_gradient(const BwdArgs &a, const Rows &rows, uint32_t leaf, const float *R,
+                                                 const float *F, float dpre_s, float dpre_g) {
+  constexpr int NY = (DEG + 1) * (DEG + 1);
   float *dst = a.grad + (size_t)leaf * a.grad_stride;
-  // dL/dw_HH[ch][idx] = dz[ch] H_idx, in record order (channel, then idx
-  // ascending over n, l, m), streamed out one 16-byte quad at a time
   float v[4];
   int j = 0;
 #pragma unroll
@@ -75,7 +90,7 @@ __device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &row
       for (int l = 0; l <= n; ++l)
 #pragma unroll
         for (int m = -l; m <= l; ++m) {
-          v[j & 3] = dz[ch] * s.R[radial_index(n, l)] * Y[l * l + l + m];
+          v[j & 3] = R[radial_index(n, l)] * F[ch * NY + l * l + l + m];
           if ((j & 3) == 3) red_add_v4(dst + 2 * KP + j - 3, v[0], v[1], v[2], v[3]);
           ++j;
         }
@@ -85,10 +100,6 @@ __device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &row
       if (k >= (j & 3)) v[k] = 0.f;
     red_add_v4(dst + 2 * KP + (j & ~3), v[0], v[1], v[2], v[3]);
   }
-  // dL/dgamma = sum_ch dz[ch] d z_ch / dgamma
-  const float dgam = dz[0] * s.u[0] + dz[1] * s.u[1] + dz[2] * s.u[2];
-  const float dpre_g = dgam * kPi * s.s_gamma * (1.f - s.s_gamma);
-  const float dpre_s = s.pre_sigma > 0.f ? dsig : 0.f;
 #pragma unroll
   for (int q = 0; q < KP / 4; ++q) {
     red_add_v4(dst + 4 * q, dpre_s * rows.A(4 * q), dpre_s * rows.A(4 * q + 1), dpre_s * rows.A(4 * q + 2),
@@ -101,6 +112,68 @@ __device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &row
     unsigned int *word = a.touched + (leaf >> 5);
     if (!(__ldcg(word) & bit)) atomicOr(word, bit);
   }
+}
+
+// Gradient of one sample, scattered by its own thread (the plain kernel).
+template <int KP, int DEG, typename E, typename Rows>
+__device__ __forceinline__ void adjoint_sample(const BwdArgs &a, const Rows &rows, const float *Y, uint32_t leaf,
+                                               float dt, AdjState &st) {
+  constexpr int NY = (DEG + 1) * (DEG + 1);
+  Sample<DEG> s;
+  float dz[3], dpre_s, dpre_g;
+  if (!sample_factors<KP, DEG, E, Rows>(a, rows, Y, leaf, dt, st, s, dz, dpre_s, dpre_g)) return;
+  float F[3 * NY];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int k = 0; k < NY; ++k) F[ch * NY + k] = dz[ch] * Y[k];
+  scatter_gradient<KP, DEG, Rows>(a, rows, leaf, s.R, F, dpre_s, dpre_g);
+}
+
+// Adjoint of one shading round of a packet, called by every present lane;
+// `has` marks the lanes that hold a sample.  Warp-aggregated scatter: lanes
+// whose samples share a leaf and a time (hence the basis rows a(u), b(u) and
+// the hyper-angle, so the radial factors R_nl) add their factors dpre_s,
+// dpre_g and F[ch][l,m] with shuffles, and the lowest lane of each such group
+// scatters the group's gradient: one set of vector atomics per distinct
+// (leaf, time) in the round instead of one per sample.
+template <int KP, int DEG, typename E, typename Rows>
+__device__ __forceinline__ void adjoint_round(const BwdArgs &a, const Rows &rows, const float *Y, uint32_t leaf,
+                                              float dt, float t, bool has, unsigned present, AdjState &st) {
+  constexpr int NY = (DEG + 1) * (DEG + 1);
+  const int lane = threadIdx.x & 31;
+  Sample<DEG> s;
+  float dz[3] = {0.f, 0.f, 0.f}, dpre_s = 0.f, dpre_g = 0.f;
+  const bool contrib = has && sample_factors<KP, DEG, E, Rows>(a, rows, Y, leaf, dt, st, s, dz, dpre_s, dpre_g);
+  // lanes without a contribution get keys of their own (leaf ids are < 2^31)
+  const unsigned long long key =
+      contrib ? (((unsigned long long)leaf << 32) | __float_as_uint(t)) : (~0ull - (unsigned long long)lane);
+  const unsigned grp = __match_any_sync(present, key);
+  const bool leader = contrib && lane == __ffs(grp) - 1;
+  float F[3 * NY];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int k = 0; k < NY; ++k) F[ch * NY + k] = dz[ch] * Y[k];
+  const int gmax = (int)__reduce_max_sync(present, contrib ? (unsigned)__popc(grp) : 1u);
+  unsigned rest = leader ? (grp & (grp - 1u)) : 0u;  // the leader's other members
+  for (int it = 1; it < gmax; ++it) {
+    const int src = rest ? __ffs(rest) - 1 : lane;
+    rest &= rest - 1u;
+    const bool add = src != lane;
+    const float xs = __shfl_sync(present, dpre_s, src);
+    const float xg = __shfl_sync(present, dpre_g, src);
+    if (add) {
+      dpre_s += xs;
+      dpre_g += xg;
+    }
+#pragma unroll
+    for (int k = 0; k < 3 * NY; ++k) {
+      const float x = __shfl_sync(present, F[k], src);
+      if (add) F[k] += x;
+    }
+  }
+  if (leader) scatter_gradient<KP, DEG, Rows>(a, rows, leaf, s.R, F, dpre_s, dpre_g);
 }
 
 // Whether a segment log was written by a forward over these rays.
@@ -150,6 +223,60 @@ __global__ void __launch_bounds__(256) render_bwd_plain_kernel(const __grid_cons
   }
 }
 
+// Counting sort of the packets by their key (the first leaf they shade) into
+// log.order, so that the adjoint runs the packets of all views that meet the
+// same region of the tree close together in time: their leaf records and
+// gradient rows are then shared in L2 instead of being fetched from and
+// written back to DRAM once per view.
+__device__ __forceinline__ int key_bin(uint32_t k, int shift) { return (int)min(k >> shift, (uint32_t)(kSortBins - 1)); }
+
+__global__ void __launch_bounds__(256) key_hist_kernel(const SampleLog l, long long n_packets, int shift) {
+  __shared__ uint32_t h[kSortBins];
+  for (int b = threadIdx.x; b < kSortBins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n_packets;
+       p += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&h[key_bin(__ldg(l.key + p), shift)], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < kSortBins; b += blockDim.x)
+    if (h[b]) atomicAdd(&l.bins[b], h[b]);
+}
+
+// Exclusive prefix sum of the bin counts, in place (one block of 1024).
+__global__ void __launch_bounds__(1024) key_scan_kernel(const SampleLog l) {
+  __shared__ uint32_t part[1024];
+  constexpr int kPer = kSortBins / 1024;
+  const int t = threadIdx.x;
+  uint32_t v[kPer], sum = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    v[j] = l.bins[kPer * t + j];
+    sum += v[j];
+  }
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const uint32_t x = t >= off ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  uint32_t base = t ? part[t - 1] : 0u;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    l.bins[kPer * t + j] = base;
+    base += v[j];
+  }
+}
+
+__global__ void __launch_bounds__(256) key_scatter_kernel(const SampleLog l, long long n_packets, int shift) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n_packets;
+       p += (long long)gridDim.x * blockDim.x) {
+    const uint32_t pos = atomicAdd(&l.bins[key_bin(__ldg(l.key + p), shift)], 1u);
+    l.order[pos] = (uint32_t)p;
+  }
+}
+
 // Packet adjoint: replays each packet's shading rounds from the forward's
 // segment log when there is one; otherwise the forward packet kernel's
 // structure (one thread per ray, walk steps and sample rounds decoupled
@@ -165,7 +292,13 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
   uint32_t *q_leaf = smem + (2 * KP + 16) * B + tid;
   float *q_dt = reinterpret_cast<float *>(q_leaf + queue * B);
   const SmemRows<KP> rows{my_rows, B};
-  const long long i = (long long)blockIdx.x * B + tid;
+  // warp w adjoins packet w, or with a valid log the w-th packet in key order
+  const long long n_packets = (a.rays.n + 31) >> 5;
+  const long long wp = ((long long)blockIdx.x * B + tid) >> 5;
+  if (wp >= n_packets) return;
+  const bool logged = a.log.n_chunks && log_matches(a.log, a.rays.n);
+  const long long pk = logged ? (long long)min(__ldg(a.log.order + wp), (uint32_t)(n_packets - 1)) : wp;
+  const long long i = (pk << 5) + (tid & 31);
   const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
   if (i >= a.rays.n) return;
   RayWalk w;
@@ -178,7 +311,7 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
     rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
     sh_real<DEG>(dn, Y);
   }
-  if (a.log.n_chunks && log_matches(a.log, a.rays.n)) {
+  if (logged) {
     // replay the forward's shading rounds from its log: no walk
     const uint32_t head = __ldg(a.log.heads + (i >> 5));
     if (head != kNoLog) {
@@ -190,15 +323,20 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
           raise_status(tr, kStatusBadIndex);
           return;
         }
+        uint32_t leaf = kEmpty;
+        float dt = 0.f;
+        bool has = false;
         if (live && st.count < st.target) {
           const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
-          const uint32_t leaf = __ldg(a.log.leaf + slot);
+          leaf = __ldg(a.log.leaf + slot);
           if (leaf != kEmpty) {
             ++st.count;
-            if (leaf < (uint32_t)tr.n_leaves) adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, __ldg(a.log.dt + slot), st);
+            has = leaf < (uint32_t)tr.n_leaves;
+            if (has) dt = __ldg(a.log.dt + slot);
             else raise_status(tr, kStatusBadIndex);
           }
         }
+        adjoint_round<KP, DEG, E>(a, rows, Y, leaf, dt, t, has, present, st);
         if (++round == kLogRounds) {
           round = 0;
           chunk = __ldg(a.log.next + chunk);
@@ -229,14 +367,17 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
     if (!have && !stepping) break;
     const int active = __popc(__ballot_sync(present, walking || qn > 0));
     if (stepping && __popc(have) < min(ready, active)) continue;
-    if (qn > 0) {
-      const uint32_t leaf = q_leaf[qh * B];
-      const float dt = q_dt[qh * B];
+    uint32_t leaf = kEmpty;
+    float dt = 0.f;
+    const bool has = qn > 0;
+    if (has) {
+      leaf = q_leaf[qh * B];
+      dt = q_dt[qh * B];
       qh = (qh + 1) & qmask;
       --qn;
       ++st.count;
-      adjoint_sample<KP, DEG, E>(a, rows, Y, leaf, dt, st);
     }
+    adjoint_round<KP, DEG, E>(a, rows, Y, leaf, dt, t, has, present, st);
   }
 }
 
@@ -252,6 +393,21 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
       cudaError_t e = cudaFuncSetAttribute(render_bwd_packet_kernel<KP, DEG, E>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
+    }
+    if (a.log.n_chunks) {
+      // packets in key order (a permutation whatever the log holds; the
+      // adjoint uses it only when the log belongs to these rays)
+      const long long n_packets = (a.rays.n + 31) >> 5;
+      int bits = 0;
+      while (bits < 32 && ((long long)1 << bits) <= a.tr.n_leaves) ++bits;
+      const int shift = bits > 12 ? bits - 12 : 0;
+      const unsigned g = (unsigned)std::min<long long>((n_packets + 255) / 256, 4LL * cfg.num_sms);
+      cudaError_t e = cudaMemsetAsync(a.log.bins, 0, kSortBins * sizeof(uint32_t), s);
+      if (e != cudaSuccess) return e;
+      key_hist_kernel<<<g, 256, 0, s>>>(a.log, n_packets, shift);
+      key_scan_kernel<<<1, 1024, 0, s>>>(a.log);
+      key_scatter_kernel<<<g, 256, 0, s>>>(a.log, n_packets, shift);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     render_bwd_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
   }

@@ -65,6 +65,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
   RayWalk w;
   const bool hit = walk_init(tr, o, d, w, dn);
   if (!hit) write_miss(a.out, i);
+  if (a.log.n_chunks && (threadIdx.x & 31) == __ffs(present) - 1) a.log.key[i >> 5] = kNoKey;
   if (__ballot_sync(present, hit) == 0) return;  // the whole packet missed the tree
   float Y[(DEG + 1) * (DEG + 1)];
   if (hit) {
@@ -92,6 +93,8 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
         q_t0[slot * B] = t0;
         q_dt[slot * B] = dt;
         ++qn;
+        // the record is read when the segment's round comes: ask L2 for it now
+        LeafRecord<KP, DEG, E>::prefetch_l2(tr, leaf);
       }
       walking = w.alive;
     }
@@ -103,6 +106,10 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
     if (logging) {
       if (round == kLogRounds) {  // next chunk: one counter add per 8 rounds
         const int leader = __ffs(present) - 1;
+        if (chunk == kNoLog) {  // the packet's sort key: the smallest leaf of its first round
+          const uint32_t k = __reduce_min_sync(present, qn > 0 ? q_leaf[qh * B] : kNoKey);
+          if (lane == leader) a.log.key[pk] = k;
+        }
         uint32_t nc = kNoLog;
         if (lane == leader) {
           const unsigned long long c = atomicAdd(a.log.counter, 1ull);

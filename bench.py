@@ -599,7 +599,7 @@ def main():
         "fp8_ablation": fp8,
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "clocks": clk,
     }
     if not args.no_extra:

@@ -269,12 +269,33 @@ __global__ void __launch_bounds__(1024) key_scan_kernel(const SampleLog l) {
   }
 }
 
-__global__ void __launch_bounds__(256) key_scatter_kernel(const SampleLog l, long long n_packets, int shift) {
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n_packets;
-       p += (long long)gridDim.x * blockDim.x) {
-    const uint32_t pos = atomicAdd(&l.bins[key_bin(__ldg(l.key + p), shift)], 1u);
-    l.order[pos] = (uint32_t)p;
+// Each block places a contiguous range of kScatterPer packets: ranks within
+// the block's share of a bin come from shared-memory counters, and one global
+// add per (block, bin) reserves the share, so that a popular bin (all the
+// packets that shade nothing share the last one) costs no global contention.
+constexpr int kScatterThreads = 256, kScatterEach = 16, kScatterPer = kScatterThreads * kScatterEach;
+
+__global__ void __launch_bounds__(kScatterThreads) key_scatter_kernel(const SampleLog l, long long n_packets,
+                                                                      int shift) {
+  __shared__ uint32_t cnt[kSortBins];
+  for (int b = threadIdx.x; b < kSortBins; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  const long long first = (long long)blockIdx.x * kScatterPer;
+  int bin[kScatterEach];
+  uint32_t rank[kScatterEach];
+#pragma unroll
+  for (int k = 0; k < kScatterEach; ++k) {
+    const long long p = first + (long long)k * kScatterThreads + threadIdx.x;
+    bin[k] = p < n_packets ? key_bin(__ldg(l.key + p), shift) : -1;
+    rank[k] = bin[k] >= 0 ? atomicAdd(&cnt[bin[k]], 1u) : 0u;
   }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kSortBins; b += blockDim.x)
+    if (cnt[b]) cnt[b] = atomicAdd(&l.bins[b], cnt[b]);  // this block's first position in bin b
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kScatterEach; ++k)
+    if (bin[k] >= 0) l.order[cnt[bin[k]] + rank[k]] = (uint32_t)(first + (long long)k * kScatterThreads + threadIdx.x);
 }
 
 // Packet adjoint: replays each packet's shading rounds from the forward's
@@ -406,7 +427,8 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
       if (e != cudaSuccess) return e;
       key_hist_kernel<<<g, 256, 0, s>>>(a.log, n_packets, shift);
       key_scan_kernel<<<1, 1024, 0, s>>>(a.log);
-      key_scatter_kernel<<<g, 256, 0, s>>>(a.log, n_packets, shift);
+      key_scatter_kernel<<<(unsigned)((n_packets + kScatterPer - 1) / kScatterPer), kScatterThreads, 0, s>>>(
+          a.log, n_packets, shift);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     render_bwd_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);

@@ -78,6 +78,7 @@ struct neuvv_tree {
   neuvv_tree_info info{};
   uint32_t *child = nullptr;
   uint32_t *bricks = nullptr;
+  uint32_t *coarse = nullptr;
   int brick_level = 0, brick_first = 0, brick_count = 0;
   void *rec = nullptr;
   float *master = nullptr, *m = nullptr, *v = nullptr;
@@ -119,6 +120,7 @@ DevTree dev_tree(const neuvv_tree *t) {
   d.brick_level = t->brick_level;
   d.brick_first = t->brick_first;
   d.brick_count = t->brick_count;
+  d.coarse = t->coarse;
   return d;
 }
 
@@ -215,6 +217,71 @@ void fill_brick(const uint32_t *child, uint32_t node, int level, int depth, int 
       for (int y = cy; y < cy + half; ++y)
         for (int z = cz; z < cz + half; ++z) brick[((size_t)x << (2 * sh)) | ((size_t)y << sh) | (size_t)z] = v;
   }
+}
+
+// Brick-map words of the subtree of `node` (an internal node at `level`, at
+// brick-map cell (ox, oy, oz) of level Lb): leaves fill the cells they cover,
+// internal nodes at level Lb are bricks, empty children are left as they are.
+void fill_coarse(const uint32_t *child, uint32_t node, int level, int Lb, int ox, int oy, int oz, int64_t first,
+                 uint32_t *map) {
+  const int half = 1 << (Lb - level - 1);
+  for (int c = 0; c < 8; ++c) {
+    const int cx = ox + ((c >> 2) & 1) * half, cy = oy + ((c >> 1) & 1) * half, cz = oz + (c & 1) * half;
+    const uint32_t e = child[(size_t)node * 8 + c];
+    if (e == kEmpty) continue;
+    if (!(e & kLeafBit)) {
+      if (level + 1 == Lb) {
+        map[((size_t)cx << (2 * Lb)) | ((size_t)cy << Lb) | (size_t)cz] = (uint32_t)((int64_t)e - first);
+      } else {
+        fill_coarse(child, e, level + 1, Lb, cx, cy, cz, first, map);
+      }
+      continue;
+    }
+    const uint32_t v = ((uint32_t)(level + 1) << 28) | (e & ~kLeafBit);
+    for (int x = cx; x < cx + half; ++x)
+      for (int y = cy; y < cy + half; ++y)
+        for (int z = cz; z < cz + half; ++z) map[((size_t)x << (2 * Lb)) | ((size_t)y << Lb) | (size_t)z] = v;
+  }
+}
+
+// Chebyshev (L-infinity) distance from every cell of an n^3 grid to the
+// nearest occupied cell (0 for occupied cells; `far` when there is none):
+// the one-dimensional distance along z, then two passes of
+// g'(y) = min over y' of max(|y - y'|, g(y')) along y and along x.
+std::vector<int32_t> chebyshev_distance(const std::vector<uint8_t> &occ, int n, int32_t far) {
+  const size_t n3 = (size_t)n * n * n;
+  std::vector<int32_t> g(n3), h(n3);
+  auto at = [n](int x, int y, int z) { return ((size_t)x * n + y) * n + z; };
+  for (int x = 0; x < n; ++x)
+    for (int y = 0; y < n; ++y) {
+      int32_t d = far;
+      for (int z = 0; z < n; ++z) {
+        d = occ[at(x, y, z)] ? 0 : std::min(far, d + 1);
+        g[at(x, y, z)] = d;
+      }
+      d = far;
+      for (int z = n - 1; z >= 0; --z) {
+        d = occ[at(x, y, z)] ? 0 : std::min(far, d + 1);
+        g[at(x, y, z)] = std::min(g[at(x, y, z)], d);
+      }
+    }
+  // min-max passes; the search around y stops once |y - y'| reaches the best
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int u = 0; u < n; ++u)
+      for (int v = 0; v < n; ++v)
+        for (int y = 0; y < n; ++y) {
+          auto idx = [&](int yy) { return pass == 0 ? at(u, yy, v) : at(yy, u, v); };
+          int32_t best = g[idx(y)];
+          for (int r = 1; r < best; ++r) {
+            if (y - r >= 0) best = std::min(best, std::max(r, g[idx(y - r)]));
+            if (y + r < n) best = std::min(best, std::max(r, g[idx(y + r)]));
+            if (y - r < 0 && y + r >= n) break;
+          }
+          h[idx(y)] = best;
+        }
+    g.swap(h);
+  }
+  return g;
 }
 
 }  // namespace
@@ -405,6 +472,20 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
       t->brick_level = Lb;
       t->brick_first = (int)first;
       t->brick_count = (int)count;
+      // brick map over the level-Lb cells (kept to 128^3 cells, 8 MB)
+      if (Lb >= 1 && Lb <= 7) {
+        const int nc = 1 << Lb;
+        const size_t n3 = (size_t)nc * nc * nc;
+        std::vector<uint32_t> map(n3, kCoarseEmpty << 28);
+        fill_coarse(d.child, 0, 0, Lb, 0, 0, 0, first, map.data());
+        std::vector<uint8_t> occ(n3);
+        for (size_t q = 0; q < n3; ++q) occ[q] = (map[q] >> 28) != kCoarseEmpty;
+        const std::vector<int32_t> dist = chebyshev_distance(occ, nc, nc);
+        for (size_t q = 0; q < n3; ++q)
+          if (!occ[q]) map[q] = (kCoarseEmpty << 28) | (uint32_t)dist[q];
+        NEUVV_TRY(cudaMalloc(&t->coarse, n3 * 4), "cudaMalloc(brick map)");
+        NEUVV_TRY(cudaMemcpy(t->coarse, map.data(), n3 * 4, cudaMemcpyHostToDevice), "copy brick map");
+      }
     }
   }
 #undef NEUVV_TRY
@@ -420,6 +501,7 @@ neuvv_status neuvv_tree_destroy(neuvv_tree *t) {
   cudaFree(t->rec);
   cudaFree(t->child);
   cudaFree(t->bricks);
+  cudaFree(t->coarse);
   cudaFree(t->m);
   cudaFree(t->v);
   cudaFree(t->A);

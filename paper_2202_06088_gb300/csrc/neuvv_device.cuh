@@ -49,7 +49,16 @@ struct DevTree {
   // tree has none.
   const uint32_t *bricks;
   int brick_level, brick_first, brick_count;
+  // Brick map: a dense grid over the cells of level brick_level, one word per
+  // cell: (0 << 28) | brick index (the cell is an internal node with a brick),
+  // (L << 28) | leaf id (the cell lies in a leaf of level L <= brick_level), or
+  // (kCoarseEmpty << 28) | k for an empty cell whose Chebyshev distance to the
+  // nearest non-empty cell is k >= 1 (the box of radius k-1 around it is
+  // empty).  Null when the tree has none; the walk then descends the octree.
+  const uint32_t *coarse;
 };
+
+constexpr uint32_t kCoarseEmpty = 15u;
 
 constexpr uint32_t kBrickEmpty = 0x0FFFFFFFu;
 
@@ -91,6 +100,8 @@ struct RayWalk {
   int cell[3];
   int steps, max_steps;
   int restart;     // level at which the next descent may start (0 = root)
+  uint32_t c_idx;  // brick-map cell of the last lookup (0xFFFFFFFF: none) ...
+  uint32_t c_word; // ... and its word
   bool alive;
 };
 
@@ -173,6 +184,8 @@ __device__ __forceinline__ void walk_start(const DevTree &tr, const float p[3], 
   w.t_lo = 0.f;
   w.t_far = tf;
   w.restart = 0;
+  w.c_idx = 0xFFFFFFFFu;
+  w.c_word = 0u;
   w.steps = 0;
   w.max_steps = 3 * N + 8;
   w.alive = tf > 0.f;
@@ -313,16 +326,76 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
     w.alive = false;
     return false;
   }
-  int level;
-  const uint32_t e = descend<kSmem, kPath>(tr, s_child, pr, w.cell, w.restart, level);
-  const int shift = tr.depth - level;
-  const int size = 1 << shift;
-  int lo[3];
+  // the box [lo, hi) the ray crosses next: the tree cell holding the current
+  // finest cell, or with a brick map possibly a larger empty box
+  uint32_t e;
+  int lo[3], hi[3];
+  bool fine = false;  // the box is a single finest cell
+  if (tr.coarse) {
+    const int cs = tr.depth - tr.brick_level, Lc = tr.brick_level;
+    const int cx = w.cell[0] >> cs, cy = w.cell[1] >> cs, cz = w.cell[2] >> cs;
+    const uint32_t ci = ((uint32_t)cx << (2 * Lc)) | ((uint32_t)cy << Lc) | (uint32_t)cz;
+    if (ci != w.c_idx) {
+      w.c_idx = ci;
+      w.c_word = __ldg(tr.coarse + ci);
+    }
+    const uint32_t cw = w.c_word, kind = cw >> 28;
+    if (kind == kCoarseEmpty) {
+      // empty box of radius k-1 brick-map cells around this one
+      const int r = (int)(cw & 0x0FFFFFFFu) - 1, Nc = 1 << Lc;
+      const int cc[3] = {cx, cy, cz};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = max(cc[a] - r, 0) << cs;
+        hi[a] = min(cc[a] + r + 1, Nc) << cs;
+      }
+      e = kEmpty;
+    } else {
+      int level;
+      if (kind == 0) {
+        const uint32_t b = cw & 0x0FFFFFFFu;
+        if (b >= (uint32_t)tr.brick_count) {
+          raise_status(tr, kStatusBadIndex);
+          w.alive = false;
+          return false;
+        }
+        const int m = (1 << cs) - 1;
+        const uint32_t idx = (uint32_t)(((w.cell[0] & m) << (2 * cs)) | ((w.cell[1] & m) << cs) | (w.cell[2] & m));
+        const uint32_t v = __ldg(tr.bricks + ((size_t)b << (3 * cs)) + idx);
+        level = (int)(v >> 28);
+        const uint32_t id = v & kBrickEmpty;
+        e = id == kBrickEmpty ? kEmpty : (kLeafBit | id);
+      } else {
+        level = (int)kind;
+        e = kLeafBit | (cw & 0x0FFFFFFFu);
+      }
+      if (e != kEmpty && (e & ~kLeafBit) >= (uint32_t)tr.n_leaves) {
+        raise_status(tr, kStatusBadIndex);
+        e = kEmpty;
+      }
+      const int size = 1 << (tr.depth - level);
+      fine = size == 1;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = w.cell[a] & -size;
+        hi[a] = lo[a] + size;
+      }
+    }
+  } else {
+    int level;
+    e = descend<kSmem, kPath>(tr, s_child, pr, w.cell, w.restart, level);
+    const int size = 1 << (tr.depth - level);
+    fine = size == 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = w.cell[a] & -size;
+      hi[a] = lo[a] + size;
+    }
+  }
   float gap[3], tx[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    lo[a] = w.cell[a] & -size;
-    gap[a] = (float)(w.gd[a] > 0.f ? lo[a] + size : lo[a]) - w.go[a];  // exact
+    gap[a] = (float)(w.gd[a] > 0.f ? hi[a] : lo[a]) - w.go[a];  // exact
     tx[a] = w.gd[a] != 0.f ? gap[a] * w.inv[a] : INFINITY;
   }
   // exit axis: first minimum (exact ties x < y < z); register-only selects
@@ -348,20 +421,27 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
       w.t_cur = t_exit;
       w.t_lo = x_lo;
     }
-    bool inside = true;
+    // on the other axes the neighbour of a finest cell across the exit face
+    // has the same coordinates; a larger box needs the exit point's cell
+    if (!fine) {
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      if (b == ax) {
-        const int nc = w.gd[b] > 0.f ? lo[b] + size : lo[b] - 1;
-        inside = nc >= 0 && nc < N;
-        w.cell[b] = nc;
-        // deepest level whose cell holds both the old node and the new cell
-        if (kPath && inside) w.restart = tr.depth - 32 + __clz(nc ^ lo[b]);
-      } else {
-        const float p = fmaf(w.t_cur, w.gd[b], w.go[b]);
-        w.cell[b] = min(max(cell_of(p, w.gd[b], N), lo[b]), lo[b] + size - 1);
+      for (int b = 0; b < 3; ++b) {
+        if (b != ax) {
+          const float p = fmaf(w.t_cur, w.gd[b], w.go[b]);
+          w.cell[b] = min(max(cell_of(p, w.gd[b], N), lo[b]), hi[b] - 1);
+        }
       }
     }
+    const int lo_ax = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
+    const int hi_ax = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
+    const float gd_ax = ax == 0 ? w.gd[0] : (ax == 1 ? w.gd[1] : w.gd[2]);
+    const int nc = gd_ax > 0.f ? hi_ax : lo_ax - 1;
+    const bool inside = nc >= 0 && nc < N;
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      if (b == ax) w.cell[b] = nc;
+    // deepest level whose cell holds both the old node and the new cell
+    if (kPath && inside && !tr.coarse) w.restart = tr.depth - 32 + __clz(nc ^ lo_ax);
     if (!inside) w.alive = false;
   }
   return found;

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ master, f
                                                    const unsigned int *__restrict__ touched, long long n_leaves,
                                                    int stride_f32, int rec_len, float lr, float b1, float b2,
                                                    float eps, float c1, float c2) {
-  const int quads = stride_f32 / 4;
+  const int quads = (rec_len + 3) / 4;  // quads past the record's entries are padding and stay zero
   const long long total = n_leaves * quads;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {

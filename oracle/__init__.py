@@ -91,6 +91,8 @@ def configure(L):
     L.or_quantize_fp8.argtypes = [p, i64, ci, p, p]
     L.or_round_e4m3.restype = None
     L.or_round_e4m3.argtypes = [p, p, i64]
+    L.or_slice.argtypes = [p, d, p, p]
+    L.or_render_slice.argtypes = [p, p, p, p, i64, p, p, p, p, p, p, p, ci]
     return L
 
 
@@ -225,6 +227,38 @@ def render_grad(tree, rays, grad_rgb, grad_alpha=None, t_stop: float = 1e-4, act
     lib().or_render_grad(ctypes.byref(ot.struct), ctypes.byref(op), n, _ptr(o), _ptr(d), _ptr(t), _ptr(g),
                          None if ga is None else _ptr(ga), _ptr(gs), _ptr(gg), _ptr(gh), nthreads or default_threads())
     return {"w_sigma": gs, "w_gamma": gg, "w_hh": gh}
+
+
+def slice_at(tree, t: float, otree: OracleTree | None = None) -> dict:
+    """Time slice (Sec. 7; caption of the HH-colour figure): at time t each
+    leaf's density sigma and spherical-harmonic colour coefficients
+    sh[leaf][ch][l^2 + l + m] = sum_{n >= l} w_nlm R_nl(gamma(t))."""
+    ot = otree or OracleTree(tree)
+    t = min(max(float(t), 0.0), 1.0)
+    ny = (ot.degree + 1) ** 2
+    sigma = np.zeros(ot.n_leaves)
+    sh = np.zeros((ot.n_leaves, 3, ny))
+    lib().or_slice(ctypes.byref(ot.struct), t * (ot.T - 1), _ptr(sigma), _ptr(sh))
+    return {"sigma": sigma, "sh": sh}
+
+
+def render_slice(tree, sl: dict, rays, t_stop: float = 1e-4, act: str = "sigmoid", nthreads: int | None = None,
+                 otree: OracleTree | None = None) -> dict:
+    """Eq. volume-rendering of a time slice: the tree's voxels and chords, the
+    slice's density, colour act(sum_lm s_lm Y_lm(d)).  Ray times are unused."""
+    ot = otree or OracleTree(tree)
+    o, d, _ = _rays64(rays)
+    n = o.shape[1]
+    sigma = np.ascontiguousarray(sl["sigma"], np.float64)
+    sh = np.ascontiguousarray(sl["sh"], np.float64)
+    out = {k: np.zeros(n) for k in ("alpha", "depth", "tau")}
+    out["rgb"] = np.zeros((n, 3))
+    out["nseg"] = np.zeros(n, np.int32)
+    op = _opts(t_stop, act)
+    lib().or_render_slice(ctypes.byref(ot.struct), ctypes.byref(op), _ptr(sigma), _ptr(sh), n, _ptr(o), _ptr(d),
+                          _ptr(out["rgb"]), _ptr(out["alpha"]), _ptr(out["depth"]), _ptr(out["tau"]),
+                          _ptr(out["nseg"]), nthreads or default_threads())
+    return out
 
 
 def compose(trees, transforms, time_offsets, tints, rays, mode: str = "sorted", t_stop: float = 1e-4,

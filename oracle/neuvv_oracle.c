@@ -20,7 +20,11 @@
  *   - spatial/temporal edits and depth-ordered blending (Eq. st_composite_affine,
  *     Algorithm 1)
  *   - Adam on touched leaves, BF16 rounding of stored coefficients, FP8 E4M3
- *     rounding with per-leaf power-of-two scales (a storage ablation).
+ *     rounding with per-leaf power-of-two scales (a storage ablation);
+ *   - the time slice (Sec. 7 and the caption of the HH-colour figure: at a
+ *     fixed time the hyper angle gamma(t) is a constant, and the 4D
+ *     harmonics reduce to 3D spherical harmonics with coefficients
+ *     s_lm = sum_n w_nlm R_nl(gamma(t))), and volume rendering of a slice.
  *
  * Readings taken where the paper is garbled or silent (kept identical in the
  * design notes):
@@ -812,4 +816,101 @@ void or_quantize_fp8(const float *in, int64_t n_groups, int len, double *out, do
 /* The plain E4M3 rounding of each value (no scale), for the pins. */
 void or_round_e4m3(const double *in, double *out, int64_t n) {
   for (int64_t i = 0; i < n; ++i) out[i] = e4m3_nearest(in[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time slice: density and spherical-harmonic colour coefficients of every   */
+/* leaf at one time (Sec. 7; the HH-colour figure's caption)                */
+/* ------------------------------------------------------------------------ */
+
+/* sigma: [n_leaves]; sh: [n_leaves][3][(degree+1)^2], index l^2 + l + m.  u is
+   the frame coordinate t (T - 1).  For each leaf gamma = pi sigmoid(b(u) .
+   w_gamma) is fixed, so sum_{n,l,m} w_nlm R_nl(gamma) Y_lm(d) regroups as
+   sum_{l,m} (sum_{n >= l} w_nlm R_nl(gamma)) Y_lm(d). */
+void or_slice(const or_tree *tr, double u, double *sigma, double *sh) {
+  double *a = (double *)malloc(sizeof(double) * tr->K), *b = (double *)malloc(sizeof(double) * tr->K);
+  basis_rows(tr, u, a, b);
+  const int Nh = or_n_hh(tr->degree), NY = (tr->degree + 1) * (tr->degree + 1);
+  for (int64_t leaf = 0; leaf < tr->n_leaves; ++leaf) {
+    double ps = 0.0, pg = 0.0;
+    for (int k = 0; k < tr->K; ++k) {
+      ps += a[k] * coef(tr, tr->w_sigma, k, leaf);
+      pg += b[k] * coef(tr, tr->w_gamma, k, leaf);
+    }
+    sigma[leaf] = ps > 0.0 ? ps : 0.0;
+    const double gamma = M_PI * sigmoid(pg);
+    for (int ch = 0; ch < 3; ++ch)
+      for (int l = 0; l <= tr->degree; ++l)
+        for (int m = -l; m <= l; ++m) {
+          double acc = 0.0;
+          for (int n = l; n <= tr->degree; ++n)
+            acc += coef(tr, tr->w_hh, (int64_t)ch * Nh + or_hh_index(n, l, m), leaf) * or_hh_radial(n, l, gamma);
+          sh[(leaf * 3 + ch) * NY + l * l + l + m] = acc;
+        }
+  }
+  free(a);
+  free(b);
+}
+
+/* Volume rendering of a slice (Eq. volume-rendering): the same voxels and
+   chords as the tree's walk, density sigma[leaf], colour act(sum_lm s_lm Y_lm(d)). */
+typedef struct {
+  const or_tree *tr;
+  const or_opts *op;
+  const double *sigma, *sh;
+  const double *o, *d;
+  int64_t n;
+  double *rgb, *alpha, *depth, *tau;
+  int32_t *nseg;
+} slice_ctx;
+
+static void slice_range(void *p, int64_t lo, int64_t hi) {
+  slice_ctx *c = (slice_ctx *)p;
+  const or_tree *tr = c->tr;
+  const int NY = (tr->degree + 1) * (tr->degree + 1);
+  or_seg *segs = (or_seg *)malloc(sizeof(or_seg) * max_segments(tr));
+  double *Y = (double *)malloc(sizeof(double) * NY);
+  for (int64_t r = lo; r < hi; ++r) {
+    double o[3] = {c->o[r], c->o[c->n + r], c->o[2 * c->n + r]};
+    double d[3] = {c->d[r], c->d[c->n + r], c->d[2 * c->n + r]}, dn[3];
+    unit(d, dn);
+    for (int l = 0; l <= tr->degree; ++l)
+      for (int m = -l; m <= l; ++m) Y[l * l + l + m] = or_sh_real(l, m, dn);
+    int ns = or_trace(tr, o, dn, segs, max_segments(tr));
+    double tau = 0.0, acc[3] = {0, 0, 0}, alpha = 0.0, dnum = 0.0;
+    int composited = 0;
+    for (int i = 0; i < ns; ++i) {
+      const int64_t leaf = segs[i].leaf;
+      const double sg = c->sigma[leaf];
+      double col[3];
+      for (int ch = 0; ch < 3; ++ch) {
+        double z = 0.0;
+        for (int k = 0; k < NY; ++k) z += c->sh[(leaf * 3 + ch) * NY + k] * Y[k];
+        col[ch] = c->op->act == 0 ? sigmoid(z) : z;
+      }
+      double delta = segs[i].t1 - segs[i].t0;
+      const double Ti = exp(-tau);                 /* transmittance in front of segment i */
+      double w = Ti * (1.0 - exp(-sg * delta));
+      for (int ch = 0; ch < 3; ++ch) acc[ch] += w * col[ch];
+      alpha += w;
+      dnum += 0.5 * w * (segs[i].t0 + segs[i].t1);
+      tau += sg * delta;
+      composited = i + 1;
+      if (exp(-tau) < c->op->t_stop) break;
+    }
+    for (int ch = 0; ch < 3; ++ch) c->rgb[3 * r + ch] = acc[ch];
+    c->alpha[r] = alpha;
+    c->tau[r] = tau;
+    c->depth[r] = alpha >= 1e-4 ? dnum / alpha : INFINITY;
+    c->nseg[r] = composited;
+  }
+  free(segs);
+  free(Y);
+}
+
+void or_render_slice(const or_tree *tr, const or_opts *op, const double *sigma, const double *sh, int64_t n,
+                     const double *o, const double *d, double *rgb, double *alpha, double *depth, double *tau,
+                     int32_t *nseg, int nthreads) {
+  slice_ctx c = {tr, op, sigma, sh, o, d, n, rgb, alpha, depth, tau, nseg};
+  parallel_for(n, nthreads, slice_range, &c);
 }

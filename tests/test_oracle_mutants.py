@@ -41,6 +41,9 @@ MUTANTS = {
                                  "return copysign(round(a / spacing) * spacing, x);"),
     "fp8_scale_search_starts_too_high": ("int p = e - 10;", "int p = e - 8;"),
     "fp8_scale_not_smallest_at_exact_fit": ("while (ldexp(448.0, p) < mx) ++p;", "while (ldexp(448.0, p) <= mx) ++p;"),
+    "slice_gamma_missing_pi": ("const double gamma = M_PI * sigmoid(pg);", "const double gamma = sigmoid(pg);"),
+    "slice_m_index_mirrored": ("sh[(leaf * 3 + ch) * NY + l * l + l + m] = acc;", "sh[(leaf * 3 + ch) * NY + l * l + l - m] = acc;"),
+    "slice_radial_l_for_n": ("* or_hh_radial(n, l, gamma);\n          sh[", "* or_hh_radial(l, l, gamma);\n          sh["),
 }
 
 
@@ -176,6 +179,12 @@ def _battery():
     fin = np.isfinite(a0["depth"])
     if np.abs(a1["depth"][fin] - s * a0["depth"][fin]).max() > 1e-10:
         failed.append("compose_scale")
+    # time slice: rendering it reproduces the HH render at its time
+    sr = _random_rays(rng, 80)
+    sr.times[:] = np.float32(0.45)
+    if np.abs(oracle.render_slice(gt, oracle.slice_at(gt, float(np.float32(0.45))), sr)["rgb"]
+              - oracle.render(gt, sr)["rgb"]).max() > 1e-12:
+        failed.append("slice")
     # FP8 E4M3: midpoints go to the even code; per-group scales are minimal
     from test_oracle_fp8 import e4m3_codes
     v = e4m3_codes()

@@ -472,6 +472,44 @@ def main():
     rgb32 = B.neuvv_render(tree32, dr, kernel="packet")["rgb"]
     del tree32
 
+    # -- time slice (Sec. 7): slice the tree at the first view's time, then
+    #    render that view from the slice and from the HH records
+    hbm_gbs0 = load_peaks()[0]
+    view = rays.subset(np.arange(1920 * 1080))
+    t_view = float(view.times[0])
+    drv = B.DeviceRays.from_host(view, device=dev)
+    sl = B.neuvv_slice(tree_d, t_view)
+    outv = B.alloc_out(view.n, dev)
+    for _ in range(2):
+        B.neuvv_slice(tree_d, t_view, out=sl)
+        B.neuvv_render_slice(tree_d, sl, drv, out=outv)
+    e0.record(stream)
+    for _ in range(reps):
+        B.neuvv_slice(tree_d, t_view, out=sl)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    slice_ms = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for _ in range(reps):
+        B.neuvv_render_slice(tree_d, sl, drv, out=outv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rs_ms = e0.elapsed_time(e1) / reps
+    rgb_slice = outv["rgb"].clone()
+    e0.record(stream)
+    for _ in range(reps):
+        B.neuvv_render(tree_d, drv, kernel="packet", out=outv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rv_ms = e0.elapsed_time(e1) / reps
+    slice_bytes = tree.n_leaves * ((tree_d.info.rec_stride * 2) + 4 * sl.shape[1])
+    time_slice = {"leaves": tree.n_leaves, "slice_ms": slice_ms, "slice_record_bytes": 4 * sl.shape[1],
+                  "slice_achieved_gbs": slice_bytes / (slice_ms / 1e3) / 1e9,
+                  "slice_frac_of_hbm": slice_bytes / (slice_ms / 1e3) / 1e9 / hbm_gbs0,
+                  "render_slice_ms_per_1080p_frame": rs_ms, "render_hh_ms_per_1080p_frame": rv_ms,
+                  "max_abs_rgb_slice_vs_hh": float((rgb_slice - outv["rgb"]).abs().max().item())}
+    del sl, outv, drv
+
     # -- storage ablation: the same training step on FP8 E4M3 records with
     #    per-leaf scales (same FP32 master, same rays and targets)
     fp8 = None
@@ -597,6 +635,7 @@ def main():
         "fwd_fp32_plain": {"ms_per_1080p_frame": plain_ms / args.views,
                            "msamples_per_s": plain_samples / (plain_ms / 1e3) / 1e6},
         "fp8_ablation": fp8,
+        "time_slice": time_slice,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": 7 * args.steps,

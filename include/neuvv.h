@@ -193,6 +193,31 @@ neuvv_status neuvv_tree_status(neuvv_tree *tree, uint32_t *flags);
 neuvv_status neuvv_render(const neuvv_tree *tree, const neuvv_rays *rays, float t, const neuvv_render_opts *opts,
                           neuvv_out *out, neuvv_stream stream);
 
+/* Time slice (Sec. 7, which proposes slicing a VOctree at one time into a
+ * PlenOctree-like representation, and the caption of the HH-colour figure: at
+ * a fixed time the hyper angle gamma(t) is a constant and the 4D harmonics
+ * reduce to 3D spherical harmonics).  Writes, for every leaf, its density
+ * sigma(t) = ReLU(a(u) . w_sigma) and its spherical-harmonic colour
+ * coefficients s[ch][l^2+l+m] = sum_{n>=l} w_HH[ch][n,l,m] R_nl(gamma(t)),
+ * gamma(t) = pi sigmoid(b(u) . w_gamma), u = t (T-1) (Eq. project-sigma,
+ * Eq. project-gamma, Eq. HH-color-2 with gamma fixed).
+ * slice: device FP32 [n_leaves][slice_stride], caller-owned, 16-byte aligned;
+ * per leaf [sigma, 0, 0, 0, s[0][0..NY), s[1][..], s[2][..]], NY =
+ * (hh_degree+1)^2, the rest of the row untouched.  slice_stride: floats per
+ * leaf, a multiple of 4 and at least 4 + 3 NY rounded up to 4 (16, 32, 52 for
+ * degree 1, 2, 3).  t must be in [0, 1]. */
+neuvv_status neuvv_slice(const neuvv_tree *tree, float t, float *slice, int32_t slice_stride, neuvv_stream stream);
+
+/* Volume rendering of a time slice made by neuvv_slice (Eq. volume-rendering
+ * over the tree's voxels and chords, density slice[leaf][0], colour
+ * act(sum_lm s_lm Y_lm(d))): the same outputs as neuvv_render at the slice's
+ * time, without evaluating the temporal bases and the hyper-angle radial
+ * factors per sample.  Always the packet kernel with the tree's launch
+ * configuration; ray times are ignored; a log in out is marked empty. */
+neuvv_status neuvv_render_slice(const neuvv_tree *tree, const float *slice, int32_t slice_stride,
+                                const neuvv_rays *rays, const neuvv_render_opts *opts, neuvv_out *out,
+                                neuvv_stream stream);
+
 /* Fused adjoint (Sec. 4.3 "Optimization": the renderer is differentiated by
  * hand for gradient descent on the leaf coefficients).  Replays every ray with
  * the forward traversal, recomputes each sample, and accumulates dL/dw for

@@ -71,7 +71,7 @@ class OptsC(ctypes.Structure):
 EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv_tree_get_info",
            "neuvv_tree_coeff_ptrs", "neuvv_tree_status", "neuvv_render", "neuvv_render_backward", "neuvv_compose",
            "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc",
-           "neuvv_tree_set_launch"]
+           "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice"]
 
 
 def library_path() -> str:
@@ -102,6 +102,8 @@ def lib(build_if_missing: bool = True):
                 "neuvv_trace": [p, p, i32, p, p, p, p, p],
                 "neuvv_autotune": [p, p, f, p, p],
                 "neuvv_tree_set_launch": [p, i32, i32, i32],
+                "neuvv_slice": [p, f, p, i32, p],
+                "neuvv_render_slice": [p, p, i32, p, p, p, p],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -285,6 +287,31 @@ def neuvv_render(tree: Tree, rays: DeviceRays, t: float = 0.0, t_stop: float = 1
     out = out if out is not None else alloc_out(rays.n)
     rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, kernel)
     _check(lib().neuvv_render(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(op), ctypes.byref(oc), _stream()))
+    return out
+
+
+def slice_stride(degree: int) -> int:
+    """Floats per leaf of a time slice: [sigma, 0, 0, 0] then 3 (degree+1)^2
+    coefficients, rounded up to a multiple of 4."""
+    return (4 + 3 * (degree + 1) ** 2 + 3) // 4 * 4
+
+
+def neuvv_slice(tree: Tree, t: float, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Time slice of the tree at t: FP32 [n_leaves, slice_stride] (density in
+    column 0, spherical-harmonic coefficients from column 4)."""
+    stride = slice_stride(tree.info.hh_degree) if out is None else out.shape[1]
+    if out is None:
+        out = torch.zeros(max(tree.info.n_leaves, 1), stride, device=f"cuda:{tree.info.device}", dtype=torch.float32)
+    _check(lib().neuvv_slice(tree.handle, float(t), _ptr(out), int(stride), _stream()))
+    return out
+
+
+def neuvv_render_slice(tree: Tree, sl: torch.Tensor, rays: DeviceRays, t_stop: float = 1e-4, act: str = "sigmoid",
+                       out: dict | None = None) -> dict:
+    out = out if out is not None else alloc_out(rays.n)
+    rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, "packet")
+    _check(lib().neuvv_render_slice(tree.handle, _ptr(sl), int(sl.shape[1]), ctypes.byref(rc), ctypes.byref(op),
+                                    ctypes.byref(oc), _stream()))
     return out
 
 

@@ -562,6 +562,8 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
   a.work = packet && cfg.dynamic_queue ? t->work + 0 : nullptr;
   a.log = packet ? log_view(out->log, out->log_bytes, rays->n) : log_view(nullptr, 0, 0);
+  a.slice = nullptr;
+  a.slice_stride = 0;
   cudaError_t e;
   if (a.log.n_chunks) {
     e = cudaMemsetAsync(a.log.counter, 0, sizeof(unsigned long long), st);
@@ -571,6 +573,56 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   }
   e = launch_render_fwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_slice(const neuvv_tree *t, float time, float *slice, int32_t slice_stride, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (!(time >= 0.f && time <= 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "t must be in [0, 1]");
+  const int deg = t->info.hh_degree;
+  if (slice_stride < slice_min_stride(deg) || (slice_stride & 3))
+    return fail(NEUVV_ERR_INVALID_ARG, "slice_stride must be a multiple of 4 and >= %d", slice_min_stride(deg));
+  if (t->info.n_leaves == 0) return NEUVV_OK;
+  if (!slice || ((uintptr_t)slice & 15)) return fail(NEUVV_ERR_INVALID_ARG, "slice must be a 16-byte aligned pointer");
+  DeviceGuard g(t->info.device);
+  const DevTree d = dev_tree(t);
+  cudaError_t e = launch_slice(t->info.K_pad, deg, (DType)t->info.dtype, d, time * (float)(t->info.T - 1), slice,
+                               slice_stride, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "slice launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_render_slice(const neuvv_tree *t, const float *slice, int32_t slice_stride, const neuvv_rays *rays,
+                                const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK) return s;
+  const int deg = t->info.hh_degree;
+  if (slice_stride < slice_min_stride(deg) || (slice_stride & 3))
+    return fail(NEUVV_ERR_INVALID_ARG, "slice_stride must be a multiple of 4 and >= %d", slice_min_stride(deg));
+  if (!out || (rays->n > 0 && (!out->rgb || !out->alpha)))
+    return fail(NEUVV_ERR_INVALID_ARG, "out->rgb and out->alpha are required");
+  if ((s = check_log(out)) != NEUVV_OK) return s;
+  if (rays->n == 0) return NEUVV_OK;
+  if (t->info.n_leaves > 0 && (!slice || ((uintptr_t)slice & 15)))
+    return fail(NEUVV_ERR_INVALID_ARG, "slice must be a 16-byte aligned pointer");
+  DeviceGuard g(t->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  FwdArgs a;
+  a.tr = dev_tree(t);
+  a.rays = dev_rays(rays, 0.f);
+  a.out = DevOut{out->rgb, out->alpha, out->depth, out->tau, out->nseg};
+  a.t_stop = opts->t_stop;
+  a.act = opts->color_act;
+  const LaunchCfg &cfg = t->packet;
+  a.work = cfg.dynamic_queue ? t->work + 0 : nullptr;
+  a.log = log_view(nullptr, 0, 0);
+  a.slice = slice;
+  a.slice_stride = slice_stride;
+  cudaError_t e = clear_log(out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear log");
+  e = launch_render_slice(deg, a, cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "slice render launch");
   return NEUVV_OK;
 }
 

@@ -755,6 +755,17 @@ __device__ __forceinline__ void rows_to_smem(const DevTree &tr, float u, float *
   }
 }
 
+// Pre-activation density a(u) . w_sigma (Eq. project-sigma), four independent
+// FMA chains; the slice kernel forms it with the same operations.
+template <int KP, typename Rows, typename Rec>
+__device__ __forceinline__ float pre_sigma_of(const Rows &rows, const Rec &r) {
+  // four partial sums: independent FMA chains
+  float p4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < KP; ++k) p4[k & 3] = fmaf(rows.A(k), r.sig(k), p4[k & 3]);
+  return ((p4[0] + p4[1]) + (p4[2] + p4[3])) * r.scale_sigma();
+}
+
 // Eq. project-sigma, Eq. project-gamma, Eq. HH-color-2 for one leaf.  When the
 // density is zero the sample cannot contribute and colour is not evaluated.
 // With kDz the gamma-derivative of each channel's pre-activation is formed
@@ -763,11 +774,7 @@ __device__ __forceinline__ void rows_to_smem(const DevTree &tr, float u, float *
 template <int KP, int DEG, typename E, typename Rows, bool kDz = false>
 __device__ __forceinline__ void eval_sample(const DevTree &tr, const Rows &rows, const float *Y,
                                             const LeafRecord<KP, DEG, E> &r, int act, Sample<DEG> &s) {
-  // four partial sums: independent FMA chains
-  float p4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int k = 0; k < KP; ++k) p4[k & 3] = fmaf(rows.A(k), r.sig(k), p4[k & 3]);
-  const float ps = ((p4[0] + p4[1]) + (p4[2] + p4[3])) * r.scale_sigma();
+  const float ps = pre_sigma_of<KP>(rows, r);
   s.pre_sigma = ps;
   s.sigma = fmaxf(ps, 0.f);
   if (!(s.sigma > 0.f)) return;
@@ -804,6 +811,48 @@ template <int KP, int DEG, typename E>
 __device__ __forceinline__ void eval_sample(const DevTree &tr, const RayConst<KP, DEG> &rc,
                                             const LeafRecord<KP, DEG, E> &r, int act, Sample<DEG> &s) {
   eval_sample<KP, DEG, E>(tr, RegRows<KP>{rc.a, rc.b}, rc.Y, r, act, s);
+}
+
+// ---------------------------------------------------------------------------
+// Time slices (Sec. 7; the caption of the HH-colour figure): at a fixed time
+// gamma(t) is a constant and the 4D harmonics reduce to 3D spherical
+// harmonics.  A slice record holds [sigma, 0, 0, 0] then the coefficients
+// s[ch][l^2 + l + m] = sum_{n >= l} w[ch][n,l,m] R_nl(gamma(t)), FP32.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int slice_len(int deg) { return 4 + 3 * (deg + 1) * (deg + 1); }
+__host__ __device__ constexpr int slice_min_stride(int deg) { return (slice_len(deg) + 3) / 4 * 4; }
+
+// Density and colour of one leaf of a slice seen along unit direction with
+// harmonics Y.
+template <int DEG>
+__device__ __forceinline__ void shade_slice(const float *slice, int stride, uint32_t leaf, const float *Y, int act,
+                                            float &sigma, float c[3]) {
+  constexpr int NY = (DEG + 1) * (DEG + 1), NV = slice_min_stride(DEG) / 4;
+  const uint4 *p = reinterpret_cast<const uint4 *>(slice + (size_t)leaf * stride);
+  float v[NV * 4];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const uint4 q = ldg_v4(p + i);
+    v[4 * i] = __uint_as_float(q.x);
+    v[4 * i + 1] = __uint_as_float(q.y);
+    v[4 * i + 2] = __uint_as_float(q.z);
+    v[4 * i + 3] = __uint_as_float(q.w);
+  }
+  sigma = v[0];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float z = 0.f;
+#pragma unroll
+    for (int k = 0; k < NY; ++k) z = fmaf(v[4 + ch * NY + k], Y[k], z);
+    c[ch] = act == 0 ? sigmoidf_fast(z) : z;
+  }
+}
+
+__device__ __forceinline__ void slice_prefetch_l2(const float *slice, int stride, int deg, uint32_t leaf) {
+  const char *p = reinterpret_cast<const char *>(slice + (size_t)leaf * stride);
+  const int bytes = slice_min_stride(deg) * 4;
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p + bytes - 1));
 }
 
 // Rays in structure-of-arrays form.

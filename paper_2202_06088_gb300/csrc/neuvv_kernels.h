@@ -52,6 +52,8 @@ struct FwdArgs {
   int act;
   unsigned long long *work;  // packet counter of persistent warps (null: one packet per warp)
   SampleLog log;             // segments to record (n_chunks == 0: none)
+  const float *slice;        // render of a time slice: [n_leaves][slice_stride] (null: the tree's records)
+  int slice_stride;
 };
 
 struct BwdArgs {
@@ -110,6 +112,11 @@ cudaError_t launch_render_bwd(int KP, int DEG, DType dt, bool packet, const BwdA
                               cudaStream_t s);
 cudaError_t launch_compose(int KP, int DEG, DType dt, const ComposeArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
+// Time slice of a tree at frame coordinate u into slice [n_leaves][stride].
+cudaError_t launch_slice(int KP, int DEG, DType dt, const DevTree &tr, float u, float *slice, int stride,
+                         cudaStream_t s);
+// Packet render of a time slice (a.slice set), with the tree's launch configuration.
+cudaError_t launch_render_slice(int DEG, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 // Device address of the static work counter used by neuvv_compose_noalloc on
 // the current device (looked up on first use per device).
 cudaError_t noalloc_queue(unsigned long long **out);

@@ -49,7 +49,8 @@ __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
 // nearly full.  Descents restart at the lowest common ancestor of successive
 // cells (path per thread in shared memory); basis rows and the queue live in
 // shared memory too.
-template <int KP, int DEG, typename E>
+// kSlice: shade from a time slice (a.slice) instead of the tree's records.
+template <int KP, int DEG, typename E, bool kSlice = false>
 __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, unsigned present, int queue, int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
@@ -69,7 +70,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
   if (__ballot_sync(present, hit) == 0) return;  // the whole packet missed the tree
   float Y[(DEG + 1) * (DEG + 1)];
   if (hit) {
-    rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+    if (!kSlice) rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
     sh_real<DEG>(dn, Y);
   }
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f, dnum = 0.f, tau = 0.f;
@@ -94,7 +95,8 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
         q_dt[slot * B] = dt;
         ++qn;
         // the record is read when the segment's round comes: ask L2 for it now
-        LeafRecord<KP, DEG, E>::prefetch_l2(tr, leaf);
+        if (kSlice) slice_prefetch_l2(a.slice, a.slice_stride, DEG, leaf);
+        else LeafRecord<KP, DEG, E>::prefetch_l2(tr, leaf);
       }
       walking = w.alive;
     }
@@ -138,18 +140,27 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
       const float t0 = q_t0[qh * B], dt = q_dt[qh * B];
       qh = (qh + 1) & qmask;
       --qn;
-      LeafRecord<KP, DEG, E> rec;
-      rec.load(tr, leaf);
-      Sample<DEG> s;
-      eval_sample<KP, DEG, E>(tr, rows, Y, rec, a.act, s);
+      float sigma, col[3];
+      if constexpr (kSlice) {
+        shade_slice<DEG>(a.slice, a.slice_stride, leaf, Y, a.act, sigma, col);
+      } else {
+        LeafRecord<KP, DEG, E> rec;
+        rec.load(tr, leaf);
+        Sample<DEG> s;
+        eval_sample<KP, DEG, E>(tr, rows, Y, rec, a.act, s);
+        sigma = s.sigma;
+        col[0] = s.c[0];
+        col[1] = s.c[1];
+        col[2] = s.c[2];
+      }
       ++nseg;
-      if (s.sigma > 0.f) {
-        const float sd = s.sigma * dt;
+      if (sigma > 0.f) {
+        const float sd = sigma * dt;
         const float e = __expf(-sd);
         const float wgt = T * alpha_of(sd);
-        C0 = fmaf(wgt, s.c[0], C0);
-        C1 = fmaf(wgt, s.c[1], C1);
-        C2 = fmaf(wgt, s.c[2], C2);
+        C0 = fmaf(wgt, col[0], C0);
+        C1 = fmaf(wgt, col[1], C1);
+        C2 = fmaf(wgt, col[2], C2);
         A += wgt;
         dnum = fmaf(wgt, w.t_base + fmaf(0.5f, dt, t0), dnum);
         tau += sd;
@@ -174,7 +185,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
 // Packet forward kernel.  With a work counter the grid is persistent: each
 // warp takes the next 32-ray packet from the counter when it finishes one, so
 // a long ray holds up only its own warp, not the other warps of its block.
-template <int KP, int DEG, typename E>
+template <int KP, int DEG, typename E, bool kSlice = false>
 __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_kernel(const __grid_constant__ FwdArgs a, int queue, int ready) {
   // one packet per warp of the grid, or (with a work counter) packets pulled
   // one after another until the counter passes the last
@@ -197,7 +208,7 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_ker
     const long long i = (pk << 5) + lane;
     // lanes past the end sit the packet out; the others stay to its end
     const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
-    if (i < a.rays.n) packet_forward<KP, DEG, E>(a, i, present, queue, ready);
+    if (i < a.rays.n) packet_forward<KP, DEG, E, kSlice>(a, i, present, queue, ready);
     __syncwarp();
     if (!a.work) break;
     unsigned long long q = 0;
@@ -290,6 +301,112 @@ cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdA
   // FP8 storage is built for the two record shapes of the workloads only
   if (KP == 8 && DEG == 2) return fwd_one<8, 2, Fp8E4M3>(packet, a, cfg, s);
   if (KP == 16 && DEG == 3) return fwd_one<16, 3, Fp8E4M3>(packet, a, cfg, s);
+  return cudaErrorInvalidValue;
+}
+
+// Time slice: one thread per leaf.  Density and hyper angle from the basis
+// rows at frame coordinate u (Eq. project-sigma, Eq. project-gamma), the
+// radial factors R_nl(gamma) by the Gegenbauer recurrence, then
+// s[ch][l,m] = sum_{n >= l} w[ch][n,l,m] R_nl (Eq. HH-color-2 with gamma fixed).
+template <int KP, int DEG, typename E>
+__global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ DevTree tr, float u, float *slice,
+                                                    int stride) {
+  constexpr int NY = (DEG + 1) * (DEG + 1), NV = slice_min_stride(DEG) / 4;
+  const long long leaf = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (leaf >= tr.n_leaves) return;
+  RayConst<KP, DEG> rc;
+  ray_const_basis<KP, DEG>(tr, u, rc);
+  const RegRows<KP> rows{rc.a, rc.b};
+  LeafRecord<KP, DEG, E> rec;
+  rec.load(tr, (uint32_t)leaf);
+  float out[NV * 4];
+#pragma unroll
+  for (int k = 0; k < NV * 4; ++k) out[k] = 0.f;
+  out[0] = fmaxf(pre_sigma_of<KP>(rows, rec), 0.f);
+  float q4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < KP; ++k) q4[k & 3] = fmaf(rows.B(k), rec.gam(k), q4[k & 3]);
+  const float pg = ((q4[0] + q4[1]) + (q4[2] + q4[3])) * rec.scale_gamma();
+  float sg, cg, R[(DEG + 1) * (DEG + 2) / 2];
+  sincospif(sigmoidf_fast(pg), &sg, &cg);
+  hh_radial<DEG, false>(cg, sg, tr.hh_norm, R, nullptr);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int l = 0; l <= DEG; ++l)
+#pragma unroll
+      for (int m = -l; m <= l; ++m) {
+        float acc = 0.f;
+#pragma unroll
+        for (int n = l; n <= DEG; ++n) acc = fmaf(rec.hh(ch, hh_index(n, l, m)), R[radial_index(n, l)], acc);
+        out[4 + ch * NY + l * l + l + m] = acc * rec.scale_hh();
+      }
+  float4 *dst = reinterpret_cast<float4 *>(slice + (size_t)leaf * stride);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) dst[i] = make_float4(out[4 * i], out[4 * i + 1], out[4 * i + 2], out[4 * i + 3]);
+}
+
+template <int KP, int DEG, typename E>
+static cudaError_t slice_one(const DevTree &tr, float u, float *slice, int stride, cudaStream_t s) {
+  if (tr.n_leaves == 0) return cudaSuccess;
+  slice_kernel<KP, DEG, E><<<(unsigned)((tr.n_leaves + 255) / 256), 256, 0, s>>>(tr, u, slice, stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice(int KP, int DEG, DType dt, const DevTree &tr, float u, float *slice, int stride,
+                         cudaStream_t s) {
+#define NEUVV_SLICE_KD(E)                                   \
+  switch (KP * 10 + DEG) {                                  \
+    case 81: return slice_one<8, 1, E>(tr, u, slice, stride, s);   \
+    case 82: return slice_one<8, 2, E>(tr, u, slice, stride, s);   \
+    case 83: return slice_one<8, 3, E>(tr, u, slice, stride, s);   \
+    case 161: return slice_one<16, 1, E>(tr, u, slice, stride, s); \
+    case 162: return slice_one<16, 2, E>(tr, u, slice, stride, s); \
+    case 163: return slice_one<16, 3, E>(tr, u, slice, stride, s); \
+    case 321: return slice_one<32, 1, E>(tr, u, slice, stride, s); \
+    case 322: return slice_one<32, 2, E>(tr, u, slice, stride, s); \
+    case 323: return slice_one<32, 3, E>(tr, u, slice, stride, s); \
+    default: return cudaErrorInvalidValue;                  \
+  }
+  if (dt == kF32) NEUVV_SLICE_KD(float)
+  if (dt == kBF16) NEUVV_SLICE_KD(__nv_bfloat16)
+#undef NEUVV_SLICE_KD
+  if (KP == 8 && DEG == 2) return slice_one<8, 2, Fp8E4M3>(tr, u, slice, stride, s);
+  if (KP == 16 && DEG == 3) return slice_one<16, 3, Fp8E4M3>(tr, u, slice, stride, s);
+  return cudaErrorInvalidValue;
+}
+
+// Packet render of a slice: the packet forward with the slice shader (the
+// basis-row part of its shared memory is laid out for K_pad = 8 and unused;
+// the storage type only sets the register budget, 128 per thread).
+template <int DEG>
+static cudaError_t render_slice_one(const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
+  if (a.rays.n == 0) return cudaSuccess;
+  const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
+  const bool persistent = a.work != nullptr;
+  cudaError_t e;
+  if (persistent && (e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  const size_t sm = smem_bytes(cfg.block, 8, cfg.queue);
+  if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(render_packet_kernel<8, DEG, __nv_bfloat16, true>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
+    return e;
+  long long grid = blocks;
+  if (persistent) {
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_packet_kernel<8, DEG, __nv_bfloat16, true>,
+                                                           cfg.block, sm)) != cudaSuccess)
+      return e;
+    const long long want = (long long)(per_sm > 0 ? per_sm : 1) * cfg.num_sms;
+    if (want < grid) grid = want;
+  }
+  render_packet_kernel<8, DEG, __nv_bfloat16, true><<<(unsigned)grid, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_slice(int DEG, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
+  if (DEG == 1) return render_slice_one<1>(a, cfg, s);
+  if (DEG == 2) return render_slice_one<2>(a, cfg, s);
+  if (DEG == 3) return render_slice_one<3>(a, cfg, s);
   return cudaErrorInvalidValue;
 }
 

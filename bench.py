@@ -6,8 +6,9 @@ bases over T=150 frames, HH degree 3), 8 camera poses on a sphere of radius
 2.5 at 1920x1080, each at its own time stamp: 16,588,800 rays per step, all
 resident in HBM.  Coefficients are stored in BF16 with an FP32 master copy.
 
-One step = forward render (packet kernel) -> MSE loss gradient against fixed
-target images -> fused adjoint -> sparse Adam on the touched leaves.  The
+One step = forward render (packet kernel) -> loss gradient against fixed
+target images (Eq. rgb-loss plus 0.1 x the image-gradient regulariser of
+Sec. 4.3) -> fused adjoint -> sparse Adam on the touched leaves.  The
 headline metric is leaf-segment samples per second of the forward+backward
 pair (a sample is one leaf segment evaluated by the forward and re-evaluated
 by the adjoint, counted once).
@@ -38,9 +39,10 @@ import numpy as np  # noqa: E402
 
 METRIC = "VOctree Msamples/s fwd+bwd (BF16 batched vs FP32 plain); ms per 1080p frame; %roof"
 UNIT = "Msamples/s"
+LAMBDA_GRAD = 0.1   # weight of the image-gradient regulariser in the total loss (Sec. 4.3)
 WORKLOAD = ("depth-9 shell VOctree (~2M leaves, K=16, T=150, HH degree 3), 8 views x 1920x1080 "
-            "at 8 time stamps (16,588,800 rays), BF16 storage + FP32 master; step = fwd + MSE grad + adjoint + "
-            "sparse Adam")
+            "at 8 time stamps (16,588,800 rays), BF16 storage + FP32 master; step = fwd + loss grad (MSE + 0.1 "
+            "image-gradient regulariser) + adjoint + sparse Adam")
 
 
 def parse_args():
@@ -372,7 +374,7 @@ def main():
     B.lib()
 
     tree = I.config2_tree()
-    rays = I.config2_rays(n_views=args.views)[0]
+    rays, view_pixels = I.config2_rays(n_views=args.views)[:2]
     n = rays.n
     dev = torch.device("cuda", local)
     dr = B.DeviceRays.from_host(rays, device=dev)
@@ -395,7 +397,14 @@ def main():
     touched = tree_d.new_touched()
     loss = torch.zeros(1, device=dev)
     stream = torch.cuda.current_stream()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    # the image-gradient regulariser needs each view's pixel -> ray map
+    W_img, H_img = 1920, 1080
+    pix_map = np.empty((args.views, H_img * W_img), np.int32)
+    for v, pv in enumerate(view_pixels):
+        pix_map[v, pv] = v * H_img * W_img + np.arange(H_img * W_img, dtype=np.int32)
+    ray_of_pixel = torch.from_numpy(pix_map.reshape(args.views, H_img, W_img)).to(dev)
+    del pix_map
 
     def step(k, evs=None):
         if evs:
@@ -407,12 +416,15 @@ def main():
         B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
         if evs:
             evs[2].record(stream)
-        B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+        B.neuvv_grad_loss(out["rgb"], target, ray_of_pixel, LAMBDA_GRAD / n, grad_rgb, loss)
         if evs:
             evs[3].record(stream)
-        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=k)
+        B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
         if evs:
             evs[4].record(stream)
+        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=k)
+        if evs:
+            evs[5].record(stream)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -448,7 +460,7 @@ def main():
     samples = 0.5 * (samples_before + int(out["nseg"].sum().item()))
     value = world * samples / (ms_step / 1e3) / 1e6
     kern = {name: statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps))
-            for i, name in enumerate(["fwd", "mse", "bwd", "adam"])}
+            for i, name in enumerate(["fwd", "mse", "lgrad", "bwd", "adam"])}
 
     # -- the BF16 forward alone and the plain FP32 single-view kernel
     reps = max(3, args.steps)
@@ -529,6 +541,7 @@ def main():
             B.neuvv_render(tree8, dr, kernel="packet", out=out)
             loss.zero_()
             B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
+            B.neuvv_grad_loss(out["rgb"], target, ray_of_pixel, LAMBDA_GRAD / n, grad_rgb, loss)
             B.neuvv_render_backward(tree8, dr, out, grad_rgb, None, g8, t8, kernel="packet")
             B.neuvv_adam_step(tree8, g8, t8, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=k)
 
@@ -604,6 +617,7 @@ def main():
         B.neuvv_render(tree_d, dr2, kernel="packet", out=out)
         loss.zero_()
         B.neuvv_mse_grad(out["rgb"], d_tgt, scale=1.0 / n, grad=grad_rgb, loss=loss)
+        B.neuvv_grad_loss(out["rgb"], d_tgt, ray_of_pixel, LAMBDA_GRAD / n, grad_rgb, loss)
         B.neuvv_render_backward(tree_d, dr2, out, grad_rgb, None, grad, touched, kernel="packet")
         B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k)
         h_loss.copy_(loss, non_blocking=True)
@@ -638,7 +652,7 @@ def main():
         "time_slice": time_slice,
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": 8 * args.steps,
         "clocks": clk,
     }
     if not args.no_extra:

@@ -278,6 +278,21 @@ neuvv_status neuvv_adam_step(neuvv_tree *tree, float *grad, uint32_t *touched, f
 neuvv_status neuvv_mse_grad(const float *rgb, const float *target, int64_t n, float scale, float *grad_rgb,
                             float *loss_accum, neuvv_stream stream);
 
+/* Image-gradient regulariser of Sec. 4.3 "Optimization" (the equation after
+ * Eq. rgb-loss; the paper weights it by lambda_grad = 0.1 in the total loss):
+ * loss_accum[0] += lambda * sum over views and pixels of ||grad |I - I_hat|||^2,
+ * with E = |target - rgb| per channel and the image gradient taken as forward
+ * differences E(x+1, y) - E(x, y) and E(x, y+1) - E(x, y) between pixels that
+ * both have a ray, summed over the three channels.  grad_rgb += its gradient
+ * (d|I - I_hat|/d I_hat = sign(I_hat - I), 0 where equal), so it can follow
+ * neuvv_mse_grad on the same buffer.
+ * rgb, target, grad_rgb: device [n][3]; ray_of_pixel: device int32
+ * [n_views][height][width], the ray index of each pixel or -1 (pixels of a
+ * view are its rays' image in any ray order); n < 2^31.  loss_accum nullable. */
+neuvv_status neuvv_grad_loss(const float *rgb, const float *target, int64_t n, const int32_t *ray_of_pixel,
+                             int32_t width, int32_t height, int32_t n_views, float lambda, float *grad_rgb,
+                             float *loss_accum, neuvv_stream stream);
+
 /* Occupied leaves each ray crosses, in order (Sec. 4.3 "Rendering": the voxels
  * on the ray and their segment lengths), without early termination.  Writes up
  * to max_out entries per ray: leaf [n][max_out] int32 (-1 past the end),

@@ -261,6 +261,31 @@ def render_slice(tree, sl: dict, rays, t_stop: float = 1e-4, act: str = "sigmoid
     return out
 
 
+def grad_loss(rgb, target, ray_of_pixel, width: int, height: int, lam: float) -> dict:
+    """The image-gradient regulariser L_grad (Sec. 4.3 "Optimization", the
+    equation after the RGB loss) and its gradient with respect to the
+    rendered colours: lam * sum over views and pixels of ||grad |I - I_hat|||^2,
+    the image gradient as forward differences between horizontally and
+    vertically adjacent pixels (a pair counts when both pixels have a ray),
+    summed over the three channels.  ray_of_pixel [n_views, height, width]
+    holds the ray of each pixel or -1.  Returns loss (float) and grad [n, 3]
+    (d|I - I_hat|/d I_hat = sign(I_hat - I), 0 where they are equal)."""
+    rgb = np.asarray(rgb, np.float64)
+    tgt = np.asarray(target, np.float64)
+    m = np.asarray(ray_of_pixel, np.int64).reshape(-1, height, width)
+    E = np.abs(tgt - rgb)                                   # [n, 3]
+    loss = 0.0
+    dE = np.zeros_like(E)
+    for a, b in ((m[:, :, :-1], m[:, :, 1:]), (m[:, :-1, :], m[:, 1:, :])):   # (left, right), (up, down)
+        ok = (a >= 0) & (b >= 0)
+        ra, rb = a[ok], b[ok]
+        D = E[rb] - E[ra]                                    # forward difference, per channel
+        loss += float((D * D).sum())
+        np.add.at(dE, rb, 2.0 * D)
+        np.add.at(dE, ra, -2.0 * D)
+    return {"loss": lam * loss, "grad": lam * np.sign(rgb - tgt) * dE}
+
+
 def compose(trees, transforms, time_offsets, tints, rays, mode: str = "sorted", t_stop: float = 1e-4,
             act: str = "sigmoid", nthreads: int | None = None) -> dict:
     """Eq. st_composite_affine per primitive, then depth-aware blending

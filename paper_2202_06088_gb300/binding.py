@@ -71,7 +71,7 @@ class OptsC(ctypes.Structure):
 EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv_tree_get_info",
            "neuvv_tree_coeff_ptrs", "neuvv_tree_status", "neuvv_render", "neuvv_render_backward", "neuvv_compose",
            "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc",
-           "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice"]
+           "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss"]
 
 
 def library_path() -> str:
@@ -103,6 +103,7 @@ def lib(build_if_missing: bool = True):
                 "neuvv_autotune": [p, p, f, p, p],
                 "neuvv_tree_set_launch": [p, i32, i32, i32],
                 "neuvv_slice": [p, f, p, i32, p],
+                "neuvv_grad_loss": [p, p, i64, p, i32, i32, i32, f, p, p, p],
                 "neuvv_render_slice": [p, p, i32, p, p, p, p],
             }
             for name, args in sig.items():
@@ -288,6 +289,17 @@ def neuvv_render(tree: Tree, rays: DeviceRays, t: float = 0.0, t_stop: float = 1
     rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, kernel)
     _check(lib().neuvv_render(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(op), ctypes.byref(oc), _stream()))
     return out
+
+
+def neuvv_grad_loss(rgb: torch.Tensor, target: torch.Tensor, ray_of_pixel: torch.Tensor, lam: float = 0.1,
+                    grad: torch.Tensor | None = None, loss: torch.Tensor | None = None) -> torch.Tensor:
+    """Adds the image-gradient regulariser's gradient to grad (zeros if None)
+    and its value to loss[0]; ray_of_pixel: int32 [n_views, height, width]."""
+    grad = grad if grad is not None else torch.zeros_like(rgb)
+    V, H, W = ray_of_pixel.shape
+    _check(lib().neuvv_grad_loss(_ptr(rgb), _ptr(target), int(rgb.shape[0]), _ptr(ray_of_pixel), int(W), int(H),
+                                 int(V), float(lam), _ptr(grad), _ptr(loss), _stream()))
+    return grad
 
 
 def slice_stride(degree: int) -> int:

@@ -878,6 +878,20 @@ neuvv_status neuvv_mse_grad(const float *rgb, const float *target, int64_t n, fl
   return NEUVV_OK;
 }
 
+neuvv_status neuvv_grad_loss(const float *rgb, const float *target, int64_t n, const int32_t *ray_of_pixel,
+                             int32_t width, int32_t height, int32_t n_views, float lambda, float *grad_rgb,
+                             float *loss_accum, neuvv_stream stream) {
+  if (n < 0 || width < 0 || height < 0 || n_views < 0) return fail(NEUVV_ERR_INVALID_ARG, "negative size");
+  if (n >= 0x7FFFFFFF) return fail(NEUVV_ERR_INVALID_ARG, "n must be below 2^31 (int32 ray ids)");
+  const long long n_pix = (long long)n_views * width * height;
+  if (n_pix > 0 && (!rgb || !target || !grad_rgb || !ray_of_pixel))
+    return fail(NEUVV_ERR_INVALID_ARG, "rgb/target/ray_of_pixel/grad_rgb is NULL");
+  cudaError_t e = launch_grad_loss(rgb, target, ray_of_pixel, width, height, n_views, (long long)n, lambda, grad_rgb,
+                                   loss_accum, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "grad loss launch");
+  return NEUVV_OK;
+}
+
 neuvv_status neuvv_trace(const neuvv_tree *t, const neuvv_rays *rays, int32_t max_out, int32_t *leaf, float *t0,
                          float *t1, int32_t *count, neuvv_stream stream) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");

@@ -125,6 +125,8 @@ cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType 
                         float lr, float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
 cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
                        cudaStream_t s);
+cudaError_t launch_grad_loss(const float *rgb, const float *target, const int *map, int width, int height,
+                             long long n_views, long long n_rays, float lam, float *grad, float *loss, cudaStream_t s);
 
 // Dynamic shared memory of the packet kernels: per thread the basis rows
 // (2 K_pad floats), the descent path (16 levels) and the segment queue

@@ -33,6 +33,69 @@ __global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ rgb,
   }
 }
 
+// Image-gradient regulariser L_grad (Sec. 4.3 "Optimization"): with
+// E = |I - I_hat| per channel, lam * sum over views of the squared forward
+// differences of E between horizontally and vertically adjacent pixels.  One
+// thread per pixel: it adds to its own ray's dL/dI_hat the derivative of the
+// (up to four) differences its pixel takes part in, and to the loss the two
+// it owns (towards its right and lower neighbours).  map: ray of each pixel
+// [n_views][height][width], -1 for none.
+__global__ void __launch_bounds__(256) grad_loss_kernel(const float *__restrict__ rgb, const float *__restrict__ target,
+                                                        const int *__restrict__ map, int width, int height,
+                                                        long long n_pix, long long n_rays, float lam,
+                                                        float *__restrict__ grad, float *__restrict__ loss) {
+  float part = 0.f;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n_pix;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int r = __ldg(map + p);
+    if (r < 0 || r >= n_rays) continue;
+    const long long img = p % ((long long)width * height);
+    const int y = (int)(img / width), x = (int)(img - (long long)y * width);
+    float E[3], g[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      E[ch] = fabsf(__ldg(target + 3 * r + ch) - __ldg(rgb + 3 * r + ch));
+      g[ch] = 0.f;
+    }
+    // neighbours: left, right, up, down; sgn = +1 when this pixel is the
+    // second of the pair (the difference is E_this - E_other), -1 otherwise
+    const int nx[4] = {x - 1, x + 1, x, x};
+    const int ny[4] = {y, y, y - 1, y + 1};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (nx[k] < 0 || nx[k] >= width || ny[k] < 0 || ny[k] >= height) continue;
+      const int q = __ldg(map + (p - img) + (long long)ny[k] * width + nx[k]);
+      if (q < 0 || q >= n_rays) continue;
+      const bool second = (k == 0 || k == 2);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float Eq = fabsf(__ldg(target + 3 * q + ch) - __ldg(rgb + 3 * q + ch));
+        const float D = second ? E[ch] - Eq : Eq - E[ch];
+        g[ch] = second ? fmaf(2.f, D, g[ch]) : fmaf(-2.f, D, g[ch]);
+        if (!second) part = fmaf(D, D, part);
+      }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const float dv = __ldg(rgb + 3 * r + ch) - __ldg(target + 3 * r + ch);
+      const float sgn = dv > 0.f ? 1.f : (dv < 0.f ? -1.f : 0.f);
+      grad[3 * r + ch] += lam * sgn * g[ch];
+    }
+  }
+  if (loss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+    __shared__ float red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      atomicAdd(loss, lam * s);
+    }
+  }
+}
+
 __device__ __forceinline__ unsigned short f32_to_bf16_rne(float f) {
   unsigned int u = __float_as_uint(f);
   if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return (unsigned short)((u >> 16) | 0x40u);
@@ -163,6 +226,16 @@ cudaError_t launch_mse(const float *rgb, const float *target, long long n, float
   const long long want = (3 * n + 255) / 256;
   const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
   mse_kernel<<<blocks, 256, 0, s>>>(rgb, target, n, scale, grad, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_loss(const float *rgb, const float *target, const int *map, int width, int height,
+                             long long n_views, long long n_rays, float lam, float *grad, float *loss, cudaStream_t s) {
+  const long long n_pix = n_views * width * height;
+  if (n_pix == 0) return cudaSuccess;
+  const long long want = (n_pix + 255) / 256;
+  const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
+  grad_loss_kernel<<<blocks, 256, 0, s>>>(rgb, target, map, width, height, n_pix, n_rays, lam, grad, loss);
   return cudaGetLastError();
 }
 

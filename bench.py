@@ -520,7 +520,35 @@ def main():
                   "slice_frac_of_hbm": slice_bytes / (slice_ms / 1e3) / 1e9 / hbm_gbs0,
                   "render_slice_ms_per_1080p_frame": rs_ms, "render_hh_ms_per_1080p_frame": rv_ms,
                   "max_abs_rgb_slice_vs_hh": float((rgb_slice - outv["rgb"]).abs().max().item())}
-    del sl, outv, drv
+    # -- spotlight shadow and distance falloff (Sec. 5): alpha map from a
+    #    256x256 camera at the light, Gaussian filter, lit view 0
+    light_cam = I.look_at(np.array([0.5, 0.5, 3.0]), np.array([0.5, 0.5, 0.5]), 256, 256, fov_y_deg=40.0)
+    # the light's rays in row-major pixel order: its alpha output is the map
+    lrays, _ = I.camera_rays(light_cam, t_view, tiled=False)
+    dlr = B.DeviceRays.from_host(lrays, device=dev)
+    lout = B.alloc_out(lrays.n, dev)
+    amap = lout["alpha"].view(1, 256, 256)
+    blurred = torch.empty_like(amap)
+    lit = torch.empty_like(outv["rgb"])
+
+    def lit_frame():
+        B.neuvv_render(tree_d, dlr, kernel="packet", out=lout)
+        B.neuvv_gaussian_blur(amap, 1.5, out=blurred)
+        B.neuvv_render(tree_d, drv, kernel="packet", out=outv)
+        B.neuvv_spotlight(drv, outv, light_cam, blurred[0], 0.0, [0.8, 0.8, 0.8], 2.5, out=lit)
+
+    lit_frame()
+    e0.record(stream)
+    for _ in range(reps):
+        lit_frame()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lit_ms = e0.elapsed_time(e1) / reps
+    time_slice["spotlight"] = {"lit_1080p_frame_ms": lit_ms, "plain_1080p_frame_ms": rv_ms,
+                               "overhead_frac": lit_ms / rv_ms - 1.0, "light_map": [256, 256], "blur_sigma": 1.5,
+                               "note": "light render (256x256) + blur + viewer render + spotlight shading; the paper "
+                                       "reports about 20% lower render speed with shadows and falloff"}
+    del sl, outv, drv, dlr, lout, amap, blurred, lit
 
     # -- storage ablation: the same training step on FP8 E4M3 records with
     #    per-leaf scales (same FP32 master, same rays and targets)
@@ -649,7 +677,7 @@ def main():
         "fwd_fp32_plain": {"ms_per_1080p_frame": plain_ms / args.views,
                            "msamples_per_s": plain_samples / (plain_ms / 1e3) / 1e6},
         "fp8_ablation": fp8,
-        "time_slice": time_slice,
+        "time_slice_and_lighting": time_slice,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": 8 * args.steps,

@@ -293,6 +293,69 @@ neuvv_status neuvv_grad_loss(const float *rgb, const float *target, int64_t n, c
                              int32_t width, int32_t height, int32_t n_views, float lambda, float *grad_rgb,
                              float *loss_accum, neuvv_stream stream);
 
+/* Terminating voxel of each ray (Sec. 5 "Appearance editing": the voxel
+ * where the accumulated alpha of the NeuVV render first reaches a threshold,
+ * 0.99 in the paper): leaf[i] = the leaf of the segment at which
+ * 1 - exp(-sum sigma delta) first reaches `threshold` (in (0, 1)), or -1.
+ * leaf: device int32 [n], caller-owned.  t: scalar time when rays->t is NULL. */
+neuvv_status neuvv_pick(const neuvv_tree *tree, const neuvv_rays *rays, float t, float threshold, int32_t *leaf,
+                        neuvv_stream stream);
+
+/* Assigns target colours to picked voxels (Sec. 5 "Appearance editing": a
+ * pattern painted over the performer from a view).  Each leaf that at least
+ * one of the n rays picked (leaf[i] >= 0, from neuvv_pick) gets the mean of
+ * those rays' colours (color [n][3]), target density sigma_d (< 0: keep the
+ * density) and time t_d (the edit is active at times >= t_d) in its edit
+ * record; other leaves keep theirs.  edits: device FP32 [n_leaves][8] =
+ * c_d (3), sigma_d, t_d, 3 unused; a record with t_d > 1 is inactive.
+ * accum: device FP32 [n_leaves][4] scratch, zeroed by the caller before the
+ * call.  Both 16-byte aligned, caller-owned. */
+neuvv_status neuvv_paint(const neuvv_tree *tree, const int32_t *leaf, const float *color, int64_t n, float sigma_d,
+                         float t_d, float *accum, float *edits, neuvv_stream stream);
+
+/* neuvv_render with appearance edits: a voxel whose edit is active at the
+ * ray's time (t >= t_d) has density sigma_d when sigma_d >= 0 and colour
+ * (1 - beta) c + beta c_d (beta in [0, 1]: 1 replaces, smaller values blend the
+ * target with the NeuVV colour).  Packet kernel; built for K <= 8 with
+ * degree 2 and 9 <= K <= 16 with degree 3, FP32 or BF16 storage
+ * (NEUVV_ERR_UNSUPPORTED otherwise).  A log in out is marked empty. */
+neuvv_status neuvv_render_edit(const neuvv_tree *tree, const neuvv_rays *rays, float t, const neuvv_render_opts *opts,
+                               const float *edits, float beta, neuvv_out *out, neuvv_stream stream);
+
+/* Gaussian low-pass filter of single-channel images (Sec. 5 "Spotlight
+ * Lighting": the shadow map is rendered at low resolution and filtered
+ * against Moire patterns).  in, out: distinct device FP32 buffers
+ * [n_images][height][width].  Weights exp(-k^2 / (2 sigma^2)) for
+ * |k| <= floor(3 sigma + 0.5) (sigma in (0, 5]), normalised, along x and along
+ * y; pixels beyond the border repeat the edge pixel. */
+neuvv_status neuvv_gaussian_blur(const float *in, float *out, int32_t width, int32_t height, int32_t n_images,
+                                 float sigma, neuvv_stream stream);
+
+/* A pinhole camera at the light, the same model as the viewer's: ray through
+ * pixel (px, py) (pixel centres at +0.5) along forward + sx right + sy up,
+ * sx = (2 (px+0.5)/width - 1) tan(fov_y/2) width/height,
+ * sy = (1 - 2 (py+0.5)/height) tan(fov_y/2); right, up, forward orthonormal. */
+typedef struct {
+  float eye[3], right[3], up[3], forward[3];
+  float fov_y_deg;
+  int32_t width, height;
+} neuvv_light;
+
+/* Spotlight shadow and distance falloff (Sec. 5 "Spotlight Lighting").  For
+ * each viewer ray with its render (rgb premultiplied [n][3], alpha [n], depth
+ * [n] along the unit direction, +inf where nothing was hit), with
+ * f(r) = (r_ref / r)^2 the falloff with the distance r to the light:
+ *   C_lit = rgb * f(|X - L|), X = o + depth * d (rgb where depth is +inf);
+ *   where the ray meets the ground plane z = ground_z ahead of its origin at
+ *   P, P is projected into the light camera and its alpha map light_alpha
+ *   [height][width] (rendered from the light and filtered; 0 outside the map)
+ *   is sampled bilinearly (texel centres at +0.5): a_L;
+ *   rgb_out = C_lit + (1 - alpha) * albedo * (1 - a_L) * f(|P - L|).
+ * All arrays device FP32, caller-owned; rgb_out may not alias rgb. */
+neuvv_status neuvv_spotlight(const neuvv_rays *rays, const float *rgb, const float *alpha, const float *depth,
+                             const neuvv_light *light, const float *light_alpha, float ground_z, const float albedo[3],
+                             float r_ref, float *rgb_out, neuvv_stream stream);
+
 /* Occupied leaves each ray crosses, in order (Sec. 4.3 "Rendering": the voxels
  * on the ray and their segment lengths), without early termination.  Writes up
  * to max_out entries per ray: leaf [n][max_out] int32 (-1 past the end),

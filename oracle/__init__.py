@@ -13,6 +13,7 @@ passage of the paper that the C function follows.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -92,6 +93,8 @@ def configure(L):
     L.or_round_e4m3.restype = None
     L.or_round_e4m3.argtypes = [p, p, i64]
     L.or_slice.argtypes = [p, d, p, p]
+    L.or_pick.argtypes = [p, p, i64, p, p, p, d, p, ci]
+    L.or_render_edit.argtypes = [p, p, p, d, i64, p, p, p, p, p, p, p, p, ci]
     L.or_render_slice.argtypes = [p, p, p, p, i64, p, p, p, p, p, p, p, ci]
     return L
 
@@ -284,6 +287,134 @@ def grad_loss(rgb, target, ray_of_pixel, width: int, height: int, lam: float) ->
         np.add.at(dE, rb, 2.0 * D)
         np.add.at(dE, ra, -2.0 * D)
     return {"loss": lam * loss, "grad": lam * np.sign(rgb - tgt) * dE}
+
+
+def pick(tree, rays, threshold: float = 0.99, t_stop: float = 1e-4, nthreads: int | None = None,
+         otree: OracleTree | None = None) -> np.ndarray:
+    """Terminating voxel of each ray (Sec. 5 "Appearance editing": the voxel
+    where the accumulated alpha of the NeuVV render first reaches the
+    threshold, 0.99 in the paper); -1 where it never does."""
+    ot = otree or OracleTree(tree)
+    o, d, t = _rays64(rays)
+    n = t.size
+    leaf = np.full(n, -1, np.int64)
+    op = _opts(t_stop, "sigmoid")
+    lib().or_pick(ctypes.byref(ot.struct), ctypes.byref(op), n, _ptr(o), _ptr(d), _ptr(t), float(threshold),
+                  _ptr(leaf), nthreads or default_threads())
+    return leaf
+
+
+def paint(n_leaves: int, leaves, colors, sigma_d: float, t_d: float, edits=None) -> np.ndarray:
+    """Assigns target colours to the picked voxels (Sec. 5 "Appearance
+    editing"): each leaf picked by at least one ray gets the mean colour of
+    those rays, with target density sigma_d and time t_d; other leaves keep
+    their edit (initially inactive: t_d = 2).  Returns edits [n_leaves, 5]."""
+    e = np.array(edits, np.float64) if edits is not None else np.tile([0.0, 0.0, 0.0, -1.0, 2.0], (n_leaves, 1))
+    leaves = np.asarray(leaves, np.int64)
+    ok = leaves >= 0
+    s = np.zeros((n_leaves, 3))
+    cnt = np.zeros(n_leaves)
+    np.add.at(s, leaves[ok], np.asarray(colors, np.float64)[ok])
+    np.add.at(cnt, leaves[ok], 1.0)
+    hit = cnt > 0
+    e[hit, :3] = s[hit] / cnt[hit, None]
+    e[hit, 3] = sigma_d
+    e[hit, 4] = t_d
+    return e
+
+
+def render_edit(tree, rays, edits, beta: float = 1.0, t_stop: float = 1e-4, act: str = "sigmoid",
+                nthreads: int | None = None, otree: OracleTree | None = None) -> dict:
+    """Eq. volume-rendering with per-voxel edits [n_leaves, 5] = (c_d, sigma_d,
+    t_d): active at ray time t >= t_d, density sigma_d when sigma_d >= 0,
+    colour (1 - beta) c + beta c_d."""
+    ot = otree or OracleTree(tree)
+    o, d, t = _rays64(rays)
+    n = t.size
+    ed = np.ascontiguousarray(edits, np.float64)
+    out = {k: np.zeros(n) for k in ("alpha", "depth", "tau")}
+    out["rgb"] = np.zeros((n, 3))
+    out["nseg"] = np.zeros(n, np.int32)
+    op = _opts(t_stop, act)
+    lib().or_render_edit(ctypes.byref(ot.struct), ctypes.byref(op), _ptr(ed), float(beta), n, _ptr(o), _ptr(d),
+                         _ptr(t), _ptr(out["rgb"]), _ptr(out["alpha"]), _ptr(out["depth"]), _ptr(out["tau"]),
+                         _ptr(out["nseg"]), nthreads or default_threads())
+    return out
+
+
+def gaussian_blur(img, sigma: float):
+    """The low-pass filter of the shadow map (Sec. 5 "Spotlight Lighting":
+    shadows rendered at low resolution and Gaussian-filtered against Moire
+    patterns).  img [n_images, height, width]; weights exp(-k^2 / (2 sigma^2))
+    for |k| <= floor(3 sigma + 0.5), normalised, applied along x then y with
+    the edge pixel repeated beyond the border."""
+    img = np.asarray(img, np.float64)
+    r = int(3.0 * sigma + 0.5)
+    k = np.arange(-r, r + 1, dtype=np.float64)
+    w = np.exp(-k * k / (2.0 * sigma * sigma))
+    w /= w.sum()
+    out = img
+    for axis in (2, 1):
+        n = out.shape[axis]
+        acc = np.zeros_like(out)
+        for wi, ki in zip(w, k):
+            idx = np.clip(np.arange(n) + int(ki), 0, n - 1)
+            acc += wi * np.take(out, idx, axis=axis)
+        out = acc
+    return out
+
+
+def spotlight(origins, dirs, rgb, alpha, depth, light, light_alpha, ground_z: float, albedo, r_ref: float):
+    """Spotlight shadow and distance falloff (Sec. 5 "Spotlight Lighting").
+    Per viewer ray (origins, dirs [3, n]) with its render (premultiplied rgb
+    [n, 3], alpha, depth along the unit direction):
+      f(r) = (r_ref / r)^2                       distance falloff from the light
+      X = o + depth d;  C_lit = C f(|X - L|)     (C unchanged where depth is inf)
+      ground point P = o + s d on z = ground_z (s > 0); P projected into the
+      light's camera (the pinhole of `light`, pixel centres at integer + 0.5)
+      samples the filtered light alpha map bilinearly (0 outside it);
+      G = albedo (1 - alpha_light(P)) f(|P - L|)
+      out = C_lit + (1 - alpha) G (C_lit where the ray misses the ground).
+    light: an inputs.Camera at the light position; light_alpha [H_l, W_l]."""
+    o = np.asarray(origins, np.float64)
+    d = np.asarray(dirs, np.float64)
+    d = d / np.linalg.norm(d, axis=0, keepdims=True)
+    C = np.asarray(rgb, np.float64)
+    A = np.asarray(alpha, np.float64)
+    D = np.asarray(depth, np.float64)
+    L = np.asarray(light.eye, np.float64)
+    Al = np.asarray(light_alpha, np.float64)
+    Hl, Wl = Al.shape
+    n = C.shape[0]
+    fall = lambda P: r_ref * r_ref / np.sum((P - L[:, None]) ** 2, axis=0)
+    out = C.copy()
+    fin = np.isfinite(D)
+    X = o[:, fin] + D[fin] * d[:, fin]
+    out[fin] = C[fin] * fall(X)[:, None]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = (ground_z - o[2]) / d[2]
+    hit = np.isfinite(s) & (s > 0)
+    P = o[:, hit] + s[hit] * d[:, hit]
+    v = P - L[:, None]
+    zc = light.forward @ v
+    th = math.tan(math.radians(light.fov_y_deg) / 2.0)
+    sx = (light.right @ v) / zc
+    sy = (light.up @ v) / zc
+    px = (sx / (th * Wl / Hl) + 1.0) * Wl / 2.0 - 0.5      # pixel coordinate, centres at integers
+    py = (1.0 - sy / th) * Hl / 2.0 - 0.5
+    x0 = np.floor(px).astype(np.int64)
+    y0 = np.floor(py).astype(np.int64)
+    fx, fy = px - x0, py - y0
+    def tex(yy, xx):
+        ok = (zc > 0) & (xx >= 0) & (xx < Wl) & (yy >= 0) & (yy < Hl)
+        val = np.zeros(xx.shape)
+        val[ok] = Al[yy[ok], xx[ok]]
+        return val
+    al = ((1 - fx) * (1 - fy) * tex(y0, x0) + fx * (1 - fy) * tex(y0, x0 + 1)
+          + (1 - fx) * fy * tex(y0 + 1, x0) + fx * fy * tex(y0 + 1, x0 + 1))
+    G = np.asarray(albedo, np.float64)[None, :] * ((1.0 - al) * fall(P))[:, None]
+    out[hit] += (1.0 - A[hit])[:, None] * G
+    return out
 
 
 def compose(trees, transforms, time_offsets, tints, rays, mode: str = "sorted", t_stop: float = 1e-4,

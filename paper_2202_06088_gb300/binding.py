@@ -71,7 +71,8 @@ class OptsC(ctypes.Structure):
 EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv_tree_get_info",
            "neuvv_tree_coeff_ptrs", "neuvv_tree_status", "neuvv_render", "neuvv_render_backward", "neuvv_compose",
            "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc",
-           "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss"]
+           "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss",
+           "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit"]
 
 
 def library_path() -> str:
@@ -104,6 +105,11 @@ def lib(build_if_missing: bool = True):
                 "neuvv_tree_set_launch": [p, i32, i32, i32],
                 "neuvv_slice": [p, f, p, i32, p],
                 "neuvv_grad_loss": [p, p, i64, p, i32, i32, i32, f, p, p, p],
+                "neuvv_gaussian_blur": [p, p, i32, i32, i32, f, p],
+                "neuvv_pick": [p, p, f, f, p, p],
+                "neuvv_paint": [p, p, p, i64, f, f, p, p, p],
+                "neuvv_render_edit": [p, p, f, p, p, f, p, p],
+                "neuvv_spotlight": [p, p, p, p, p, p, f, p, f, p, p],
                 "neuvv_render_slice": [p, p, i32, p, p, p, p],
             }
             for name, args in sig.items():
@@ -300,6 +306,76 @@ def neuvv_grad_loss(rgb: torch.Tensor, target: torch.Tensor, ray_of_pixel: torch
     _check(lib().neuvv_grad_loss(_ptr(rgb), _ptr(target), int(rgb.shape[0]), _ptr(ray_of_pixel), int(W), int(H),
                                  int(V), float(lam), _ptr(grad), _ptr(loss), _stream()))
     return grad
+
+
+def neuvv_pick(tree: Tree, rays: DeviceRays, threshold: float = 0.99, t: float = 0.0) -> torch.Tensor:
+    """Terminating leaf of each ray (int32, -1 where alpha never reaches the threshold)."""
+    leaf = torch.empty(rays.n, dtype=torch.int32, device=rays.o.device)
+    rc = rays.c()
+    _check(lib().neuvv_pick(tree.handle, ctypes.byref(rc), float(t), float(threshold), _ptr(leaf), _stream()))
+    return leaf
+
+
+def new_edits(tree: Tree) -> torch.Tensor:
+    """Edit records [n_leaves, 8], all inactive (t_d = 2)."""
+    e = torch.zeros(max(tree.info.n_leaves, 1), 8, device=f"cuda:{tree.info.device}")
+    e[:, 3] = -1.0
+    e[:, 4] = 2.0
+    return e
+
+
+def neuvv_paint(tree: Tree, leaf: torch.Tensor, colors: torch.Tensor, sigma_d: float, t_d: float,
+                edits: torch.Tensor) -> torch.Tensor:
+    accum = torch.zeros(max(tree.info.n_leaves, 1), 4, device=edits.device)
+    _check(lib().neuvv_paint(tree.handle, _ptr(leaf), _ptr(colors.contiguous()), int(leaf.numel()), float(sigma_d),
+                             float(t_d), _ptr(accum), _ptr(edits), _stream()))
+    return edits
+
+
+def neuvv_render_edit(tree: Tree, rays: DeviceRays, edits: torch.Tensor, beta: float = 1.0, t: float = 0.0,
+                      t_stop: float = 1e-4, act: str = "sigmoid", out: dict | None = None) -> dict:
+    out = out if out is not None else alloc_out(rays.n)
+    rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, "packet")
+    _check(lib().neuvv_render_edit(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(op), _ptr(edits),
+                                   float(beta), ctypes.byref(oc), _stream()))
+    return out
+
+
+class LightC(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("right", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("forward", ctypes.c_float * 3), ("fov_y_deg", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+def light_of(cam) -> LightC:
+    """The C description of a pinhole camera placed at the light (any object
+    with eye, right, up, forward, fov_y_deg, width, height)."""
+    L = LightC()
+    for k in range(3):
+        L.eye[k], L.right[k], L.up[k], L.forward[k] = (float(cam.eye[k]), float(cam.right[k]), float(cam.up[k]),
+                                                       float(cam.forward[k]))
+    L.fov_y_deg, L.width, L.height = float(cam.fov_y_deg), int(cam.width), int(cam.height)
+    return L
+
+
+def neuvv_gaussian_blur(img: torch.Tensor, sigma: float, out: torch.Tensor | None = None) -> torch.Tensor:
+    """img: FP32 [n_images, height, width] on the device."""
+    out = out if out is not None else torch.empty_like(img)
+    n, h, w = img.shape
+    _check(lib().neuvv_gaussian_blur(_ptr(img.contiguous()), _ptr(out), int(w), int(h), int(n), float(sigma),
+                                     _stream()))
+    return out
+
+
+def neuvv_spotlight(rays: DeviceRays, render: dict, light_cam, light_alpha: torch.Tensor, ground_z: float,
+                    albedo, r_ref: float, out: torch.Tensor | None = None) -> torch.Tensor:
+    out = out if out is not None else torch.empty_like(render["rgb"])
+    rc, L = rays.c(), light_of(light_cam)
+    alb = (ctypes.c_float * 3)(*[float(x) for x in albedo])
+    _check(lib().neuvv_spotlight(ctypes.byref(rc), _ptr(render["rgb"]), _ptr(render["alpha"]), _ptr(render["depth"]),
+                                 ctypes.byref(L), _ptr(light_alpha.contiguous()), float(ground_z), alb, float(r_ref),
+                                 _ptr(out), _stream()))
+    return out
 
 
 def slice_stride(degree: int) -> int:

@@ -564,6 +564,8 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   a.log = packet ? log_view(out->log, out->log_bytes, rays->n) : log_view(nullptr, 0, 0);
   a.slice = nullptr;
   a.slice_stride = 0;
+  a.edits = nullptr;
+  a.edit_beta = 0.f;
   cudaError_t e;
   if (a.log.n_chunks) {
     e = cudaMemsetAsync(a.log.counter, 0, sizeof(unsigned long long), st);
@@ -586,8 +588,10 @@ neuvv_status neuvv_slice(const neuvv_tree *t, float time, float *slice, int32_t 
   if (!slice || ((uintptr_t)slice & 15)) return fail(NEUVV_ERR_INVALID_ARG, "slice must be a 16-byte aligned pointer");
   DeviceGuard g(t->info.device);
   const DevTree d = dev_tree(t);
+  const int esize = t->info.dtype == NEUVV_F32 ? 4 : (t->info.dtype == NEUVV_BF16 ? 2 : 1);
   cudaError_t e = launch_slice(t->info.K_pad, deg, (DType)t->info.dtype, d, time * (float)(t->info.T - 1), slice,
-                               slice_stride, (cudaStream_t)stream);
+                               slice_stride, t->info.rec_stride * esize, t->num_sms > 0 ? t->num_sms : 1,
+                               (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "slice launch");
   return NEUVV_OK;
 }
@@ -619,6 +623,8 @@ neuvv_status neuvv_render_slice(const neuvv_tree *t, const float *slice, int32_t
   a.log = log_view(nullptr, 0, 0);
   a.slice = slice;
   a.slice_stride = slice_stride;
+  a.edits = nullptr;
+  a.edit_beta = 0.f;
   cudaError_t e = clear_log(out, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear log");
   e = launch_render_slice(deg, a, cfg, st);
@@ -889,6 +895,129 @@ neuvv_status neuvv_grad_loss(const float *rgb, const float *target, int64_t n, c
   cudaError_t e = launch_grad_loss(rgb, target, ray_of_pixel, width, height, n_views, (long long)n, lambda, grad_rgb,
                                    loss_accum, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "grad loss launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_pick(const neuvv_tree *t, const neuvv_rays *rays, float time, float threshold, int32_t *leaf,
+                        neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_time(rays, time)) != NEUVV_OK) return s;
+  if (!(threshold > 0.f && threshold < 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "threshold must be in (0, 1)");
+  if (rays->n == 0) return NEUVV_OK;
+  if (!leaf) return fail(NEUVV_ERR_INVALID_ARG, "leaf is NULL");
+  DeviceGuard g(t->info.device);
+  FwdArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.tr = dev_tree(t);
+  a.rays = dev_rays(rays, time);
+  cudaError_t e = launch_pick(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, a, threshold, leaf,
+                              (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pick launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_paint(const neuvv_tree *t, const int32_t *leaf, const float *color, int64_t n, float sigma_d,
+                         float t_d, float *accum, float *edits, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (n < 0) return fail(NEUVV_ERR_INVALID_ARG, "n < 0");
+  if ((n > 0 && (!leaf || !color)) || (t->info.n_leaves > 0 && (!accum || !edits)))
+    return fail(NEUVV_ERR_INVALID_ARG, "leaf/color/accum/edits is NULL");
+  if (((uintptr_t)accum & 15) || ((uintptr_t)edits & 15))
+    return fail(NEUVV_ERR_INVALID_ARG, "accum and edits must be 16-byte aligned");
+  DeviceGuard g(t->info.device);
+  cudaError_t e = launch_paint(leaf, color, n, t->info.n_leaves, accum, sigma_d, t_d, edits, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "paint launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_render_edit(const neuvv_tree *t, const neuvv_rays *rays, float time, const neuvv_render_opts *opts,
+                               const float *edits, float beta, neuvv_out *out, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK || (s = check_time(rays, time)))
+    return s;
+  if (!(beta >= 0.f && beta <= 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "beta must be in [0, 1]");
+  if (!out || (rays->n > 0 && (!out->rgb || !out->alpha)))
+    return fail(NEUVV_ERR_INVALID_ARG, "out->rgb and out->alpha are required");
+  if ((s = check_log(out)) != NEUVV_OK) return s;
+  if (rays->n == 0) return NEUVV_OK;
+  if (t->info.n_leaves > 0 && (!edits || ((uintptr_t)edits & 15)))
+    return fail(NEUVV_ERR_INVALID_ARG, "edits must be a 16-byte aligned pointer");
+  DeviceGuard g(t->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  FwdArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.tr = dev_tree(t);
+  a.rays = dev_rays(rays, time);
+  a.out = DevOut{out->rgb, out->alpha, out->depth, out->tau, out->nseg};
+  a.t_stop = opts->t_stop;
+  a.act = opts->color_act;
+  const LaunchCfg &cfg = t->packet;
+  a.work = cfg.dynamic_queue ? t->work + 0 : nullptr;
+  a.log = log_view(nullptr, 0, 0);
+  a.edits = edits;
+  a.edit_beta = beta;
+  cudaError_t e = clear_log(out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear log");
+  e = launch_render_edit(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, a, cfg, st);
+  if (e == cudaErrorNotSupported)
+    return fail(NEUVV_ERR_UNSUPPORTED, "edited renders are built for K <= 8 with degree 2 and 9 <= K <= 16 with degree 3, FP32 or BF16 storage");
+  if (e != cudaSuccess) return cuda_fail(e, "edit render launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_gaussian_blur(const float *in, float *out, int32_t width, int32_t height, int32_t n_images,
+                                 float sigma, neuvv_stream stream) {
+  if (width < 0 || height < 0 || n_images < 0) return fail(NEUVV_ERR_INVALID_ARG, "negative size");
+  if (!(sigma > 0.f && sigma <= 5.f)) return fail(NEUVV_ERR_INVALID_ARG, "sigma must be in (0, 5]");
+  const long long n_pix = (long long)n_images * width * height;
+  if (n_pix == 0) return NEUVV_OK;
+  if (!in || !out || in == out) return fail(NEUVV_ERR_INVALID_ARG, "in/out NULL or the same buffer");
+  BlurWeights bw;
+  bw.radius = (int)(3.0 * sigma + 0.5);
+  if (bw.radius > kMaxBlurRadius) bw.radius = kMaxBlurRadius;
+  double sum = 0.0, w[2 * kMaxBlurRadius + 1];
+  for (int k = -bw.radius; k <= bw.radius; ++k) sum += (w[k + bw.radius] = std::exp(-0.5 * k * k / ((double)sigma * sigma)));
+  for (int k = 0; k <= 2 * bw.radius; ++k) bw.w[k] = (float)(w[k] / sum);
+  cudaError_t e = launch_gaussian_blur(in, out, width, height, n_images, bw, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "blur launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_spotlight(const neuvv_rays *rays, const float *rgb, const float *alpha, const float *depth,
+                             const neuvv_light *light, const float *light_alpha, float ground_z, const float albedo[3],
+                             float r_ref, float *rgb_out, neuvv_stream stream) {
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK) return s;
+  if (!light || !albedo) return fail(NEUVV_ERR_INVALID_ARG, "light/albedo is NULL");
+  if (light->width < 1 || light->height < 1 || !(light->fov_y_deg > 0.f && light->fov_y_deg < 180.f))
+    return fail(NEUVV_ERR_INVALID_ARG, "light camera needs a positive size and a field of view in (0, 180)");
+  if (!(r_ref > 0.f)) return fail(NEUVV_ERR_INVALID_ARG, "r_ref must be positive");
+  if (rays->n == 0) return NEUVV_OK;
+  if (!rgb || !alpha || !depth || !light_alpha || !rgb_out || rgb_out == rgb)
+    return fail(NEUVV_ERR_INVALID_ARG, "rgb/alpha/depth/light_alpha/rgb_out NULL or rgb_out == rgb");
+  SpotArgs a;
+  a.rays = dev_rays(rays, 0.f);
+  a.rgb = rgb;
+  a.alpha = alpha;
+  a.depth = depth;
+  for (int k = 0; k < 3; ++k) {
+    a.light.eye[k] = light->eye[k];
+    a.light.right[k] = light->right[k];
+    a.light.up[k] = light->up[k];
+    a.light.forward[k] = light->forward[k];
+    a.albedo[k] = albedo[k];
+  }
+  a.light.fov_y_deg = light->fov_y_deg;
+  a.light.width = light->width;
+  a.light.height = light->height;
+  a.light_alpha = light_alpha;
+  a.ground_z = ground_z;
+  a.r_ref = r_ref;
+  a.out = rgb_out;
+  cudaError_t e = launch_spotlight(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "spotlight launch");
   return NEUVV_OK;
 }
 

@@ -603,6 +603,11 @@ struct LeafRecord {
 #pragma unroll
     for (int i = 0; i < NV; ++i) Elem<E>::unpack(raw[i], w + i * PV);
   }
+  // The same record from a copy in shared memory (a staged tile).
+  __device__ __forceinline__ void load_shared(const uint4 *p) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Elem<E>::unpack(p[i], w + i * PV);
+  }
   // Asks L2 for the lines of a leaf's record ahead of its use (no registers held).
   __device__ __forceinline__ static void prefetch_l2(const DevTree &tr, uint32_t leaf) {
     const char *p = reinterpret_cast<const char *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
@@ -645,6 +650,14 @@ struct LeafRecord<KP, DEG, Fp8E4M3> {
     const uint4 h = ldg_v4(p);
 #pragma unroll
     for (int i = 0; i < NV; ++i) raw[i] = ldg_v4(p + 1 + i);
+    sc[0] = __uint_as_float(h.x);
+    sc[1] = __uint_as_float(h.y);
+    sc[2] = __uint_as_float(h.z);
+  }
+  __device__ __forceinline__ void load_shared(const uint4 *p) {
+    const uint4 h = p[0];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) raw[i] = p[1 + i];
     sc[0] = __uint_as_float(h.x);
     sc[1] = __uint_as_float(h.y);
     sc[2] = __uint_as_float(h.z);

@@ -54,6 +54,8 @@ struct FwdArgs {
   SampleLog log;             // segments to record (n_chunks == 0: none)
   const float *slice;        // render of a time slice: [n_leaves][slice_stride] (null: the tree's records)
   int slice_stride;
+  const float *edits;        // appearance edits [n_leaves][8]: c_d (3), sigma_d, t_d, 0, 0, 0
+  float edit_beta;           // colour blend weight of an active edit
 };
 
 struct BwdArgs {
@@ -104,6 +106,29 @@ struct TraceArgs {
   int *count;
 };
 
+// Normalised 1D Gaussian weights w[0 .. 2 radius] of the shadow-map filter.
+constexpr int kMaxBlurRadius = 16;
+struct BlurWeights {
+  float w[2 * kMaxBlurRadius + 1];
+  int radius;
+};
+
+struct LightCam {
+  float eye[3], right[3], up[3], forward[3];
+  float fov_y_deg;
+  int width, height;
+};
+
+struct SpotArgs {
+  DevRays rays;
+  const float *rgb, *alpha, *depth;  // the viewer's render [n][3], [n], [n]
+  LightCam light;
+  const float *light_alpha;          // filtered alpha map [height][width] of the light camera
+  float ground_z, r_ref;
+  float albedo[3];
+  float *out;                        // [n][3]
+};
+
 // Each returns cudaGetLastError() of its launch (or cudaErrorInvalidValue for
 // an unsupported template combination).
 cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdArgs &a, const LaunchCfg &cfg,
@@ -112,9 +137,16 @@ cudaError_t launch_render_bwd(int KP, int DEG, DType dt, bool packet, const BwdA
                               cudaStream_t s);
 cudaError_t launch_compose(int KP, int DEG, DType dt, const ComposeArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
+cudaError_t launch_pick(int KP, int DEG, DType dt, const FwdArgs &a, float threshold, int *leaf_out, cudaStream_t s);
+cudaError_t launch_paint(const int *leaf, const float *color, long long n, long long n_leaves, float *accum,
+                         float sigma_d, float t_d, float *edits, cudaStream_t s);
+cudaError_t launch_render_edit(int KP, int DEG, DType dt, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+cudaError_t launch_gaussian_blur(const float *in, float *out, int width, int height, long long n_images,
+                                 const BlurWeights &bw, cudaStream_t s);
+cudaError_t launch_spotlight(const SpotArgs &a, cudaStream_t s);
 // Time slice of a tree at frame coordinate u into slice [n_leaves][stride].
 cudaError_t launch_slice(int KP, int DEG, DType dt, const DevTree &tr, float u, float *slice, int stride,
-                         cudaStream_t s);
+                         int rec_bytes, int num_sms, cudaStream_t s);
 // Packet render of a time slice (a.slice set), with the tree's launch configuration.
 cudaError_t launch_render_slice(int DEG, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 // Device address of the static work counter used by neuvv_compose_noalloc on

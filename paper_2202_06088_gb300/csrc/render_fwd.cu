@@ -49,8 +49,10 @@ __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
 // nearly full.  Descents restart at the lowest common ancestor of successive
 // cells (path per thread in shared memory); basis rows and the queue live in
 // shared memory too.
-// kSlice: shade from a time slice (a.slice) instead of the tree's records.
-template <int KP, int DEG, typename E, bool kSlice = false>
+// kShade: kShadeTree (the tree's records), kShadeSlice (a time slice,
+// a.slice) or kShadeEdit (the tree's records with appearance edits, a.edits).
+constexpr int kShadeTree = 0, kShadeSlice = 1, kShadeEdit = 2;
+template <int KP, int DEG, typename E, int kShade = kShadeTree>
 __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, unsigned present, int queue, int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
@@ -70,7 +72,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
   if (__ballot_sync(present, hit) == 0) return;  // the whole packet missed the tree
   float Y[(DEG + 1) * (DEG + 1)];
   if (hit) {
-    if (!kSlice) rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+    if (kShade != kShadeSlice) rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
     sh_real<DEG>(dn, Y);
   }
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f, dnum = 0.f, tau = 0.f;
@@ -95,7 +97,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
         q_dt[slot * B] = dt;
         ++qn;
         // the record is read when the segment's round comes: ask L2 for it now
-        if (kSlice) slice_prefetch_l2(a.slice, a.slice_stride, DEG, leaf);
+        if (kShade == kShadeSlice) slice_prefetch_l2(a.slice, a.slice_stride, DEG, leaf);
         else LeafRecord<KP, DEG, E>::prefetch_l2(tr, leaf);
       }
       walking = w.alive;
@@ -141,7 +143,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
       qh = (qh + 1) & qmask;
       --qn;
       float sigma, col[3];
-      if constexpr (kSlice) {
+      if constexpr (kShade == kShadeSlice) {
         shade_slice<DEG>(a.slice, a.slice_stride, leaf, Y, a.act, sigma, col);
       } else {
         LeafRecord<KP, DEG, E> rec;
@@ -152,6 +154,17 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
         col[0] = s.c[0];
         col[1] = s.c[1];
         col[2] = s.c[2];
+        if constexpr (kShade == kShadeEdit) {
+          // appearance edit of the voxel, active from its time t_d on
+          const float4 e0 = __ldg(reinterpret_cast<const float4 *>(a.edits) + 2 * (size_t)leaf);
+          const float4 e1 = __ldg(reinterpret_cast<const float4 *>(a.edits) + 2 * (size_t)leaf + 1);
+          if (t >= e1.x) {
+            if (e0.w >= 0.f) sigma = e0.w;
+            col[0] = fmaf(a.edit_beta, e0.x - col[0], col[0]);
+            col[1] = fmaf(a.edit_beta, e0.y - col[1], col[1]);
+            col[2] = fmaf(a.edit_beta, e0.z - col[2], col[2]);
+          }
+        }
       }
       ++nseg;
       if (sigma > 0.f) {
@@ -185,7 +198,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
 // Packet forward kernel.  With a work counter the grid is persistent: each
 // warp takes the next 32-ray packet from the counter when it finishes one, so
 // a long ray holds up only its own warp, not the other warps of its block.
-template <int KP, int DEG, typename E, bool kSlice = false>
+template <int KP, int DEG, typename E, int kShade = kShadeTree>
 __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_kernel(const __grid_constant__ FwdArgs a, int queue, int ready) {
   // one packet per warp of the grid, or (with a work counter) packets pulled
   // one after another until the counter passes the last
@@ -208,7 +221,7 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_ker
     const long long i = (pk << 5) + lane;
     // lanes past the end sit the packet out; the others stay to its end
     const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
-    if (i < a.rays.n) packet_forward<KP, DEG, E, kSlice>(a, i, present, queue, ready);
+    if (i < a.rays.n) packet_forward<KP, DEG, E, kShade>(a, i, present, queue, ready);
     __syncwarp();
     if (!a.work) break;
     unsigned long long q = 0;
@@ -304,21 +317,15 @@ cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdA
   return cudaErrorInvalidValue;
 }
 
-// Time slice: one thread per leaf.  Density and hyper angle from the basis
-// rows at frame coordinate u (Eq. project-sigma, Eq. project-gamma), the
-// radial factors R_nl(gamma) by the Gegenbauer recurrence, then
-// s[ch][l,m] = sum_{n >= l} w[ch][n,l,m] R_nl (Eq. HH-color-2 with gamma fixed).
+// Time slice of one leaf whose record is loaded: density and hyper angle from
+// the basis rows at frame coordinate u (Eq. project-sigma, Eq. project-gamma),
+// the radial factors R_nl(gamma) by the Gegenbauer recurrence, then
+// s[ch][l,m] = sum_{n >= l} w[ch][n,l,m] R_nl (Eq. HH-color-2 with gamma
+// fixed), written as one slice row of NV float4.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ DevTree tr, float u, float *slice,
-                                                    int stride) {
+__device__ __forceinline__ void slice_row(const DevTree &tr, const RegRows<KP> &rows, const LeafRecord<KP, DEG, E> &rec,
+                                          float4 *dst) {
   constexpr int NY = (DEG + 1) * (DEG + 1), NV = slice_min_stride(DEG) / 4;
-  const long long leaf = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (leaf >= tr.n_leaves) return;
-  RayConst<KP, DEG> rc;
-  ray_const_basis<KP, DEG>(tr, u, rc);
-  const RegRows<KP> rows{rc.a, rc.b};
-  LeafRecord<KP, DEG, E> rec;
-  rec.load(tr, (uint32_t)leaf);
   float out[NV * 4];
 #pragma unroll
   for (int k = 0; k < NV * 4; ++k) out[k] = 0.f;
@@ -341,38 +348,153 @@ __global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ DevT
         for (int n = l; n <= DEG; ++n) acc = fmaf(rec.hh(ch, hh_index(n, l, m)), R[radial_index(n, l)], acc);
         out[4 + ch * NY + l * l + l + m] = acc * rec.scale_hh();
       }
-  float4 *dst = reinterpret_cast<float4 *>(slice + (size_t)leaf * stride);
 #pragma unroll
   for (int i = 0; i < NV; ++i) dst[i] = make_float4(out[4 * i], out[4 * i + 1], out[4 * i + 2], out[4 * i + 3]);
 }
 
+// Time slice, one thread per leaf, records read from global memory (any
+// record and row size).
 template <int KP, int DEG, typename E>
-static cudaError_t slice_one(const DevTree &tr, float u, float *slice, int stride, cudaStream_t s) {
+__global__ void __launch_bounds__(256) slice_kernel(const __grid_constant__ DevTree tr, float u, float *slice,
+                                                    int stride) {
+  const long long leaf = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (leaf >= tr.n_leaves) return;
+  RayConst<KP, DEG> rc;
+  ray_const_basis<KP, DEG>(tr, u, rc);
+  LeafRecord<KP, DEG, E> rec;
+  rec.load(tr, (uint32_t)leaf);
+  slice_row<KP, DEG, E>(tr, RegRows<KP>{rc.a, rc.b}, rec, reinterpret_cast<float4 *>(slice + (size_t)leaf * stride));
+}
+
+// Bulk copies between global and shared memory through the TMA unit.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Waits until the mbarrier's phase `parity` completes, for at most `limit`
+// polls; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int k = 0; k < limit; ++k) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+constexpr int kSliceTile = 128;   // leaves per tile (one per thread)
+constexpr int kSliceWaitPolls = 1 << 22;
+
+// Time slice with TMA staging: a block takes tiles of kSliceTile consecutive
+// leaves; one thread loads the tile's records (consecutive in memory) into
+// shared memory with a single bulk copy completed on an mbarrier, every
+// thread turns its record into its slice row in a shared output tile, and one
+// bulk copy stores the tile's rows (consecutive in memory when the row
+// stride is the minimal one).  A wait that does not complete flags the
+// device status and ends the block.
+template <int KP, int DEG, typename E>
+__global__ void __launch_bounds__(kSliceTile) slice_tma_kernel(const __grid_constant__ DevTree tr, float u,
+                                                               float *slice, int rec_bytes) {
+  constexpr int NV = slice_min_stride(DEG) / 4;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) unsigned long long bar;
+  uint4 *in = reinterpret_cast<uint4 *>(sm);
+  float4 *out = reinterpret_cast<float4 *>(sm + (size_t)kSliceTile * rec_bytes);
+  const uint32_t bar_a = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  RayConst<KP, DEG> rc;
+  ray_const_basis<KP, DEG>(tr, u, rc);
+  const RegRows<KP> rows{rc.a, rc.b};
+  const long long n_tiles = (tr.n_leaves + kSliceTile - 1) / kSliceTile;
+  uint32_t parity = 0;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, parity ^= 1u) {
+    const long long first = tile * kSliceTile;
+    const int count = (int)min((long long)kSliceTile, tr.n_leaves - first);
+    if (threadIdx.x == 0) {
+      const uint32_t bytes = (uint32_t)count * (uint32_t)rec_bytes;
+      const char *src = static_cast<const char *>(tr.rec) + (size_t)first * rec_bytes;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(in)),
+          "l"(src), "r"(bytes), "r"(bar_a)
+          : "memory");
+    }
+    if (!mbar_wait(bar_a, parity, kSliceWaitPolls)) {
+      if (threadIdx.x == 0) raise_status(tr, kStatusSegCap);
+      return;
+    }
+    if ((int)threadIdx.x < count) {
+      LeafRecord<KP, DEG, E> rec;
+      rec.load_shared(in + (size_t)threadIdx.x * (rec_bytes / 16));
+      slice_row<KP, DEG, E>(tr, rows, rec, out + (size_t)threadIdx.x * NV);
+    }
+    // the rows become visible to the bulk copy (async proxy), then one store
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(slice + (size_t)first * NV * 4),
+                   "r"(smem_addr(out)), "r"((uint32_t)count * NV * 16)
+                   : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      // the output tile and the input buffer are reused by the next tile
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
+}
+
+template <int KP, int DEG, typename E>
+static cudaError_t slice_one(const DevTree &tr, float u, float *slice, int stride, int rec_bytes, int num_sms,
+                             cudaStream_t s) {
   if (tr.n_leaves == 0) return cudaSuccess;
+  if (stride == slice_min_stride(DEG) && rec_bytes % 16 == 0) {
+    const size_t sm = (size_t)kSliceTile * (rec_bytes + slice_min_stride(DEG) * 4);
+    cudaError_t e;
+    if (sm > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(slice_tma_kernel<KP, DEG, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm)) != cudaSuccess)
+      return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_tma_kernel<KP, DEG, E>, kSliceTile, sm)) !=
+        cudaSuccess)
+      return e;
+    const long long tiles = (tr.n_leaves + kSliceTile - 1) / kSliceTile;
+    long long grid = (long long)(per_sm > 0 ? per_sm : 1) * num_sms;
+    if (grid > tiles) grid = tiles;
+    slice_tma_kernel<KP, DEG, E><<<(unsigned)grid, kSliceTile, sm, s>>>(tr, u, slice, rec_bytes);
+    return cudaGetLastError();
+  }
   slice_kernel<KP, DEG, E><<<(unsigned)((tr.n_leaves + 255) / 256), 256, 0, s>>>(tr, u, slice, stride);
   return cudaGetLastError();
 }
 
 cudaError_t launch_slice(int KP, int DEG, DType dt, const DevTree &tr, float u, float *slice, int stride,
-                         cudaStream_t s) {
+                         int rec_bytes, int num_sms, cudaStream_t s) {
 #define NEUVV_SLICE_KD(E)                                   \
   switch (KP * 10 + DEG) {                                  \
-    case 81: return slice_one<8, 1, E>(tr, u, slice, stride, s);   \
-    case 82: return slice_one<8, 2, E>(tr, u, slice, stride, s);   \
-    case 83: return slice_one<8, 3, E>(tr, u, slice, stride, s);   \
-    case 161: return slice_one<16, 1, E>(tr, u, slice, stride, s); \
-    case 162: return slice_one<16, 2, E>(tr, u, slice, stride, s); \
-    case 163: return slice_one<16, 3, E>(tr, u, slice, stride, s); \
-    case 321: return slice_one<32, 1, E>(tr, u, slice, stride, s); \
-    case 322: return slice_one<32, 2, E>(tr, u, slice, stride, s); \
-    case 323: return slice_one<32, 3, E>(tr, u, slice, stride, s); \
+    case 81: return slice_one<8, 1, E>(tr, u, slice, stride, rec_bytes, num_sms, s);   \
+    case 82: return slice_one<8, 2, E>(tr, u, slice, stride, rec_bytes, num_sms, s);   \
+    case 83: return slice_one<8, 3, E>(tr, u, slice, stride, rec_bytes, num_sms, s);   \
+    case 161: return slice_one<16, 1, E>(tr, u, slice, stride, rec_bytes, num_sms, s); \
+    case 162: return slice_one<16, 2, E>(tr, u, slice, stride, rec_bytes, num_sms, s); \
+    case 163: return slice_one<16, 3, E>(tr, u, slice, stride, rec_bytes, num_sms, s); \
+    case 321: return slice_one<32, 1, E>(tr, u, slice, stride, rec_bytes, num_sms, s); \
+    case 322: return slice_one<32, 2, E>(tr, u, slice, stride, rec_bytes, num_sms, s); \
+    case 323: return slice_one<32, 3, E>(tr, u, slice, stride, rec_bytes, num_sms, s); \
     default: return cudaErrorInvalidValue;                  \
   }
   if (dt == kF32) NEUVV_SLICE_KD(float)
   if (dt == kBF16) NEUVV_SLICE_KD(__nv_bfloat16)
 #undef NEUVV_SLICE_KD
-  if (KP == 8 && DEG == 2) return slice_one<8, 2, Fp8E4M3>(tr, u, slice, stride, s);
-  if (KP == 16 && DEG == 3) return slice_one<16, 3, Fp8E4M3>(tr, u, slice, stride, s);
+  if (KP == 8 && DEG == 2) return slice_one<8, 2, Fp8E4M3>(tr, u, slice, stride, rec_bytes, num_sms, s);
+  if (KP == 16 && DEG == 3) return slice_one<16, 3, Fp8E4M3>(tr, u, slice, stride, rec_bytes, num_sms, s);
   return cudaErrorInvalidValue;
 }
 
@@ -387,19 +509,19 @@ static cudaError_t render_slice_one(const FwdArgs &a, const LaunchCfg &cfg, cuda
   cudaError_t e;
   if (persistent && (e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
   const size_t sm = smem_bytes(cfg.block, 8, cfg.queue);
-  if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(render_packet_kernel<8, DEG, __nv_bfloat16, true>,
+  if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(render_packet_kernel<8, DEG, __nv_bfloat16, kShadeSlice>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
     return e;
   long long grid = blocks;
   if (persistent) {
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_packet_kernel<8, DEG, __nv_bfloat16, true>,
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_packet_kernel<8, DEG, __nv_bfloat16, kShadeSlice>,
                                                            cfg.block, sm)) != cudaSuccess)
       return e;
     const long long want = (long long)(per_sm > 0 ? per_sm : 1) * cfg.num_sms;
     if (want < grid) grid = want;
   }
-  render_packet_kernel<8, DEG, __nv_bfloat16, true><<<(unsigned)grid, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
+  render_packet_kernel<8, DEG, __nv_bfloat16, kShadeSlice><<<(unsigned)grid, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
   return cudaGetLastError();
 }
 
@@ -408,6 +530,138 @@ cudaError_t launch_render_slice(int DEG, const FwdArgs &a, const LaunchCfg &cfg,
   if (DEG == 2) return render_slice_one<2>(a, cfg, s);
   if (DEG == 3) return render_slice_one<3>(a, cfg, s);
   return cudaErrorInvalidValue;
+}
+
+// Terminating voxel of each ray (Sec. 5 "Appearance editing"): the leaf of the
+// segment at which 1 - exp(-sum sigma delta) of the unedited render first
+// reaches the threshold; -1 when it never does.  One thread per ray.
+template <int KP, int DEG, typename E>
+__global__ void __launch_bounds__(256) pick_kernel(const __grid_constant__ FwdArgs a, float threshold, int *leaf_out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.rays.n) return;
+  float o[3], d[3], t, dn[3];
+  load_ray(a.rays, i, o, d, t);
+  int picked = -1;
+  RayWalk w;
+  if (walk_init(a.tr, o, d, w, dn)) {
+    RayConst<KP, DEG> rc;
+    ray_const_basis<KP, DEG>(a.tr, t * (float)(a.tr.T - 1), rc);
+    const RegRows<KP> rows{rc.a, rc.b};
+    float optical = 0.f;
+    uint32_t leaf;
+    float t0, dt;
+    while (walk_next<false>(a.tr, nullptr, w, leaf, t0, dt)) {
+      LeafRecord<KP, DEG, E> rec;
+      rec.load(a.tr, leaf);
+      optical = fmaf(fmaxf(pre_sigma_of<KP>(rows, rec), 0.f), dt, optical);
+      if (-expm1f(-optical) >= threshold) {
+        picked = (int)leaf;
+        break;
+      }
+    }
+  }
+  leaf_out[i] = picked;
+}
+
+template <int KP, int DEG, typename E>
+static cudaError_t pick_one(const FwdArgs &a, float threshold, int *leaf_out, cudaStream_t s) {
+  if (a.rays.n == 0) return cudaSuccess;
+  pick_kernel<KP, DEG, E><<<(unsigned)((a.rays.n + 127) / 128), 128, 0, s>>>(a, threshold, leaf_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pick(int KP, int DEG, DType dt, const FwdArgs &a, float threshold, int *leaf_out, cudaStream_t s) {
+#define NEUVV_PICK_KD(E)                                   \
+  switch (KP * 10 + DEG) {                                 \
+    case 81: return pick_one<8, 1, E>(a, threshold, leaf_out, s);   \
+    case 82: return pick_one<8, 2, E>(a, threshold, leaf_out, s);   \
+    case 83: return pick_one<8, 3, E>(a, threshold, leaf_out, s);   \
+    case 161: return pick_one<16, 1, E>(a, threshold, leaf_out, s); \
+    case 162: return pick_one<16, 2, E>(a, threshold, leaf_out, s); \
+    case 163: return pick_one<16, 3, E>(a, threshold, leaf_out, s); \
+    case 321: return pick_one<32, 1, E>(a, threshold, leaf_out, s); \
+    case 322: return pick_one<32, 2, E>(a, threshold, leaf_out, s); \
+    case 323: return pick_one<32, 3, E>(a, threshold, leaf_out, s); \
+    default: return cudaErrorInvalidValue;                 \
+  }
+  if (dt == kF32) NEUVV_PICK_KD(float)
+  if (dt == kBF16) NEUVV_PICK_KD(__nv_bfloat16)
+#undef NEUVV_PICK_KD
+  if (KP == 8 && DEG == 2) return pick_one<8, 2, Fp8E4M3>(a, threshold, leaf_out, s);
+  if (KP == 16 && DEG == 3) return pick_one<16, 3, Fp8E4M3>(a, threshold, leaf_out, s);
+  return cudaErrorInvalidValue;
+}
+
+// Painting: the colours of the rays that picked each leaf are summed (with
+// their count) into accum [n_leaves][4], then every leaf with a count gets
+// the mean colour, sigma_d and t_d in its edit record [n_leaves][8].
+__global__ void __launch_bounds__(256) paint_accum_kernel(const int *leaf, const float *color, long long n,
+                                                          long long n_leaves, float *accum) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int l = leaf[i];
+  if (l < 0 || l >= n_leaves) return;
+  atomicAdd(accum + 4 * (size_t)l + 0, color[3 * i + 0]);
+  atomicAdd(accum + 4 * (size_t)l + 1, color[3 * i + 1]);
+  atomicAdd(accum + 4 * (size_t)l + 2, color[3 * i + 2]);
+  atomicAdd(accum + 4 * (size_t)l + 3, 1.f);
+}
+
+__global__ void __launch_bounds__(256) paint_finish_kernel(const float *accum, long long n_leaves, float sigma_d,
+                                                           float t_d, float *edits) {
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_leaves) return;
+  const float4 s = reinterpret_cast<const float4 *>(accum)[l];
+  if (s.w > 0.f) {
+    float4 *e = reinterpret_cast<float4 *>(edits) + 2 * l;
+    e[0] = make_float4(s.x / s.w, s.y / s.w, s.z / s.w, sigma_d);
+    e[1] = make_float4(t_d, 0.f, 0.f, 0.f);
+  }
+}
+
+cudaError_t launch_paint(const int *leaf, const float *color, long long n, long long n_leaves, float *accum,
+                         float sigma_d, float t_d, float *edits, cudaStream_t s) {
+  if (n > 0) paint_accum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(leaf, color, n, n_leaves, accum);
+  if (n_leaves > 0)
+    paint_finish_kernel<<<(unsigned)((n_leaves + 255) / 256), 256, 0, s>>>(accum, n_leaves, sigma_d, t_d, edits);
+  return cudaGetLastError();
+}
+
+// Packet render with appearance edits (built for the two record shapes of the
+// workloads: K_pad 8 with degree 2, K_pad 16 with degree 3).
+template <int KP, int DEG, typename E>
+static cudaError_t edit_one(const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
+  if (a.rays.n == 0) return cudaSuccess;
+  const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
+  const size_t sm = smem_bytes(cfg.block, KP, cfg.queue);
+  cudaError_t e;
+  if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(render_packet_kernel<KP, DEG, E, kShadeEdit>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
+    return e;
+  long long grid = blocks;
+  if (a.work) {
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_packet_kernel<KP, DEG, E, kShadeEdit>,
+                                                           cfg.block, sm)) != cudaSuccess)
+      return e;
+    const long long want = (long long)(per_sm > 0 ? per_sm : 1) * cfg.num_sms;
+    if (want < grid) grid = want;
+    if ((e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  }
+  render_packet_kernel<KP, DEG, E, kShadeEdit><<<(unsigned)grid, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_edit(int KP, int DEG, DType dt, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
+  if (KP == 8 && DEG == 2) {
+    if (dt == kF32) return edit_one<8, 2, float>(a, cfg, s);
+    if (dt == kBF16) return edit_one<8, 2, __nv_bfloat16>(a, cfg, s);
+  }
+  if (KP == 16 && DEG == 3) {
+    if (dt == kF32) return edit_one<16, 3, float>(a, cfg, s);
+    if (dt == kBF16) return edit_one<16, 3, __nv_bfloat16>(a, cfg, s);
+  }
+  return cudaErrorNotSupported;
 }
 
 cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s) {

@@ -41,6 +41,9 @@ MUTANTS = {
                                  "return copysign(round(a / spacing) * spacing, x);"),
     "fp8_scale_search_starts_too_high": ("int p = e - 10;", "int p = e - 8;"),
     "fp8_scale_not_smallest_at_exact_fit": ("while (ldexp(448.0, p) < mx) ++p;", "while (ldexp(448.0, p) <= mx) ++p;"),
+    "edit_blend_weights_swapped": ("e.c[ch] = (1.0 - c->beta) * e.c[ch] + c->beta * E[ch];",
+                                   "e.c[ch] = c->beta * e.c[ch] + (1.0 - c->beta) * E[ch];"),
+    "pick_uses_transmittance": ("if (1.0 - exp(-optical) >= c->threshold) {", "if (exp(-optical) >= c->threshold) {"),
     "slice_gamma_missing_pi": ("const double gamma = M_PI * sigmoid(pg);", "const double gamma = sigmoid(pg);"),
     "slice_m_index_mirrored": ("sh[(leaf * 3 + ch) * NY + l * l + l + m] = acc;", "sh[(leaf * 3 + ch) * NY + l * l + l - m] = acc;"),
     "slice_radial_l_for_n": ("* or_hh_radial(n, l, gamma);\n          sh[", "* or_hh_radial(l, l, gamma);\n          sh["),
@@ -185,6 +188,27 @@ def _battery():
     if np.abs(oracle.render_slice(gt, oracle.slice_at(gt, float(np.float32(0.45))), sr)["rgb"]
               - oracle.render(gt, sr)["rgb"]).max() > 1e-12:
         failed.append("slice")
+    # appearance edits: every voxel edited gives the constant-slab closed form;
+    # the pick on a constant density lands where alpha passes the threshold
+    et = _const_tree(3, 2.0)
+    e_all = np.tile([0.2, 0.5, 0.9, 1.5, 0.0], (et.n_leaves, 1))
+    eo = oracle.render_edit(et, rays, e_all, beta=1.0, t_stop=0.0)
+    if np.abs(eo["rgb"][:, 2] - 0.9 * (1 - np.exp(-1.5 * L))).max() > 1e-12:
+        failed.append("edit")
+    pt = _const_tree(3, float(np.float32(12.0)))
+    pk = oracle.pick(pt, rays, 0.99, t_stop=0.0)
+    ptr = oracle.trace(pt, rays, max_out=64)
+    s_star = math.log(100.0) / float(np.float32(12.0))
+    for i in range(rays.n):
+        if L[i] < s_star + 1e-6:
+            if pk[i] != -1:
+                failed.append("pick")
+                break
+            continue
+        k = np.searchsorted(ptr["t1"][i, :ptr["count"][i]] - ptr["t0"][i, 0], s_star - 1e-12)
+        if pk[i] != ptr["leaf"][i, k]:
+            failed.append("pick")
+            break
     # FP8 E4M3: midpoints go to the even code; per-group scales are minimal
     from test_oracle_fp8 import e4m3_codes
     v = e4m3_codes()

@@ -384,7 +384,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
   return false;
 }
 
-constexpr int kSliceTile = 128;   // leaves per tile (one per thread)
+constexpr int kSliceTile = 64;    // leaves per tile (one per thread)
 constexpr int kSliceWaitPolls = 1 << 22;
 
 // Time slice with TMA staging: a block takes tiles of kSliceTile consecutive

@@ -35,62 +35,84 @@ __global__ void __launch_bounds__(256) mse_kernel(const float *__restrict__ rgb,
 
 // Image-gradient regulariser L_grad (Sec. 4.3 "Optimization"): with
 // E = |I - I_hat| per channel, lam * sum over views of the squared forward
-// differences of E between horizontally and vertically adjacent pixels.  One
-// thread per pixel: it adds to its own ray's dL/dI_hat the derivative of the
-// (up to four) differences its pixel takes part in, and to the loss the two
-// it owns (towards its right and lower neighbours).  map: ray of each pixel
-// [n_views][height][width], -1 for none.
-__global__ void __launch_bounds__(256) grad_loss_kernel(const float *__restrict__ rgb, const float *__restrict__ target,
-                                                        const int *__restrict__ map, int width, int height,
-                                                        long long n_pix, long long n_rays, float lam,
-                                                        float *__restrict__ grad, float *__restrict__ loss) {
+// differences of E between horizontally and vertically adjacent pixels.
+// map: ray of each pixel [n_views][height][width], -1 for none.
+//
+// A block takes tiles of kGradTileW x kGradTileH pixels of one view.  It
+// stages I - I_hat of the tile and a one-pixel halo in shared memory (the
+// map, rendered colours and targets are read about 1.3 times each instead of
+// five), then each thread adds to its own ray's dL/dI_hat the derivative of
+// the (up to four) differences its pixel takes part in, and to the loss the
+// two it owns (towards its right and lower neighbours).
+constexpr int kGradTileW = 32, kGradTileH = 8;
+constexpr int kGradHaloW = kGradTileW + 2, kGradHaloH = kGradTileH + 2;
+
+__global__ void __launch_bounds__(kGradTileW *kGradTileH)
+    grad_loss_kernel(const float *__restrict__ rgb, const float *__restrict__ target, const int *__restrict__ map,
+                     int width, int height, long long n_views, long long n_rays, float lam, float *__restrict__ grad,
+                     float *__restrict__ loss) {
+  __shared__ float dv[3][kGradHaloH][kGradHaloW];  // I - I_hat, per channel
+  __shared__ int ray[kGradHaloH][kGradHaloW];      // -1: no ray (missing pixel or outside the image)
+  const int tiles_x = (width + kGradTileW - 1) / kGradTileW, tiles_y = (height + kGradTileH - 1) / kGradTileH;
+  const long long per_view = (long long)tiles_x * tiles_y, n_tiles = per_view * n_views;
+  const int lx = threadIdx.x % kGradTileW, ly = threadIdx.x / kGradTileW;
   float part = 0.f;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n_pix;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int r = __ldg(map + p);
-    if (r < 0 || r >= n_rays) continue;
-    const long long img = p % ((long long)width * height);
-    const int y = (int)(img / width), x = (int)(img - (long long)y * width);
-    float E[3], g[3];
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long long view = tile / per_view;
+    const long long rest = tile - view * per_view;
+    const int y0 = (int)(rest / tiles_x) * kGradTileH - 1, x0 = (int)(rest % tiles_x) * kGradTileW - 1;
+    const int *vmap = map + view * (long long)width * height;
+    for (int h = threadIdx.x; h < kGradHaloH * kGradHaloW; h += blockDim.x) {
+      const int hy = h / kGradHaloW, hx = h - hy * kGradHaloW;
+      const int y = y0 + hy, x = x0 + hx;
+      int q = -1;
+      if (x >= 0 && x < width && y >= 0 && y < height) q = __ldg(vmap + (long long)y * width + x);
+      if (q >= n_rays) q = -1;
+      ray[hy][hx] = q < 0 ? -1 : q;
+      if (q >= 0) {
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      E[ch] = fabsf(__ldg(target + 3 * r + ch) - __ldg(rgb + 3 * r + ch));
-      g[ch] = 0.f;
-    }
-    // neighbours: left, right, up, down; sgn = +1 when this pixel is the
-    // second of the pair (the difference is E_this - E_other), -1 otherwise
-    const int nx[4] = {x - 1, x + 1, x, x};
-    const int ny[4] = {y, y, y - 1, y + 1};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (nx[k] < 0 || nx[k] >= width || ny[k] < 0 || ny[k] >= height) continue;
-      const int q = __ldg(map + (p - img) + (long long)ny[k] * width + nx[k]);
-      if (q < 0 || q >= n_rays) continue;
-      const bool second = (k == 0 || k == 2);
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        const float Eq = fabsf(__ldg(target + 3 * q + ch) - __ldg(rgb + 3 * q + ch));
-        const float D = second ? E[ch] - Eq : Eq - E[ch];
-        g[ch] = second ? fmaf(2.f, D, g[ch]) : fmaf(-2.f, D, g[ch]);
-        if (!second) part = fmaf(D, D, part);
+        for (int ch = 0; ch < 3; ++ch) dv[ch][hy][hx] = __ldg(rgb + 3LL * q + ch) - __ldg(target + 3LL * q + ch);
       }
     }
+    __syncthreads();
+    const int hy = ly + 1, hx = lx + 1;
+    const int r = ray[hy][hx];
+    if (r >= 0) {
+      float g[3] = {0.f, 0.f, 0.f};
+      // neighbours: left, right, up, down; sgn = +1 when this pixel is the
+      // second of the pair (the difference is E_this - E_other), -1 otherwise
+      const int ny[4] = {hy, hy, hy - 1, hy + 1};
+      const int nx[4] = {hx - 1, hx + 1, hx, hx};
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      const float dv = __ldg(rgb + 3 * r + ch) - __ldg(target + 3 * r + ch);
-      const float sgn = dv > 0.f ? 1.f : (dv < 0.f ? -1.f : 0.f);
-      grad[3 * r + ch] += lam * sgn * g[ch];
+      for (int k = 0; k < 4; ++k) {
+        if (ray[ny[k]][nx[k]] < 0) continue;
+        const bool second = (k == 0 || k == 2);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          const float E = fabsf(dv[ch][hy][hx]), Eq = fabsf(dv[ch][ny[k]][nx[k]]);
+          const float D = second ? E - Eq : Eq - E;
+          g[ch] = second ? fmaf(2.f, D, g[ch]) : fmaf(-2.f, D, g[ch]);
+          if (!second) part = fmaf(D, D, part);
+        }
+      }
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float d = dv[ch][hy][hx];
+        const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+        grad[3LL * r + ch] += lam * sgn * g[ch];
+      }
     }
+    __syncthreads();  // the staging arrays are refilled by the next tile
   }
   if (loss) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-    __shared__ float red[8];
+    __shared__ float red[kGradTileW * kGradTileH / 32];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
     __syncthreads();
     if (threadIdx.x == 0) {
       float s = 0.f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      for (int w = 0; w < kGradTileW * kGradTileH / 32; ++w) s += red[w];
       atomicAdd(loss, lam * s);
     }
   }
@@ -231,11 +253,11 @@ cudaError_t launch_mse(const float *rgb, const float *target, long long n, float
 
 cudaError_t launch_grad_loss(const float *rgb, const float *target, const int *map, int width, int height,
                              long long n_views, long long n_rays, float lam, float *grad, float *loss, cudaStream_t s) {
-  const long long n_pix = n_views * width * height;
-  if (n_pix == 0) return cudaSuccess;
-  const long long want = (n_pix + 255) / 256;
-  const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
-  grad_loss_kernel<<<blocks, 256, 0, s>>>(rgb, target, map, width, height, n_pix, n_rays, lam, grad, loss);
+  if (n_views * width * height == 0) return cudaSuccess;
+  const long long tiles = n_views * ((width + kGradTileW - 1) / kGradTileW) * ((height + kGradTileH - 1) / kGradTileH);
+  const int blocks = (int)(tiles < 152 * 8 ? tiles : 152 * 8);
+  grad_loss_kernel<<<blocks, kGradTileW * kGradTileH, 0, s>>>(rgb, target, map, width, height, n_views, n_rays, lam,
+                                                              grad, loss);
   return cudaGetLastError();
 }
 

@@ -374,7 +374,7 @@ def main():
     B.lib()
 
     tree = I.config2_tree()
-    rays, view_pixels = I.config2_rays(n_views=args.views)[:2]
+    rays, view_pixels, view_cams, view_times = I.config2_rays(n_views=args.views)
     n = rays.n
     dev = torch.device("cuda", local)
     dr = B.DeviceRays.from_host(rays, device=dev)
@@ -546,6 +546,7 @@ def main():
     lit_ms = e0.elapsed_time(e1) / reps
     # the parts one at a time
     parts = {"light_render_256x256": lambda: B.neuvv_render(tree_d, dlr, kernel="packet", out=lout),
+             "light_render_256x256_plain_kernel": lambda: B.neuvv_render(tree_d, dlr, kernel="plain", out=lout),
              "gaussian_blur": lambda: B.neuvv_gaussian_blur(amap, 1.5, out=blurred),
              "spotlight_shading": lambda: B.neuvv_spotlight(drv, outv, light_cam, blurred[0], 0.0, [0.8, 0.8, 0.8],
                                                             2.5, out=lit)}
@@ -558,11 +559,41 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         part_ms[name] = e0.elapsed_time(e1) / reps
+    # the light pass (plain kernel: no shared work counter) and its filter on a
+    # second stream, concurrent with the viewer's render
+    side = torch.cuda.Stream(device=dev)
+    light_done = torch.cuda.Event()
+
+    def lit_frame_concurrent():
+        side.wait_stream(stream)                            # the previous frame is done with the buffers
+        with torch.cuda.stream(side):
+            B.neuvv_render(tree_d, dlr, kernel="plain", out=lout)
+            B.neuvv_gaussian_blur(amap, 1.5, out=blurred)
+            light_done.record(side)
+        B.neuvv_render(tree_d, drv, kernel="packet", out=outv)
+        stream.wait_event(light_done)
+        B.neuvv_spotlight(drv, outv, light_cam, blurred[0], 0.0, [0.8, 0.8, 0.8], 2.5, out=lit)
+
+    lit_frame_concurrent()
+    torch.cuda.synchronize()
+    lit_cc = lit.clone()
+    lit_frame()
+    torch.cuda.synchronize()
+    same = float((lit_cc - lit).abs().max().item())         # plain vs packet light pass
+    e0.record(stream)
+    for _ in range(reps):
+        lit_frame_concurrent()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lit_cc_ms = e0.elapsed_time(e1) / reps
     time_slice["spotlight"] = {"lit_1080p_frame_ms": lit_ms, "plain_1080p_frame_ms": rv_ms, "parts_ms": part_ms,
+                               "lit_1080p_frame_ms_light_pass_concurrent": lit_cc_ms,
+                               "overhead_frac_light_pass_concurrent": lit_cc_ms / rv_ms - 1.0,
+                               "max_abs_lit_concurrent_vs_sequential": same,
                                "overhead_frac": lit_ms / rv_ms - 1.0, "light_map": [256, 256], "blur_sigma": 1.5,
                                "note": "light render (256x256) + blur + viewer render + spotlight shading; the paper "
                                        "reports about 20% lower render speed with shadows and falloff"}
-    del sl, outv, drv, dlr, lout, amap, blurred, lit
+    del sl, outv, drv, dlr, lout, amap, blurred, lit, lit_cc
 
     # -- storage ablation: the same training step on FP8 E4M3 records with
     #    per-leaf scales (same FP32 master, same rays and targets)
@@ -642,15 +673,15 @@ def main():
     roof["algorithmic_flops"] = flops_
 
     # -- end to end through the C ABI with host buffers.  Every step copies its
-    # rays and targets in from pinned host memory and its loss out.  The
-    # inputs go to one of two device buffers on a copy stream, so that step
-    # k + 1's upload runs while step k computes (what a training loop with a
-    # prefetching loader does); all uploads lie inside the timed region.
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
-    h_o, h_d, h_t = pin(rays.origins), pin(rays.dirs), pin(rays.times)
+    # inputs in from pinned host memory -- the target images and the views'
+    # camera poses and times -- generates the rays of its views on the device
+    # (neuvv_camera_rays) and copies its loss out.  The targets go to one of
+    # two device buffers on a copy stream, so that step k + 1's upload runs
+    # while step k computes (what a training loop with a prefetching loader
+    # does); all uploads lie inside the timed region.
     h_tgt = target.cpu().pin_memory()
-    bufs = [(torch.empty_like(dr.o), torch.empty_like(dr.d), torch.empty_like(dr.t), torch.empty_like(target))
-            for _ in range(2)]
+    bufs = [torch.empty_like(target) for _ in range(2)]
+    dr_e2e = B.DeviceRays(torch.empty_like(dr.o), torch.empty_like(dr.d), torch.empty_like(dr.t))
     h_loss = torch.zeros(1).pin_memory()
     e2e_steps = max(3, args.steps // 2)
     copy_stream = torch.cuda.Stream(device=dev)
@@ -661,22 +692,20 @@ def main():
         b = j % 2
         with torch.cuda.stream(copy_stream):
             copy_stream.wait_event(used[b])              # the buffer's previous step is done with it
-            for d_x, h_x in zip(bufs[b], (h_o, h_d, h_t, h_tgt)):
-                d_x.copy_(h_x, non_blocking=True)
+            bufs[b].copy_(h_tgt, non_blocking=True)
             copied[b].record(copy_stream)
 
     def e2e_step(j, k):
         b = j % 2
-        d_o, d_d, d_t, d_tgt = bufs[b]
+        B.neuvv_camera_rays(view_cams, view_times, tiled=True, out=dr_e2e)
+        B.neuvv_render(tree_d, dr_e2e, kernel="packet", out=out)
         stream.wait_event(copied[b])
-        dr2 = B.DeviceRays(d_o, d_d, d_t)
-        B.neuvv_render(tree_d, dr2, kernel="packet", out=out)
         loss.zero_()
-        B.neuvv_mse_grad(out["rgb"], d_tgt, scale=1.0 / n, grad=grad_rgb, loss=loss)
-        B.neuvv_grad_loss(out["rgb"], d_tgt, ray_of_pixel, LAMBDA_GRAD / n, grad_rgb, loss)
-        B.neuvv_render_backward(tree_d, dr2, out, grad_rgb, None, grad, touched, kernel="packet")
-        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k)
+        B.neuvv_mse_grad(out["rgb"], bufs[b], scale=1.0 / n, grad=grad_rgb, loss=loss)
+        B.neuvv_grad_loss(out["rgb"], bufs[b], ray_of_pixel, LAMBDA_GRAD / n, grad_rgb, loss)
         used[b].record(stream)
+        B.neuvv_render_backward(tree_d, dr_e2e, out, grad_rgb, None, grad, touched, kernel="packet")
+        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k)
         h_loss.copy_(loss, non_blocking=True)
 
     def e2e_run(n_steps, k0):
@@ -690,16 +719,18 @@ def main():
 
     e2e_run(2, args.warmup + args.steps + 1)
     torch.cuda.synchronize()
+    e2e_samples = float(out["nseg"].sum().item())       # samples of the device-generated rays
     e0.record(stream)
     e2e_run(e2e_steps, args.warmup + args.steps + 3)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    h2d = n * 7 * 4 + n * 12
-    e2e = {"value": world * samples / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms,
-           "overlap": "step k+1's inputs uploaded on a second stream while step k computes (two input buffers)"}
-    del bufs
+    h2d = n * 12 + len(view_cams) * (15 + 1) * 4          # targets + camera structs and times (launch parameters)
+    e2e = {"value": world * e2e_samples / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms, "samples_per_step": e2e_samples,
+           "pipeline": "per step: targets uploaded (on a copy stream, one step ahead, two buffers), rays generated "
+                       "on the device from the views' cameras, fwd + loss + adjoint + Adam, loss read back"}
+    del bufs, dr_e2e
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

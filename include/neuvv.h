@@ -19,6 +19,13 @@
  *    during the call only.
  *  - Calls that take a stream are asynchronous on it: no host synchronisation,
  *    no allocation.  neuvv_tree_create/destroy/status/autotune synchronise.
+ *  - The packet kernels of neuvv_render, neuvv_render_slice, neuvv_render_edit
+ *    and neuvv_compose pull work from a counter owned by the tree (by the
+ *    first tree for compose; neuvv_compose_noalloc's is a library global):
+ *    two such calls on one tree must be ordered (one stream, or events
+ *    between streams).  The plain kernel (NEUVV_KERNEL_PLAIN) and the other
+ *    calls use no such counter and may run concurrently on different streams,
+ *    as long as their outputs do not overlap.
  *  - Errors found on the device (a ray that exceeds its segment cap, an index
  *    outside the tree) are recorded in a per-tree status word read by
  *    neuvv_tree_status(); the affected ray ends early, nothing traps.
@@ -331,15 +338,35 @@ neuvv_status neuvv_render_edit(const neuvv_tree *tree, const neuvv_rays *rays, f
 neuvv_status neuvv_gaussian_blur(const float *in, float *out, int32_t width, int32_t height, int32_t n_images,
                                  float sigma, neuvv_stream stream);
 
-/* A pinhole camera at the light, the same model as the viewer's: ray through
- * pixel (px, py) (pixel centres at +0.5) along forward + sx right + sy up,
+/* A pinhole camera (the viewers' and the light's): ray through pixel (px, py)
+ * (pixel centres at +0.5) from eye along forward + sx right + sy up,
  * sx = (2 (px+0.5)/width - 1) tan(fov_y/2) width/height,
  * sy = (1 - 2 (py+0.5)/height) tan(fov_y/2); right, up, forward orthonormal. */
 typedef struct {
   float eye[3], right[3], up[3], forward[3];
   float fov_y_deg;
   int32_t width, height;
-} neuvv_light;
+} neuvv_camera;
+typedef neuvv_camera neuvv_light;
+
+/* Ray setup (Sec. 4.3 "Rendering": a ray through the centre of each pixel of
+ * each view).  cams: host [n_cams] (1..32 per call; chunk longer lists);
+ * times: host [n_cams], each in [0, 1].  Camera c owns rays
+ * [off_c, off_c + width_c * height_c), off_c the sum of the earlier cameras'
+ * pixel counts; n must equal the total.  Ray j of a camera goes through pixel
+ * j in row-major order when tiled == 0; when tiled != 0 the pixels are listed
+ * by 8x4 tiles (tiles in row-major order, pixels of a tile row-major, the
+ * tiles at the right and bottom edges narrower or shorter), so a 32-ray packet
+ * covers one tile.  Writes, all device and caller-owned: origins [3][n] (the
+ * eye), dirs [3][n] (unit: the direction above divided by its FP32 norm),
+ * times_out [n] (times[c]) and, when pixel_of_ray is not NULL, pixel_of_ray
+ * [n] (py * width + px of the ray's own camera).  Errors: NULL pointers, a
+ * camera with a non-positive size or a field of view outside (0, 180), a time
+ * outside [0, 1] or a mismatched n give NEUVV_ERR_INVALID_ARG before any
+ * launch. */
+neuvv_status neuvv_camera_rays(const neuvv_camera *cams, const float *times, int32_t n_cams, int32_t tiled,
+                               float *origins, float *dirs, float *times_out, int32_t *pixel_of_ray, int64_t n,
+                               neuvv_stream stream);
 
 /* Spotlight shadow and distance falloff (Sec. 5 "Spotlight Lighting").  For
  * each viewer ray with its render (rgb premultiplied [n][3], alpha [n], depth

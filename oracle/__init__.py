@@ -342,6 +342,38 @@ def render_edit(tree, rays, edits, beta: float = 1.0, t_stop: float = 1e-4, act:
     return out
 
 
+def camera_rays(cam, t: float, tiled: bool = True) -> dict:
+    """Pinhole camera rays through pixel centres (Sec. 4.3 "Rendering": one
+    ray per pixel of a view).  cam: eye, orthonormal right/up/forward,
+    fov_y_deg, width, height.  Pixel (px, py) looks along
+    forward + sx right + sy up with sx = (2 (px + 1/2) / W - 1) tan(fov_y / 2) W / H
+    and sy = (1 - 2 (py + 1/2) / H) tan(fov_y / 2), normalised.  The rays list
+    the pixels row-major, or (tiled) tile by tile: 8 x 4 tiles in row-major
+    order of the tiles, the pixels of each tile row-major, the tiles at the
+    right and bottom edges cut to the image.  Returns origins and dirs
+    [3, n], times [n] and the row-major pixel of each ray."""
+    W, H = int(cam.width), int(cam.height)
+    if tiled:
+        parts = []
+        for y0 in range(0, H, 4):
+            ys = np.arange(y0, min(y0 + 4, H))
+            for x0 in range(0, W, 8):
+                xs = np.arange(x0, min(x0 + 8, W))
+                parts.append((ys[:, None] * W + xs[None, :]).ravel())
+        pix = np.concatenate(parts)
+    else:
+        pix = np.arange(W * H)
+    py, px = pix // W, pix % W
+    th = math.tan(math.radians(float(cam.fov_y_deg)) / 2.0)
+    sx = (2.0 * (px + 0.5) / W - 1.0) * th * (W / H)
+    sy = (1.0 - 2.0 * (py + 0.5) / H) * th
+    f, r, u = (np.asarray(x, np.float64) for x in (cam.forward, cam.right, cam.up))
+    d = f[:, None] + r[:, None] * sx[None, :] + u[:, None] * sy[None, :]
+    d = d / np.linalg.norm(d, axis=0, keepdims=True)
+    o = np.repeat(np.asarray(cam.eye, np.float64)[:, None], pix.size, axis=1)
+    return {"origins": o, "dirs": d, "times": np.full(pix.size, float(t)), "pixel": pix}
+
+
 def gaussian_blur(img, sigma: float):
     """The low-pass filter of the shadow map (Sec. 5 "Spotlight Lighting":
     shadows rendered at low resolution and Gaussian-filtered against Moire

@@ -72,7 +72,8 @@ EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv
            "neuvv_tree_coeff_ptrs", "neuvv_tree_status", "neuvv_render", "neuvv_render_backward", "neuvv_compose",
            "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc",
            "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss",
-           "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit"]
+           "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit",
+           "neuvv_camera_rays"]
 
 
 def library_path() -> str:
@@ -111,6 +112,7 @@ def lib(build_if_missing: bool = True):
                 "neuvv_render_edit": [p, p, f, p, p, f, p, p],
                 "neuvv_spotlight": [p, p, p, p, p, p, f, p, f, p, p],
                 "neuvv_render_slice": [p, p, i32, p, p, p, p],
+                "neuvv_camera_rays": [p, p, i32, i32, p, p, p, p, i64, p],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -364,6 +366,39 @@ def neuvv_gaussian_blur(img: torch.Tensor, sigma: float, out: torch.Tensor | Non
     n, h, w = img.shape
     _check(lib().neuvv_gaussian_blur(_ptr(img.contiguous()), _ptr(out), int(w), int(h), int(n), float(sigma),
                                      _stream()))
+    return out
+
+
+def neuvv_camera_rays(cams, times, tiled: bool = True, out: DeviceRays | None = None,
+                      pixel_of_ray: torch.Tensor | None = None, device="cuda") -> DeviceRays:
+    """Rays through the pixel centres of each camera (any objects with eye,
+    right, up, forward, fov_y_deg, width, height), generated on the device:
+    camera c's rays follow camera c-1's, in 8x4 tile order when tiled, at time
+    times[c].  out (optional): DeviceRays of the total size to write into;
+    pixel_of_ray (optional, int32 [n]) receives each ray's row-major pixel."""
+    cams, times = list(cams), [float(x) for x in times]
+    if len(cams) != len(times):
+        raise NeuvvError("one time per camera")
+    n = sum(int(c.width) * int(c.height) for c in cams)
+    if out is None:
+        out = DeviceRays(torch.empty(3, n, device=device), torch.empty(3, n, device=device),
+                         torch.empty(n, device=device))
+    if out.n != n or out.t is None:
+        raise NeuvvError("out must hold the cameras' total pixel count, with times")
+    done = 0
+    for c0 in range(0, len(cams), 32):
+        part = cams[c0:c0 + 32]
+        arr = (LightC * len(part))(*[light_of(c) for c in part])
+        ts = (ctypes.c_float * len(part))(*times[c0:c0 + 32])
+        m = sum(int(c.width) * int(c.height) for c in part)
+        o, d, t = out.o[:, done:done + m].contiguous(), out.d[:, done:done + m].contiguous(), out.t[done:done + m]
+        pix = None if pixel_of_ray is None else pixel_of_ray[done:done + m]
+        _check(lib().neuvv_camera_rays(arr, ts, len(part), int(bool(tiled)), _ptr(o), _ptr(d), _ptr(t),
+                                       None if pix is None else _ptr(pix), m, _stream()))
+        if o.data_ptr() != out.o[:, done:done + m].data_ptr():  # a chunk of several: copy the [3][m] block back
+            out.o[:, done:done + m].copy_(o)
+            out.d[:, done:done + m].copy_(d)
+        done += m
     return out
 
 

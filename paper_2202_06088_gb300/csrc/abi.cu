@@ -1021,6 +1021,46 @@ neuvv_status neuvv_spotlight(const neuvv_rays *rays, const float *rgb, const flo
   return NEUVV_OK;
 }
 
+neuvv_status neuvv_camera_rays(const neuvv_camera *cams, const float *times, int32_t n_cams, int32_t tiled,
+                               float *origins, float *dirs, float *times_out, int32_t *pixel_of_ray, int64_t n,
+                               neuvv_stream stream) {
+  if (n_cams < 1 || n_cams > kMaxCams) return fail(NEUVV_ERR_INVALID_ARG, "n_cams must be in [1, 32]");
+  if (!cams || !times) return fail(NEUVV_ERR_INVALID_ARG, "cams/times is NULL");
+  CamBatch cb;
+  std::memset(&cb, 0, sizeof cb);
+  long long total = 0;
+  for (int c = 0; c < n_cams; ++c) {
+    const neuvv_camera &k = cams[c];
+    if (k.width < 1 || k.height < 1 || !(k.fov_y_deg > 0.f && k.fov_y_deg < 180.f))
+      return fail(NEUVV_ERR_INVALID_ARG, "camera needs a positive size and a field of view in (0, 180)");
+    if ((long long)k.width * k.height >= 0x7FFFFFFFll)
+      return fail(NEUVV_ERR_INVALID_ARG, "a camera's pixel count must be below 2^31 (int32 pixel ids)");
+    if (!(times[c] >= 0.f && times[c] <= 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "camera time outside [0, 1]");
+    for (int a = 0; a < 3; ++a) {
+      cb.cam[c].eye[a] = k.eye[a];
+      cb.cam[c].right[a] = k.right[a];
+      cb.cam[c].up[a] = k.up[a];
+      cb.cam[c].forward[a] = k.forward[a];
+    }
+    cb.cam[c].fov_y_deg = k.fov_y_deg;
+    cb.cam[c].width = k.width;
+    cb.cam[c].height = k.height;
+    cb.tan_half[c] = (float)std::tan((double)k.fov_y_deg * 3.14159265358979323846 / 360.0);
+    cb.aspect[c] = (float)((double)k.width / (double)k.height);
+    cb.t[c] = times[c];
+    cb.off[c] = total;
+    total += (long long)k.width * k.height;
+  }
+  for (int c = n_cams; c <= kMaxCams; ++c) cb.off[c] = total;
+  cb.n_cams = n_cams;
+  cb.tiled = tiled != 0;
+  if (n != total) return fail(NEUVV_ERR_INVALID_ARG, "n differs from the cameras' total pixel count");
+  if (!origins || !dirs || !times_out) return fail(NEUVV_ERR_INVALID_ARG, "origins/dirs/times_out is NULL");
+  cudaError_t e = launch_camera_rays(cb, origins, dirs, times_out, pixel_of_ray, (long long)n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "camera rays launch");
+  return NEUVV_OK;
+}
+
 neuvv_status neuvv_trace(const neuvv_tree *t, const neuvv_rays *rays, int32_t max_out, int32_t *leaf, float *t0,
                          float *t1, int32_t *count, neuvv_stream stream) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");

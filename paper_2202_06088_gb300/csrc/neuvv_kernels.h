@@ -119,6 +119,18 @@ struct LightCam {
   int width, height;
 };
 
+// Pinhole cameras of one ray-setup launch (camera_rays_kernel).  Camera c
+// owns rays [off[c], off[c + 1]); tan_half = tan(fov_y / 2) and
+// aspect = width / height, both rounded from double on the host.
+constexpr int kMaxCams = 32;
+constexpr int kCamTileW = 8, kCamTileH = 4;
+struct CamBatch {
+  LightCam cam[kMaxCams];
+  float tan_half[kMaxCams], aspect[kMaxCams], t[kMaxCams];
+  long long off[kMaxCams + 1];
+  int n_cams, tiled;
+};
+
 struct SpotArgs {
   DevRays rays;
   const float *rgb, *alpha, *depth;  // the viewer's render [n][3], [n], [n]
@@ -131,6 +143,8 @@ struct SpotArgs {
 
 // Each returns cudaGetLastError() of its launch (or cudaErrorInvalidValue for
 // an unsupported template combination).
+cudaError_t launch_camera_rays(const CamBatch &cb, float *o, float *d, float *t, int *pixel, long long n,
+                               cudaStream_t s);
 cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdArgs &a, const LaunchCfg &cfg,
                               cudaStream_t s);
 cudaError_t launch_render_bwd(int KP, int DEG, DType dt, bool packet, const BwdArgs &a, const LaunchCfg &cfg,

@@ -102,3 +102,27 @@ def test_render_argument_checks_precede_any_launch(L):
     assert L.neuvv_compose(arr, xf.ctypes.data, z.ctypes.data, z.ctypes.data, 0, ctypes.byref(rays), 0.0,
                            ctypes.byref(op), None, None) == 1
     assert L.neuvv_mse_grad(None, None, -1, 1.0, None, None, None) == 1
+
+
+def test_camera_rays_arguments_are_checked_on_the_host(L):
+    from paper_2202_06088_gb300 import binding as B
+    cam = B.LightC()
+    cam.forward[2], cam.right[0], cam.up[1] = 1.0, 1.0, 1.0
+    cam.fov_y_deg, cam.width, cam.height = 40.0, 8, 4
+    cams = (B.LightC * 1)(cam)
+    t = (ctypes.c_float * 1)(0.5)
+    buf = ctypes.c_void_p(16)        # never dereferenced: every call below fails its checks first
+    assert L.neuvv_camera_rays(cams, t, 0, 1, buf, buf, buf, None, 32, None) == 1
+    assert b"n_cams" in L.neuvv_last_error()
+    assert L.neuvv_camera_rays(None, t, 1, 1, buf, buf, buf, None, 32, None) == 1
+    assert L.neuvv_camera_rays(cams, t, 1, 1, buf, buf, buf, None, 31, None) == 1
+    assert b"pixel count" in L.neuvv_last_error()
+    assert L.neuvv_camera_rays(cams, t, 1, 1, None, buf, buf, None, 32, None) == 1
+    t[0] = 1.5
+    assert L.neuvv_camera_rays(cams, t, 1, 1, buf, buf, buf, None, 32, None) == 1
+    assert b"time" in L.neuvv_last_error()
+    t[0] = 0.5
+    cams[0].fov_y_deg = 180.0
+    assert L.neuvv_camera_rays(cams, t, 1, 1, buf, buf, buf, None, 32, None) == 1
+    cams[0].fov_y_deg, cams[0].width = 40.0, 0
+    assert L.neuvv_camera_rays(cams, t, 1, 1, buf, buf, buf, None, 0, None) == 1

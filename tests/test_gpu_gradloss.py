@@ -66,3 +66,16 @@ def test_grad_loss_at_bench_size(B):
     rgb = rng.uniform(0, 1, (n, 3)).astype(np.float32).astype(np.float64)
     tgt = np.clip(rgb + rng.normal(0, 0.05, (n, 3)), 0, 1).astype(np.float32).astype(np.float64)
     _check(B, rgb, tgt, m.reshape(V, H, W), 0.1, W, H)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 40), (40, 1), (9, 33), (8, 32)])
+def test_grad_loss_degenerate_shapes(B, H, W):
+    # single pixels, single rows and columns (no vertical or horizontal
+    # pairs), one pixel past a 32x8 tile, and exactly one tile
+    rng = np.random.default_rng(H * 1000 + W)
+    V = 2
+    n = V * H * W
+    m = rng.permutation(n).reshape(V, H, W)
+    rgb = rng.uniform(0, 1, (n, 3)).astype(np.float32).astype(np.float64)
+    tgt = rng.uniform(0, 1, (n, 3)).astype(np.float32).astype(np.float64)
+    _check(B, rgb, tgt, m, 0.1, W, H)

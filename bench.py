@@ -531,69 +531,67 @@ def main():
     blurred = torch.empty_like(amap)
     lit = torch.empty_like(outv["rgb"])
 
-    def lit_frame():
-        B.neuvv_render(tree_d, dlr, kernel="packet", out=lout)
+    def light_pass():
+        # the light's alpha map: a density-only render (no colour)
+        B.neuvv_render_alpha(tree_d, dlr, out=lout)
         B.neuvv_gaussian_blur(amap, 1.5, out=blurred)
+
+    def lit_frame():
+        light_pass()
         B.neuvv_render(tree_d, drv, kernel="packet", out=outv)
         B.neuvv_spotlight(drv, outv, light_cam, blurred[0], 0.0, [0.8, 0.8, 0.8], 2.5, out=lit)
 
-    lit_frame()
-    e0.record(stream)
-    for _ in range(reps):
-        lit_frame()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    lit_ms = e0.elapsed_time(e1) / reps
-    # the parts one at a time
-    parts = {"light_render_256x256": lambda: B.neuvv_render(tree_d, dlr, kernel="packet", out=lout),
-             "light_render_256x256_plain_kernel": lambda: B.neuvv_render(tree_d, dlr, kernel="plain", out=lout),
-             "gaussian_blur": lambda: B.neuvv_gaussian_blur(amap, 1.5, out=blurred),
-             "spotlight_shading": lambda: B.neuvv_spotlight(drv, outv, light_cam, blurred[0], 0.0, [0.8, 0.8, 0.8],
-                                                            2.5, out=lit)}
-    part_ms = {}
-    for name, fn in parts.items():
-        fn()
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        part_ms[name] = e0.elapsed_time(e1) / reps
-    # the light pass (plain kernel: no shared work counter) and its filter on a
-    # second stream, concurrent with the viewer's render
+    # the light pass (no shared work counter) on a second stream, concurrent
+    # with the viewer's render
     side = torch.cuda.Stream(device=dev)
     light_done = torch.cuda.Event()
 
     def lit_frame_concurrent():
         side.wait_stream(stream)                            # the previous frame is done with the buffers
         with torch.cuda.stream(side):
-            B.neuvv_render(tree_d, dlr, kernel="plain", out=lout)
-            B.neuvv_gaussian_blur(amap, 1.5, out=blurred)
+            light_pass()
             light_done.record(side)
         B.neuvv_render(tree_d, drv, kernel="packet", out=outv)
         stream.wait_event(light_done)
         B.neuvv_spotlight(drv, outv, light_cam, blurred[0], 0.0, [0.8, 0.8, 0.8], 2.5, out=lit)
 
-    lit_frame_concurrent()
+    def timed(fn):
+        fn()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # the light map of the density-only pass equals the full render's alpha
+    B.neuvv_render(tree_d, dlr, kernel="packet", out=lout)
+    alpha_full = lout["alpha"].clone()
+    light_pass()
     torch.cuda.synchronize()
-    lit_cc = lit.clone()
-    lit_frame()
-    torch.cuda.synchronize()
-    same = float((lit_cc - lit).abs().max().item())         # plain vs packet light pass
-    e0.record(stream)
-    for _ in range(reps):
-        lit_frame_concurrent()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    lit_cc_ms = e0.elapsed_time(e1) / reps
-    time_slice["spotlight"] = {"lit_1080p_frame_ms": lit_ms, "plain_1080p_frame_ms": rv_ms, "parts_ms": part_ms,
+    alpha_same = bool(torch.equal(alpha_full, lout["alpha"]))
+    lit_ms = timed(lit_frame)
+    lit_seq = lit.clone()
+    lit_cc_ms = timed(lit_frame_concurrent)
+    same = float((lit_seq - lit).abs().max().item())
+    part_ms = {name: timed(fn) for name, fn in (
+        ("light_alpha_256x256", lambda: B.neuvv_render_alpha(tree_d, dlr, out=lout)),
+        ("light_full_render_256x256", lambda: B.neuvv_render(tree_d, dlr, kernel="packet", out=lout)),
+        ("gaussian_blur", lambda: B.neuvv_gaussian_blur(amap, 1.5, out=blurred)),
+        ("spotlight_shading", lambda: B.neuvv_spotlight(drv, outv, light_cam, blurred[0], 0.0, [0.8, 0.8, 0.8], 2.5,
+                                                        out=lit)))}
+    time_slice["spotlight"] = {"lit_1080p_frame_ms": lit_ms, "plain_1080p_frame_ms": rv_ms,
+                               "overhead_frac": lit_ms / rv_ms - 1.0,
                                "lit_1080p_frame_ms_light_pass_concurrent": lit_cc_ms,
                                "overhead_frac_light_pass_concurrent": lit_cc_ms / rv_ms - 1.0,
+                               "parts_ms": part_ms, "light_alpha_equals_full_render_alpha": alpha_same,
                                "max_abs_lit_concurrent_vs_sequential": same,
-                               "overhead_frac": lit_ms / rv_ms - 1.0, "light_map": [256, 256], "blur_sigma": 1.5,
-                               "note": "light render (256x256) + blur + viewer render + spotlight shading; the paper "
-                                       "reports about 20% lower render speed with shadows and falloff"}
-    del sl, outv, drv, dlr, lout, amap, blurred, lit, lit_cc
+                               "light_map": [256, 256], "blur_sigma": 1.5,
+                               "note": "density-only light render (256x256) + blur + viewer render + spotlight "
+                                       "shading; the paper reports about 20% lower render speed with shadows and "
+                                       "falloff"}
+    del alpha_full
+    del sl, outv, drv, dlr, lout, amap, blurred, lit, lit_seq
 
     # -- storage ablation: the same training step on FP8 E4M3 records with
     #    per-leaf scales (same FP32 master, same rays and targets)

@@ -338,6 +338,18 @@ neuvv_status neuvv_render_edit(const neuvv_tree *tree, const neuvv_rays *rays, f
 neuvv_status neuvv_gaussian_blur(const float *in, float *out, int32_t width, int32_t height, int32_t n_images,
                                  float sigma, neuvv_stream stream);
 
+/* Density-only render (Sec. 5 "Spotlight Lighting": the shadow map is the
+ * alpha of the VOctree seen from the light).  Walks and composites exactly as
+ * neuvv_render's packet kernel but reads only the w_sigma part of each leaf
+ * record and evaluates no colour: out->alpha (required), depth, tau and nseg
+ * (each optional) equal neuvv_render's for the same rays; out->rgb and
+ * out->log are not used.  Launches one packet per warp without the tree's
+ * work counter, so it may run on another stream beside any call on the same
+ * tree.  Built for K_pad 8 with degree 2 and K_pad 16 with degree 3 (else
+ * NEUVV_ERR_UNSUPPORTED); other errors as neuvv_render. */
+neuvv_status neuvv_render_alpha(const neuvv_tree *tree, const neuvv_rays *rays, float t, const neuvv_render_opts *opts,
+                                neuvv_out *out, neuvv_stream stream);
+
 /* A pinhole camera (the viewers' and the light's): ray through pixel (px, py)
  * (pixel centres at +0.5) from eye along forward + sx right + sy up,
  * sx = (2 (px+0.5)/width - 1) tan(fov_y/2) width/height,

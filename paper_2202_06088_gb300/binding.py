@@ -73,7 +73,7 @@ EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv
            "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc",
            "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss",
            "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit",
-           "neuvv_camera_rays"]
+           "neuvv_camera_rays", "neuvv_render_alpha"]
 
 
 def library_path() -> str:
@@ -113,6 +113,7 @@ def lib(build_if_missing: bool = True):
                 "neuvv_spotlight": [p, p, p, p, p, p, f, p, f, p, p],
                 "neuvv_render_slice": [p, p, i32, p, p, p, p],
                 "neuvv_camera_rays": [p, p, i32, i32, p, p, p, p, i64, p],
+                "neuvv_render_alpha": [p, p, f, p, p, p],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -296,6 +297,20 @@ def neuvv_render(tree: Tree, rays: DeviceRays, t: float = 0.0, t_stop: float = 1
     out = out if out is not None else alloc_out(rays.n)
     rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, kernel)
     _check(lib().neuvv_render(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(op), ctypes.byref(oc), _stream()))
+    return out
+
+
+def neuvv_render_alpha(tree: Tree, rays: DeviceRays, t: float = 0.0, t_stop: float = 1e-4,
+                       out: dict | None = None) -> dict:
+    """Density-only render: alpha, depth, tau and nseg as neuvv_render, no colour."""
+    if out is None:
+        dev = rays.o.device
+        out = {"alpha": torch.empty(rays.n, device=dev), "depth": torch.empty(rays.n, device=dev),
+               "tau": torch.empty(rays.n, device=dev), "nseg": torch.empty(rays.n, device=dev, dtype=torch.int32)}
+    oc = _outc({k: v for k, v in out.items() if k not in ("rgb", "log")})
+    rc, op = rays.c(), _opts(t_stop, "sigmoid", "packet")
+    _check(lib().neuvv_render_alpha(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(op), ctypes.byref(oc),
+                                    _stream()))
     return out
 
 

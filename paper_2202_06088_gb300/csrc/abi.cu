@@ -578,6 +578,35 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   return NEUVV_OK;
 }
 
+neuvv_status neuvv_render_alpha(const neuvv_tree *t, const neuvv_rays *rays, float time, const neuvv_render_opts *opts,
+                                neuvv_out *out, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  neuvv_status s;
+  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK || (s = check_time(rays, time)))
+    return s;
+  if (!out || (rays->n > 0 && !out->alpha)) return fail(NEUVV_ERR_INVALID_ARG, "out->alpha is required");
+  if (rays->n == 0) return NEUVV_OK;
+  DeviceGuard g(t->info.device);
+  FwdArgs a;
+  a.tr = dev_tree(t);
+  a.rays = dev_rays(rays, time);
+  a.out = DevOut{nullptr, out->alpha, out->depth, out->tau, out->nseg};
+  a.t_stop = opts->t_stop;
+  a.act = opts->color_act;
+  a.work = nullptr;
+  a.log = log_view(nullptr, 0, 0);
+  a.slice = nullptr;
+  a.slice_stride = 0;
+  a.edits = nullptr;
+  a.edit_beta = 0.f;
+  cudaError_t e = launch_render_alpha(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, a, t->packet,
+                                      (cudaStream_t)stream);
+  if (e == cudaErrorNotSupported)
+    return fail(NEUVV_ERR_UNSUPPORTED, "density-only render is built for K_pad 8 / degree 2 and K_pad 16 / degree 3");
+  if (e != cudaSuccess) return cuda_fail(e, "alpha render launch");
+  return NEUVV_OK;
+}
+
 neuvv_status neuvv_slice(const neuvv_tree *t, float time, float *slice, int32_t slice_stride, neuvv_stream stream) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
   if (!(time >= 0.f && time <= 1.f)) return fail(NEUVV_ERR_INVALID_ARG, "t must be in [0, 1]");

@@ -608,6 +608,21 @@ struct LeafRecord {
 #pragma unroll
     for (int i = 0; i < NV; ++i) Elem<E>::unpack(p[i], w + i * PV);
   }
+  // Only the vectors that hold w_sigma (a density-only pass).
+  __device__ __forceinline__ void load_sigma(const DevTree &tr, uint32_t leaf) {
+    constexpr int NS = (KP + PV - 1) / PV;
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
+    uint4 raw[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) raw[i] = ldg_v4(p + i);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) Elem<E>::unpack(raw[i], w + i * PV);
+  }
+  __device__ __forceinline__ static void prefetch_sigma_l2(const DevTree &tr, uint32_t leaf) {
+    const char *p = reinterpret_cast<const char *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + KP * sizeof(E) - 1));
+  }
   // Asks L2 for the lines of a leaf's record ahead of its use (no registers held).
   __device__ __forceinline__ static void prefetch_l2(const DevTree &tr, uint32_t leaf) {
     const char *p = reinterpret_cast<const char *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
@@ -661,6 +676,23 @@ struct LeafRecord<KP, DEG, Fp8E4M3> {
     sc[0] = __uint_as_float(h.x);
     sc[1] = __uint_as_float(h.y);
     sc[2] = __uint_as_float(h.z);
+  }
+  // The header and the code vectors that hold w_sigma (a density-only pass).
+  __device__ __forceinline__ void load_sigma(const DevTree &tr, uint32_t leaf) {
+    constexpr int NS = (KP + 15) / 16;
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(tr.rec) +
+                                                     (size_t)leaf * tr.rec_stride);
+    const uint4 h = ldg_v4(p);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) raw[i] = i < NS ? ldg_v4(p + 1 + i) : make_uint4(0u, 0u, 0u, 0u);
+    sc[0] = __uint_as_float(h.x);
+    sc[1] = __uint_as_float(h.y);
+    sc[2] = __uint_as_float(h.z);
+  }
+  __device__ __forceinline__ static void prefetch_sigma_l2(const DevTree &tr, uint32_t leaf) {
+    const char *p = reinterpret_cast<const char *>(tr.rec) + (size_t)leaf * tr.rec_stride;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 16 + KP - 1));
   }
   __device__ __forceinline__ static void prefetch_l2(const DevTree &tr, uint32_t leaf) {
     const char *p = reinterpret_cast<const char *>(tr.rec) + (size_t)leaf * tr.rec_stride;

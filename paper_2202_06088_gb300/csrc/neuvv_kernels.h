@@ -155,6 +155,7 @@ cudaError_t launch_pick(int KP, int DEG, DType dt, const FwdArgs &a, float thres
 cudaError_t launch_paint(const int *leaf, const float *color, long long n, long long n_leaves, float *accum,
                          float sigma_d, float t_d, float *edits, cudaStream_t s);
 cudaError_t launch_render_edit(int KP, int DEG, DType dt, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+cudaError_t launch_render_alpha(int KP, int DEG, DType dt, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 cudaError_t launch_gaussian_blur(const float *in, float *out, int width, int height, long long n_images,
                                  const BlurWeights &bw, cudaStream_t s);
 cudaError_t launch_spotlight(const SpotArgs &a, cudaStream_t s);

@@ -29,9 +29,11 @@ __global__ void __launch_bounds__(256) render_plain_kernel(const __grid_constant
 }
 
 __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
-  out.rgb[3 * i + 0] = 0.f;
-  out.rgb[3 * i + 1] = 0.f;
-  out.rgb[3 * i + 2] = 0.f;
+  if (out.rgb) {
+    out.rgb[3 * i + 0] = 0.f;
+    out.rgb[3 * i + 1] = 0.f;
+    out.rgb[3 * i + 2] = 0.f;
+  }
   out.alpha[i] = 0.f;
   if (out.depth) out.depth[i] = INFINITY;
   if (out.tau) out.tau[i] = 0.f;
@@ -50,8 +52,11 @@ __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
 // cells (path per thread in shared memory); basis rows and the queue live in
 // shared memory too.
 // kShade: kShadeTree (the tree's records), kShadeSlice (a time slice,
-// a.slice) or kShadeEdit (the tree's records with appearance edits, a.edits).
-constexpr int kShadeTree = 0, kShadeSlice = 1, kShadeEdit = 2;
+// a.slice), kShadeEdit (the tree's records with appearance edits, a.edits) or
+// kShadeAlpha (density only: the w_sigma part of each record is read, colour
+// is neither evaluated nor written; alpha, depth, tau and nseg are those of
+// the full render).
+constexpr int kShadeTree = 0, kShadeSlice = 1, kShadeEdit = 2, kShadeAlpha = 3;
 template <int KP, int DEG, typename E, int kShade = kShadeTree>
 __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, unsigned present, int queue, int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -73,7 +78,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
   float Y[(DEG + 1) * (DEG + 1)];
   if (hit) {
     if (kShade != kShadeSlice) rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
-    sh_real<DEG>(dn, Y);
+    if (kShade != kShadeAlpha) sh_real<DEG>(dn, Y);
   }
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f, dnum = 0.f, tau = 0.f;
   int nseg = 0;
@@ -98,6 +103,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
         ++qn;
         // the record is read when the segment's round comes: ask L2 for it now
         if (kShade == kShadeSlice) slice_prefetch_l2(a.slice, a.slice_stride, DEG, leaf);
+        else if (kShade == kShadeAlpha) LeafRecord<KP, DEG, E>::prefetch_sigma_l2(tr, leaf);
         else LeafRecord<KP, DEG, E>::prefetch_l2(tr, leaf);
       }
       walking = w.alive;
@@ -145,6 +151,11 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
       float sigma, col[3];
       if constexpr (kShade == kShadeSlice) {
         shade_slice<DEG>(a.slice, a.slice_stride, leaf, Y, a.act, sigma, col);
+      } else if constexpr (kShade == kShadeAlpha) {
+        LeafRecord<KP, DEG, E> rec;
+        rec.load_sigma(tr, leaf);
+        sigma = fmaxf(pre_sigma_of<KP>(rows, rec), 0.f);
+        col[0] = col[1] = col[2] = 0.f;
       } else {
         LeafRecord<KP, DEG, E> rec;
         rec.load(tr, leaf);
@@ -186,9 +197,11 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
     }
   }
   if (!hit) return;
-  a.out.rgb[3 * i + 0] = C0;
-  a.out.rgb[3 * i + 1] = C1;
-  a.out.rgb[3 * i + 2] = C2;
+  if (kShade != kShadeAlpha) {
+    a.out.rgb[3 * i + 0] = C0;
+    a.out.rgb[3 * i + 1] = C1;
+    a.out.rgb[3 * i + 2] = C2;
+  }
   a.out.alpha[i] = A;
   if (a.out.depth) a.out.depth[i] = A >= 1e-4f ? dnum / A : INFINITY;
   if (a.out.tau) a.out.tau[i] = tau;
@@ -650,6 +663,38 @@ static cudaError_t edit_one(const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t
   }
   render_packet_kernel<KP, DEG, E, kShadeEdit><<<(unsigned)grid, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
   return cudaGetLastError();
+}
+
+// Density-only packet render (alpha, depth, tau and nseg of the full render,
+// no colour): one packet per warp of a full grid, no work counter, so it may
+// run beside other calls on the same tree.  Built for the two record shapes
+// of the workloads (K_pad 8 with degree 2, K_pad 16 with degree 3).
+template <int KP, int DEG, typename E>
+static cudaError_t alpha_one(const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
+  if (a.rays.n == 0) return cudaSuccess;
+  const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
+  const size_t sm = smem_bytes(cfg.block, KP, cfg.queue);
+  cudaError_t e;
+  if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(render_packet_kernel<KP, DEG, E, kShadeAlpha>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
+    return e;
+  render_packet_kernel<KP, DEG, E, kShadeAlpha><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_alpha(int KP, int DEG, DType dt, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
+  if (a.work || a.log.n_chunks) return cudaErrorInvalidValue;
+  if (KP == 8 && DEG == 2) {
+    if (dt == kF32) return alpha_one<8, 2, float>(a, cfg, s);
+    if (dt == kBF16) return alpha_one<8, 2, __nv_bfloat16>(a, cfg, s);
+    return alpha_one<8, 2, Fp8E4M3>(a, cfg, s);
+  }
+  if (KP == 16 && DEG == 3) {
+    if (dt == kF32) return alpha_one<16, 3, float>(a, cfg, s);
+    if (dt == kBF16) return alpha_one<16, 3, __nv_bfloat16>(a, cfg, s);
+    return alpha_one<16, 3, Fp8E4M3>(a, cfg, s);
+  }
+  return cudaErrorNotSupported;
 }
 
 cudaError_t launch_render_edit(int KP, int DEG, DType dt, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {

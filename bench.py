@@ -56,6 +56,8 @@ def parse_args():
     p.add_argument("--views", type=int, default=8, help="1920x1080 views per step (8 = the benchmark workload)")
     p.add_argument("--no-autotune", action="store_true", help="keep the default packet launch configuration")
     p.add_argument("--no-fp8", action="store_true", help="skip the FP8-storage ablation leg")
+    p.add_argument("--no-gather", action="store_true",
+                   help="adjoint with the atomic scatter only (no leaf-major workspace reserved)")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the legs of the other workloads (depth-8 and depth-10 training, stereo composition)")
     p.add_argument("--launch", default=None, help="packet launch block,queue,ready (profiling case; default: library's)")
@@ -243,7 +245,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def train_step_leg(B, tree, rays, dtype, steps, seed):
+def reserve_adjoint(B, tree_d, dr, out, enable=True):
+    """Reserves the leaf-major adjoint's workspace for the log chunks one
+    forward over these rays hands out (plus a quarter).  Returns the chunks
+    used and the chunks the log holds."""
+    import numpy as np
+    import torch
+    B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+    torch.cuda.synchronize()
+    head = out["log"][:3].cpu().numpy().astype(np.int64)
+    used, n_chunks = int(head[0]), int(head[2])
+    if enable:
+        tree_d.reserve_adjoint(min(n_chunks, used + used // 4 + 1) * 256)
+    return used, n_chunks
+
+
+def train_step_leg(B, tree, rays, dtype, steps, seed, gather=True):
     """ms per training step (fwd + MSE + adjoint + Adam) and samples/s on one
     workload, targets rendered from perturbed coefficients."""
     import torch
@@ -256,6 +273,7 @@ def train_step_leg(B, tree, rays, dtype, steps, seed):
     tree_d = B.Tree(tree, dtype, with_optimizer=True)
     B.neuvv_autotune(tree_d, dr)
     out = B.alloc_out(n, dr.o.device, log_bytes_per_ray=64)
+    reserve_adjoint(B, tree_d, dr, out, gather)
     grad_rgb = torch.empty(n, 3, device=dr.o.device)
     grad = tree_d.new_grad()
     touched = tree_d.new_touched()
@@ -283,7 +301,7 @@ def train_step_leg(B, tree, rays, dtype, steps, seed):
             "leaves": tree.n_leaves, "samples_per_step": samples, "storage": dtype, "steps": steps}
 
 
-def extra_workloads(B, steps):
+def extra_workloads(B, steps, gather=True):
     """The other synthetic workloads, one leg each: the depth-8 differentiable
     render (262,144 rays over 16 cameras x 16 times), the 8-primitive stereo
     composition at 2 x 2160^2 replayed from a CUDA graph, and the depth-10
@@ -292,7 +310,7 @@ def extra_workloads(B, steps):
     from paper_2202_06088_gb300 import inputs as I
     res = {}
     tree3 = I.config3_tree()
-    res["depth8_train_262k_rays"] = train_step_leg(B, tree3, I.config3_rays(), "bf16", steps, 1003)
+    res["depth8_train_262k_rays"] = train_step_leg(B, tree3, I.config3_rays(), "bf16", steps, 1003, gather)
     del tree3
     tree1 = I.config1_tree()
     prims = I.config4_primitives(8, T=tree1.T)
@@ -327,8 +345,8 @@ def extra_workloads(B, steps):
     del graph, t4, dr4, out4
     tree5 = I.config5_tree()
     rays5 = I.config5_rays()
-    res["depth10_train_1m_rays"] = train_step_leg(B, tree5, rays5, "bf16", steps, 1005)
-    res["depth10_train_1m_rays_fp8"] = train_step_leg(B, tree5, rays5, "fp8", steps, 1005)
+    res["depth10_train_1m_rays"] = train_step_leg(B, tree5, rays5, "bf16", steps, 1005, gather)
+    res["depth10_train_1m_rays_fp8"] = train_step_leg(B, tree5, rays5, "fp8", steps, 1005, gather)
     return res
 
 
@@ -338,7 +356,8 @@ def profile_case(args, B, tree, dr):
     tree_d = B.Tree(tree, "bf16", with_optimizer=args.profile_kernel == "adam")
     if args.launch:
         tree_d.set_launch(*[int(x) for x in args.launch.split(",")])
-    out = B.neuvv_render(tree_d, dr, kernel="packet", out=B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=64))
+    out = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=64)
+    reserve_adjoint(B, tree_d, dr, out, not args.no_gather)
     grad_rgb = torch.randn(dr.n, 3, device=dr.o.device) * 1e-3
     grad = tree_d.new_grad()
     touched = tree_d.new_touched()
@@ -392,6 +411,7 @@ def main():
               "ready": tree_d.info.packet_ready,
               "autotuned": not args.no_autotune}
     out = B.alloc_out(n, dev, log_bytes_per_ray=64)
+    log_used, log_chunks = reserve_adjoint(B, tree_d, dr, out, not args.no_gather)
     grad_rgb = torch.empty(n, 3, device=dev)
     grad = tree_d.new_grad()
     touched = tree_d.new_touched()
@@ -461,6 +481,21 @@ def main():
     value = world * samples / (ms_step / 1e3) / 1e6
     kern = {name: statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps))
             for i, name in enumerate(["fwd", "mse", "lgrad", "bwd", "adam"])}
+    # the same adjoint call with the atomic scatter only, for comparison
+    if not args.no_gather:
+        tree_d.reserve_adjoint(0)
+        B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+        a0.record(stream)
+        for _ in range(5):
+            B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+        a1.record(stream)
+        torch.cuda.synchronize()
+        kern["bwd_atomic_scatter_only"] = a0.elapsed_time(a1) / 5
+        grad.zero_()
+        touched.zero_()
+        reserve_adjoint(B, tree_d, dr, out)
 
     # -- the BF16 forward alone and the plain FP32 single-view kernel
     reps = max(3, args.steps)
@@ -599,6 +634,7 @@ def main():
     if not args.no_fp8:
         tree8 = B.Tree(tree, "fp8", with_optimizer=True)
         tree8.set_launch(launch["block"], launch["queue"], launch["ready"])
+        reserve_adjoint(B, tree8, dr, out, not args.no_gather)
         rgb8 = B.neuvv_render(tree8, dr, kernel="packet")["rgb"]
         mse8 = float(((rgb8 - rgb32) ** 2).mean().item())
         rgb16 = B.neuvv_render(tree_d, dr, kernel="packet")["rgb"]
@@ -654,7 +690,7 @@ def main():
         "adam": (touched_leaves * (8 * rec_f32 + rec_bytes) + 4 * ((info.n_leaves + 31) // 32), 0),
         "mse": (n * 36, 0),
     }
-    dom = max(kern, key=kern.get)
+    dom = max(("fwd", "mse", "bwd", "adam"), key=kern.get)
     bytes_, flops_ = traffic[dom]
     t_s = kern[dom] / 1e3
     if flops_ / (fp32_tflops * 1e12) > bytes_ / (hbm_gbs * 1e9):
@@ -739,6 +775,8 @@ def main():
                    "samples_per_step": samples, "touched_leaves": touched_leaves,
                    "l2": "inputs larger than L2 (rays 464 MB + records 512 MB per step)",
                    "parallelism": f"replicas x{world}", "launch": launch,
+                   "segment_log": {"chunks_used": log_used, "chunks": log_chunks,
+                                   "adjoint": "atomic scatter" if args.no_gather else "leaf-major reduction"},
                    "clocks_window": "warm-up and timed steps"},
         "kernels_ms": kern,
         "fwd_bf16_packet": {"ms_per_1080p_frame": fwd_ms / args.views, "msamples_per_s": fwd_samples / (fwd_ms / 1e3) / 1e6},
@@ -748,11 +786,11 @@ def main():
         "time_slice_and_lighting": time_slice,
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": 8 * args.steps,
+        "gpu_launches": (8 if args.no_gather else 13) * args.steps,
         "clocks": clk,
     }
     if not args.no_extra:
-        line["other_workloads"] = extra_workloads(B, max(5, args.steps // 2))
+        line["other_workloads"] = extra_workloads(B, max(5, args.steps // 2), not args.no_gather)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(tree, rays, args.cpu_seconds)
     if rank == 0:

@@ -225,6 +225,21 @@ neuvv_status neuvv_render_slice(const neuvv_tree *tree, const float *slice, int3
                                 const neuvv_rays *rays, const neuvv_render_opts *opts, neuvv_out *out,
                                 neuvv_stream stream);
 
+/* Reserves device memory for the leaf-major adjoint (synchronous; frees an
+ * earlier reservation; n_slots = 0 only frees).  A slot is one lane of one
+ * shading round of a segment log (a log of B bytes holds fewer than B / 8);
+ * the reservation takes 56 B per slot plus 4 B per leaf.  With it,
+ * neuvv_render_backward (packet kernel, with a log from the forward over the
+ * same rays) leaves each logged sample's gradient factors in its slot, lists
+ * each leaf's samples by a counting sort, and sums them one leaf per thread
+ * into the leaf's gradient record: no gradient atomics for those samples.
+ * Samples in chunks beyond the reservation, and packets the log could not
+ * hold, use the atomic scatter.  The result equals the atomic path's up to
+ * FP32 summation order.  Trees of more than 2^24 leaves: NEUVV_ERR_UNSUPPORTED;
+ * n_slots outside [0, 2^32 - 256]: NEUVV_ERR_INVALID_ARG; allocation failure:
+ * NEUVV_ERR_OOM (the tree keeps no reservation). */
+neuvv_status neuvv_tree_reserve_adjoint(neuvv_tree *tree, int64_t n_slots);
+
 /* Fused adjoint (Sec. 4.3 "Optimization": the renderer is differentiated by
  * hand for gradient descent on the leaf coefficients).  Replays every ray with
  * the forward traversal, recomputes each sample, and accumulates dL/dw for

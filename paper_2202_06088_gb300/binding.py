@@ -73,7 +73,7 @@ EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv
            "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc",
            "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss",
            "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit",
-           "neuvv_camera_rays", "neuvv_render_alpha"]
+           "neuvv_camera_rays", "neuvv_render_alpha", "neuvv_tree_reserve_adjoint"]
 
 
 def library_path() -> str:
@@ -114,6 +114,7 @@ def lib(build_if_missing: bool = True):
                 "neuvv_render_slice": [p, p, i32, p, p, p, p],
                 "neuvv_camera_rays": [p, p, i32, i32, p, p, p, p, i64, p],
                 "neuvv_render_alpha": [p, p, f, p, p, p],
+                "neuvv_tree_reserve_adjoint": [p, i64],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -230,6 +231,11 @@ class Tree:
     def set_launch(self, block: int, queue: int, ready: int) -> None:
         _check(lib().neuvv_tree_set_launch(self.handle, int(block), int(queue), int(ready)))
         self.refresh_info()
+
+    def reserve_adjoint(self, n_slots: int) -> None:
+        """Workspace of the leaf-major adjoint for logs of up to n_slots slots
+        (56 B per slot; 0 frees it)."""
+        _check(lib().neuvv_tree_reserve_adjoint(self.handle, int(n_slots)))
 
     def status(self) -> int:
         f = ctypes.c_uint32()

@@ -85,6 +85,7 @@ struct neuvv_tree {
   float *A = nullptr, *B = nullptr;
   uint32_t *status = nullptr;
   unsigned long long *work = nullptr;
+  GatherWs gws{};           // workspace of the leaf-major adjoint (neuvv_tree_reserve_adjoint)
   bool master_is_storage = false;
   float bmin[3], bmax[3], scale[3];
   float hh_norm[16];
@@ -95,6 +96,15 @@ struct neuvv_tree {
 };
 
 namespace {
+
+void free_gather(neuvv_tree *t) {
+  cudaFree(t->gws.fac);
+  cudaFree(t->gws.fl);
+  cudaFree(t->gws.idx);
+  cudaFree(t->gws.off);
+  cudaFree(t->gws.part);
+  t->gws = GatherWs{};
+}
 
 DevTree dev_tree(const neuvv_tree *t) {
   DevTree d;
@@ -508,7 +518,45 @@ neuvv_status neuvv_tree_destroy(neuvv_tree *t) {
   cudaFree(t->B);
   cudaFree(t->status);
   cudaFree(t->work);
+  free_gather(t);
   delete t;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_tree_reserve_adjoint(neuvv_tree *t, int64_t n_slots) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (n_slots < 0 || n_slots > (int64_t)0xFFFFFFFFll - kLogRounds * 32)
+    return fail(NEUVV_ERR_INVALID_ARG, "n_slots must be in [0, 2^32 - 256]");
+  const long long nl = t->info.n_leaves;
+  if (n_slots > 0 && nl > (long long)kScanTile * kScanParts)
+    return fail(NEUVV_ERR_UNSUPPORTED, "the leaf-major adjoint handles up to %d leaves", kScanTile * kScanParts);
+  DeviceGuard g(t->info.device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  free_gather(t);
+  const long long chunks = n_slots / (kLogRounds * 32);
+  if (chunks == 0) return NEUVV_OK;
+  const size_t slots = (size_t)chunks * kLogRounds * 32;
+  GatherWs w{};
+  if (cudaMalloc(&w.fac, slots * 3 * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&w.fl, slots * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&w.idx, slots * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&w.off, (size_t)(nl + 1) * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&w.part, kScanParts * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    t->gws = w;
+    free_gather(t);
+    return fail(NEUVV_ERR_OOM, "cudaMalloc of the adjoint workspace (%zu slots)", slots);
+  }
+  w.cap_chunks = (uint32_t)chunks;
+  if ((e = cudaMemset(w.fl, 0xFF, slots * sizeof(uint32_t))) != cudaSuccess ||  // all kEmpty
+      (e = cudaMemset(w.idx, 0, slots * sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    t->gws = w;
+    free_gather(t);
+    return cuda_fail(e, "initialise the adjoint workspace");
+  }
+  t->gws = w;
   return NEUVV_OK;
 }
 
@@ -691,6 +739,7 @@ neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, 
   a.act = opts->color_act;
   a.log = log_view(saved->log, saved->log_bytes, rays->n);
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
+  a.gws = packet && a.log.n_chunks ? t->gws : GatherWs{};
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
   cudaError_t e = launch_render_bwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");

@@ -608,6 +608,16 @@ struct LeafRecord {
 #pragma unroll
     for (int i = 0; i < NV; ++i) Elem<E>::unpack(p[i], w + i * PV);
   }
+  // Only the vectors that hold w_sigma and w_gamma.
+  __device__ __forceinline__ void load_sigma_gamma(const DevTree &tr, uint32_t leaf) {
+    constexpr int NS = (2 * KP + PV - 1) / PV;
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
+    uint4 raw[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) raw[i] = ldg_v4(p + i);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) Elem<E>::unpack(raw[i], w + i * PV);
+  }
   // Only the vectors that hold w_sigma (a density-only pass).
   __device__ __forceinline__ void load_sigma(const DevTree &tr, uint32_t leaf) {
     constexpr int NS = (KP + PV - 1) / PV;
@@ -673,6 +683,18 @@ struct LeafRecord<KP, DEG, Fp8E4M3> {
     const uint4 h = p[0];
 #pragma unroll
     for (int i = 0; i < NV; ++i) raw[i] = p[1 + i];
+    sc[0] = __uint_as_float(h.x);
+    sc[1] = __uint_as_float(h.y);
+    sc[2] = __uint_as_float(h.z);
+  }
+  // The header and the code vectors that hold w_sigma and w_gamma.
+  __device__ __forceinline__ void load_sigma_gamma(const DevTree &tr, uint32_t leaf) {
+    constexpr int NS = (2 * KP + 15) / 16;
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(tr.rec) +
+                                                     (size_t)leaf * tr.rec_stride);
+    const uint4 h = ldg_v4(p);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) raw[i] = i < NS ? ldg_v4(p + 1 + i) : make_uint4(0u, 0u, 0u, 0u);
     sc[0] = __uint_as_float(h.x);
     sc[1] = __uint_as_float(h.y);
     sc[2] = __uint_as_float(h.z);

@@ -58,7 +58,24 @@ struct FwdArgs {
   float edit_beta;           // colour blend weight of an active edit
 };
 
+// Workspace of the leaf-major adjoint (owned by the tree; fac, fl and idx
+// have one entry per slot of the first cap_chunks chunks of a segment log).
+// A replayed sample leaves its gradient factors in its slot; a counting sort
+// lists each leaf's slots; one thread per leaf then sums them into its
+// gradient record.  fl is all kEmpty between launches.
+struct GatherWs {
+  float4 *fac;           // [slots][3]: dpre_s, dpre_g, dz0, dz1 | dz2, u, dn0, dn1 | dn2, 0, 0, 0
+  uint32_t *fl;          // [slots] leaf of the slot's sample, kEmpty for none
+  uint32_t *off;         // [n_leaves + 1] samples per leaf, then their offsets
+  uint32_t *idx;         // [slots] slots listed leaf by leaf
+  uint32_t *part;        // [kScanParts] block sums of the offsets' scan
+  uint32_t cap_chunks;   // 0: no workspace (the atomic scatter only)
+};
+// Offsets are scanned in tiles of kScanTile leaves, at most kScanParts tiles.
+constexpr int kScanTile = 4096, kScanParts = 4096;
+
 struct BwdArgs {
+  GatherWs gws;
   DevTree tr;
   DevRays rays;
   const float *rgb;       // saved C [n][3]

@@ -176,6 +176,26 @@ __device__ __forceinline__ void adjoint_round(const BwdArgs &a, const Rows &rows
   if (leader) scatter_gradient<KP, DEG, Rows>(a, rows, leaf, s.R, F, dpre_s, dpre_g);
 }
 
+// Adjoint of one shading round for the leaf-major reduction: a lane with a
+// contributing sample leaves its gradient factors (dpre_s, dpre_g, dz) and
+// its ray's frame coordinate u and unit direction in the sample's log slot,
+// notes the leaf in fl and counts the sample for its leaf.  No gradient
+// atomics; the per-leaf sums are formed by leaf_reduce_kernel.
+template <int KP, int DEG, typename E, typename Rows>
+__device__ __forceinline__ void adjoint_round_gather(const BwdArgs &a, const Rows &rows, const float *Y, uint32_t leaf,
+                                                     float dt, float u, const float dn[3], bool has, AdjState &st,
+                                                     size_t slot) {
+  Sample<DEG> s;
+  float dz[3] = {0.f, 0.f, 0.f}, dpre_s = 0.f, dpre_g = 0.f;
+  if (!(has && sample_factors<KP, DEG, E, Rows>(a, rows, Y, leaf, dt, st, s, dz, dpre_s, dpre_g))) return;
+  float4 *f = a.gws.fac + 3 * slot;
+  f[0] = make_float4(dpre_s, dpre_g, dz[0], dz[1]);
+  f[1] = make_float4(dz[2], u, dn[0], dn[1]);
+  f[2] = make_float4(dn[2], 0.f, 0.f, 0.f);
+  a.gws.fl[slot] = leaf;
+  atomicAdd(a.gws.off + leaf, 1u);
+}
+
 // Whether a segment log was written by a forward over these rays.
 __device__ __forceinline__ bool log_matches(const SampleLog &l, long long n) {
   return __ldg(l.header + 4) == 1u && __ldg(l.header) == l.n_chunks && __ldg(l.header + 1) == (uint32_t)kLogRounds &&
@@ -337,6 +357,7 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
     const uint32_t head = __ldg(a.log.heads + (i >> 5));
     if (head != kNoLog) {
       const int lane = tid & 31;
+      const float u = t * (float)(tr.T - 1);
       uint32_t chunk = head;
       int round = 0;
       while (__ballot_sync(present, live && st.count < st.target)) {
@@ -347,8 +368,8 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
         uint32_t leaf = kEmpty;
         float dt = 0.f;
         bool has = false;
+        const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
         if (live && st.count < st.target) {
-          const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
           leaf = __ldg(a.log.leaf + slot);
           if (leaf != kEmpty) {
             ++st.count;
@@ -357,7 +378,9 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
             else raise_status(tr, kStatusBadIndex);
           }
         }
-        adjoint_round<KP, DEG, E>(a, rows, Y, leaf, dt, t, has, present, st);
+        // chunks with room in the workspace: factors to the slot; others: atomics
+        if (chunk < a.gws.cap_chunks) adjoint_round_gather<KP, DEG, E>(a, rows, Y, leaf, dt, u, dn, has, st, slot);
+        else adjoint_round<KP, DEG, E>(a, rows, Y, leaf, dt, t, has, present, st);
         if (++round == kLogRounds) {
           round = 0;
           chunk = __ldg(a.log.next + chunk);
@@ -402,6 +425,246 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
   }
 }
 
+// ---------------------------------------------------------------------------
+// Leaf-major reduction of the gradient factors.
+// ---------------------------------------------------------------------------
+
+// Exclusive scan of the per-leaf sample counts, in place, tile by tile: each
+// block scans kScanTile counts (4 per thread) and leaves the tile's total in
+// part[tile].
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(uint32_t *v, long long n, uint32_t *part) {
+  __shared__ uint32_t warp_sum[32];
+  const long long base = (long long)blockIdx.x * kScanTile + 4 * threadIdx.x;
+  uint32_t x[4], sum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    x[k] = base + k < n ? v[base + k] : 0u;
+    sum += x[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = sum;  // inclusive scan of the threads' sums within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t ws = warp_sum[lane], wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    warp_sum[lane] = wi - ws;  // exclusive over warps
+    if (lane == 31) part[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  uint32_t run = warp_sum[wid] + incl - sum;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (base + k < n) v[base + k] = run;
+    run += x[k];
+  }
+}
+
+// Exclusive scan of the tile totals (one block; at most kScanParts tiles);
+// v[n] receives the number of samples.
+__global__ void __launch_bounds__(1024) scan_parts_kernel(uint32_t *part, int n_parts, uint32_t *v, long long n) {
+  __shared__ uint32_t warp_sum[32];
+  uint32_t x[4], sum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int j = 4 * threadIdx.x + k;
+    x[k] = j < n_parts ? part[j] : 0u;
+    sum += x[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t ws = warp_sum[lane], wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    warp_sum[lane] = wi - ws;
+    if (lane == 31) v[n] = wi;
+  }
+  __syncthreads();
+  uint32_t run = warp_sum[wid] + incl - sum;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int j = 4 * threadIdx.x + k;
+    if (j < n_parts) part[j] = run;
+    run += x[k];
+  }
+}
+
+__global__ void __launch_bounds__(256) scan_add_kernel(uint32_t *v, long long n, const uint32_t *part) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] += __ldg(part + i / kScanTile);
+}
+
+// Lists each leaf's slots: off[leaf] advances from the leaf's first position
+// to the next leaf's, so afterwards leaf l owns [off[l-1], off[l]) (0 for the
+// first).  Resets fl to kEmpty for the next launch.
+__global__ void __launch_bounds__(256) slot_scatter_kernel(const GatherWs g, const SampleLog l, long long n_leaves) {
+  const unsigned long long used = *l.counter;  // chunks the forward handed out
+  const long long chunks = (long long)min(used, (unsigned long long)min(l.n_chunks, g.cap_chunks));
+  const long long n_slots = chunks * kLogRounds * 32;
+  for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < n_slots;
+       sl += (long long)gridDim.x * blockDim.x) {
+    const uint32_t leaf = g.fl[sl];
+    if (leaf == kEmpty) continue;
+    g.fl[sl] = kEmpty;
+    if (leaf >= (uint32_t)n_leaves) continue;
+    const uint32_t pos = atomicAdd(g.off + leaf, 1u);
+    if (pos < (uint32_t)(g.cap_chunks * kLogRounds * 32)) g.idx[pos] = (uint32_t)sl;
+  }
+}
+
+// One thread per leaf: sums the factors of the leaf's samples.  Samples of
+// one frame coordinate u share the basis rows a(u), b(u) and the radial
+// factors R_nl(gamma(u)), so they are summed first (dpre_s, dpre_g and
+// F[ch][l,m] = sum dz[ch] Y_lm) and expanded into the record when u changes:
+// dL/dw_sigma += a(u) sum dpre_s, dL/dw_gamma += b(u) sum dpre_g,
+// dL/dw_HH[ch][n,l,m] += R_nl F[ch][l,m].  The record accumulates in shared
+// memory; the block then adds its records (consecutive leaves, consecutive
+// in memory) to the gradient buffer with coalesced 16-byte accesses, and sets
+// the touched bits.
+template <int KP, int DEG>
+__host__ __device__ constexpr int reduce_pitch() { return (2 * KP + 3 * n_hh(DEG)) | 1; }
+
+template <int KP, int DEG, typename E>
+__device__ __forceinline__ void leaf_flush(const DevTree &tr, const LeafRecord<KP, DEG, E> &rec, float u,
+                                           float ps, float pg, const float *F, float *acc) {
+  constexpr int NY = (DEG + 1) * (DEG + 1);
+  RayConst<KP, DEG> rc;
+  ray_const_basis<KP, DEG>(tr, u, rc);
+  const RegRows<KP> rows{rc.a, rc.b};
+  float q4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < KP; ++k) q4[k & 3] = fmaf(rows.B(k), rec.gam(k), q4[k & 3]);
+  const float pgam = ((q4[0] + q4[1]) + (q4[2] + q4[3])) * rec.scale_gamma();
+  float sg, cg, R[(DEG + 1) * (DEG + 2) / 2];
+  sincospif(sigmoidf_fast(pgam), &sg, &cg);
+  hh_radial<DEG, false>(cg, sg, tr.hh_norm, R, nullptr);
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    acc[k] = fmaf(ps, rows.A(k), acc[k]);
+    acc[KP + k] = fmaf(pg, rows.B(k), acc[KP + k]);
+  }
+  int j = 0;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+    for (int n = 0; n <= DEG; ++n)
+#pragma unroll
+      for (int l = 0; l <= n; ++l)
+#pragma unroll
+        for (int m = -l; m <= l; ++m) {
+          acc[2 * KP + j] = fmaf(R[radial_index(n, l)], F[ch * NY + l * l + l + m], acc[2 * KP + j]);
+          ++j;
+        }
+}
+
+template <int KP, int DEG, typename E>
+__global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant__ BwdArgs a) {
+  constexpr int NY = (DEG + 1) * (DEG + 1);
+  constexpr int LEN = 2 * KP + 3 * n_hh(DEG), PITCH = reduce_pitch<KP, DEG>(), Q4 = (LEN + 3) / 4;
+  extern __shared__ float acc_s[];  // [blockDim][PITCH], then one flag per thread
+  int *has = reinterpret_cast<int *>(acc_s + blockDim.x * PITCH);
+  const DevTree &tr = a.tr;
+  const long long first = (long long)blockIdx.x * blockDim.x;
+  const long long leaf = first + threadIdx.x;
+  float *acc = acc_s + threadIdx.x * PITCH;
+  for (int j = 0; j < LEN; ++j) acc[j] = 0.f;
+  uint32_t lo = 0, hi = 0;
+  const uint32_t cap = a.gws.cap_chunks * kLogRounds * 32;  // slots of the workspace
+  if (leaf < tr.n_leaves) {
+    lo = leaf > 0 ? __ldg(a.gws.off + leaf - 1) : 0u;
+    hi = min(__ldg(a.gws.off + leaf), cap);
+    lo = min(lo, hi);
+  }
+  has[threadIdx.x] = lo < hi;
+  if (lo < hi) {
+    LeafRecord<KP, DEG, E> rec;
+    rec.load_sigma_gamma(tr, (uint32_t)leaf);
+    float F[3 * NY];
+#pragma unroll
+    for (int k = 0; k < 3 * NY; ++k) F[k] = 0.f;
+    float ps = 0.f, pg = 0.f, u_cur = 0.f;
+    float4 n0, n1, n2;  // the record of the sample after the current one
+    {
+      const float4 *f = a.gws.fac + 3 * (size_t)min(__ldg(a.gws.idx + lo), cap - 1);
+      n0 = __ldg(f);
+      n1 = __ldg(f + 1);
+      n2 = __ldg(f + 2);
+    }
+    uint32_t nidx = lo + 1 < hi ? __ldg(a.gws.idx + lo + 1) : 0u;
+    for (uint32_t p = lo; p < hi; ++p) {
+      const float4 f0 = n0, f1 = n1, f2 = n2;
+      if (p + 1 < hi) {
+        const float4 *f = a.gws.fac + 3 * (size_t)min(nidx, cap - 1);
+        n0 = __ldg(f);
+        n1 = __ldg(f + 1);
+        n2 = __ldg(f + 2);
+        if (p + 2 < hi) nidx = __ldg(a.gws.idx + p + 2);
+      }
+      if (p > lo && f1.y != u_cur) {  // a new frame coordinate: expand the finished group
+        leaf_flush<KP, DEG, E>(tr, rec, u_cur, ps, pg, F, acc);
+#pragma unroll
+        for (int k = 0; k < 3 * NY; ++k) F[k] = 0.f;
+        ps = pg = 0.f;
+      }
+      u_cur = f1.y;
+      ps += f0.x;
+      pg += f0.y;
+      const float dn[3] = {f1.z, f1.w, f2.x}, dz[3] = {f0.z, f0.w, f1.x};
+      float Y[NY];
+      sh_real<DEG>(dn, Y);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+        for (int k = 0; k < NY; ++k) F[ch * NY + k] = fmaf(dz[ch], Y[k], F[ch * NY + k]);
+    }
+    leaf_flush<KP, DEG, E>(tr, rec, u_cur, ps, pg, F, acc);
+  }
+  if (a.touched) {
+    const unsigned bits = __ballot_sync(0xFFFFFFFFu, lo < hi);
+    if ((threadIdx.x & 31) == 0 && bits) atomicOr(a.touched + (leaf >> 5), bits);
+  }
+  __syncthreads();
+  // add the block's records to the gradient buffer, 16 bytes per thread
+  const int rows_here = (int)min((long long)blockDim.x, tr.n_leaves - first);
+  for (int q = threadIdx.x; q < rows_here * Q4; q += blockDim.x) {
+    const int r = q / Q4, v = q - r * Q4;
+    if (!has[r]) continue;
+    const float *src = acc_s + r * PITCH + 4 * v;
+    float4 *dst = reinterpret_cast<float4 *>(a.grad + (size_t)(first + r) * a.grad_stride) + v;
+    float4 g = *dst;
+    g.x += src[0];
+    if (4 * v + 1 < LEN) g.y += src[1];
+    if (4 * v + 2 < LEN) g.z += src[2];
+    if (4 * v + 3 < LEN) g.w += src[3];
+    *dst = g;
+  }
+}
+
+template <int KP, int DEG>
+__host__ __device__ constexpr size_t reduce_smem_bytes(int block) {
+  return (size_t)block * (reduce_pitch<KP, DEG>() * sizeof(float) + sizeof(int));
+}
+
 template <int KP, int DEG, typename E>
 static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
   if (a.rays.n == 0) return cudaSuccess;
@@ -431,7 +694,32 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
           a.log, n_packets, shift);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    const bool gather = a.log.n_chunks && a.gws.cap_chunks;
+    const long long nl = a.tr.n_leaves;
+    if (gather) {
+      cudaError_t e = cudaMemsetAsync(a.gws.off, 0, (size_t)(nl + 1) * sizeof(uint32_t), s);
+      if (e != cudaSuccess) return e;
+    }
     render_bwd_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
+    if (gather && nl > 0) {
+      // per-leaf offsets, the slots listed leaf by leaf, then the per-leaf sums
+      const int tiles = (int)((nl + kScanTile - 1) / kScanTile);
+      scan_tiles_kernel<<<tiles, 1024, 0, s>>>(a.gws.off, nl, a.gws.part);
+      scan_parts_kernel<<<1, 1024, 0, s>>>(a.gws.part, tiles, a.gws.off, nl);
+      scan_add_kernel<<<(unsigned)std::min<long long>((nl + 255) / 256, 8LL * cfg.num_sms), 256, 0, s>>>(
+          a.gws.off, nl, a.gws.part);
+      const long long slots = (long long)std::min(a.log.n_chunks, a.gws.cap_chunks) * kLogRounds * 32;
+      slot_scatter_kernel<<<(unsigned)std::min<long long>((slots + 255) / 256, 16LL * cfg.num_sms), 256, 0, s>>>(
+          a.gws, a.log, nl);
+      constexpr int kReduceBlock = 64;
+      const size_t rsm = reduce_smem_bytes<KP, DEG>(kReduceBlock);
+      if (rsm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(leaf_reduce_kernel<KP, DEG, E>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        if (e != cudaSuccess) return e;
+      }
+      leaf_reduce_kernel<KP, DEG, E><<<(unsigned)((nl + kReduceBlock - 1) / kReduceBlock), kReduceBlock, rsm, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }

@@ -126,3 +126,8 @@ def test_camera_rays_arguments_are_checked_on_the_host(L):
     assert L.neuvv_camera_rays(cams, t, 1, 1, buf, buf, buf, None, 32, None) == 1
     cams[0].fov_y_deg, cams[0].width = 40.0, 0
     assert L.neuvv_camera_rays(cams, t, 1, 1, buf, buf, buf, None, 0, None) == 1
+
+
+def test_reserve_adjoint_arguments_are_checked_on_the_host(L):
+    assert L.neuvv_tree_reserve_adjoint(None, 0) == 1
+    assert b"NULL" in L.neuvv_last_error()

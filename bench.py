@@ -273,6 +273,8 @@ def train_step_leg(B, tree, rays, dtype, steps, seed, gather=True):
     tree_d = B.Tree(tree, dtype, with_optimizer=True)
     B.neuvv_autotune(tree_d, dr)
     out = B.alloc_out(n, dr.o.device, log_bytes_per_ray=64)
+    # the per-leaf pass pays per leaf: worth it with at least a sample per leaf
+    gather = gather and n >= tree.n_leaves
     reserve_adjoint(B, tree_d, dr, out, gather)
     grad_rgb = torch.empty(n, 3, device=dr.o.device)
     grad = tree_d.new_grad()
@@ -298,7 +300,8 @@ def train_step_leg(B, tree, rays, dtype, steps, seed, gather=True):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     return {"ms_per_step": ms, "msamples_per_s": samples / (ms / 1e3) / 1e6, "rays": n,
-            "leaves": tree.n_leaves, "samples_per_step": samples, "storage": dtype, "steps": steps}
+            "leaves": tree.n_leaves, "samples_per_step": samples, "storage": dtype, "steps": steps,
+            "adjoint": "leaf-major reduction" if gather else "atomic scatter"}
 
 
 def extra_workloads(B, steps, gather=True):

@@ -245,6 +245,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def slowest_rank_ms(ms, world, device):
+    """The job's time: the maximum over the ranks of each rank's timed
+    region (every rank runs the same replica workload)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_msamples_per_s(samples_per_rank, ms_step, world):
+    """Whole-job throughput: all ranks' samples over the slowest rank's step."""
+    return world * samples_per_rank / (ms_step / 1e3) / 1e6
+
+
 def reserve_adjoint(B, tree_d, dr, out, enable=True):
     """Reserves the leaf-major adjoint's workspace for the log chunks one
     forward over these rays hands out (plus a quarter).  Returns the chunks
@@ -473,15 +490,13 @@ def main():
         step(args.warmup + k + 1, ev[k])
     t_end.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
     if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = slowest_rank_ms(t_start.elapsed_time(t_end), world, dev)
     ms_step = ms_total / args.steps
     samples = 0.5 * (samples_before + int(out["nseg"].sum().item()))
-    value = world * samples / (ms_step / 1e3) / 1e6
+    value = job_msamples_per_s(samples, ms_step, world)
     kern = {name: statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps))
             for i, name in enumerate(["fwd", "mse", "lgrad", "bwd", "adam"])}
     # the same adjoint call with the atomic scatter only, for comparison

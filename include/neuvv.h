@@ -23,9 +23,11 @@
  *    and neuvv_compose pull work from a counter owned by the tree (by the
  *    first tree for compose; neuvv_compose_noalloc's is a library global):
  *    two such calls on one tree must be ordered (one stream, or events
- *    between streams).  The plain kernel (NEUVV_KERNEL_PLAIN) and the other
- *    calls use no such counter and may run concurrently on different streams,
- *    as long as their outputs do not overlap.
+ *    between streams).  So must two neuvv_render_backward calls on a tree with
+ *    an adjoint reservation (they share its workspace).  The plain kernel
+ *    (NEUVV_KERNEL_PLAIN) and the other calls use no such counter and may run
+ *    concurrently on different streams, as long as their outputs do not
+ *    overlap.
  *  - Errors found on the device (a ray that exceeds its segment cap, an index
  *    outside the tree) are recorded in a per-tree status word read by
  *    neuvv_tree_status(); the affected ray ends early, nothing traps.

@@ -1,7 +1,7 @@
 """The pins of the oracle's Python functions are strong enough to catch
 plausible mistakes.  The functions are the pinhole camera rays, the
-image-gradient regulariser, the shadow map's Gaussian filter and the
-spotlight.
+image-gradient regulariser, the shadow map's Gaussian filter, the spotlight
+and the painting of picked voxels.
 
 Each case plants one mistake (a dropped term, a wrong sign, factor or index
 order) in a copy of `oracle/__init__.py`.  It loads the copy as a module and
@@ -41,6 +41,9 @@ MUTANTS = {
     "spot_texel_centre_shifted": ("spotlight", "* Wl / 2.0 - 0.5", "* Wl / 2.0"),
     "spot_shadow_not_reversed": ("spotlight", "((1.0 - al) * fall(P))", "(al * fall(P))"),
     "spot_ground_ignores_viewer_alpha": ("spotlight", "out[hit] += (1.0 - A[hit])[:, None] * G", "out[hit] += G"),
+    "paint_sum_not_mean": ("paint", "e[hit, :3] = s[hit] / cnt[hit, None]", "e[hit, :3] = s[hit]"),
+    "paint_time_not_set": ("paint", "e[hit, 4] = t_d", "e[hit, 4] = 2.0"),
+    "paint_counts_unpicked_rays": ("paint", "ok = leaves >= 0", "ok = leaves >= -1"),
 }
 
 
@@ -62,6 +65,9 @@ def _pins(which):
                 ("times_origins", TC.test_times_and_origins)]
     if which == "gradloss":
         return [(n, getattr(TG, n)) for n in dir(TG) if n.startswith("test_")]
+    if which == "paint":
+        import test_oracle_edit as TE
+        return [("paint_means", TE.test_paint_means)]
     import test_oracle_spotlight as TS
     pins = [(n, getattr(TS, n)) for n in dir(TS) if n.startswith("test_") and n != "test_blur_is_the_gaussian_filter"]
     return pins + [("blur_1.5", lambda: TS.test_blur_is_the_gaussian_filter(1.5))]
@@ -70,7 +76,8 @@ def _pins(which):
 def _failures(mod, which, monkeypatch):
     import test_oracle_camera
     import test_oracle_gradloss
-    targets = [test_oracle_camera, test_oracle_gradloss]
+    import test_oracle_edit
+    targets = [test_oracle_camera, test_oracle_gradloss, test_oracle_edit]
     if which == "spotlight":
         import test_oracle_spotlight
         targets.append(test_oracle_spotlight)
@@ -85,7 +92,7 @@ def _failures(mod, which, monkeypatch):
     return failed
 
 
-@pytest.mark.parametrize("which", ["camera", "gradloss", "spotlight"])
+@pytest.mark.parametrize("which", ["camera", "gradloss", "spotlight", "paint"])
 def test_unmodified_copy_passes_the_pins(which, monkeypatch):
     if which == "spotlight":
         pytest.importorskip("scipy.ndimage")

@@ -8,7 +8,9 @@ resident in HBM.  Coefficients are stored in BF16 with an FP32 master copy.
 
 One step = forward render (packet kernel) -> loss gradient against fixed
 target images (Eq. rgb-loss plus 0.1 x the image-gradient regulariser of
-Sec. 4.3) -> fused adjoint -> sparse Adam on the touched leaves.  The
+Sec. 4.3) -> fused adjoint (gradient sums formed per leaf after a counting
+sort of the samples, where a step has at least one ray per leaf) -> sparse
+Adam on the touched leaves.  The
 headline metric is leaf-segment samples per second of the forward+backward
 pair (a sample is one leaf segment evaluated by the forward and re-evaluated
 by the adjoint, counted once).

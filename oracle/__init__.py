@@ -77,13 +77,13 @@ def configure(L):
     L.or_hh_index.restype = ci
     L.or_hh_index.argtypes = [ci, ci, ci]
     L.or_render.restype = None
-    L.or_render.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, p, ci]
+    L.or_render.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, p, p, ci]
     L.or_trace_batch.restype = None
-    L.or_trace_batch.argtypes = [p, i64, p, p, ci, p, p, p, p, ci]
+    L.or_trace_batch.argtypes = [p, i64, p, p, ci, p, p, p, p, p, ci]
     L.or_render_grad.restype = None
     L.or_render_grad.argtypes = [p, p, i64, p, p, p, p, p, p, p, p, ci]
     L.or_compose.restype = None
-    L.or_compose.argtypes = [p, p, p, p, ci, ci, p, i64, p, p, p, p, p, p, p, ci]
+    L.or_compose.argtypes = [p, p, p, p, ci, ci, p, i64, p, p, p, p, p, p, p, p, p, ci]
     L.or_adam.restype = None
     L.or_adam.argtypes = [i64, ci, p, p, p, p, p, d, d, d, d, ci]
     L.or_round_bf16.restype = None
@@ -183,25 +183,30 @@ def render(tree, rays, t_stop: float = 1e-4, act: str = "sigmoid", nthreads: int
     """Eq. volume-rendering over the voxels each ray crosses (Sec. 4.3 "Rendering").
 
     Returns rgb [n,3] (premultiplied, black background), alpha, depth, tau
-    (optical depth sum sigma*delta), nseg (composited segments) and
-    stop_margin (|tau_{i+1} - ln(1/t_stop)| minimum, for near-threshold checks).
+    (optical depth sum sigma*delta), nseg (composited segments),
+    stop_margin (|tau_{i+1} - ln(1/t_stop)| minimum, for near-threshold checks)
+    and trace_margin: the traversal's decision margin (reading A8) up to the
+    early stop, in finest cells -- the smallest distance along the ray
+    between two plane crossings whose order decides which leaves are visited.
     """
     ot = otree or OracleTree(tree)
     o, d, t = _rays64(rays)
     n = t.size
-    out = {k: np.zeros(n) for k in ("alpha", "depth", "tau", "stop_margin")}
+    out = {k: np.zeros(n) for k in ("alpha", "depth", "tau", "stop_margin", "trace_margin")}
     out["rgb"] = np.zeros((n, 3))
     out["nseg"] = np.zeros(n, np.int32)
     op = _opts(t_stop, act)
     lib().or_render(ctypes.byref(ot.struct), ctypes.byref(op), n, _ptr(o), _ptr(d), _ptr(t), _ptr(out["rgb"]),
                     _ptr(out["alpha"]), _ptr(out["depth"]), _ptr(out["tau"]), _ptr(out["nseg"]),
-                    _ptr(out["stop_margin"]), nthreads or default_threads())
+                    _ptr(out["stop_margin"]), _ptr(out["trace_margin"]), nthreads or default_threads())
     return out
 
 
 def trace(tree, rays, max_out: int = 64, nthreads: int | None = None, otree: OracleTree | None = None) -> dict:
     """Occupied leaves each ray crosses, with entry/exit distances (Sec. 4.3
-    "Rendering": voxels on the path and the lengths of the segments inside)."""
+    "Rendering": voxels on the path and the lengths of the segments inside),
+    and each ray's decision margin over its whole length in finest cells
+    (reading A8; see ``render``)."""
     ot = otree or OracleTree(tree)
     o, d, _ = _rays64(rays)
     n = o.shape[1]
@@ -209,9 +214,10 @@ def trace(tree, rays, max_out: int = 64, nthreads: int | None = None, otree: Ora
     t0 = np.zeros((n, max_out))
     t1 = np.zeros((n, max_out))
     cnt = np.zeros(n, np.int32)
+    margin = np.zeros(n)
     lib().or_trace_batch(ctypes.byref(ot.struct), n, _ptr(o), _ptr(d), max_out, _ptr(leaf), _ptr(t0), _ptr(t1),
-                         _ptr(cnt), nthreads or default_threads())
-    return {"leaf": leaf, "t0": t0, "t1": t1, "count": cnt}
+                         _ptr(cnt), _ptr(margin), nthreads or default_threads())
+    return {"leaf": leaf, "t0": t0, "t1": t1, "count": cnt, "margin": margin}
 
 
 def render_grad(tree, rays, grad_rgb, grad_alpha=None, t_stop: float = 1e-4, act: str = "sigmoid",
@@ -453,7 +459,13 @@ def compose(trees, transforms, time_offsets, tints, rays, mode: str = "sorted", 
             act: str = "sigmoid", nthreads: int | None = None) -> dict:
     """Eq. st_composite_affine per primitive, then depth-aware blending
     (Algorithm 1; mode 'sorted' = stable depth sort + premultiplied over,
-    'alg1' = Algorithm 1 literally on premultiplied layers)."""
+    'alg1' = Algorithm 1 literally on premultiplied layers).
+
+    Besides rgb, alpha, depth and the early-stop margin, reports per pixel
+    trace_margin (the smallest decision margin of the layers' traversals, in
+    finest cells of each layer's tree) and depth_margin (the smallest gap
+    between two layers' finite depths: below the depths' rounding error the
+    blending order is not determined)."""
     ots = [t if isinstance(t, OracleTree) else OracleTree(t) for t in trees]
     P = len(ots)
     arr = (ctypes.c_void_p * P)(*[ctypes.addressof(x.struct) for x in ots])
@@ -466,11 +478,14 @@ def compose(trees, transforms, time_offsets, tints, rays, mode: str = "sorted", 
     alpha = np.zeros(n)
     depth = np.zeros(n)
     margin = np.zeros(n)
+    tmargin = np.zeros(n)
+    dmargin = np.zeros(n)
     op = _opts(t_stop, act)
     lib().or_compose(arr, _ptr(xf), _ptr(toff), _ptr(tint), P, {"sorted": 0, "alg1": 1}[mode], ctypes.byref(op), n,
-                     _ptr(o), _ptr(d), _ptr(t), _ptr(rgb), _ptr(alpha), _ptr(depth), _ptr(margin),
-                     nthreads or default_threads())
-    return {"rgb": rgb, "alpha": alpha, "depth": depth, "stop_margin": margin}
+                     _ptr(o), _ptr(d), _ptr(t), _ptr(rgb), _ptr(alpha), _ptr(depth), _ptr(margin), _ptr(tmargin),
+                     _ptr(dmargin), nthreads or default_threads())
+    return {"rgb": rgb, "alpha": alpha, "depth": depth, "stop_margin": margin, "trace_margin": tmargin,
+            "depth_margin": dmargin}
 
 
 def adam(w, m, v, g, touched, lr, b1, b2, eps, step):

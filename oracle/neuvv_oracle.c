@@ -257,6 +257,41 @@ static int64_t lookup(const or_tree *tr, const int64_t cell[3]) {
   return -1;
 }
 
+/* As lookup, and -1 for a cell outside the root box. */
+static int64_t lookup_any(const or_tree *tr, const int64_t cell[3]) {
+  int64_t N = (int64_t)1 << tr->depth;
+  for (int a = 0; a < 3; ++a)
+    if (cell[a] < 0 || cell[a] >= N) return -1;
+  return lookup(tr, cell);
+}
+
+/* The occupied leaves met going from finest cell c one cell along axis a
+   (direction sa) and then one along axis b (direction sb): empty cells
+   dropped, repeats merged.  Returns their number (<= 3). */
+static int path_leaves(const or_tree *tr, const int64_t c[3], int a, int sa, int b, int sb, int64_t out[3]) {
+  int64_t c1[3] = {c[0], c[1], c[2]};
+  c1[a] += sa;
+  int64_t c2[3] = {c1[0], c1[1], c1[2]};
+  c2[b] += sb;
+  int64_t ids[3] = {lookup_any(tr, c), lookup_any(tr, c1), lookup_any(tr, c2)};
+  int n = 0;
+  for (int i = 0; i < 3; ++i)
+    if (ids[i] >= 0 && (n == 0 || out[n - 1] != ids[i])) out[n++] = ids[i];
+  return n;
+}
+
+/* Whether crossing a plane of axis a and one of axis b in the other order
+   (the two crossings meet at an edge or nearly so) changes the sequence of
+   occupied leaves the ray visits. */
+static int order_matters(const or_tree *tr, const int64_t c[3], int a, int sa, int b, int sb) {
+  int64_t p[3], q[3];
+  int np = path_leaves(tr, c, a, sa, b, sb, p), nq = path_leaves(tr, c, b, sb, a, sa, q);
+  if (np != nq) return 1;
+  for (int i = 0; i < np; ++i)
+    if (p[i] != q[i]) return 1;
+  return 0;
+}
+
 /* Cell index on one axis of the point p moving with velocity v: the cell the
    ray occupies just after this instant. */
 static int64_t cell_of(double p, double v, int64_t N) {
@@ -269,11 +304,22 @@ static int64_t cell_of(double p, double v, int64_t N) {
 }
 
 /* Occupied-leaf segments of a ray (unit direction dn), in order.  Returns the
-   count (<= max_seg), or -1 if max_seg was too small. */
-int or_trace(const or_tree *tr, const double o[3], const double dn[3], or_seg *segs, int max_seg) {
+   count (<= max_seg), or -1 if max_seg was too small.
+
+   Decision margin (reading A8), when margin != NULL: the smallest distance
+   along the ray between two plane crossings on different axes whose order
+   decides which occupied leaves the ray visits (order_matters), over the
+   crossings at distances up to t_limit; the ray's entry into the root box
+   counts as a crossing of its entry plane.  +inf when no such pair exists.
+   A ray whose margin exceeds the error of a traversal's crossing distances
+   visits the same leaves in that traversal. */
+int or_trace_m(const or_tree *tr, const double o[3], const double dn[3], or_seg *segs, int max_seg, double t_limit,
+               double *margin) {
   int64_t N = (int64_t)1 << tr->depth;
   double go[3], gd[3];
   double tn = -INFINITY, tf = INFINITY;
+  int ax_in = -1;
+  if (margin) *margin = INFINITY;
   for (int a = 0; a < 3; ++a) {
     double sc = (double)N / (tr->bmax[a] - tr->bmin[a]);
     go[a] = (o[a] - tr->bmin[a]) * sc;
@@ -283,7 +329,7 @@ int or_trace(const or_tree *tr, const double o[3], const double dn[3], or_seg *s
     } else {
       double t0 = (0.0 - go[a]) / gd[a], t1 = ((double)N - go[a]) / gd[a];
       if (t0 > t1) { double s = t0; t0 = t1; t1 = s; }
-      if (t0 > tn) tn = t0;
+      if (t0 > tn) { tn = t0; ax_in = a; }
       if (t1 < tf) tf = t1;
     }
   }
@@ -291,6 +337,31 @@ int or_trace(const or_tree *tr, const double o[3], const double dn[3], or_seg *s
   if (!(tin < tf)) return 0;
   int64_t cell[3];
   for (int a = 0; a < 3; ++a) cell[a] = cell_of(go[a] + tin * gd[a], gd[a], N);
+  if (margin) {
+    /* crossings next to the start: the planes of the other axes just behind
+       and just ahead of the entry point (or of an origin inside the box) */
+    for (int x = 0; x < 3; ++x) {
+      if (gd[x] == 0.0 || (tn > 0.0 && x == ax_in)) continue;
+      int sx = gd[x] > 0.0 ? 1 : -1;
+      double behind = ((double)(sx > 0 ? cell[x] : cell[x] + 1) - go[x]) / gd[x];
+      double ahead = ((double)(sx > 0 ? cell[x] + 1 : cell[x]) - go[x]) / gd[x];
+      if (tn > 0.0) {
+        int si = gd[ax_in] > 0.0 ? 1 : -1;
+        int64_t c_out[3] = {cell[0], cell[1], cell[2]};
+        c_out[ax_in] -= si;                       /* the cell just outside the entry face */
+        if (ahead - tin < *margin && order_matters(tr, c_out, ax_in, si, x, sx)) *margin = ahead - tin;
+        int64_t c_prev[3] = {c_out[0], c_out[1], c_out[2]};
+        c_prev[x] -= sx;
+        if (tin - behind < *margin && order_matters(tr, c_prev, x, sx, ax_in, si)) *margin = tin - behind;
+      } else {
+        /* origin inside: it could start in the cell behind plane x instead */
+        int64_t c_b[3] = {cell[0], cell[1], cell[2]};
+        c_b[x] -= sx;
+        int64_t lb = lookup_any(tr, c_b), lc = lookup_any(tr, cell);
+        if (tin - behind < *margin && lb >= 0 && lb != lc) *margin = tin - behind;
+      }
+    }
+  }
   double t_cur = tin;
   int count = 0;
   int64_t cur = -1;
@@ -305,6 +376,14 @@ int or_trace(const or_tree *tr, const double o[3], const double dn[3], or_seg *s
     int ax = 0;
     if (tnext[1] < tnext[ax]) ax = 1;
     if (tnext[2] < tnext[ax]) ax = 2;
+    if (margin && tnext[ax] <= t_limit) {
+      int sa = gd[ax] > 0.0 ? 1 : -1;
+      for (int x = 0; x < 3; ++x) {
+        if (x == ax || gd[x] == 0.0) continue;
+        double gap = tnext[x] - tnext[ax];
+        if (gap < *margin && order_matters(tr, cell, ax, sa, x, gd[x] > 0.0 ? 1 : -1)) *margin = gap;
+      }
+    }
     double t_end = tnext[ax] < tf ? tnext[ax] : tf;
     int64_t leaf = lookup(tr, cell);
     if (leaf >= 0 && leaf == cur) {
@@ -330,6 +409,21 @@ int or_trace(const or_tree *tr, const double o[3], const double dn[3], or_seg *s
   return count;
 }
 
+int or_trace(const or_tree *tr, const double o[3], const double dn[3], or_seg *segs, int max_seg) {
+  return or_trace_m(tr, o, dn, segs, max_seg, INFINITY, NULL);
+}
+
+/* Edge of the tree's finest cell (the smallest over the axes), the unit of
+   the reported decision margins. */
+static double finest_cell(const or_tree *tr) {
+  double c = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    double e = (tr->bmax[a] - tr->bmin[a]) / (double)((int64_t)1 << tr->depth);
+    if (e < c) c = e;
+  }
+  return c;
+}
+
 static int max_segments(const or_tree *tr) { return 3 * (1 << tr->depth) + 8; }
 
 static void unit(const double v[3], double out[3]) {
@@ -345,6 +439,8 @@ typedef struct {
   double rgb[3], alpha, depth, tau;
   int nseg;              /* segments composited (early stop included) */
   double stop_margin;    /* min |tau_{i+1} - ln(1/t_stop)| over composited segments */
+  double trace_margin;   /* decision margin of the traversal up to the early stop, in finest cells
+                            (computed only when render_ray is asked for it) */
 } or_ray_out;
 
 /* Per-sample record kept for the gradient. */
@@ -357,7 +453,8 @@ typedef struct {
 /* Renders one ray at frame coordinate u.  If samples != NULL, fills it with the
    composited samples (capacity max_segments).  Scratch: segs, H (N_h). */
 static void render_ray(const or_tree *tr, const or_opts *op, const double o[3], const double d[3], double u,
-                       or_seg *segs, double *H, double *a, double *b, or_ray_out *out, or_sample *samples) {
+                       or_seg *segs, double *H, double *a, double *b, or_ray_out *out, or_sample *samples,
+                       int want_margin) {
   double dn[3];
   unit(d, dn);
   basis_rows(tr, u, a, b);
@@ -393,6 +490,13 @@ static void render_ray(const or_tree *tr, const or_opts *op, const double o[3], 
   out->tau = tau;
   out->depth = alpha >= 1e-4 ? dnum / alpha : INFINITY;
   out->nseg = composited;
+  out->trace_margin = INFINITY;
+  if (want_margin) {
+    /* crossings after an early stop cannot change the composited segments */
+    double t_limit = composited < ns ? segs[composited - 1].t1 : INFINITY, m;
+    or_trace_m(tr, o, dn, segs, max_segments(tr), t_limit, &m);
+    out->trace_margin = m / finest_cell(tr);
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -432,7 +536,7 @@ typedef struct {
   const or_opts *op;
   const double *o, *d, *t; /* o, d: [3][n] planes; t: [n] */
   int64_t n;
-  double *rgb, *alpha, *depth, *tau, *margin;
+  double *rgb, *alpha, *depth, *tau, *margin, *trace_margin;
   int32_t *nseg;
 } render_ctx;
 
@@ -449,20 +553,22 @@ static void render_range(void *p, int64_t lo, int64_t hi) {
     if (t < 0.0) t = 0.0;
     if (t > 1.0) t = 1.0;
     or_ray_out out;
-    render_ray(tr, c->op, o, d, t * (tr->T - 1), segs, H, a, b, &out, NULL);
+    render_ray(tr, c->op, o, d, t * (tr->T - 1), segs, H, a, b, &out, NULL, c->trace_margin != NULL);
     for (int ch = 0; ch < 3; ++ch) c->rgb[3 * r + ch] = out.rgb[ch];
     c->alpha[r] = out.alpha;
     c->depth[r] = out.depth;
     c->tau[r] = out.tau;
     c->nseg[r] = out.nseg;
     if (c->margin) c->margin[r] = out.stop_margin;
+    if (c->trace_margin) c->trace_margin[r] = out.trace_margin;
   }
   free(segs); free(H); free(a); free(b);
 }
 
 void or_render(const or_tree *tr, const or_opts *op, int64_t n, const double *o, const double *d, const double *t,
-               double *rgb, double *alpha, double *depth, double *tau, int32_t *nseg, double *margin, int nthreads) {
-  render_ctx c = {tr, op, o, d, t, n, rgb, alpha, depth, tau, margin, nseg};
+               double *rgb, double *alpha, double *depth, double *tau, int32_t *nseg, double *margin,
+               double *trace_margin, int nthreads) {
+  render_ctx c = {tr, op, o, d, t, n, rgb, alpha, depth, tau, margin, trace_margin, nseg};
   parallel_for(n, nthreads, render_range, &c);
 }
 
@@ -478,6 +584,7 @@ typedef struct {
   int64_t *leaf;
   double *t0, *t1;
   int32_t *count;
+  double *margin;     /* decision margin over the whole ray, in finest cells (may be NULL) */
 } trace_ctx;
 
 static void trace_range(void *p, int64_t lo, int64_t hi) {
@@ -487,8 +594,10 @@ static void trace_range(void *p, int64_t lo, int64_t hi) {
     double o[3] = {c->o[r], c->o[c->n + r], c->o[2 * c->n + r]};
     double d[3] = {c->d[r], c->d[c->n + r], c->d[2 * c->n + r]}, dn[3];
     unit(d, dn);
-    int ns = or_trace(c->tr, o, dn, segs, max_segments(c->tr));
+    double m;
+    int ns = or_trace_m(c->tr, o, dn, segs, max_segments(c->tr), INFINITY, c->margin ? &m : NULL);
     c->count[r] = ns;
+    if (c->margin) c->margin[r] = m / finest_cell(c->tr);
     for (int i = 0; i < ns && i < c->max_out; ++i) {
       c->leaf[r * c->max_out + i] = segs[i].leaf;
       c->t0[r * c->max_out + i] = segs[i].t0;
@@ -499,8 +608,8 @@ static void trace_range(void *p, int64_t lo, int64_t hi) {
 }
 
 void or_trace_batch(const or_tree *tr, int64_t n, const double *o, const double *d, int max_out, int64_t *leaf,
-                    double *t0, double *t1, int32_t *count, int nthreads) {
-  trace_ctx c = {tr, o, d, n, max_out, leaf, t0, t1, count};
+                    double *t0, double *t1, int32_t *count, double *margin, int nthreads) {
+  trace_ctx c = {tr, o, d, n, max_out, leaf, t0, t1, count, margin};
   parallel_for(n, nthreads, trace_range, &c);
 }
 
@@ -550,7 +659,7 @@ static void grad_range(void *p, int64_t lo, int64_t hi) {
     if (t < 0.0) t = 0.0;
     if (t > 1.0) t = 1.0;
     or_ray_out out;
-    render_ray(tr, c->op, o, d, t * (tr->T - 1), segs, H, a, b, &out, sm);
+    render_ray(tr, c->op, o, d, t * (tr->T - 1), segs, H, a, b, &out, sm, 0);
     int M = out.nseg;
     /* suffix sums over j > i of w_j c_j and w_j */
     for (int q = 0; q < 4; ++q) suffix[4 * M + q] = 0.0;
@@ -638,6 +747,8 @@ typedef struct {
   const double *o, *d, *t;
   int64_t n;
   double *rgb, *alpha, *depth, *margin;
+  double *trace_margin;  /* min over the layers of their decision margins, in finest cells (may be NULL) */
+  double *depth_margin;  /* min |D_i - D_j| over pairs of layers with finite depths (may be NULL) */
 } compose_ctx;
 
 static void compose_range(void *p, int64_t lo, int64_t hi) {
@@ -662,7 +773,7 @@ static void compose_range(void *p, int64_t lo, int64_t hi) {
     double t = c->t[r];
     if (t < 0.0) t = 0.0;
     if (t > 1.0) t = 1.0;
-    double margin = INFINITY;
+    double margin = INFINITY, tmargin = INFINITY, dmargin = INFINITY;
     for (int j = 0; j < P; ++j) {
       const or_tree *tr = c->trees[j];
       const double *M = c->xf + 12 * j;
@@ -678,12 +789,16 @@ static void compose_range(void *p, int64_t lo, int64_t hi) {
       double u = fmod(t * period + c->toff[j], period);
       if (u < 0.0) u += period;
       or_ray_out out;
-      render_ray(tr, c->op, ol, dl, u, segs, H, a, b, &out, NULL);
+      render_ray(tr, c->op, ol, dl, u, segs, H, a, b, &out, NULL, c->trace_margin != NULL);
       if (out.stop_margin < margin) margin = out.stop_margin;
+      if (out.trace_margin < tmargin) tmargin = out.trace_margin;
       for (int ch = 0; ch < 3; ++ch) LC[3 * j + ch] = c->tint[3 * j + ch] * out.rgb[ch];
       LA[j] = out.alpha;
       LD[j] = isinf(out.depth) ? INFINITY : out.depth / inv_s;
     }
+    for (int i = 0; i < P; ++i)
+      for (int j = i + 1; j < P; ++j)
+        if (!isinf(LD[i]) && !isinf(LD[j]) && fabs(LD[i] - LD[j]) < dmargin) dmargin = fabs(LD[i] - LD[j]);
     double I[3], A, D;
     if (c->mode == 0) {
       for (int j = 0; j < P; ++j) ord[j] = j;
@@ -717,14 +832,18 @@ static void compose_range(void *p, int64_t lo, int64_t hi) {
     c->alpha[r] = A;
     c->depth[r] = D;
     if (c->margin) c->margin[r] = margin;
+    if (c->trace_margin) c->trace_margin[r] = tmargin;
+    if (c->depth_margin) c->depth_margin[r] = dmargin;
   }
   free(segs); free(H); free(a); free(b); free(LC); free(LA); free(LD); free(ord);
 }
 
 void or_compose(const or_tree *const *trees, const double *xf, const double *toff, const double *tint, int n_prims,
                 int mode, const or_opts *op, int64_t n, const double *o, const double *d, const double *t,
-                double *rgb, double *alpha, double *depth, double *margin, int nthreads) {
-  compose_ctx c = {trees, xf, toff, tint, n_prims, mode, op, o, d, t, n, rgb, alpha, depth, margin};
+                double *rgb, double *alpha, double *depth, double *margin, double *trace_margin,
+                double *depth_margin, int nthreads) {
+  compose_ctx c = {trees, xf, toff, tint, n_prims, mode, op, o, d, t, n, rgb, alpha, depth, margin, trace_margin,
+                   depth_margin};
   parallel_for(n, nthreads, compose_range, &c);
 }
 

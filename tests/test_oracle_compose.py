@@ -2,8 +2,10 @@
 its sparse Adam (Sec. 4.3 "Optimization") and its BF16 rounding.
 
 Composition is pinned by reductions (identity transform = plain render,
-disjoint primitives = union, scale invariance, looping re-time) and by the
-two-layer case worked by hand; Adam and BF16 by library routines."""
+disjoint primitives = union, scale invariance, looping re-time), by the
+two-layer case worked by hand and by three layers in Algorithm 1's literal
+mode, where the sequential merge depends on the layers' order; Adam and BF16
+by library routines."""
 import math
 
 import numpy as np
@@ -123,6 +125,56 @@ def test_two_layers_by_hand(c1):
                 assert np.allclose(out["rgb"][i], I_, atol=1e-14)
                 assert abs(out["alpha"][i] - A_) < 1e-14
                 assert out["depth"][i] == min(D)
+
+
+def _three_layers(c1, n=64):
+    """Three half-size copies of the depth-6 tree behind one another as seen
+    from a camera on the -y side, shifted sideways so that they overlap in
+    part: near, mid and far."""
+    cam = I.look_at(np.array([0.5, -4.0, 0.5]), np.array([0.5, 0.5, 0.5]), n, n, fov_y_deg=12.0)
+    rays, _ = I.camera_rays(cam, 0.6)
+    prims = {}
+    for name, dy, dx in (("near", -0.6, -0.03), ("mid", 0.0, 0.0), ("far", 0.6, 0.03)):
+        prims[name] = (np.concatenate([0.6 * np.eye(3), np.array([[0.2 + dx], [0.2 + dy], [0.2]])], 1),
+                       {"near": 2.0, "mid": 5.0, "far": 11.0}[name],
+                       {"near": [1.0, 0.8, 0.6], "mid": [0.5, 1.0, 0.7], "far": [0.9, 0.9, 1.0]}[name])
+    layers = {k: oracle.compose([c1], [M], [o], [t], rays) for k, (M, o, t) in prims.items()}
+    return rays, prims, layers
+
+
+@pytest.mark.parametrize("order", [("near", "far", "mid"), ("far", "near", "mid"), ("mid", "near", "far")])
+def test_algorithm1_three_layers_by_hand(c1, order):
+    """Algorithm 1 taken literally on three premultiplied layers, worked by
+    hand for pixels where all three are present with depths near < mid < far:
+      (near, far, mid): far goes behind near (D_f > D_n); mid is not nearer
+        than the running depth D_n, so it goes behind everything so far:
+        I = P_n + (1-A_n) P_f + (1-A_n)(1-A_f) P_m;
+      (far, near, mid): near goes in front (D_n <= D_f), mid behind:
+        the same I as above;
+      (mid, near, far): near in front of mid, far behind: the depth-sorted
+        result I = P_n + (1-A_n) P_m + (1-A_n)(1-A_m) P_f.
+    Alpha is 1 - (1-A_n)(1-A_m)(1-A_f) and depth D_n in every order.  In the
+    first two orders the literal algorithm differs from the sorted mode, which
+    always gives the last formula."""
+    rays, prims, L = _three_layers(c1)
+    ps = [prims[k] for k in order]
+    out = oracle.compose([c1] * 3, [p[0] for p in ps], [p[1] for p in ps], [p[2] for p in ps], rays, mode="alg1")
+    srt = oracle.compose([c1] * 3, [p[0] for p in ps], [p[1] for p in ps], [p[2] for p in ps], rays, mode="sorted")
+    n, m, f = L["near"], L["mid"], L["far"]
+    sel = ((n["alpha"] > 0.05) & (m["alpha"] > 0.05) & (f["alpha"] > 0.05)
+           & (n["depth"] < m["depth"]) & (m["depth"] < f["depth"]))
+    assert sel.sum() >= 20
+    An, Am, Af = (x["alpha"][sel, None] for x in (n, m, f))
+    Pn, Pm, Pf = (x["rgb"][sel] for x in (n, m, f))
+    sorted_I = Pn + (1 - An) * Pm + (1 - An) * (1 - Am) * Pf
+    mid_last_I = Pn + (1 - An) * Pf + (1 - An) * (1 - Af) * Pm
+    want = mid_last_I if order[2] == "mid" else sorted_I
+    assert np.abs(out["rgb"][sel] - want).max() < 1e-13
+    assert np.abs(srt["rgb"][sel] - sorted_I).max() < 1e-13
+    assert np.abs(out["alpha"][sel] - (1 - (1 - An) * (1 - Am) * (1 - Af))[:, 0]).max() < 1e-13
+    assert np.array_equal(out["depth"][sel], n["depth"][sel])
+    if order[2] == "mid":
+        assert np.abs(mid_last_I - sorted_I).max() > 1e-3
 
 
 def test_adam_matches_torch_on_touched_rows():

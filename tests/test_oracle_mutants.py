@@ -47,6 +47,15 @@ MUTANTS = {
     "slice_gamma_missing_pi": ("const double gamma = M_PI * sigmoid(pg);", "const double gamma = sigmoid(pg);"),
     "slice_m_index_mirrored": ("sh[(leaf * 3 + ch) * NY + l * l + l + m] = acc;", "sh[(leaf * 3 + ch) * NY + l * l + l - m] = acc;"),
     "slice_radial_l_for_n": ("* or_hh_radial(n, l, gamma);\n          sh[", "* or_hh_radial(l, l, gamma);\n          sh["),
+    "alg1_compares_first_depth": ("if (LD[i] <= D) {", "if (LD[i] <= LD[0]) {"),
+    "margin_skips_entry_crossings": (
+        "if (ahead - tin < *margin && order_matters(tr, c_out, ax_in, si, x, sx)) *margin = ahead - tin;", ""),
+    "margin_plane_behind_on_wrong_side": ("c_prev[x] -= sx;", "c_prev[x] += sx;"),
+    "margin_counts_every_near_tie": (
+        "if (gap < *margin && order_matters(tr, cell, ax, sa, x, gd[x] > 0.0 ? 1 : -1)) *margin = gap;",
+        "if (gap < *margin) *margin = gap;"),
+    "margin_gap_from_segment_start": ("double gap = tnext[x] - tnext[ax];", "double gap = tnext[x] - t_cur;"),
+    "margin_past_the_early_stop": ("if (margin && tnext[ax] <= t_limit) {", "if (margin) {"),
 }
 
 
@@ -208,6 +217,24 @@ def _battery():
         k = np.searchsorted(ptr["t1"][i, :ptr["count"][i]] - ptr["t0"][i, 0], s_star - 1e-12)
         if pk[i] != ptr["leaf"][i, k]:
             failed.append("pick")
+            break
+    # Algorithm 1 literally on three layers (near, far, mid): mid goes behind
+    import test_oracle_compose as toc
+    try:
+        toc.test_algorithm1_three_layers_by_hand(c1, ("far", "near", "mid"))
+    except AssertionError:
+        failed.append("alg1_three_layers")
+    # decision margins: the hand-built edge rays, moved crossings, the workload
+    import test_oracle_margin as tom
+    for fn in (tom.test_ray_through_an_edge_between_leaves_has_zero_margin,
+               tom.test_margin_is_the_gap_between_the_two_crossings,
+               tom.test_margin_ignores_near_ties_whose_order_does_not_matter,
+               tom.test_few_rays_of_the_render_workload_have_small_margins,
+               lambda: tom.test_crossings_moved_within_half_the_margin_keep_the_leaves(11, 3)):
+        try:
+            fn()
+        except AssertionError:
+            failed.append("margin")
             break
     # FP8 E4M3: midpoints go to the even code; per-group scales are minimal
     from test_oracle_fp8 import e4m3_codes

@@ -28,9 +28,10 @@
  *    (NEUVV_KERNEL_PLAIN) and the other calls use no such counter and may run
  *    concurrently on different streams, as long as their outputs do not
  *    overlap.
- *  - Errors found on the device (a ray that exceeds its segment cap, an index
- *    outside the tree) are recorded in a per-tree status word read by
- *    neuvv_tree_status(); the affected ray ends early, nothing traps.
+ *  - Errors found on the device (a ray that exceeds its walk-step cap, an
+ *    index outside the tree, a bounded wait that gives up) are recorded in a
+ *    per-tree status word read by neuvv_tree_status(); the affected ray or
+ *    tile ends early, nothing traps and no wait is unbounded.
  *  - Ray directions need not be normalised.  Per-ray times are clamped to [0,1].
  *
  * Numerical readings of the paper that the library implements (the FP64
@@ -65,7 +66,7 @@ typedef enum {
   NEUVV_ERR_INVALID_ARG = 1, /* bad pointer, size, shape or value */
   NEUVV_ERR_CUDA = 2,        /* a CUDA runtime call failed */
   NEUVV_ERR_OOM = 3,         /* device allocation failed */
-  NEUVV_ERR_TIMEOUT = 4,     /* a ray exceeded its segment cap (device status) */
+  NEUVV_ERR_TIMEOUT = 4,     /* reserved (device-detected limits are reported as status bits) */
   NEUVV_ERR_UNSUPPORTED = 5, /* a valid request this build does not implement */
   NEUVV_ERR_DEVICE = 6       /* other device-detected error (status word) */
 } neuvv_status;
@@ -77,8 +78,11 @@ typedef enum {
 typedef enum { NEUVV_F32 = 0, NEUVV_BF16 = 1, NEUVV_FP8_E4M3 = 2 } neuvv_dtype;
 
 /* Device status bits (neuvv_tree_status). */
-#define NEUVV_STATUS_SEGMENT_CAP 0x1u /* a ray needed more than 3*2^depth+8 steps */
-#define NEUVV_STATUS_BAD_INDEX 0x2u   /* a child entry pointed outside the tree */
+#define NEUVV_STATUS_SEGMENT_CAP 0x1u /* a ray reached its walk-step cap (neuvv_tree_set_limits;
+                                         by default 3*2^depth+8, more than any ray needs) and ended */
+#define NEUVV_STATUS_BAD_INDEX 0x2u   /* a child, brick, leaf or log entry pointed outside its table */
+#define NEUVV_STATUS_TIMEOUT 0x4u     /* a bounded device wait (the time slice's copy into shared
+                                         memory) gave up; the block ended after its copy landed */
 
 /* Tree description, all host memory, read during neuvv_tree_create only.
  * child: [n_nodes][8] uint32, slot c = 4*xbit + 2*ybit + zbit; entry 0xFFFFFFFF
@@ -191,6 +195,19 @@ neuvv_status neuvv_tree_get_info(const neuvv_tree *tree, neuvv_tree_info *info);
  * dtype is F32; NULL without optimizer state), Adam moments m and v (NULL
  * without optimizer state).  For views from PyTorch and for tests. */
 neuvv_status neuvv_tree_coeff_ptrs(neuvv_tree *tree, void **storage, float **master, float **adam_m, float **adam_v);
+
+/* Replaces the tree's coefficients (Sec. 4.3: the VOctree's per-voxel
+ * vectors w_sigma, w_gamma, w_HH, optimised by gradient descent) with
+ * records: device FP32 [n_leaves][rec_stride_f32] in the record layout of
+ * neuvv_tree_info (the layout of gradients and of the master copy; entries
+ * past rec_len are ignored), 16-byte aligned, caller-owned, read on the
+ * stream.  Writes the FP32 master copy (when the tree has optimizer state
+ * and its storage is not FP32) and the storage records, rounded to nearest
+ * even for BF16 and re-encoded with fresh per-leaf group scales for
+ * FP8_E4M3, exactly as at tree creation.  Adam's moments are kept.  The
+ * records may be the tree's own master copy (then only the storage is
+ * refreshed from it).  Asynchronous. */
+neuvv_status neuvv_tree_set_records(neuvv_tree *tree, const float *records, neuvv_stream stream);
 
 /* Reads and clears the device status word (NEUVV_STATUS_* bits).  Synchronous. */
 neuvv_status neuvv_tree_status(neuvv_tree *tree, uint32_t *flags);
@@ -423,6 +440,28 @@ neuvv_status neuvv_spotlight(const neuvv_rays *rays, const float *rgb, const flo
  * count [n] (total, may exceed max_out).  Uses the renderer's traversal. */
 neuvv_status neuvv_trace(const neuvv_tree *tree, const neuvv_rays *rays, int32_t max_out, int32_t *leaf, float *t0,
                          float *t1, int32_t *count, neuvv_stream stream);
+
+/* Device limits of a tree's calls (host only; no counterpart in the paper:
+ * failure detection).  step_cap: walk steps a ray may take before it ends and
+ * raises NEUVV_STATUS_SEGMENT_CAP (0 = the default 3*2^depth+8, which no ray
+ * reaches); wait_polls: polls of a bounded wait on the device before it gives
+ * up and raises NEUVV_STATUS_TIMEOUT (default 2^22; 0 gives up at once).
+ * Both >= 0, else NEUVV_ERR_INVALID_ARG.  Small values exist to exercise the
+ * error paths: the affected rays or tiles end early, no kernel waits forever
+ * and nothing traps. */
+neuvv_status neuvv_tree_set_limits(neuvv_tree *tree, int32_t step_cap, int32_t wait_polls);
+
+/* Reads back the segment log written by a packet neuvv_render into saved->log
+ * (Sec. 4.3 "Rendering": the voxels each ray composited and their chord
+ * lengths, as the timed kernel found them).  n: the rays of that render;
+ * saved->nseg: its segment counts (required).  Writes leaf [n][max_out]
+ * (-1 past the end) and chord [n][max_out] (length along the unit direction)
+ * of each ray's first max_out composited segments in order, and count [n]:
+ * the ray's number of segments, or -1 when its packet is not in the log (no
+ * log, a log written for other rays, or a packet that did not fit).  All
+ * device, caller-owned; asynchronous. */
+neuvv_status neuvv_log_read(const neuvv_out *saved, int64_t n, int32_t max_out, int32_t *leaf, float *chord,
+                            int32_t *count, neuvv_stream stream);
 
 /* Sets the packet kernels' launch explicitly instead of neuvv_autotune:
  * block (a multiple of 32 in [32, 256]), queue (a power of two in [1, 32]:

@@ -23,6 +23,8 @@ _lock = threading.Lock()
 _lib = None
 
 F32, BF16, FP8 = 0, 1, 2
+# device status bits (neuvv_tree_status)
+STATUS_SEGMENT_CAP, STATUS_BAD_INDEX, STATUS_TIMEOUT = 0x1, 0x2, 0x4
 _DTYPES = {"f32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16, "fp8": FP8, "fp8_e4m3": FP8}
 _ACT = {"sigmoid": 0, "identity": 1}
 _KERNEL = {"auto": 0, "plain": 1, "packet": 2}
@@ -73,7 +75,8 @@ EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv
            "neuvv_adam_step", "neuvv_mse_grad", "neuvv_trace", "neuvv_autotune", "neuvv_compose_noalloc",
            "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss",
            "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit",
-           "neuvv_camera_rays", "neuvv_render_alpha", "neuvv_tree_reserve_adjoint"]
+           "neuvv_camera_rays", "neuvv_render_alpha", "neuvv_tree_reserve_adjoint", "neuvv_tree_set_limits",
+           "neuvv_log_read", "neuvv_tree_set_records"]
 
 
 def library_path() -> str:
@@ -115,6 +118,9 @@ def lib(build_if_missing: bool = True):
                 "neuvv_camera_rays": [p, p, i32, i32, p, p, p, p, i64, p],
                 "neuvv_render_alpha": [p, p, f, p, p, p],
                 "neuvv_tree_reserve_adjoint": [p, i64],
+                "neuvv_tree_set_limits": [p, i32, i32],
+                "neuvv_log_read": [p, i64, i32, p, p, p, p],
+                "neuvv_tree_set_records": [p, p, p],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -231,6 +237,24 @@ class Tree:
     def set_launch(self, block: int, queue: int, ready: int) -> None:
         _check(lib().neuvv_tree_set_launch(self.handle, int(block), int(queue), int(ready)))
         self.refresh_info()
+
+    def records_ptr(self) -> int:
+        """Device address of the tree's FP32 records: the master copy, or the
+        storage itself for an FP32 tree without optimizer state (0 if none)."""
+        s, m, _, _ = self._ptrs()
+        return m or (s if self.dtype == F32 else 0)
+
+    def set_records(self, records: torch.Tensor) -> None:
+        """Replaces the coefficients with FP32 records [n_leaves, rec_stride_f32]
+        (neuvv_tree_set_records: master copy and storage, re-rounded)."""
+        if records.shape != (self.n_leaves, self.info.rec_stride_f32) or records.dtype != torch.float32:
+            raise NeuvvError("records must be float32 [n_leaves, rec_stride_f32]")
+        _check(lib().neuvv_tree_set_records(self.handle, _ptr(records.contiguous()), _stream()))
+
+    def set_limits(self, step_cap: int = 0, wait_polls: int = 1 << 22) -> None:
+        """Walk-step cap per ray (0: the default, which no ray reaches) and
+        polls of a bounded device wait (neuvv_tree_set_limits)."""
+        _check(lib().neuvv_tree_set_limits(self.handle, int(step_cap), int(wait_polls)))
 
     def reserve_adjoint(self, n_slots: int) -> None:
         """Workspace of the leaf-major adjoint for logs of up to n_slots slots
@@ -496,8 +520,9 @@ def neuvv_compose_noalloc(trees, transforms, time_offsets, tints, rays: DeviceRa
     toff = np.ascontiguousarray(np.asarray(time_offsets, np.float32).reshape(P))
     tint = np.ascontiguousarray(np.asarray(tints, np.float32).reshape(P, 3))
     if out is None:
-        out = {"rgb": torch.empty(rays.n, 3, device="cuda"), "alpha": torch.empty(rays.n, device="cuda"),
-               "depth": torch.empty(rays.n, device="cuda")}
+        dev = f"cuda:{trees[0].info.device}"
+        out = {"rgb": torch.empty(rays.n, 3, device=dev), "alpha": torch.empty(rays.n, device=dev),
+               "depth": torch.empty(rays.n, device=dev)}
     rc, oc, op = rays.c(), _outc(out), _opts(t_stop, act, "auto", mode)
     _check(lib().neuvv_compose_noalloc(arr, xf.ctypes.data, toff.ctypes.data, tint.ctypes.data, P,
                                        ctypes.byref(rc), float(t), ctypes.byref(op), ctypes.byref(oc), _stream()))
@@ -530,6 +555,19 @@ def neuvv_trace(tree: Tree, rays: DeviceRays, max_out: int = 64) -> dict:
     return {"leaf": leaf, "t0": t0, "t1": t1, "count": count}
 
 
+def neuvv_log_read(saved: dict, n: int, max_out: int = 64) -> dict:
+    """The (leaf, chord) lists the packet forward logged in saved["log"], per
+    ray, with count = -1 for rays whose packet is not in the log."""
+    dev = saved["nseg"].device
+    leaf = torch.empty(n, max_out, device=dev, dtype=torch.int32)
+    chord = torch.empty(n, max_out, device=dev)
+    count = torch.empty(n, device=dev, dtype=torch.int32)
+    sc = _outc(saved)
+    _check(lib().neuvv_log_read(ctypes.byref(sc), int(n), int(max_out), _ptr(leaf), _ptr(chord), _ptr(count),
+                                _stream()))
+    return {"leaf": leaf, "chord": chord, "count": count}
+
+
 def neuvv_autotune(tree: Tree, rays: DeviceRays, t: float = 0.0) -> float:
     ms = ctypes.c_float()
     rc = rays.c()
@@ -540,12 +578,18 @@ def neuvv_autotune(tree: Tree, rays: DeviceRays, t: float = 0.0) -> float:
 
 class VOctreeRender(torch.autograd.Function):
     """Differentiable VOctree render: forward = neuvv_render, backward =
-    neuvv_render_backward (fused adjoint).  ``coeffs`` is the tensor that
-    receives the gradient (the tree's FP32 master records, shape
-    [n_leaves, rec_stride_f32]); the forward reads the tree's storage records."""
+    neuvv_render_backward (fused adjoint).  ``coeffs`` holds the coefficients
+    to render, FP32 records [n_leaves, rec_stride_f32] in the tree's record
+    layout, and receives the gradient.  The forward renders from them: unless
+    ``coeffs`` is the tree's own FP32 record buffer (its master copy, or the
+    storage of an FP32 tree), they are written into the tree first
+    (neuvv_tree_set_records, rounded to the storage type), so an optimiser
+    step on ``coeffs`` changes the next render."""
 
     @staticmethod
     def forward(ctx, coeffs, tree, rays, t, t_stop, act):
+        if coeffs.data_ptr() != tree.records_ptr():
+            tree.set_records(coeffs.detach())
         out = neuvv_render(tree, rays, t=t, t_stop=t_stop, act=act,
                            out=alloc_out(rays.n, rays.o.device, log_bytes_per_ray=64))
         ctx.tree, ctx.rays, ctx.t, ctx.t_stop, ctx.act = tree, rays, t, t_stop, act

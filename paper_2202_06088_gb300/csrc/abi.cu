@@ -93,6 +93,8 @@ struct neuvv_tree {
   LaunchCfg plain{128, 1, 1, 0, 0, 0};
   LaunchCfg packet{64, 8, 16, 0, 1, 0};
   LaunchCfg compose{128, 1, 1, 0, 1, 0};
+  int step_cap = 0;             // walk steps per ray (0: 3 * 2^depth + 8)
+  int wait_polls = 1 << 22;     // polls of a bounded device wait
 };
 
 namespace {
@@ -131,6 +133,8 @@ DevTree dev_tree(const neuvv_tree *t) {
   d.brick_first = t->brick_first;
   d.brick_count = t->brick_count;
   d.coarse = t->coarse;
+  d.step_cap = t->step_cap;
+  d.wait_polls = t->wait_polls;
   return d;
 }
 
@@ -578,6 +582,19 @@ neuvv_status neuvv_tree_coeff_ptrs(neuvv_tree *t, void **storage, float **master
   return NEUVV_OK;
 }
 
+neuvv_status neuvv_tree_set_records(neuvv_tree *t, const float *records, neuvv_stream stream) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (t->info.n_leaves == 0) return NEUVV_OK;
+  if (!records || ((uintptr_t)records & 15)) return fail(NEUVV_ERR_INVALID_ARG, "records must be a 16-byte aligned pointer");
+  DeviceGuard g(t->info.device);
+  float *master = t->master_is_storage ? nullptr : t->master;
+  cudaError_t e = launch_store_records(records, master, t->rec, (DType)t->info.dtype, t->info.rec_stride,
+                                       t->info.n_leaves, t->info.rec_stride_f32, t->info.rec_len, t->info.K_pad,
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "store records launch");
+  return NEUVV_OK;
+}
+
 neuvv_status neuvv_tree_status(neuvv_tree *t, uint32_t *flags) {
   if (!t || !flags) return fail(NEUVV_ERR_INVALID_ARG, "tree/flags is NULL");
   DeviceGuard g(t->info.device);
@@ -746,9 +763,13 @@ neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, 
   return NEUVV_OK;
 }
 
-neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transforms, const float *time_offsets,
-                           const float *tints, int32_t n_prims, const neuvv_rays *rays, float time,
-                           const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream) {
+namespace {
+
+// Checks the arguments of a composition and fills the launch arguments (all
+// but the work counter); shared by neuvv_compose and neuvv_compose_noalloc.
+neuvv_status prepare_compose(const neuvv_tree *const *trees, const float *transforms, const float *time_offsets,
+                             const float *tints, int32_t n_prims, const neuvv_rays *rays, float time,
+                             const neuvv_render_opts *opts, neuvv_out *out, ComposeArgs &a, const neuvv_tree *&t0) {
   if (!trees || !transforms || !time_offsets || !tints)
     return fail(NEUVV_ERR_INVALID_ARG, "trees/transforms/time_offsets/tints is NULL");
   if (n_prims < 1 || n_prims > kMaxPrims) return fail(NEUVV_ERR_INVALID_ARG, "n_prims must be in [1, %d]", kMaxPrims);
@@ -757,9 +778,8 @@ neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transfor
     return s;
   if (!out || (rays->n > 0 && (!out->rgb || !out->alpha)))
     return fail(NEUVV_ERR_INVALID_ARG, "out->rgb and out->alpha are required");
-  const neuvv_tree *t0 = trees[0];
+  t0 = trees[0];
   if (!t0) return fail(NEUVV_ERR_INVALID_ARG, "trees[0] is NULL");
-  ComposeArgs a;
   std::memset(&a, 0, sizeof a);
   int n_trees = 0;
   const neuvv_tree *uniq[kMaxPrims];
@@ -802,9 +822,23 @@ neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transfor
                        m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
     if (!(det > 0.0)) return fail(NEUVV_ERR_INVALID_ARG, "transform %d must have positive determinant", j);
     PrimParam &p = a.prim[j];
-    // (sR)^-1 = R^T / s = M^T / s^2
+    // the inverse of the given 3x3 part in double (cofactors / determinant),
+    // kept as FP32 value + FP32 remainder for the kernel's double-float ray
+    double inv[3][3];
+    inv[0][0] = (m[1][1] * m[2][2] - m[1][2] * m[2][1]) / det;
+    inv[0][1] = (m[0][2] * m[2][1] - m[0][1] * m[2][2]) / det;
+    inv[0][2] = (m[0][1] * m[1][2] - m[0][2] * m[1][1]) / det;
+    inv[1][0] = (m[1][2] * m[2][0] - m[1][0] * m[2][2]) / det;
+    inv[1][1] = (m[0][0] * m[2][2] - m[0][2] * m[2][0]) / det;
+    inv[1][2] = (m[0][2] * m[1][0] - m[0][0] * m[1][2]) / det;
+    inv[2][0] = (m[1][0] * m[2][1] - m[1][1] * m[2][0]) / det;
+    inv[2][1] = (m[0][1] * m[2][0] - m[0][0] * m[2][1]) / det;
+    inv[2][2] = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) / det;
     for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) p.minv[3 * r + c] = (float)(m[c][r] / s2);
+      for (int c = 0; c < 3; ++c) {
+        p.minv[3 * r + c] = (float)inv[r][c];
+        p.minv_lo[3 * r + c] = (float)(inv[r][c] - (double)p.minv[3 * r + c]);
+      }
     for (int r = 0; r < 3; ++r) p.trans[r] = (float)tr[r];
     p.scale = (float)std::sqrt(s2);
     if (!std::isfinite(time_offsets[j])) return fail(NEUVV_ERR_INVALID_ARG, "time offset %d not finite", j);
@@ -815,15 +849,27 @@ neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transfor
     }
     p.tree = slot;
   }
-  if (rays->n == 0) return NEUVV_OK;
-  DeviceGuard g(t0->info.device);
-  cudaStream_t st = (cudaStream_t)stream;
   a.n_prims = n_prims;
   a.rays = dev_rays(rays, time);
   a.out = DevOut{out->rgb, out->alpha, out->depth, nullptr, nullptr};
   a.t_stop = opts->t_stop;
   a.act = opts->color_act;
   a.mode = opts->compose_mode;
+  return NEUVV_OK;
+}
+
+}  // namespace
+
+neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transforms, const float *time_offsets,
+                           const float *tints, int32_t n_prims, const neuvv_rays *rays, float time,
+                           const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream) {
+  ComposeArgs a;
+  const neuvv_tree *t0 = nullptr;
+  neuvv_status s = prepare_compose(trees, transforms, time_offsets, tints, n_prims, rays, time, opts, out, a, t0);
+  if (s != NEUVV_OK) return s;
+  if (rays->n == 0) return NEUVV_OK;
+  DeviceGuard g(t0->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
   a.work = t0->work + 2;
   const LaunchCfg &cfg = t0->compose;
   if (cfg.dynamic_queue) {
@@ -838,86 +884,18 @@ neuvv_status neuvv_compose(const neuvv_tree *const *trees, const float *transfor
 }
 
 neuvv_status neuvv_compose_noalloc(const neuvv_tree *const *trees, const float *transforms, const float *time_offsets,
-                           const float *tints, int32_t n_prims, const neuvv_rays *rays, float time,
-                           const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream) {
-  if (!trees || !transforms || !time_offsets || !tints)
-    return fail(NEUVV_ERR_INVALID_ARG, "trees/transforms/time_offsets/tints is NULL");
-  if (n_prims < 1 || n_prims > kMaxPrims) return fail(NEUVV_ERR_INVALID_ARG, "n_prims must be in [1, %d]", kMaxPrims);
-  neuvv_status s;
-  if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK || (s = check_time(rays, time)))
-    return s;
-  if (!out || (rays->n > 0 && (!out->rgb || !out->alpha)))
-    return fail(NEUVV_ERR_INVALID_ARG, "out->rgb and out->alpha are required");
-  const neuvv_tree *t0 = trees[0];
-  if (!t0) return fail(NEUVV_ERR_INVALID_ARG, "trees[0] is NULL");
+                                   const float *tints, int32_t n_prims, const neuvv_rays *rays, float time,
+                                   const neuvv_render_opts *opts, neuvv_out *out, neuvv_stream stream) {
   ComposeArgs a;
-  std::memset(&a, 0, sizeof a);
-  int n_trees = 0;
-  const neuvv_tree *uniq[kMaxPrims];
-  for (int j = 0; j < n_prims; ++j) {
-    const neuvv_tree *t = trees[j];
-    if (!t) return fail(NEUVV_ERR_INVALID_ARG, "trees[%d] is NULL", j);
-    if (t->info.K_pad != t0->info.K_pad || t->info.hh_degree != t0->info.hh_degree || t->info.dtype != t0->info.dtype ||
-        t->info.device != t0->info.device)
-      return fail(NEUVV_ERR_UNSUPPORTED, "all trees of one compose call must share K_pad, degree, dtype, device");
-    int slot = -1;
-    for (int k = 0; k < n_trees; ++k)
-      if (uniq[k] == t) slot = k;
-    if (slot < 0) {
-      slot = n_trees;
-      uniq[n_trees++] = t;
-      a.trees[slot] = dev_tree(t);
-    }
-    const float *M = transforms + 12 * j;
-    double m[3][3], tr[3];
-    for (int r = 0; r < 3; ++r) {
-      for (int c = 0; c < 3; ++c) m[r][c] = M[4 * r + c];
-      tr[r] = M[4 * r + 3];
-    }
-    // uniform scale: M^T M = s^2 I
-    double s2 = 0.0;
-    for (int r = 0; r < 3; ++r) s2 += m[r][0] * m[r][0];
-    if (!(s2 > 0.0) || !std::isfinite(s2)) return fail(NEUVV_ERR_INVALID_ARG, "transform %d is degenerate", j);
-    for (int c1 = 0; c1 < 3; ++c1)
-      for (int c2 = 0; c2 < 3; ++c2) {
-        double dot = 0.0;
-        for (int r = 0; r < 3; ++r) dot += m[r][c1] * m[r][c2];
-        const double want = c1 == c2 ? s2 : 0.0;
-        if (std::fabs(dot - want) > 1e-4 * s2)
-          return fail(NEUVV_ERR_INVALID_ARG, "transform %d is not a rotation times a uniform scale", j);
-      }
-    for (int r = 0; r < 3; ++r)
-      if (!std::isfinite(tr[r])) return fail(NEUVV_ERR_INVALID_ARG, "transform %d translation not finite", j);
-    const double det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
-                       m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
-                       m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
-    if (!(det > 0.0)) return fail(NEUVV_ERR_INVALID_ARG, "transform %d must have positive determinant", j);
-    PrimParam &p = a.prim[j];
-    // (sR)^-1 = R^T / s = M^T / s^2
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) p.minv[3 * r + c] = (float)(m[c][r] / s2);
-    for (int r = 0; r < 3; ++r) p.trans[r] = (float)tr[r];
-    p.scale = (float)std::sqrt(s2);
-    if (!std::isfinite(time_offsets[j])) return fail(NEUVV_ERR_INVALID_ARG, "time offset %d not finite", j);
-    p.toff = time_offsets[j];
-    for (int c = 0; c < 3; ++c) {
-      if (!std::isfinite(tints[3 * j + c])) return fail(NEUVV_ERR_INVALID_ARG, "tint %d not finite", j);
-      p.tint[c] = tints[3 * j + c];
-    }
-    p.tree = slot;
-  }
+  const neuvv_tree *t0 = nullptr;
+  neuvv_status s = prepare_compose(trees, transforms, time_offsets, tints, n_prims, rays, time, opts, out, a, t0);
+  if (s != NEUVV_OK) return s;
   if (rays->n > NEUVV_NOALLOC_MAX_RAYS)
     return fail(NEUVV_ERR_INVALID_ARG, "neuvv_compose_noalloc: %lld rays exceed the maximum of %lld",
                 (long long)rays->n, (long long)NEUVV_NOALLOC_MAX_RAYS);
   if (rays->n == 0) return NEUVV_OK;
   DeviceGuard g(t0->info.device);
   cudaStream_t st = (cudaStream_t)stream;
-  a.n_prims = n_prims;
-  a.rays = dev_rays(rays, time);
-  a.out = DevOut{out->rgb, out->alpha, out->depth, nullptr, nullptr};
-  a.t_stop = opts->t_stop;
-  a.act = opts->color_act;
-  a.mode = opts->compose_mode;
   // the packet counter is the library's static device array, not tree memory
   cudaError_t e = noalloc_queue(&a.work);
   if (e != cudaSuccess) return cuda_fail(e, "neuvv_compose_noalloc: device address of the static counter");
@@ -1159,6 +1137,31 @@ neuvv_status neuvv_trace(const neuvv_tree *t, const neuvv_rays *rays, int32_t ma
   a.count = count;
   cudaError_t e = launch_trace(a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_tree_set_limits(neuvv_tree *t, int32_t step_cap, int32_t wait_polls) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (step_cap < 0) return fail(NEUVV_ERR_INVALID_ARG, "step_cap must be >= 0");
+  if (wait_polls < 0) return fail(NEUVV_ERR_INVALID_ARG, "wait_polls must be >= 0");
+  t->step_cap = step_cap;
+  t->wait_polls = wait_polls;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_log_read(const neuvv_out *saved, int64_t n, int32_t max_out, int32_t *leaf, float *chord,
+                            int32_t *count, neuvv_stream stream) {
+  if (!saved || !saved->nseg) return fail(NEUVV_ERR_INVALID_ARG, "saved and saved->nseg are required");
+  neuvv_status s;
+  if ((s = check_log(saved)) != NEUVV_OK) return s;
+  if (n < 0 || n > ((int64_t)1 << 37)) return fail(NEUVV_ERR_INVALID_ARG, "n out of range");
+  if (max_out < 0) return fail(NEUVV_ERR_INVALID_ARG, "max_out < 0");
+  if (n > 0 && (!count || (max_out > 0 && (!leaf || !chord))))
+    return fail(NEUVV_ERR_INVALID_ARG, "output pointer is NULL");
+  if (n == 0) return NEUVV_OK;
+  const SampleLog l = log_view(saved->log, saved->log_bytes, n);
+  cudaError_t e = launch_log_read(l, (long long)n, saved->nseg, max_out, leaf, chord, count, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "log read launch");
   return NEUVV_OK;
 }
 

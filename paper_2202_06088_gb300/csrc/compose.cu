@@ -10,12 +10,124 @@
 // (tint_j * C_j, A_j, s * D_j).  The layers are then merged: sorted by depth
 // (stable) with front-to-back "over" on premultiplied colour, or Algorithm 1
 // taken literally (sequential pairwise merge) on premultiplied colour.
+//
+// The local ray is formed in double-float arithmetic (a value carried as an
+// unevaluated sum hi + lo of two FP32 numbers; Dekker's error-free products
+// and Knuth's two-sum), and so is its entry point into the local box: a ray
+// from a camera far from the primitive then reaches the voxels with the
+// precision of a ray given in the tree's own frame, and a grazing crossing
+// of a voxel face does not magnify the rounding of the transform.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "neuvv_kernels.h"
 #include "neuvv_ray.cuh"
 
 namespace neuvv {
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_norm(float s, float e) {
+  const float hi = s + e;
+  return DF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df_norm(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_mul(DF a, float b) {
+  float p, e;
+  two_prod(a.hi, b, p, e);
+  return df_norm(p, fmaf(a.lo, b, e));
+}
+// sum_j m[j] q[j] with m = mh + ml given as two FP32 rows
+__device__ __forceinline__ DF df_dot3(const float *mh, const float *ml, const DF q[3]) {
+  DF acc{0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    DF p = df_mul(q[j], mh[j]);
+    p.lo = fmaf(q[j].hi, ml[j], p.lo);
+    acc = df_add(acc, p);
+  }
+  return acc;
+}
+
+// Starts the walk of world ray (o, d) through primitive pp's tree in the
+// tree's frame.  Returns false when the ray misses the local box; otherwise
+// dn (unit local direction), the world distance of the entry point from o
+// and the world length of one local unit along the ray.
+__device__ __forceinline__ bool walk_init_local(const DevTree &tr, const PrimParam &pp, const float o[3],
+                                                const float d[3], RayWalk &w, float dn[3], float &t_base,
+                                                float &dist_scale) {
+  DF q[3], dd[3], ol[3], dl[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float s, e;
+    two_sum(o[k], -pp.trans[k], s, e);
+    q[k] = DF{s, e};
+    dd[k] = DF{d[k], 0.f};
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    ol[r] = df_dot3(pp.minv + 3 * r, pp.minv_lo + 3 * r, q);
+    dl[r] = df_dot3(pp.minv + 3 * r, pp.minv_lo + 3 * r, dd);
+  }
+  const float olh[3] = {ol[0].hi, ol[1].hi, ol[2].hi}, dlh[3] = {dl[0].hi, dl[1].hi, dl[2].hi};
+  const float dlen = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  const float llen = sqrtf(dlh[0] * dlh[0] + dlh[1] * dlh[1] + dlh[2] * dlh[2]);
+  float s_in, s_out;
+  int ax;
+  if (!(dlen > 0.f && llen > 0.f) || !box_interval(tr, olh, dlh, s_in, s_out, ax)) return false;
+  // entry point ol + s dl in double-float: s from the entry face's equation,
+  // the entry coordinate set to the face exactly
+  float p[3], pl[3];
+  float s_hi = 0.f;
+  if (ax < 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      p[k] = ol[k].hi;
+      pl[k] = ol[k].lo;
+    }
+  } else {
+    DF ola = ol[0], dla = dl[0];
+    float f = tr.bmin[0];
+#pragma unroll
+    for (int k = 1; k < 3; ++k)
+      if (k == ax) { ola = ol[k]; dla = dl[k]; f = tr.bmin[k]; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k == ax && dla.hi < 0.f) f = tr.bmax[k];
+    const DF num = df_add(DF{f, 0.f}, DF{-ola.hi, -ola.lo});
+    s_hi = num.hi / dla.hi;
+    const float s_lo = ((fmaf(-s_hi, dla.hi, num.hi) + num.lo) - s_hi * dla.lo) / dla.hi;
+    const DF s = df_norm(s_hi, s_lo);
+    s_hi = s.hi;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (k == ax) {
+        p[k] = f;
+        pl[k] = 0.f;
+      } else {
+        DF sd = df_mul(dl[k], s.hi);
+        sd.lo = fmaf(dl[k].hi, s.lo, sd.lo);
+        const DF pk = df_add(ol[k], sd);
+        p[k] = pk.hi;
+        pl[k] = pk.lo;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dn[k] = dlh[k] / llen;
+  walk_start(tr, p, pl, dn, w);
+  // the local point ol + s dl is the world point o + s d
+  t_base = s_hi * dlen;
+  dist_scale = dlen / llen;
+  return w.alive;
+}
 
 template <int KP, int DEG, typename E>
 __global__ void __launch_bounds__(256) compose_kernel(const __grid_constant__ ComposeArgs a, int dynamic) {
@@ -40,44 +152,16 @@ __global__ void __launch_bounds__(256) compose_kernel(const __grid_constant__ Co
       for (int j = 0; j < a.n_prims; ++j) {
         const PrimParam &pp = a.prim[j];
         const DevTree &tr = a.trees[pp.tree];
-        // rough local ray: enough to find where the line enters the local box
-        const float q[3] = {o[0] - pp.trans[0], o[1] - pp.trans[1], o[2] - pp.trans[2]};
-        float ol[3], dl[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          ol[r] = pp.minv[3 * r] * q[0] + pp.minv[3 * r + 1] * q[1] + pp.minv[3 * r + 2] * q[2];
-          dl[r] = pp.minv[3 * r] * d[0] + pp.minv[3 * r + 1] * d[1] + pp.minv[3 * r + 2] * d[2];
-        }
         RayResult r;
         clear(r);
-        float s_in, s_out;
-        int ax;
-        const float dlen = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const float llen = sqrtf(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]);
-        if (dlen > 0.f && llen > 0.f && box_interval(tr, ol, dl, s_in, s_out, ax)) {
-          // entry point formed in world space from the exact input line, then
-          // taken to the local frame (small magnitudes: little rounding)
-          float pw[3], pl[3], dn[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) pw[k] = fmaf(s_in, d[k], o[k]) - pp.trans[k];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            pl[k] = pp.minv[3 * k] * pw[0] + pp.minv[3 * k + 1] * pw[1] + pp.minv[3 * k + 2] * pw[2];
-            dn[k] = dl[k] / llen;
-          }
-#pragma unroll
-          for (int k = 0; k < 3; ++k)
-            if (k == ax) pl[k] = dl[k] > 0.f ? tr.bmin[k] : tr.bmax[k];
-          RayWalk w;
-          const float zero[3] = {0.f, 0.f, 0.f};
-          walk_start(tr, pl, zero, dn, w);
-          if (w.alive) {
-            const float period = (float)(tr.T - 1);
-            float u = fmodf(t * period + pp.toff, period);
-            if (u < 0.f) u += period;
-            // world distance = s_in |d| + (local distance) * |d| / |dl|
-            integrate_walk<KP, DEG, E, false>(tr, nullptr, w, dn, u, a.t_stop, a.act, s_in * dlen, dlen / llen, r);
-          }
+        RayWalk w;
+        float dn[3], t_base, dist_scale;
+        if (walk_init_local(tr, pp, o, d, w, dn, t_base, dist_scale)) {
+          const float period = (float)(tr.T - 1);
+          float u = fmodf(t * period + pp.toff, period);
+          if (u < 0.f) u += period;
+          // world distance = t_base + (local distance) * |d| / |dl|
+          integrate_walk<KP, DEG, E, false>(tr, nullptr, w, dn, u, a.t_stop, a.act, t_base, dist_scale, r);
         }
         Lc[j][0] = pp.tint[0] * r.C[0];
         Lc[j][1] = pp.tint[1] * r.C[1];
@@ -188,28 +272,60 @@ cudaError_t launch_compose(int KP, int DEG, DType dt, const ComposeArgs &a, cons
 }
 
 // Work counter for neuvv_compose_noalloc: file-scope device memory (one
-// 64-bit packet counter, 256-byte aligned) that exists on every device where
-// the library is loaded, so that entry point needs no allocation.  Host code
-// must not use the symbol as an address: noalloc_queue() asks the runtime for
-// the device address once per device (with that device current) and caches it.
+// 64-bit packet counter, 256-byte aligned) that exists in every context where
+// the library's module is loaded, so that entry point needs no allocation.
+// Host code must not use the symbol as an address: noalloc_queue() asks the
+// runtime for the device address once per CUDA context (with the context
+// current) and caches it under the context's unique id, which is never
+// reused within a process.  A device reset makes a new primary context (a new
+// id), so a stale address is never handed out: the first call after a reset
+// looks the address up again.
 static __device__ __align__(256) unsigned long long g_noalloc_queue[1];
 
+namespace {
+using CtxGetCurrentFn = CUresult(CUDAAPI *)(CUcontext *);
+using CtxGetIdFn = CUresult(CUDAAPI *)(CUcontext, unsigned long long *);
+}  // namespace
+
 cudaError_t noalloc_queue(unsigned long long **out) {
-  constexpr int kMaxDevices = 64;
+  constexpr int kMaxContexts = 64;
   static std::mutex mu;
-  static unsigned long long *ptrs[kMaxDevices] = {};
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static unsigned long long ids[kMaxContexts] = {};
+  static unsigned long long *ptrs[kMaxContexts] = {};
+  static int used = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  // cudaSetDevice makes the device's primary context current on this thread
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!ptrs[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_queue);
-    if (e != cudaSuccess) return e;
-    ptrs[dev] = static_cast<unsigned long long *>(p);
+  if (e != cudaSuccess || (e = cudaSetDevice(dev)) != cudaSuccess) return e;
+  if (!get_current || !get_id) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if ((e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1)) != cudaSuccess)
+      return e;
+    if ((e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2)) != cudaSuccess)
+      return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorSymbolNotFound;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
   }
-  *out = ptrs[dev];
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  for (int k = 0; k < used; ++k)
+    if (ids[k] == id) {
+      *out = ptrs[k];
+      return cudaSuccess;
+    }
+  void *p = nullptr;
+  if ((e = cudaGetSymbolAddress(&p, g_noalloc_queue)) != cudaSuccess) return e;
+  const int slot = used < kMaxContexts ? used++ : (int)(id % kMaxContexts);  // evict when full
+  ids[slot] = id;
+  ptrs[slot] = static_cast<unsigned long long *>(p);
+  *out = ptrs[slot];
   return cudaSuccess;
 }
 

@@ -23,8 +23,9 @@ namespace neuvv {
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr float kPi = 3.14159265358979323846f;
-constexpr uint32_t kStatusSegCap = 0x1u;
-constexpr uint32_t kStatusBadIndex = 0x2u;
+constexpr uint32_t kStatusSegCap = 0x1u;    // a ray reached its walk-step cap
+constexpr uint32_t kStatusBadIndex = 0x2u;  // a child, brick, leaf or log index out of range
+constexpr uint32_t kStatusTimeout = 0x4u;   // a bounded wait (an mbarrier poll) gave up
 
 __host__ __device__ constexpr int n_hh(int deg) { return deg < 0 ? 0 : n_hh(deg - 1) + (deg + 1) * (deg + 1); }
 __host__ __device__ constexpr int hh_index(int n, int l, int m) { return n * (n + 1) * (2 * n + 1) / 6 + l * l + l + m; }
@@ -56,6 +57,9 @@ struct DevTree {
   // nearest non-empty cell is k >= 1 (the box of radius k-1 around it is
   // empty).  Null when the tree has none; the walk then descends the octree.
   const uint32_t *coarse;
+  // Limits: walk steps per ray (0: 3 * 2^depth + 8, enough for any ray) and
+  // polls of a bounded wait before it gives up and flags kStatusTimeout.
+  int step_cap, wait_polls;
 };
 
 constexpr uint32_t kCoarseEmpty = 15u;
@@ -187,7 +191,7 @@ __device__ __forceinline__ void walk_start(const DevTree &tr, const float p[3], 
   w.c_idx = 0xFFFFFFFFu;
   w.c_word = 0u;
   w.steps = 0;
-  w.max_steps = 3 * N + 8;
+  w.max_steps = tr.step_cap > 0 ? tr.step_cap : 3 * N + 8;
   w.alive = tf > 0.f;
 }
 
@@ -396,14 +400,17 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     gap[a] = (float)(w.gd[a] > 0.f ? hi[a] : lo[a]) - w.go[a];  // exact
-    tx[a] = w.gd[a] != 0.f ? gap[a] * w.inv[a] : INFINITY;
+    // the plane's distance gap * inv - c with one rounding, so that the exit
+    // axis is decided on distances accurate to an ulp
+    tx[a] = w.gd[a] != 0.f ? fmaf(gap[a], w.inv[a], -w.c[a]) : INFINITY;
   }
   // exit axis: first minimum (exact ties x < y < z); register-only selects
   int ax = 0;
   float t_exit = tx[0], g_ax = gap[0], i_ax = w.inv[0], c_ax = w.c[0];
   if (tx[1] < t_exit) { ax = 1; t_exit = tx[1]; g_ax = gap[1]; i_ax = w.inv[1]; c_ax = w.c[1]; }
   if (tx[2] < t_exit) { ax = 2; t_exit = tx[2]; g_ax = gap[2]; i_ax = w.inv[2]; c_ax = w.c[2]; }
-  // the exit plane lies at t_exit + x_lo: the exact product gap * inv minus c
+  // the exit plane lies at t_exit + x_lo: x_lo = (gap * inv - t_exit) - c
+  // (the product exact inside the FMA)
   const float x_lo = fmaf(g_ax, i_ax, -t_exit) - c_ax;
   const float chord = (t_exit - w.t_cur) + (x_lo - w.t_lo);
   bool found = false;

@@ -94,8 +94,9 @@ struct BwdArgs {
 constexpr int kMaxPrims = 16;
 
 struct PrimParam {
-  float minv[9];   // (s R)^-1, row-major
-  float trans[3];  // translation of world-from-local
+  float minv[9];     // (s R)^-1, row-major, rounded to FP32 ...
+  float minv_lo[9];  // ... and the remainders: minv + minv_lo is the inverse to ~2^-48
+  float trans[3];    // translation of world-from-local
   float scale;     // s
   float toff;      // time offset, frames
   float tint[3];
@@ -181,12 +182,17 @@ cudaError_t launch_slice(int KP, int DEG, DType dt, const DevTree &tr, float u, 
                          int rec_bytes, int num_sms, cudaStream_t s);
 // Packet render of a time slice (a.slice set), with the tree's launch configuration.
 cudaError_t launch_render_slice(int DEG, const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s);
-// Device address of the static work counter used by neuvv_compose_noalloc on
-// the current device (looked up on first use per device).
+// Device address of the static work counter used by neuvv_compose_noalloc in
+// the current CUDA context (looked up on first use per context).
 cudaError_t noalloc_queue(unsigned long long **out);
+// Decodes a packet forward's segment log into per-ray (leaf, chord) lists.
+cudaError_t launch_log_read(const SampleLog &l, long long n_rays, const int *nseg, int max_out, int *leaf,
+                            float *chord, int *count, cudaStream_t s);
 cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType dt, int storage_stride, float *grad,
                         const unsigned int *touched, long long n_leaves, int stride_f32, int rec_len, int kp,
                         float lr, float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
+cudaError_t launch_store_records(const float *src, float *master, void *storage, DType dt, int storage_stride,
+                                 long long n_leaves, int stride_f32, int rec_len, int kp, cudaStream_t s);
 cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
                        cudaStream_t s);
 cudaError_t launch_grad_loss(const float *rgb, const float *target, const int *map, int width, int height,

@@ -242,6 +242,60 @@ __global__ void __launch_bounds__(256) adam_fp8_kernel(float *__restrict__ maste
   }
 }
 
+// Writes FP32 records (the gradient / master layout) into a tree: the master
+// copy when there is one, and the storage records in the storage type (BF16
+// rounded to nearest even; FP8 with the per-leaf group scales of tree
+// creation).  One warp per leaf; entries past rec_len stay zero.
+__global__ void __launch_bounds__(256) store_records_kernel(const float *__restrict__ src, float *__restrict__ master,
+                                                            void *__restrict__ storage, int dt, int storage_stride,
+                                                            long long n_leaves, int stride_f32, int rec_len, int kp) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long leaf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < n_leaves; leaf += nwarps) {
+    const float *r = src + (size_t)leaf * stride_f32;
+    float mx[3] = {0.f, 0.f, 0.f};
+    for (int j = lane; j < stride_f32; j += 32) {
+      const float w = j < rec_len ? r[j] : 0.f;
+      if (master) master[(size_t)leaf * stride_f32 + j] = w;
+      if (dt == kF32) static_cast<float *>(storage)[(size_t)leaf * storage_stride + j] = w;
+      else if (dt == kBF16 && j < storage_stride)
+        static_cast<unsigned short *>(storage)[(size_t)leaf * storage_stride + j] = f32_to_bf16_rne(w);
+      const int grp = j < kp ? 0 : (j < 2 * kp ? 1 : 2);
+      mx[grp] = fmaxf(mx[grp], fabsf(w));
+    }
+    if (dt != kFP8) continue;
+    int p[3];
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx[g] = fmaxf(mx[g], __shfl_xor_sync(0xFFFFFFFFu, mx[g], o));
+      p[g] = fp8_scale_exp(mx[g]);
+    }
+    unsigned char *rec = static_cast<unsigned char *>(storage) + (size_t)leaf * storage_stride;
+    if (lane == 0)
+      *reinterpret_cast<uint4 *>(rec) = make_uint4(__float_as_uint(ldexpf(1.f, p[0])), __float_as_uint(ldexpf(1.f, p[1])),
+                                                   __float_as_uint(ldexpf(1.f, p[2])), 0u);
+    for (int j = lane; 16 + j < storage_stride; j += 32) {
+      unsigned char code = 0;
+      if (j < rec_len) {
+        const int grp = j < kp ? 0 : (j < 2 * kp ? 1 : 2);
+        code = (unsigned char)__nv_cvt_float_to_fp8(ldexpf(r[j], -p[grp]), __NV_SATFINITE, __NV_E4M3);
+      }
+      rec[16 + j] = code;
+    }
+  }
+}
+
+cudaError_t launch_store_records(const float *src, float *master, void *storage, DType dt, int storage_stride,
+                                 long long n_leaves, int stride_f32, int rec_len, int kp, cudaStream_t s) {
+  if (n_leaves == 0) return cudaSuccess;
+  const long long want = (n_leaves * 32 + 255) / 256;
+  const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  store_records_kernel<<<blocks, 256, 0, s>>>(src, master, storage, (int)dt, storage_stride, n_leaves, stride_f32,
+                                              rec_len, kp);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mse(const float *rgb, const float *target, long long n, float scale, float *grad, float *loss,
                        cudaStream_t s) {
   if (n == 0) return cudaSuccess;

@@ -73,7 +73,10 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
   RayWalk w;
   const bool hit = walk_init(tr, o, d, w, dn);
   if (!hit) write_miss(a.out, i);
-  if (a.log.n_chunks && (threadIdx.x & 31) == __ffs(present) - 1) a.log.key[i >> 5] = kNoKey;
+  if (a.log.n_chunks && (threadIdx.x & 31) == __ffs(present) - 1) {
+    a.log.key[i >> 5] = kNoKey;
+    a.log.heads[i >> 5] = kNoLog;  // until the packet's first chunk
+  }
   if (__ballot_sync(present, hit) == 0) return;  // the whole packet missed the tree
   float Y[(DEG + 1) * (DEG + 1)];
   if (hit) {
@@ -398,15 +401,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
 }
 
 constexpr int kSliceTile = 64;    // leaves per tile (one per thread)
-constexpr int kSliceWaitPolls = 1 << 22;
+// Polls of the wait that lets a tile's copy in flight land after the tile's
+// own wait gave up (the block must not exit while the copy writes into its
+// shared memory).
+constexpr int kSliceDrainPolls = 1 << 22;
 
 // Time slice with TMA staging: a block takes tiles of kSliceTile consecutive
 // leaves; one thread loads the tile's records (consecutive in memory) into
 // shared memory with a single bulk copy completed on an mbarrier, every
 // thread turns its record into its slice row in a shared output tile, and one
 // bulk copy stores the tile's rows (consecutive in memory when the row
-// stride is the minimal one).  A wait that does not complete flags the
-// device status and ends the block.
+// stride is the minimal one).  A wait that does not complete within the
+// tree's poll limit flags kStatusTimeout; the whole block then waits (again
+// bounded) for its copy in flight to land and ends.
 template <int KP, int DEG, typename E>
 __global__ void __launch_bounds__(kSliceTile) slice_tma_kernel(const __grid_constant__ DevTree tr, float u,
                                                                float *slice, int rec_bytes) {
@@ -438,8 +445,11 @@ __global__ void __launch_bounds__(kSliceTile) slice_tma_kernel(const __grid_cons
           "l"(src), "r"(bytes), "r"(bar_a)
           : "memory");
     }
-    if (!mbar_wait(bar_a, parity, kSliceWaitPolls)) {
-      if (threadIdx.x == 0) raise_status(tr, kStatusSegCap);
+    // one decision for the block, so that no thread leaves while others sync
+    if (!__syncthreads_and(mbar_wait(bar_a, parity, tr.wait_polls))) {
+      if (threadIdx.x == 0) raise_status(tr, kStatusTimeout);
+      mbar_wait(bar_a, parity, kSliceDrainPolls);
+      if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
       return;
     }
     if ((int)threadIdx.x < count) {
@@ -707,6 +717,62 @@ cudaError_t launch_render_edit(int KP, int DEG, DType dt, const FwdArgs &a, cons
     if (dt == kBF16) return edit_one<16, 3, __nv_bfloat16>(a, cfg, s);
   }
   return cudaErrorNotSupported;
+}
+
+// Segment log decoder: ray i's composited segments are the entries of its
+// lane in its packet's chunks that hold a leaf, in round order, nseg[i] of
+// them.  count[i] = -1 when the ray's packet is not in the log (no log, a log
+// of other rays, or a packet that did not fit); chunk links are checked
+// against the log's size.
+__global__ void __launch_bounds__(256) log_read_kernel(const SampleLog l, long long n, const int *nseg, int max_out,
+                                                        int *leaf, float *chord, int *count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = -1;
+  const bool valid = l.n_chunks && __ldg(l.header + 4) == 1u && __ldg(l.header) == l.n_chunks &&
+                     __ldg(l.header + 1) == (uint32_t)kLogRounds &&
+                     __ldg(l.header + 2) == (uint32_t)(n & 0xFFFFFFFFll) && __ldg(l.header + 3) == (uint32_t)(n >> 32);
+  if (valid) {
+    uint32_t chunk = __ldg(l.heads + (i >> 5));
+    const int want = __ldg(nseg + i);
+    if (want == 0) {
+      c = 0;
+    } else if (chunk != kNoLog) {
+      c = 0;
+      int round = 0;
+      for (long long guard = 0; c < want && guard < (long long)l.n_chunks * kLogRounds; ++guard) {
+        if (chunk >= l.n_chunks) {
+          c = -1;
+          break;
+        }
+        const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + (i & 31);
+        const uint32_t lf = __ldg(l.leaf + slot);
+        if (lf != kEmpty) {
+          if (c < max_out) {
+            leaf[i * max_out + c] = (int)lf;
+            chord[i * max_out + c] = __ldg(l.dt + slot);
+          }
+          ++c;
+        }
+        if (++round == kLogRounds) {
+          round = 0;
+          chunk = __ldg(l.next + chunk);
+        }
+      }
+    }
+  }
+  for (int k = c < 0 ? 0 : c; k < max_out; ++k) {
+    leaf[i * max_out + k] = -1;
+    chord[i * max_out + k] = 0.f;
+  }
+  count[i] = c;
+}
+
+cudaError_t launch_log_read(const SampleLog &l, long long n_rays, const int *nseg, int max_out, int *leaf,
+                            float *chord, int *count, cudaStream_t s) {
+  if (n_rays == 0) return cudaSuccess;
+  log_read_kernel<<<(unsigned)((n_rays + 255) / 256), 256, 0, s>>>(l, n_rays, nseg, max_out, leaf, chord, count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s) {

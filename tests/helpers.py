@@ -1,27 +1,14 @@
-"""Comparison helpers shared by the GPU parity tests."""
+"""Comparison helpers shared by the GPU parity tests.
+
+Leaf sequences (reading A8) are compared exactly, except on rays whose
+oracle decision margin -- the smallest distance along the ray between two
+plane crossings whose order decides which leaves are visited -- is below the
+rounding of an FP32 traversal: ``decision_eps_cells``.  Those rays are counted
+and must stay below 0.1 % of a batch."""
 import numpy as np
 
-
-def align_sequences(a_ids, a_len, b_ids, b_len, eps):
-    """Matches two leaf sequences of one ray.  Equal ids pair up in order; a
-    segment present on one side only is allowed when its chord is below eps
-    (the extra cell that a near-tie between two crossing planes puts on the
-    ray, with a chord no longer than the tie's width).  Returns (ok, pairs)."""
-    i = j = 0
-    pairs = []
-    na, nb = len(a_ids), len(b_ids)
-    while i < na or j < nb:
-        if i < na and j < nb and a_ids[i] == b_ids[j]:
-            pairs.append((i, j))
-            i += 1
-            j += 1
-        elif i < na and a_len[i] < eps:
-            i += 1
-        elif j < nb and b_len[j] < eps:
-            j += 1
-        else:
-            return False, pairs
-    return True, pairs
+U32 = 2.0 ** -24           # FP32 unit roundoff
+MAX_EXEMPT_FRACTION = 1e-3
 
 
 def psnr(a, b, peak=1.0):
@@ -33,49 +20,62 @@ def finest_cell(tree):
     return min((tree.aabb_max[k] - tree.aabb_min[k]) for k in range(3)) / (1 << tree.depth)
 
 
-def compare_traces(tree, ref, gpu, max_out, eps_rel=1e-3, chord_tol_rel=5e-3):
-    """Per-ray leaf sequences: ids must align exactly (tiny near-tie cells
-    excepted), chords agree within chord_tol_rel of a finest cell.  Returns
-    counts (n_ok, n_bad, bad_rays)."""
+def decision_eps_cells(tree):
+    """Decision margin, in finest cells, below which an FP32 traversal may
+    order two crossings differently from the FP64 oracle: 8 unit roundoffs of
+    the root box's diagonal (the longest distance a crossing is measured
+    over from the ray's entry).  Each crossing distance of the FP32 walk is
+    within about two roundings of its value, so a margin above this bound
+    decides the same order on both sides."""
+    diag = float(np.linalg.norm(np.asarray(tree.aabb_max, np.float64) - np.asarray(tree.aabb_min, np.float64)))
+    return 8.0 * U32 * diag / finest_cell(tree)
+
+
+def compare_sequences(tree, ref_leaf, ref_chord, ref_count, got_leaf, got_chord, got_count, margin,
+                      chord_tol_cells=1e-3):
+    """Per ray: leaf ids equal exactly and chords within chord_tol_cells
+    finest cells, unless the ray's oracle margin is below decision_eps_cells
+    (exempt).  Counts are compared as given (callers cut both sides to the
+    segments they composite).  Returns (exempt ray indices, failing ray
+    indices with a reason)."""
+    eps = decision_eps_cells(tree)
     cell = finest_cell(tree)
-    eps = eps_rel * cell
-    bad = []
-    n = ref["count"].shape[0]
-    for r in range(n):
-        ca, cb = int(ref["count"][r]), int(gpu["count"][r])
-        if ca > max_out or cb > max_out:
-            bad.append((r, "overflow"))
+    exempt, bad = [], []
+    for r in range(len(ref_count)):
+        if margin[r] < eps:
+            exempt.append(r)
             continue
-        a_ids = ref["leaf"][r, :ca]
-        b_ids = gpu["leaf"][r, :cb]
-        a_len = ref["t1"][r, :ca] - ref["t0"][r, :ca]
-        b_len = gpu["t1"][r, :cb] - gpu["t0"][r, :cb]
-        ok, pairs = align_sequences(a_ids, a_len, b_ids, b_len, eps)
-        if ok:
-            for i, j in pairs:
-                if abs(a_len[i] - b_len[j]) > chord_tol_rel * cell:
-                    ok = False
-                    break
-        if not ok:
-            bad.append((r, "mismatch"))
-    return n - len(bad), len(bad), bad
+        ca, cb = int(ref_count[r]), int(got_count[r])
+        if ca != cb:
+            bad.append((r, f"count {cb} != {ca}"))
+            continue
+        if not np.array_equal(np.asarray(ref_leaf[r, :ca], np.int64), np.asarray(got_leaf[r, :cb], np.int64)):
+            bad.append((r, "leaf ids"))
+            continue
+        if ca and np.abs(np.asarray(ref_chord[r, :ca], np.float64) - got_chord[r, :cb]).max() > chord_tol_cells * cell:
+            bad.append((r, "chord"))
+    return exempt, bad
 
 
-def nseg_mismatch_explained(B, tree, tree_d, rays, idx, max_out=None):
-    """For rays whose composited-segment counts differ between the GPU and the
-    oracle, checks that their leaf sequences still align under the tiny-cell
-    rule (the difference is a near-tie cell with a chord below 1e-3 of a
-    finest cell).  Returns the indices that are not explained."""
-    import oracle
-    if len(idx) == 0:
-        return []
-    sub = rays.subset(np.asarray(idx))
-    mo = max_out or 4 * (1 << tree.depth)
-    ref = oracle.trace(tree, sub, max_out=mo)
-    dr = B.DeviceRays.from_host(sub)
-    got = {k: v.cpu().numpy() for k, v in B.neuvv_trace(tree_d, dr, mo).items()}
-    _, _, bad = compare_traces(tree, ref, got, mo)
-    bad_rows = {r for r, _ in bad}
-    # aligned sequences of equal length cannot explain a different count
-    bad_rows |= {r for r in range(len(idx)) if int(ref["count"][r]) == int(got["count"][r])}
-    return [int(np.asarray(idx)[r]) for r in sorted(bad_rows)]
+def compare_traces(tree, ref, gpu, max_out, chord_tol_cells=1e-3):
+    """Whole-ray traces (neuvv_trace against oracle.trace, which carries the
+    margin over the whole ray)."""
+    n = ref["count"].shape[0]
+    over = [r for r in range(n) if ref["count"][r] > max_out or gpu["count"][r] > max_out]
+    assert not over, over[:10]
+    return compare_sequences(tree, ref["leaf"], ref["t1"] - ref["t0"], ref["count"], gpu["leaf"],
+                             gpu["t1"] - gpu["t0"], gpu["count"], ref["margin"], chord_tol_cells)
+
+
+def nseg_differences_unexplained(ref, got, tree, stop_eps=1e-3):
+    """Rays whose composited-segment counts differ although neither the early
+    stop (oracle stop margin below stop_eps) nor the traversal (oracle
+    decision margin below decision_eps_cells) is ambiguous on them."""
+    diff = got["nseg"] != ref["nseg"]
+    diff &= ref["stop_margin"] >= stop_eps
+    diff &= ref["trace_margin"] >= decision_eps_cells(tree)
+    return np.nonzero(diff)[0]
+
+
+def exempt_fraction(ref, tree):
+    return float((ref["trace_margin"] < decision_eps_cells(tree)).mean())

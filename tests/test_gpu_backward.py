@@ -147,6 +147,43 @@ def test_autograd_function_matches_direct_calls(B):
     assert torch.allclose(coeffs.grad, direct, rtol=1e-5, atol=1e-7)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_autograd_function_renders_from_its_input(B, dtype):
+    """VOctreeRender renders the coefficients it is given: perturbed records
+    passed as ``coeffs`` give the image of a tree built from those
+    coefficients (bit for bit: the same storage rounding), and a torch
+    optimiser step on ``coeffs`` changes the next render accordingly."""
+    tree, rays, g, ga = _setup(81, 8, 2, 4, 1024)
+    tree_d = B.Tree(tree, dtype, with_optimizer=True)
+    dr = B.DeviceRays.from_host(rays)
+    info = tree_d.info
+    K, Kp, Nh = info.K, info.K_pad, info.N_h
+    pert = I.perturbed(tree, seed=5, std=0.2)
+    rec = np.zeros((tree.n_leaves, info.rec_stride_f32), np.float32)
+    rec[:, :K] = pert.w_sigma.T
+    rec[:, Kp:Kp + K] = pert.w_gamma.T
+    rec[:, 2 * Kp:2 * Kp + 3 * Nh] = pert.w_hh.reshape(3 * Nh, -1).T
+    coeffs = torch.from_numpy(rec).cuda().requires_grad_(True)
+    rgb, alpha, _ = B.render_differentiable(coeffs, tree_d, dr)
+    fresh = B.neuvv_render(B.Tree(pert, dtype), dr)
+    assert torch.equal(rgb, fresh["rgb"]) and torch.equal(alpha, fresh["alpha"])
+    # one SGD step on coeffs, then the next render is that of the stepped records
+    loss = (rgb * torch.from_numpy(g).cuda()).sum()
+    loss.backward()
+    opt = torch.optim.SGD([coeffs], lr=0.05)
+    opt.step()
+    rgb2, _, _ = B.render_differentiable(coeffs, tree_d, dr)
+    stepped = coeffs.detach().cpu().numpy()
+    again = pert.with_coeffs(np.ascontiguousarray(stepped[:, :K].T), np.ascontiguousarray(stepped[:, Kp:Kp + K].T),
+                             np.ascontiguousarray(stepped[:, 2 * Kp:2 * Kp + 3 * Nh].T.reshape(3, Nh, -1)))
+    assert torch.equal(rgb2, B.neuvv_render(B.Tree(again, dtype), dr)["rgb"])
+    assert not torch.equal(rgb2, rgb)
+    # the tree's own master copy as coeffs: nothing is written, the storage renders
+    own = tree_d.master()
+    r3, _, _ = B.render_differentiable(own, tree_d, dr)
+    assert torch.equal(r3, rgb2)
+
+
 def test_mse_grad_matches_numpy(B):
     rng = np.random.default_rng(90)
     n = 10007

@@ -2,7 +2,15 @@
 Algorithm 1) through the C ABI against the FP64 oracle: the workload of
 8 seeded duplicates of one tree (rigid transform, scale in [0.5, 1.5], time
 offset, tint) at reduced resolution, in both blending modes; plus the
-argument checks that need a device."""
+argument checks that need a device.
+
+Both sides get the same FP32 transforms, offsets and tints.  Every pixel is
+held to the FP32 bar of 1e-4 except those the oracle marks ambiguous: a
+layer's early stop within 1e-3 of the threshold, or two layers whose depths
+lie closer than their FP32 rounding (the blending order is then not
+determined); they are counted and stay below 1 %.  Early-stop and depth
+ties are the only exemptions: a voxel crossing of a ray taken into a
+primitive's frame is as exact as in the tree's own frame."""
 import numpy as np
 import pytest
 
@@ -33,29 +41,25 @@ def test_compose_matches_oracle(B, scene, mode, dtype):
     tree_d = B.Tree(tree, dtype)
     src = tree if dtype == "f32" else tree.with_coeffs(oracle.round_bf16(tree.w_sigma),
                                                        oracle.round_bf16(tree.w_gamma), oracle.round_bf16(tree.w_hh))
-    xf = [p.transform for p in prims]
-    off = [p.time_offset for p in prims]
-    tint = [p.tint for p in prims]
+    # the inputs both sides see: the transforms, offsets and tints in FP32
+    xf = [np.asarray(p.transform, np.float32).astype(np.float64) for p in prims]
+    off = [float(np.float32(p.time_offset)) for p in prims]
+    tint = [np.asarray(p.tint, np.float32).astype(np.float64) for p in prims]
     ref = oracle.compose([src] * 8, xf, off, tint, rays, mode=mode)
     dr = B.DeviceRays.from_host(rays)
     got = B.neuvv_compose([tree_d] * 8, xf, off, tint, dr, mode=mode)
     got = {k: got[k].cpu().numpy() for k in ("rgb", "alpha", "depth")}
     assert (ref["alpha"] > 0.01).mean() > 0.05       # the duplicates are in view
-    # pixels where a layer's early-stop decision sits at the threshold are
-    # exempt (as in the render tests)
-    ok = ref["stop_margin"] > 1e-3
+    fin = np.isfinite(ref["depth"])
+    depth_tie = ref["depth_margin"] < 1e-5 * np.where(fin, np.abs(ref["depth"]), 1.0)
+    ok = (ref["stop_margin"] > 1e-3) & ~depth_tie
+    print(f"exempt pixels: {(~ok).sum()} of {ok.size} (early stop {(ref['stop_margin'] <= 1e-3).sum()}, "
+          f"depth ties {depth_tie.sum()})")
     assert ok.mean() > 0.99
     err = np.abs(got["rgb"] - ref["rgb"])[ok]
     aerr = np.abs(got["alpha"] - ref["alpha"])[ok]
-    # Allowed on at most 0.1% of pixels: two layers whose depths coincide within
-    # float32 error blend in the other order (rgb), and a ray that crosses a
-    # voxel face at a grazing angle, where the ~1e-5 grid-unit float32 error of
-    # the ray taken into the primitive's frame moves the crossing by
-    # 1/sin(angle) times that (rgb and alpha).  Every pixel stays within 2e-3.
-    bad = (err.max(1) > 1e-4) | (aerr > 1e-4)
-    assert bad.mean() <= 1e-3, (bad.sum(), err.max(), aerr.max())
-    assert err.max() <= 2e-3 and aerr.max() <= 2e-3
-    fin = np.isfinite(ref["depth"])
+    assert err.max() <= 1e-4, err.max()
+    assert aerr.max() <= 1e-4, aerr.max()
     assert np.array_equal(fin, np.isfinite(got["depth"]))
     assert np.abs(got["depth"][fin] - ref["depth"][fin]).max() <= 1e-3
 
@@ -68,9 +72,9 @@ def test_compose_identity_equals_render(B):
     eye = np.concatenate([np.eye(3), np.zeros((3, 1))], 1)
     c = B.neuvv_compose([tree_d], [eye], [0.0], [[1, 1, 1]], dr)
     r = B.neuvv_render(tree_d, dr)
-    # the two paths form the entry point slightly differently (float32 rounding)
-    assert (c["rgb"] - r["rgb"]).abs().max().item() <= 1e-5
-    assert (c["alpha"] - r["alpha"]).abs().max().item() <= 1e-5
+    # the two paths form the entry point each with error-free steps of their own
+    assert (c["rgb"] - r["rgb"]).abs().max().item() <= 1e-6
+    assert (c["alpha"] - r["alpha"]).abs().max().item() <= 1e-6
 
 
 def test_compose_rejects_non_similarity_transforms(B):

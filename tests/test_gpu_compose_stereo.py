@@ -5,8 +5,9 @@ stereo pair of 2160x2160 views = 9,331,200 rays in one persistent launch
 captured in a CUDA graph.
 
 * The graph replay gives the same image as the eager call, bit for bit.
-* A seeded sample of 20,000 pixels matches the oracle within the compose
-  tolerances (1e-4, at most 0.1 % of pixels above it, none above 2e-3).
+* A seeded sample of 20,000 pixels matches the oracle within 1e-4, except
+  pixels the oracle marks ambiguous (an early stop within 1e-3 of the
+  threshold, or two layers' depths within their FP32 rounding).
 * The frame time of a replay is printed.
 """
 import numpy as np
@@ -39,9 +40,9 @@ def test_stereo_2160_graph_replay_and_sampled_parity(B, scene, dtype):
     assert rays.n == 2 * 2160 * 2160
     tree_d = B.Tree(tree, dtype)
     dr = B.DeviceRays.from_host(rays)
-    xf = [p.transform for p in prims]
-    off = [p.time_offset for p in prims]
-    tint = [p.tint for p in prims]
+    xf = [np.asarray(p.transform, np.float32).astype(np.float64) for p in prims]
+    off = [float(np.float32(p.time_offset)) for p in prims]
+    tint = [np.asarray(p.tint, np.float32).astype(np.float64) for p in prims]
     eager = B.neuvv_compose([tree_d] * 8, xf, off, tint, dr)
     eager = {k: v.clone() for k, v in eager.items()}
     out = B.alloc_out(rays.n)
@@ -76,14 +77,14 @@ def test_stereo_2160_graph_replay_and_sampled_parity(B, scene, dtype):
     ref = oracle.compose([src] * 8, xf, off, tint, rays.subset(idx))
     got = {k: eager[k].cpu().numpy()[idx] for k in ("rgb", "alpha", "depth")}
     assert (ref["alpha"] > 0.01).mean() > 0.05
-    ok = ref["stop_margin"] > 1e-3
+    fin = np.isfinite(ref["depth"])
+    depth_tie = ref["depth_margin"] < 1e-5 * np.where(fin, np.abs(ref["depth"]), 1.0)
+    ok = (ref["stop_margin"] > 1e-3) & ~depth_tie
     assert ok.mean() > 0.99
     err = np.abs(got["rgb"] - ref["rgb"])[ok].max(1)
     aerr = np.abs(got["alpha"] - ref["alpha"])[ok]
-    bad = (err > 1e-4) | (aerr > 1e-4)
-    assert bad.mean() <= 1e-3, (bad.sum(), err.max(), aerr.max())
-    assert err.max() <= 2e-3 and aerr.max() <= 2e-3
-    fin = np.isfinite(ref["depth"])
+    assert err.max() <= 1e-4, err.max()
+    assert aerr.max() <= 1e-4, aerr.max()
     assert np.array_equal(fin, np.isfinite(got["depth"]))
     assert np.abs(got["depth"][fin] - ref["depth"][fin]).max() <= 1e-3
     assert tree_d.status() == 0

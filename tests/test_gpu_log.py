@@ -1,0 +1,150 @@
+"""The timed kernel's own leaf sequences (Sec. 4.3 "Rendering": the voxels
+each ray crosses and the lengths of its segments inside them).
+
+The packet forward -- the kernel the bench times, in the launch the
+autotuner picks -- records every segment it composites in its segment log;
+neuvv_log_read decodes that log per ray.  Each ray's logged (leaf, chord)
+list must equal the oracle's traversal up to the composited count: leaf ids
+exactly, chords within 1e-3 of a finest cell.  Exempt are only rays the
+oracle itself marks ambiguous: a traversal decision margin below the FP32
+rounding of the crossings (reading A8), counted and below 0.1 % of the rays,
+and, for where the composited prefix ends, an early-stop margin below 1e-3
+(then the common prefix is compared).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2202_06088_gb300 import inputs as I
+
+from helpers import MAX_EXEMPT_FRACTION, compare_sequences
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B(cuda_lib):
+    from paper_2202_06088_gb300 import binding
+    return binding
+
+
+def _rounded(tree, dtype):
+    if dtype == "bf16":
+        return tree.with_coeffs(oracle.round_bf16(tree.w_sigma), oracle.round_bf16(tree.w_gamma),
+                                oracle.round_bf16(tree.w_hh))
+    return tree
+
+
+def _check_log(tree, ref, tr, got_leaf, got_chord, got_count, nseg):
+    """ref: oracle.render (nseg, margins); tr: oracle.trace; got_*: the log."""
+    assert (got_count >= 0).all(), "a packet is missing from the log"
+    assert np.array_equal(got_count, nseg)
+    stop_amb = ref["stop_margin"] < 1e-3
+    n_ref = np.where(stop_amb, np.minimum(ref["nseg"], nseg), ref["nseg"])
+    n_got = np.where(stop_amb, n_ref, nseg)
+    exempt, bad = compare_sequences(tree, tr["leaf"], tr["t1"] - tr["t0"], n_ref, got_leaf, got_chord, n_got,
+                                    ref["trace_margin"])
+    assert bad == [], bad[:10]
+    assert len(exempt) < MAX_EXEMPT_FRACTION * len(nseg) + 1, len(exempt)
+    return exempt
+
+
+def _render_and_read(B, tree_d, dr, max_out):
+    out = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=64)
+    B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+    log = B.neuvv_log_read(out, dr.n, max_out)
+    return out, log
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_packet_log_matches_oracle_c1(B, dtype):
+    tree = I.config1_tree()
+    rays, _ = I.config1_rays()
+    tree_d = B.Tree(tree, dtype)
+    dr = B.DeviceRays.from_host(rays)
+    B.neuvv_autotune(tree_d, dr)
+    mo = 4 * (1 << tree.depth)
+    out, log = _render_and_read(B, tree_d, dr, mo)
+    src = _rounded(tree, dtype)
+    ref = oracle.render(src, rays)
+    tr = oracle.trace(src, rays, max_out=mo)
+    exempt = _check_log(tree, ref, tr, log["leaf"].cpu().numpy(), log["chord"].cpu().numpy(),
+                        log["count"].cpu().numpy(), out["nseg"].cpu().numpy())
+    print(f"exempt rays: {len(exempt)} of {rays.n}")
+    assert tree_d.status() == 0
+
+
+@pytest.mark.parametrize("seed,depth,bricks", [(1, 4, True), (2, 5, True), (5, 6, False), (6, 7, True)])
+def test_packet_log_matches_oracle_mixed_trees(B, seed, depth, bricks):
+    """Leaves at every level, empty nodes, origins inside the box; with the
+    brick map (depth >= 3) and without bricks (descents from the lowest common
+    ancestor)."""
+    rng = np.random.default_rng(seed)
+    tree = I.make_coefficients(rng, I.random_mixed_tree(depth, seed), K=3, T=5, hh_degree=2, mean_sigma=8.0)
+    from test_oracle_render import _random_rays
+    rays = _random_rays(rng, 3000 + 17)     # several packets and a ragged tail
+    rays.times[:] = rng.uniform(0, 1, rays.n).astype(np.float32)
+    tree_d = B.Tree(tree, "f32", bricks=bricks)
+    dr = B.DeviceRays.from_host(rays)
+    mo = 4 * (1 << depth)
+    out, log = _render_and_read(B, tree_d, dr, mo)
+    ref = oracle.render(tree, rays)
+    tr = oracle.trace(tree, rays, max_out=mo)
+    _check_log(tree, ref, tr, log["leaf"].cpu().numpy(), log["chord"].cpu().numpy(), log["count"].cpu().numpy(),
+               out["nseg"].cpu().numpy())
+    assert tree_d.status() == 0
+
+
+def test_packet_log_full_size_sampled(B):
+    """The bench's workload and launch (8 x 1080p views of the depth-9 shell
+    tree, BF16 storage, autotuned packet kernel, 64 log bytes per ray): the
+    log of every ray is decoded and 4000 seeded rays are compared with the
+    oracle on the BF16-rounded coefficients."""
+    tree = I.config2_tree()
+    rays = I.config2_rays()[0]
+    tree_d = B.Tree(tree, "bf16")
+    dr = B.DeviceRays.from_host(rays)
+    B.neuvv_autotune(tree_d, dr)
+    mo = 96
+    out, log = _render_and_read(B, tree_d, dr, mo)
+    cnt = log["count"]
+    assert (cnt >= 0).all().item()                      # 64 B per ray holds every packet
+    assert torch.equal(cnt, out["nseg"])
+    idx = np.sort(np.random.default_rng(77).choice(rays.n, size=4000, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    sub = rays.subset(idx)
+    src = _rounded(tree, "bf16")
+    ref = oracle.render(src, sub)
+    tr = oracle.trace(src, sub, max_out=4096)
+    nseg = out["nseg"][it].cpu().numpy()
+    keep = nseg <= mo                                   # rays with more segments than max_out: not decoded whole
+    assert keep.mean() > 0.999
+    sel = np.nonzero(keep)[0]
+    refk = {k: v[sel] for k, v in ref.items()}
+    trk = {k: v[sel] for k, v in tr.items()}
+    exempt = _check_log(tree, refk, trk, log["leaf"][it].cpu().numpy()[sel], log["chord"][it].cpu().numpy()[sel],
+                        cnt[it].cpu().numpy()[sel], nseg[sel])
+    print(f"exempt rays: {len(exempt)} of {sel.size}")
+    assert tree_d.status() == 0
+
+
+def test_log_read_marks_rays_without_a_log(B):
+    tree = I.config1_tree()
+    rays, _ = I.config1_rays()
+    tree_d = B.Tree(tree, "f32")
+    dr = B.DeviceRays.from_host(rays)
+    out = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=64)
+    B.neuvv_render(tree_d, dr, kernel="plain", out=out)          # the plain kernel marks the log empty
+    log = B.neuvv_log_read(out, dr.n, 8)
+    assert (log["count"] == -1).all().item()
+    B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+    sub = B.neuvv_log_read(out, dr.n - 32, 8)                    # a log written for other rays
+    assert (sub["count"] == -1).all().item()
+    tiny = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=4)   # room for few packets: the rest walk
+    B.neuvv_render(tree_d, dr, kernel="packet", out=tiny)
+    t = B.neuvv_log_read(tiny, dr.n, 64)
+    c, ns = t["count"], tiny["nseg"]
+    logged = c >= 0
+    assert torch.equal(c[logged], ns[logged])
+    assert ((c == -1) | logged).all().item() and (~logged).any().item() and logged.any().item()

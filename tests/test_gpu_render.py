@@ -6,8 +6,8 @@ Tolerances (from the task's numerical bar): FP32 colour/alpha within 1e-4 max
 abs on a [0, 1] scale; BF16-stored coefficients within 4e-3 max abs and
 >= 50 dB PSNR against the oracle on the unrounded coefficients, and within
 1e-4 against the oracle on the BF16-rounded coefficients.  Leaf sequences
-must match exactly, except for cells whose chord is below 1e-3 of a finest
-cell (the extra cell of a near-tie between two crossing planes).
+must match exactly, except on rays whose oracle decision margin is below the
+rounding of an FP32 traversal (reading A8; fewer than 0.1 % of the rays).
 """
 import numpy as np
 import pytest
@@ -15,7 +15,7 @@ import pytest
 import oracle
 from paper_2202_06088_gb300 import inputs as I
 
-from helpers import compare_traces, nseg_mismatch_explained, psnr
+from helpers import MAX_EXEMPT_FRACTION, compare_traces, exempt_fraction, nseg_differences_unexplained, psnr
 
 pytestmark = pytest.mark.gpu
 
@@ -48,39 +48,34 @@ def _render(B, tree_d, rays, kernel, t_stop=1e-4, act="sigmoid"):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-def _ambiguous_stop(ref, t_stop=1e-4):
+def _ambiguous_stop(ref):
+    """Rays whose optical depth passes the early-stop threshold within 1e-3."""
     return ref["stop_margin"] < 1e-3
 
 
-def _explainer(B, tree, tree_d, rays):
-    """Rays whose composited-segment counts differ must owe it to a near-tie
-    cell (chord below 1e-3 of a finest cell) on one side (the traversal
-    reading); returns the rays that do not."""
-    return lambda idx: nseg_mismatch_explained(B, tree, tree_d, rays, idx)
-
-
-def _check_render(ref, got, tol, stop_ok=None, explain=None):
-    """explain(idx) -> unexplained subset of rays whose segment counts differ."""
+def _check_render(ref, got, tol, tree):
+    """Colour and alpha within tol everywhere; depth within 1e-3 where the
+    oracle's alpha is above 1e-3; composited-segment counts equal except on
+    rays where the oracle marks the early stop or the traversal ambiguous
+    (few of them)."""
     assert np.abs(got["rgb"] - ref["rgb"]).max() <= tol, np.abs(got["rgb"] - ref["rgb"]).max()
     assert np.abs(got["alpha"] - ref["alpha"]).max() <= tol
     fin = np.isfinite(ref["depth"]) & (ref["alpha"] > 1e-3)
     assert np.all(np.isfinite(got["depth"][fin]))
     assert np.abs(got["depth"][fin] - ref["depth"][fin]).max() <= 1e-3
-    diff = got["nseg"] != ref["nseg"]
-    if stop_ok is not None:
-        diff &= ~stop_ok
-    bad = np.nonzero(diff)[0]
-    if explain is not None:
-        bad = explain(bad)
+    bad = nseg_differences_unexplained(ref, got, tree)
     assert len(bad) == 0, bad[:10]
+    assert exempt_fraction(ref, tree) < MAX_EXEMPT_FRACTION
 
 
 def test_trace_matches_oracle_c1(B, c1, c1_rays):
     tree_d = B.Tree(c1, "f32")
     ref = oracle.trace(c1, c1_rays, max_out=96)
     got = _gpu_trace(B, tree_d, c1_rays, 96)
-    ok, nbad, bad = compare_traces(c1, ref, got, 96)
-    assert nbad == 0, bad[:10]
+    exempt, bad = compare_traces(c1, ref, got, 96)
+    assert bad == [], bad[:10]
+    print(f"exempt rays: {len(exempt)} of {c1_rays.n}")
+    assert len(exempt) < MAX_EXEMPT_FRACTION * c1_rays.n
     assert tree_d.status() == 0
 
 
@@ -95,8 +90,9 @@ def test_trace_matches_oracle_mixed_trees(B, seed, depth):
     mo = 4 * (1 << depth)
     ref = oracle.trace(tree, rays, max_out=mo)
     got = _gpu_trace(B, tree_d, rays, mo)
-    ok, nbad, bad = compare_traces(tree, ref, got, mo)
-    assert nbad == 0, bad[:10]
+    exempt, bad = compare_traces(tree, ref, got, mo)
+    assert bad == [], bad[:10]
+    assert len(exempt) < MAX_EXEMPT_FRACTION * rays.n + 1
 
 
 @pytest.mark.parametrize("kernel", ["plain", "packet"])
@@ -104,7 +100,7 @@ def test_render_fp32_matches_oracle_c1(B, c1, c1_rays, kernel):
     tree_d = B.Tree(c1, "f32")
     ref = oracle.render(c1, c1_rays)
     got = _render(B, tree_d, c1_rays, kernel)
-    _check_render(ref, got, 1e-4, _ambiguous_stop(ref), _explainer(B, c1, tree_d, c1_rays))
+    _check_render(ref, got, 1e-4, c1)
     assert tree_d.status() == 0
 
 
@@ -117,7 +113,7 @@ def test_render_bf16_against_unrounded_and_rounded_oracle(B, c1, c1_rays):
     assert psnr(got["rgb"], ref["rgb"]) >= 50.0
     rounded = c1.with_coeffs(oracle.round_bf16(c1.w_sigma), oracle.round_bf16(c1.w_gamma), oracle.round_bf16(c1.w_hh))
     ref_q = oracle.render(rounded, c1_rays)
-    _check_render(ref_q, got, 1e-4, _ambiguous_stop(ref_q), _explainer(B, rounded, B.Tree(rounded, "f32"), c1_rays))
+    _check_render(ref_q, got, 1e-4, rounded)
 
 
 @pytest.mark.parametrize("K,deg", [(4, 1), (16, 3), (31, 2)])
@@ -133,8 +129,7 @@ def test_render_other_shapes_and_identity_activation(B, K, deg):
         for kernel in ("plain", "packet"):
             td = B.Tree(tree, "f32")
             got = _render(B, td, rays, kernel, act=act)
-            _check_render(ref, got, 1e-4 if act == "sigmoid" else 3e-4, _ambiguous_stop(ref),
-                          _explainer(B, tree, td, rays))
+            _check_render(ref, got, 1e-4 if act == "sigmoid" else 3e-4, tree)
 
 
 def test_render_edge_cases(B, c1):
@@ -160,6 +155,6 @@ def test_render_stops_early_and_respects_t_stop_zero(B, c1, c1_rays):
     tree_d = B.Tree(c1, "f32")
     ref0 = oracle.render(c1, c1_rays, t_stop=0.0)
     got0 = _render(B, tree_d, c1_rays, "packet", t_stop=0.0)
-    _check_render(ref0, got0, 1e-4, None, _explainer(B, c1, tree_d, c1_rays))
+    _check_render(ref0, got0, 1e-4, c1)
     got = _render(B, tree_d, c1_rays, "packet")
     assert (got["nseg"] <= got0["nseg"]).all() and (got["nseg"] < got0["nseg"]).any()

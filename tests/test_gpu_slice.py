@@ -17,7 +17,7 @@ import oracle
 from paper_2202_06088_gb300 import inputs as I
 
 from helpers import psnr
-from test_gpu_render import _ambiguous_stop, _check_render, _explainer
+from test_gpu_render import _check_render
 
 pytestmark = pytest.mark.gpu
 
@@ -101,7 +101,7 @@ def test_render_slice_matches_oracle_and_hh_render(B, c1, dtype):
     ref = oracle.render_slice(src, oracle.slice_at(src, t), rays)
     ref_hh = oracle.render(src, rays)
     assert np.abs(ref["rgb"] - ref_hh["rgb"]).max() <= 1e-12
-    _check_render(ref_hh, got, 1e-4, _ambiguous_stop(ref_hh), _explainer(B, src, B.Tree(src, "f32"), rays))
+    _check_render(ref_hh, got, 1e-4, src)
     # the same frame through the HH path of the library
     hh = {k: v.cpu().numpy() for k, v in B.neuvv_render(tree_d, dr, kernel="packet").items()}
     assert np.abs(hh["rgb"] - got["rgb"]).max() <= 1e-4

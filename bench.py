@@ -8,9 +8,10 @@ resident in HBM.  Coefficients are stored in BF16 with an FP32 master copy.
 
 One step = forward render (packet kernel) -> loss gradient against fixed
 target images (Eq. rgb-loss plus 0.1 x the image-gradient regulariser of
-Sec. 4.3) -> fused adjoint (gradient sums formed per leaf after a counting
-sort of the samples, where a step has at least one ray per leaf) -> sparse
-Adam on the touched leaves.  The
+Sec. 4.3) -> fused adjoint and sparse Adam on the touched leaves in one call
+(gradient sums formed per leaf after a counting sort of the samples, where a
+step has at least one ray per leaf, and the Adam update applied by the same
+per-leaf pass).  The
 headline metric is leaf-segment samples per second of the forward+backward
 pair (a sample is one leaf segment evaluated by the forward and re-evaluated
 by the adjoint, counted once).
@@ -63,7 +64,7 @@ def parse_args():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the legs of the other workloads (depth-8 and depth-10 training, stereo composition)")
     p.add_argument("--launch", default=None, help="packet launch block,queue,ready (profiling case; default: library's)")
-    p.add_argument("--profile-kernel", choices=["fwd", "bwd", "adam"], default=None,
+    p.add_argument("--profile-kernel", choices=["fwd", "bwd", "bwd_adam"], default=None,
                    help="profiling case: launch that kernel twice on the workload and exit (no JSON)")
     return p.parse_args()
 
@@ -304,8 +305,7 @@ def train_step_leg(B, tree, rays, dtype, steps, seed, gather=True):
         B.neuvv_render(tree_d, dr, kernel="packet", out=out)
         loss.zero_()
         B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
-        B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
-        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k)
+        B.neuvv_render_backward_adam(tree_d, dr, out, grad_rgb, None, grad, touched, lr=1e-3, step=k)
 
     for k in range(3):
         step(k + 1)
@@ -375,7 +375,7 @@ def extra_workloads(B, steps, gather=True):
 def profile_case(args, B, tree, dr):
     """Two launches of one kernel of the step on the given views (for ncu)."""
     import torch
-    tree_d = B.Tree(tree, "bf16", with_optimizer=args.profile_kernel == "adam")
+    tree_d = B.Tree(tree, "bf16", with_optimizer=args.profile_kernel == "bwd_adam")
     if args.launch:
         tree_d.set_launch(*[int(x) for x in args.launch.split(",")])
     out = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=64)
@@ -389,8 +389,7 @@ def profile_case(args, B, tree, dr):
         elif args.profile_kernel == "bwd":
             B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
         else:
-            B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
-            B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k + 1)
+            B.neuvv_render_backward_adam(tree_d, dr, out, grad_rgb, None, grad, touched, lr=1e-3, step=k + 1)
     torch.cuda.synchronize()
     print(f"profile case done: {args.profile_kernel} on {dr.n} rays", flush=True)
 
@@ -439,7 +438,7 @@ def main():
     touched = tree_d.new_touched()
     loss = torch.zeros(1, device=dev)
     stream = torch.cuda.current_stream()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     # the image-gradient regulariser needs each view's pixel -> ray map
     W_img, H_img = 1920, 1080
     pix_map = np.empty((args.views, H_img * W_img), np.int32)
@@ -461,12 +460,10 @@ def main():
         B.neuvv_grad_loss(out["rgb"], target, ray_of_pixel, LAMBDA_GRAD / n, grad_rgb, loss)
         if evs:
             evs[3].record(stream)
-        B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+        B.neuvv_render_backward_adam(tree_d, dr, out, grad_rgb, None, grad, touched, lr=1e-3, beta1=0.9,
+                                     beta2=0.999, eps=1e-8, step=k)
         if evs:
             evs[4].record(stream)
-        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=k)
-        if evs:
-            evs[5].record(stream)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -500,7 +497,22 @@ def main():
     samples = 0.5 * (samples_before + int(out["nseg"].sum().item()))
     value = job_msamples_per_s(samples, ms_step, world)
     kern = {name: statistics.mean(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps))
-            for i, name in enumerate(["fwd", "mse", "lgrad", "bwd", "adam"])}
+            for i, name in enumerate(["fwd", "mse", "lgrad", "bwd_adam"])}
+    # the adjoint and Adam as two calls (no fusion), for comparison
+    B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+    a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    bwd_ms, adam_ms = [], []
+    for r in range(3):
+        a0.record(stream)
+        B.neuvv_render_backward(tree_d, dr, out, grad_rgb, None, grad, touched, kernel="packet")
+        a1.record(stream)
+        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=args.warmup + args.steps + 1 + r)
+        a2.record(stream)
+        torch.cuda.synchronize()
+        bwd_ms.append(a0.elapsed_time(a1))
+        adam_ms.append(a1.elapsed_time(a2))
+    kern["bwd_unfused"] = statistics.mean(bwd_ms[1:])
+    kern["adam_unfused"] = statistics.mean(adam_ms[1:])
     # the same adjoint call with the atomic scatter only, for comparison
     if not args.no_gather:
         tree_d.reserve_adjoint(0)
@@ -669,8 +681,8 @@ def main():
             loss.zero_()
             B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
             B.neuvv_grad_loss(out["rgb"], target, ray_of_pixel, LAMBDA_GRAD / n, grad_rgb, loss)
-            B.neuvv_render_backward(tree8, dr, out, grad_rgb, None, g8, t8, kernel="packet")
-            B.neuvv_adam_step(tree8, g8, t8, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, step=k)
+            B.neuvv_render_backward_adam(tree8, dr, out, grad_rgb, None, g8, t8, lr=1e-3, beta1=0.9, beta2=0.999,
+                                         eps=1e-8, step=k)
 
         for k in range(3):
             step8(k + 1)
@@ -700,17 +712,22 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     fp32_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     info = tree_d.info
-    rec_bytes = info.rec_stride * (2 if info.dtype == B.BF16 else 4)
-    rec_f32 = info.rec_stride_f32 * 4
+    elem = 2 if info.dtype == B.BF16 else 4
+    rec_bytes = info.rec_stride * elem
     ray_in, fwd_out = 28, 28
+    # the fused adjoint + Adam call: each touched leaf's record read once, its
+    # FP32 master, m and v (rec_len entries each) read and written, its
+    # storage entries written; per ray its ray, saved colour, dL/dC, tau and
+    # segment count
     traffic = {
         "fwd": (touched_leaves * rec_bytes + n * (ray_in + fwd_out), samples * flops_per_sample(info.K, info.hh_degree)),
-        "bwd": (touched_leaves * (rec_bytes + 2 * rec_f32) + n * (ray_in + 12 + 12 + 4 + 4),
-                samples * flops_per_sample(info.K, info.hh_degree, backward=True)),
-        "adam": (touched_leaves * (8 * rec_f32 + rec_bytes) + 4 * ((info.n_leaves + 31) // 32), 0),
+        "bwd_adam": (touched_leaves * (rec_bytes + 6 * 4 * info.rec_len + elem * info.rec_len)
+                     + n * (ray_in + 12 + 12 + 4 + 4),
+                     samples * flops_per_sample(info.K, info.hh_degree, backward=True)
+                     + touched_leaves * info.rec_len * 10),
         "mse": (n * 36, 0),
     }
-    dom = max(("fwd", "mse", "bwd", "adam"), key=kern.get)
+    dom = max(("fwd", "mse", "bwd_adam"), key=kern.get)
     bytes_, flops_ = traffic[dom]
     t_s = kern[dom] / 1e3
     if flops_ / (fp32_tflops * 1e12) > bytes_ / (hbm_gbs * 1e9):
@@ -758,8 +775,7 @@ def main():
         B.neuvv_mse_grad(out["rgb"], bufs[b], scale=1.0 / n, grad=grad_rgb, loss=loss)
         B.neuvv_grad_loss(out["rgb"], bufs[b], ray_of_pixel, LAMBDA_GRAD / n, grad_rgb, loss)
         used[b].record(stream)
-        B.neuvv_render_backward(tree_d, dr_e2e, out, grad_rgb, None, grad, touched, kernel="packet")
-        B.neuvv_adam_step(tree_d, grad, touched, lr=1e-3, step=k)
+        B.neuvv_render_backward_adam(tree_d, dr_e2e, out, grad_rgb, None, grad, touched, lr=1e-3, step=k)
         h_loss.copy_(loss, non_blocking=True)
 
     def e2e_run(n_steps, k0):
@@ -806,7 +822,7 @@ def main():
         "time_slice_and_lighting": time_slice,
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": (8 if args.no_gather else 13) * args.steps,
+        "gpu_launches": (8 if args.no_gather else 12) * args.steps,
         "clocks": clk,
     }
     if not args.no_extra:

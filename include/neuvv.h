@@ -275,6 +275,27 @@ neuvv_status neuvv_render_backward(const neuvv_tree *tree, const neuvv_rays *ray
                                    const neuvv_render_opts *opts, const neuvv_out *saved, const float *grad_rgb,
                                    const float *grad_alpha, float *grad, uint32_t *touched, neuvv_stream stream);
 
+/* One optimisation step on the leaf coefficients (Sec. 4.3 "Optimization":
+ * the renderer's gradient followed by Adam): the same result as
+ * neuvv_render_backward(tree, ..., grad, touched) followed by
+ * neuvv_adam_step(tree, grad, touched, lr, beta1, beta2, eps, step), in one
+ * call.  When the adjoint takes the leaf-major path (packet kernel, a log
+ * from the forward over these rays, a reservation from
+ * neuvv_tree_reserve_adjoint, K_pad <= 16), the Adam update runs inside the
+ * per-leaf reduction: each leaf's gradient is summed in registers and
+ * applied to its FP32 master, m, v and storage record at once, without
+ * passing through grad; otherwise the two steps run one after the other.
+ * grad (device FP32 [n_leaves][rec_stride_f32], 16-byte aligned) holds what
+ * the atomic scatter adds for samples beyond the reservation; as after
+ * neuvv_adam_step, its rows of touched leaves are zero afterwards, and rows
+ * of leaves whose touched bit is clear must be zero on entry.  touched
+ * (required) is clear afterwards.  Needs optimizer state; errors as the two
+ * calls. */
+neuvv_status neuvv_render_backward_adam(neuvv_tree *tree, const neuvv_rays *rays, float t,
+                                        const neuvv_render_opts *opts, const neuvv_out *saved, const float *grad_rgb,
+                                        const float *grad_alpha, float *grad, uint32_t *touched, float lr,
+                                        float beta1, float beta2, float eps, int32_t step, neuvv_stream stream);
+
 /* Spatial-temporal composition (Eq. st_composite_affine) with depth-aware
  * blending (Algorithm 1).  n_prims in 1..16 primitives; trees[j] may repeat
  * (duplicates share one tree, Sec. 5.1 "Varied Manifestations"); all trees

@@ -76,7 +76,7 @@ EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv
            "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss",
            "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit",
            "neuvv_camera_rays", "neuvv_render_alpha", "neuvv_tree_reserve_adjoint", "neuvv_tree_set_limits",
-           "neuvv_log_read", "neuvv_tree_set_records"]
+           "neuvv_log_read", "neuvv_tree_set_records", "neuvv_render_backward_adam"]
 
 
 def library_path() -> str:
@@ -121,6 +121,7 @@ def lib(build_if_missing: bool = True):
                 "neuvv_tree_set_limits": [p, i32, i32],
                 "neuvv_log_read": [p, i64, i32, p, p, p, p],
                 "neuvv_tree_set_records": [p, p, p],
+                "neuvv_render_backward_adam": [p, p, f, p, p, p, p, p, p, f, f, f, f, i32, p],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -494,6 +495,21 @@ def neuvv_render_backward(tree: Tree, rays: DeviceRays, saved: dict, grad_rgb: t
                                        _ptr(None if grad_alpha is None else grad_alpha.contiguous()), _ptr(grad),
                                        _ptr(touched), _stream()))
     return grad
+
+
+def neuvv_render_backward_adam(tree: Tree, rays: DeviceRays, saved: dict, grad_rgb: torch.Tensor,
+                               grad_alpha: torch.Tensor | None, grad: torch.Tensor, touched: torch.Tensor, lr: float,
+                               beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, step: int = 1,
+                               t: float = 0.0, t_stop: float = 1e-4, act: str = "sigmoid",
+                               kernel: str = "packet") -> None:
+    """Adjoint followed by Adam on the touched leaves in one call (fused into
+    the per-leaf reduction on the leaf-major path)."""
+    rc, sc, op = rays.c(), _outc(saved), _opts(t_stop, act, kernel)
+    _check(lib().neuvv_render_backward_adam(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(op),
+                                            ctypes.byref(sc), _ptr(grad_rgb.contiguous()),
+                                            _ptr(None if grad_alpha is None else grad_alpha.contiguous()), _ptr(grad),
+                                            _ptr(touched), float(lr), float(beta1), float(beta2), float(eps),
+                                            int(step), _stream()))
 
 
 def neuvv_compose(trees, transforms, time_offsets, tints, rays: DeviceRays, t: float = 0.0, t_stop: float = 1e-4,

@@ -726,9 +726,13 @@ neuvv_status neuvv_render_slice(const neuvv_tree *t, const float *slice, int32_t
   return NEUVV_OK;
 }
 
-neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, float time,
-                                   const neuvv_render_opts *opts, const neuvv_out *saved, const float *grad_rgb,
-                                   const float *grad_alpha, float *grad, uint32_t *touched, neuvv_stream stream) {
+namespace {
+
+// Checks the arguments of an adjoint call and fills its launch arguments;
+// shared by neuvv_render_backward and neuvv_render_backward_adam.
+neuvv_status prepare_backward(const neuvv_tree *t, const neuvv_rays *rays, float time, const neuvv_render_opts *opts,
+                              const neuvv_out *saved, const float *grad_rgb, const float *grad_alpha, float *grad,
+                              uint32_t *touched, BwdArgs &a) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
   neuvv_status s;
   if ((s = check_rays(rays)) != NEUVV_OK || (s = check_opts(opts)) != NEUVV_OK || (s = check_time(rays, time)))
@@ -739,9 +743,6 @@ neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, 
   if ((s = check_log(saved)) != NEUVV_OK) return s;
   if (!grad_rgb || !grad) return fail(NEUVV_ERR_INVALID_ARG, "grad_rgb and grad are required");
   if (((uintptr_t)grad & 15) != 0) return fail(NEUVV_ERR_INVALID_ARG, "grad must be 16-byte aligned");
-  DeviceGuard g(t->info.device);
-  cudaStream_t st = (cudaStream_t)stream;
-  BwdArgs a;
   a.tr = dev_tree(t);
   a.rays = dev_rays(rays, time);
   a.rgb = saved->rgb;
@@ -757,9 +758,83 @@ neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, 
   a.log = log_view(saved->log, saved->log_bytes, rays->n);
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   a.gws = packet && a.log.n_chunks ? t->gws : GatherWs{};
+  return NEUVV_OK;
+}
+
+neuvv_status check_adam(const neuvv_tree *t, float lr, float b1, float b2, float eps, int32_t step) {
+  if (!t->m || !t->v || !t->master) return fail(NEUVV_ERR_INVALID_ARG, "tree was created without optimizer state");
+  if (step < 1) return fail(NEUVV_ERR_INVALID_ARG, "step must be >= 1");
+  if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps > 0.f && std::isfinite(lr)))
+    return fail(NEUVV_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+  return NEUVV_OK;
+}
+
+// Adam on the touched leaves, then the bitmap cleared (neuvv_adam_step).
+cudaError_t run_adam(neuvv_tree *t, float *grad, uint32_t *touched, float lr, float b1, float b2, float eps,
+                     int32_t step, cudaStream_t st) {
+  const float c1 = (float)(1.0 - std::pow((double)b1, step));
+  const float c2 = (float)(1.0 - std::pow((double)b2, step));
+  cudaError_t e = launch_adam(t->master, t->m, t->v, t->master_is_storage ? nullptr : t->rec, (DType)t->info.dtype,
+                              t->info.rec_stride, grad, touched, t->info.n_leaves, t->info.rec_stride_f32,
+                              t->info.rec_len, t->info.K_pad, lr, b1, b2, eps, c1, c2, st);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(touched, 0, (size_t)((t->info.n_leaves + 31) / 32) * 4, st);
+}
+
+}  // namespace
+
+neuvv_status neuvv_render_backward(const neuvv_tree *t, const neuvv_rays *rays, float time,
+                                   const neuvv_render_opts *opts, const neuvv_out *saved, const float *grad_rgb,
+                                   const float *grad_alpha, float *grad, uint32_t *touched, neuvv_stream stream) {
+  BwdArgs a;
+  neuvv_status s = prepare_backward(t, rays, time, opts, saved, grad_rgb, grad_alpha, grad, touched, a);
+  if (s != NEUVV_OK || rays->n == 0) return s;
+  DeviceGuard g(t->info.device);
+  const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
-  cudaError_t e = launch_render_bwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st);
+  cudaError_t e = launch_render_bwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg,
+                                    (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_render_backward_adam(neuvv_tree *t, const neuvv_rays *rays, float time,
+                                        const neuvv_render_opts *opts, const neuvv_out *saved, const float *grad_rgb,
+                                        const float *grad_alpha, float *grad, uint32_t *touched, float lr, float b1,
+                                        float b2, float eps, int32_t step, neuvv_stream stream) {
+  BwdArgs a;
+  neuvv_status s = prepare_backward(t, rays, time, opts, saved, grad_rgb, grad_alpha, grad, touched, a);
+  if (s != NEUVV_OK) return s;
+  if (!touched) return fail(NEUVV_ERR_INVALID_ARG, "touched is required");
+  if ((s = check_adam(t, lr, b1, b2, eps, step)) != NEUVV_OK) return s;
+  DeviceGuard g(t->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool fused = false;
+  if (rays->n > 0) {
+    AdamArgs ad;
+    ad.master = t->master;
+    ad.m = t->m;
+    ad.v = t->v;
+    ad.storage = t->master_is_storage ? nullptr : t->rec;
+    ad.dt = t->info.dtype;
+    ad.storage_stride = t->info.rec_stride;
+    ad.lr = lr;
+    ad.b1 = b1;
+    ad.b2 = b2;
+    ad.eps = eps;
+    ad.c1 = (float)(1.0 - std::pow((double)b1, step));
+    ad.c2 = (float)(1.0 - std::pow((double)b2, step));
+    ad.on = 1;
+    const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
+    const LaunchCfg &cfg = packet ? t->packet : t->plain;
+    cudaError_t e = launch_render_bwd(t->info.K_pad, t->info.hh_degree, (DType)t->info.dtype, packet, a, cfg, st, &ad,
+                                      &fused);
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  }
+  if (!fused) {
+    cudaError_t e = run_adam(t, grad, touched, lr, b1, b2, eps, step, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adam launch");
+  }
   return NEUVV_OK;
 }
 
@@ -912,22 +987,13 @@ neuvv_status neuvv_compose_noalloc(const neuvv_tree *const *trees, const float *
 neuvv_status neuvv_adam_step(neuvv_tree *t, float *grad, uint32_t *touched, float lr, float b1, float b2, float eps,
                              int32_t step, neuvv_stream stream) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
-  if (!t->m || !t->v || !t->master) return fail(NEUVV_ERR_INVALID_ARG, "tree was created without optimizer state");
+  neuvv_status s;
+  if ((s = check_adam(t, lr, b1, b2, eps, step)) != NEUVV_OK) return s;
   if (!grad || !touched) return fail(NEUVV_ERR_INVALID_ARG, "grad and touched are required");
   if (((uintptr_t)grad & 15) != 0) return fail(NEUVV_ERR_INVALID_ARG, "grad must be 16-byte aligned");
-  if (step < 1) return fail(NEUVV_ERR_INVALID_ARG, "step must be >= 1");
-  if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps > 0.f && std::isfinite(lr)))
-    return fail(NEUVV_ERR_INVALID_ARG, "bad Adam hyper-parameters");
   DeviceGuard g(t->info.device);
-  cudaStream_t st = (cudaStream_t)stream;
-  const float c1 = (float)(1.0 - std::pow((double)b1, step));
-  const float c2 = (float)(1.0 - std::pow((double)b2, step));
-  cudaError_t e = launch_adam(t->master, t->m, t->v, t->master_is_storage ? nullptr : t->rec, (DType)t->info.dtype,
-                              t->info.rec_stride, grad, touched, t->info.n_leaves, t->info.rec_stride_f32,
-                              t->info.rec_len, t->info.K_pad, lr, b1, b2, eps, c1, c2, st);
+  cudaError_t e = run_adam(t, grad, touched, lr, b1, b2, eps, step, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "adam launch");
-  e = cudaMemsetAsync(touched, 0, (size_t)((t->info.n_leaves + 31) / 32) * 4, st);
-  if (e != cudaSuccess) return cuda_fail(e, "clear touched");
   return NEUVV_OK;
 }
 

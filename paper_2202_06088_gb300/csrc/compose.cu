@@ -120,8 +120,10 @@ __device__ __forceinline__ bool walk_init_local(const DevTree &tr, const PrimPar
       }
     }
   }
+  // unit direction rounded as the render path rounds it (times 1/|d|)
+  const float il = 1.f / llen;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) dn[k] = dlh[k] / llen;
+  for (int k = 0; k < 3; ++k) dn[k] = dlh[k] * il;
   walk_start(tr, p, pl, dn, w);
   // the local point ol + s dl is the world point o + s d
   t_base = s_hi * dlen;

@@ -625,6 +625,13 @@ struct LeafRecord {
 #pragma unroll
     for (int i = 0; i < NS; ++i) Elem<E>::unpack(raw[i], w + i * PV);
   }
+  // Only the vectors that hold w_gamma.
+  __device__ __forceinline__ void load_gamma(const DevTree &tr, uint32_t leaf) {
+    constexpr int V0 = KP / PV, V1 = (2 * KP + PV - 1) / PV;
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const E *>(tr.rec) + (size_t)leaf * tr.rec_stride);
+#pragma unroll
+    for (int i = V0; i < V1; ++i) Elem<E>::unpack(ldg_v4(p + i), w + i * PV);
+  }
   // Only the vectors that hold w_sigma (a density-only pass).
   __device__ __forceinline__ void load_sigma(const DevTree &tr, uint32_t leaf) {
     constexpr int NS = (KP + PV - 1) / PV;
@@ -706,6 +713,18 @@ struct LeafRecord<KP, DEG, Fp8E4M3> {
     sc[1] = __uint_as_float(h.y);
     sc[2] = __uint_as_float(h.z);
   }
+  // The header and the code vectors that hold w_gamma.
+  __device__ __forceinline__ void load_gamma(const DevTree &tr, uint32_t leaf) {
+    constexpr int V0 = KP / 16, V1 = (2 * KP + 15) / 16;
+    const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(tr.rec) +
+                                                     (size_t)leaf * tr.rec_stride);
+    const uint4 h = ldg_v4(p);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) raw[i] = (i >= V0 && i < V1) ? ldg_v4(p + 1 + i) : make_uint4(0u, 0u, 0u, 0u);
+    sc[0] = __uint_as_float(h.x);
+    sc[1] = __uint_as_float(h.y);
+    sc[2] = __uint_as_float(h.z);
+  }
   // The header and the code vectors that hold w_sigma (a density-only pass).
   __device__ __forceinline__ void load_sigma(const DevTree &tr, uint32_t leaf) {
     constexpr int NS = (KP + 15) / 16;
@@ -776,6 +795,14 @@ __device__ __forceinline__ void ray_const_basis(const DevTree &tr, float u, RayC
 }
 
 __device__ __forceinline__ float sigmoidf_fast(float x) { return 1.f / (1.f + __expf(-x)); }
+
+// float -> bfloat16 bits, round to nearest even (a NaN stays a quiet NaN).
+__device__ __forceinline__ unsigned short f32_to_bf16_rne(float f) {
+  unsigned int u = __float_as_uint(f);
+  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return (unsigned short)((u >> 16) | 0x40u);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (unsigned short)(u >> 16);
+}
 
 // Opacity of a segment of optical depth sd, 1 - exp(-sd), without the
 // cancellation of 1 - expf(-sd) when sd is small (a thin or faint segment):

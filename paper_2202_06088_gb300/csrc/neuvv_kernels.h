@@ -91,6 +91,17 @@ struct BwdArgs {
   SampleLog log;          // the forward's segment log (n_chunks == 0: walk every packet)
 };
 
+// Adam step applied by the per-leaf reduction of the adjoint (the fused
+// adjoint + optimizer call): the hyper-parameters of neuvv_adam_step, the
+// tree's optimizer state and its storage records.
+struct AdamArgs {
+  float *master, *m, *v;   // FP32 record layout, BwdArgs::grad_stride floats per leaf
+  void *storage;           // storage records, null when they are the master
+  int dt, storage_stride;  // storage type; entries (FP8: bytes) per leaf
+  float lr, b1, b2, eps, c1, c2;
+  int on;                  // 0: accumulate into the gradient buffer instead
+};
+
 constexpr int kMaxPrims = 16;
 
 struct PrimParam {
@@ -165,8 +176,11 @@ cudaError_t launch_camera_rays(const CamBatch &cb, float *o, float *d, float *t,
                                cudaStream_t s);
 cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdArgs &a, const LaunchCfg &cfg,
                               cudaStream_t s);
+// With adam (nullable, adam->on = 1) the per-leaf reduction also applies the
+// Adam step and clears the touched bitmap; *fused tells whether it did (the
+// caller runs the separate Adam step otherwise).
 cudaError_t launch_render_bwd(int KP, int DEG, DType dt, bool packet, const BwdArgs &a, const LaunchCfg &cfg,
-                              cudaStream_t s);
+                              cudaStream_t s, const AdamArgs *adam = nullptr, bool *fused = nullptr);
 cudaError_t launch_compose(int KP, int DEG, DType dt, const ComposeArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs &a, cudaStream_t s);
 cudaError_t launch_pick(int KP, int DEG, DType dt, const FwdArgs &a, float threshold, int *leaf_out, cudaStream_t s);

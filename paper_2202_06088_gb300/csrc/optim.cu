@@ -118,12 +118,6 @@ __global__ void __launch_bounds__(kGradTileW *kGradTileH)
   }
 }
 
-__device__ __forceinline__ unsigned short f32_to_bf16_rne(float f) {
-  unsigned int u = __float_as_uint(f);
-  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return (unsigned short)((u >> 16) | 0x40u);
-  u += 0x7FFFu + ((u >> 16) & 1u);
-  return (unsigned short)(u >> 16);
-}
 
 // One thread per (leaf, 4-float quad of the record).
 __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ master, float *__restrict__ m,

@@ -660,13 +660,213 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Per-leaf reduction by teams of four threads, optionally followed by the
+// Adam step of the leaf (K_pad <= 16).  Role 0 of a team owns the leaf's
+// w_sigma and w_gamma entries, role 1 + c the w_HH entries of colour channel
+// c, each as register accumulators (no shared memory).  Every role reads the
+// leaf's samples (the same addresses: one transaction per team); role 0 sums
+// dpre_s and dpre_g, roles 1..3 their channel's F[l,m] = sum dz[c] Y_lm, and
+// when the frame coordinate u changes each role expands its part: role 0
+// acc += dpre_s a(u) | dpre_g b(u), role 1 + c acc[n,l,m] += R_nl(gamma(u)) F.
+// Then, without Adam, each role adds its part to the leaf's gradient record
+// and role 0 sets the touched bit.  With Adam (Sec. 4.3 "Optimization"), the
+// leaf's gradient -- this call's sums plus what the atomic scatter left in
+// its row when its touched bit was already set -- updates the FP32 master,
+// m and v and the storage record in place; the row is cleared, and the
+// caller clears the touched bitmap afterwards.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void adam_update(const AdamArgs &ad, float g, float &w, float &m, float &v) {
+  m = ad.b1 * m + (1.f - ad.b1) * g;
+  v = ad.b2 * v + (1.f - ad.b2) * g * g;
+  w -= ad.lr * (m / ad.c1) / (sqrtf(v / ad.c2) + ad.eps);
+}
+
+template <int KP, int DEG, typename E>
+__device__ __forceinline__ void team_flush(const DevTree &tr, int role, const LeafRecord<KP, DEG, E> &rec, float u,
+                                           float ps, float pg, const float *F, float *acc) {
+  constexpr int NH = n_hh(DEG);
+  const float umax = (float)(tr.T - 1);
+  u = fminf(fmaxf(u, 0.f), umax);
+  const int f0 = min((int)floorf(u), tr.T - 1), f1 = min(f0 + 1, tr.T - 1);
+  const float fr = u - (float)f0;
+  const float *B0 = tr.B + (size_t)f0 * KP, *B1 = tr.B + (size_t)f1 * KP;
+  if (role == 0) {
+    const float *A0 = tr.A + (size_t)f0 * KP, *A1 = tr.A + (size_t)f1 * KP;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      acc[k] = fmaf(ps, (1.f - fr) * __ldg(A0 + k) + fr * __ldg(A1 + k), acc[k]);
+      acc[KP + k] = fmaf(pg, (1.f - fr) * __ldg(B0 + k) + fr * __ldg(B1 + k), acc[KP + k]);
+    }
+  } else {
+    float q4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < KP; ++k)
+      q4[k & 3] = fmaf((1.f - fr) * __ldg(B0 + k) + fr * __ldg(B1 + k), rec.gam(k), q4[k & 3]);
+    const float pgam = ((q4[0] + q4[1]) + (q4[2] + q4[3])) * rec.scale_gamma();
+    float sg, cg, R[(DEG + 1) * (DEG + 2) / 2];
+    sincospif(sigmoidf_fast(pgam), &sg, &cg);
+    hh_radial<DEG, false>(cg, sg, tr.hh_norm, R, nullptr);
+    int j = 0;
+#pragma unroll
+    for (int n = 0; n <= DEG; ++n)
+#pragma unroll
+      for (int l = 0; l <= n; ++l)
+#pragma unroll
+        for (int m = -l; m <= l; ++m) {
+          acc[j] = fmaf(R[radial_index(n, l)], F[l * l + l + m], acc[j]);
+          ++j;
+        }
+    static_assert(NH <= 2 * KP || NH <= 32, "w_HH of one channel must fit a role's accumulators");
+  }
+}
+
+constexpr int kTeamBlock = 256;
+
+template <int KP, int DEG, typename E>
+__global__ void __launch_bounds__(kTeamBlock) leaf_team_kernel(const __grid_constant__ BwdArgs a,
+                                                               const __grid_constant__ AdamArgs ad) {
+  constexpr int NY = (DEG + 1) * (DEG + 1), NH = n_hh(DEG);
+  constexpr int NA = 2 * KP > NH ? 2 * KP : NH;
+  const DevTree &tr = a.tr;
+  const int role = threadIdx.x & 3, lane = threadIdx.x & 31;
+  const long long leaf = ((long long)blockIdx.x * kTeamBlock + threadIdx.x) >> 2;
+  const bool in = leaf < tr.n_leaves;
+  const uint32_t cap = a.gws.cap_chunks * kLogRounds * 32;  // slots of the workspace
+  uint32_t lo = 0, hi = 0;
+  bool before = false;  // touched before this kernel: the atomic scatter left a part in the row
+  if (in) {
+    lo = leaf > 0 ? __ldg(a.gws.off + leaf - 1) : 0u;
+    hi = min(__ldg(a.gws.off + leaf), cap);
+    lo = min(lo, hi);
+    if (ad.on && a.touched) before = (a.touched[leaf >> 5] >> (leaf & 31)) & 1u;
+  }
+  float acc[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) acc[j] = 0.f;
+  if (lo < hi) {
+    LeafRecord<KP, DEG, E> rec;
+    rec.load_gamma(tr, (uint32_t)leaf);
+    float F[NY];
+#pragma unroll
+    for (int k = 0; k < NY; ++k) F[k] = 0.f;
+    float ps = 0.f, pg = 0.f, u_cur = 0.f;
+    float4 n0, n1, n2;  // the record of the sample after the current one
+    {
+      const float4 *f = a.gws.fac + 3 * (size_t)min(__ldg(a.gws.idx + lo), cap - 1);
+      n0 = __ldg(f);
+      n1 = __ldg(f + 1);
+      n2 = __ldg(f + 2);
+    }
+    uint32_t nidx = lo + 1 < hi ? __ldg(a.gws.idx + lo + 1) : 0u;
+    for (uint32_t p = lo; p < hi; ++p) {
+      const float4 f0 = n0, f1 = n1, f2 = n2;
+      if (p + 1 < hi) {
+        const float4 *f = a.gws.fac + 3 * (size_t)min(nidx, cap - 1);
+        n0 = __ldg(f);
+        n1 = __ldg(f + 1);
+        n2 = __ldg(f + 2);
+        if (p + 2 < hi) nidx = __ldg(a.gws.idx + p + 2);
+      }
+      if (p > lo && f1.y != u_cur) {  // a new frame coordinate: expand the finished group
+        team_flush<KP, DEG, E>(tr, role, rec, u_cur, ps, pg, F, acc);
+#pragma unroll
+        for (int k = 0; k < NY; ++k) F[k] = 0.f;
+        ps = pg = 0.f;
+      }
+      u_cur = f1.y;
+      ps += f0.x;
+      pg += f0.y;
+      if (role > 0) {
+        const float dz = role == 1 ? f0.z : (role == 2 ? f0.w : f1.x);
+        const float dn[3] = {f1.z, f1.w, f2.x};
+        float Y[NY];
+        sh_real<DEG>(dn, Y);
+#pragma unroll
+        for (int k = 0; k < NY; ++k) F[k] = fmaf(dz, Y[k], F[k]);
+      }
+    }
+    team_flush<KP, DEG, E>(tr, role, rec, u_cur, ps, pg, F, acc);
+  }
+  // this role's entries of the leaf's record: [first, first + len)
+  const int first = role == 0 ? 0 : 2 * KP + (role - 1) * NH;
+  const int len = role == 0 ? 2 * KP : NH;
+  const size_t row = (size_t)leaf * a.grad_stride + first;
+  if (!ad.on) {
+    if (lo < hi) {
+#pragma unroll
+      for (int j = 0; j < NA; ++j)
+        if (j < len) a.grad[row + j] += acc[j];
+    }
+    if (a.touched) {
+      const unsigned bits = __ballot_sync(0xFFFFFFFFu, role == 0 && lo < hi);
+      // the warp's 8 leaves are consecutive and 8-aligned: one byte of a touched word
+      unsigned byte = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) byte |= ((bits >> (4 * k)) & 1u) << k;
+      const long long leaf0 = ((long long)blockIdx.x * kTeamBlock + (threadIdx.x & ~31)) >> 2;
+      if (lane == 0 && byte) atomicOr(a.touched + (leaf0 >> 5), byte << (leaf0 & 31));
+    }
+    return;
+  }
+  const bool active = in && (lo < hi || before);
+  float mx = 0.f, mx_g = 0.f;  // FP8: largest magnitude of the role's group(s)
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      if (j >= len) continue;
+      float g = acc[j];
+      if (before) {
+        g += a.grad[row + j];
+        a.grad[row + j] = 0.f;
+      }
+      float w = ad.master[row + j], m = ad.m[row + j], v = ad.v[row + j];
+      adam_update(ad, g, w, m, v);
+      ad.master[row + j] = w;
+      ad.m[row + j] = m;
+      ad.v[row + j] = v;
+      acc[j] = w;  // the updated weight, for the storage record
+      if (role == 0 && j >= KP) mx_g = fmaxf(mx_g, fabsf(w));
+      else mx = fmaxf(mx, fabsf(w));
+    }
+    if (ad.dt == kBF16) {
+      unsigned short *st = static_cast<unsigned short *>(ad.storage) + (size_t)leaf * ad.storage_stride + first;
+#pragma unroll
+      for (int j = 0; j < NA; ++j)
+        if (j < len) st[j] = f32_to_bf16_rne(acc[j]);
+    }
+  }
+  if (ad.dt == kFP8) {
+    // group scales: w_sigma and w_gamma in role 0, w_HH across roles 1..3
+    float mh = role == 0 ? 0.f : mx;
+    mh = fmaxf(mh, __shfl_xor_sync(0xFFFFFFFFu, mh, 1));
+    mh = fmaxf(mh, __shfl_xor_sync(0xFFFFFFFFu, mh, 2));
+    if (active) {
+      unsigned char *rec = static_cast<unsigned char *>(ad.storage) + (size_t)leaf * ad.storage_stride;
+      const int ps_ = fp8_scale_exp(mx), pg_ = fp8_scale_exp(mx_g), ph_ = fp8_scale_exp(mh);
+      if (role == 0)
+        *reinterpret_cast<uint4 *>(rec) = make_uint4(__float_as_uint(ldexpf(1.f, ps_)),
+                                                     __float_as_uint(ldexpf(1.f, pg_)),
+                                                     __float_as_uint(ldexpf(1.f, ph_)), 0u);
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        if (j >= len) continue;
+        const int p = role == 0 ? (j < KP ? ps_ : pg_) : ph_;
+        rec[16 + first + j] = (unsigned char)__nv_cvt_float_to_fp8(ldexpf(acc[j], -p), __NV_SATFINITE, __NV_E4M3);
+      }
+    }
+  }
+}
+
 template <int KP, int DEG>
 __host__ __device__ constexpr size_t reduce_smem_bytes(int block) {
   return (size_t)block * (reduce_pitch<KP, DEG>() * sizeof(float) + sizeof(int));
 }
 
 template <int KP, int DEG, typename E>
-static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
+static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, cudaStream_t s, const AdamArgs *adam,
+                           bool *fused) {
+  if (fused) *fused = false;
   if (a.rays.n == 0) return cudaSuccess;
   const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
   if (!packet) {
@@ -711,6 +911,21 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
       const long long slots = (long long)std::min(a.log.n_chunks, a.gws.cap_chunks) * kLogRounds * 32;
       slot_scatter_kernel<<<(unsigned)std::min<long long>((slots + 255) / 256, 16LL * cfg.num_sms), 256, 0, s>>>(
           a.gws, a.log, nl);
+      if constexpr (KP <= 16) {
+        // teams of four threads per leaf, with the Adam step when asked
+        AdamArgs ad{};
+        if (adam && adam->on) ad = *adam;
+        const long long blocks_t = (nl * 4 + kTeamBlock - 1) / kTeamBlock;
+        leaf_team_kernel<KP, DEG, E><<<(unsigned)blocks_t, kTeamBlock, 0, s>>>(a, ad);
+        if (ad.on) {
+          cudaError_t e = cudaGetLastError();
+          if (e != cudaSuccess) return e;
+          if (a.touched && (e = cudaMemsetAsync(a.touched, 0, (size_t)((nl + 31) / 32) * 4, s)) != cudaSuccess)
+            return e;
+          if (fused) *fused = true;
+        }
+        return cudaGetLastError();
+      }
       constexpr int kReduceBlock = 64;
       const size_t rsm = reduce_smem_bytes<KP, DEG>(kReduceBlock);
       if (rsm > 48 * 1024) {
@@ -725,27 +940,28 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
 }
 
 template <typename E>
-static cudaError_t bwd_dispatch(int KP, int DEG, bool packet, const BwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
+static cudaError_t bwd_dispatch(int KP, int DEG, bool packet, const BwdArgs &a, const LaunchCfg &cfg, cudaStream_t s,
+                                const AdamArgs *adam, bool *fused) {
   switch (KP * 10 + DEG) {
-    case 81: return bwd_one<8, 1, E>(packet, a, cfg, s);
-    case 82: return bwd_one<8, 2, E>(packet, a, cfg, s);
-    case 83: return bwd_one<8, 3, E>(packet, a, cfg, s);
-    case 161: return bwd_one<16, 1, E>(packet, a, cfg, s);
-    case 162: return bwd_one<16, 2, E>(packet, a, cfg, s);
-    case 163: return bwd_one<16, 3, E>(packet, a, cfg, s);
-    case 321: return bwd_one<32, 1, E>(packet, a, cfg, s);
-    case 322: return bwd_one<32, 2, E>(packet, a, cfg, s);
-    case 323: return bwd_one<32, 3, E>(packet, a, cfg, s);
+    case 81: return bwd_one<8, 1, E>(packet, a, cfg, s, adam, fused);
+    case 82: return bwd_one<8, 2, E>(packet, a, cfg, s, adam, fused);
+    case 83: return bwd_one<8, 3, E>(packet, a, cfg, s, adam, fused);
+    case 161: return bwd_one<16, 1, E>(packet, a, cfg, s, adam, fused);
+    case 162: return bwd_one<16, 2, E>(packet, a, cfg, s, adam, fused);
+    case 163: return bwd_one<16, 3, E>(packet, a, cfg, s, adam, fused);
+    case 321: return bwd_one<32, 1, E>(packet, a, cfg, s, adam, fused);
+    case 322: return bwd_one<32, 2, E>(packet, a, cfg, s, adam, fused);
+    case 323: return bwd_one<32, 3, E>(packet, a, cfg, s, adam, fused);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_render_bwd(int KP, int DEG, DType dt, bool packet, const BwdArgs &a, const LaunchCfg &cfg,
-                              cudaStream_t s) {
-  if (dt == kF32) return bwd_dispatch<float>(KP, DEG, packet, a, cfg, s);
-  if (dt == kBF16) return bwd_dispatch<__nv_bfloat16>(KP, DEG, packet, a, cfg, s);
-  if (KP == 8 && DEG == 2) return bwd_one<8, 2, Fp8E4M3>(packet, a, cfg, s);
-  if (KP == 16 && DEG == 3) return bwd_one<16, 3, Fp8E4M3>(packet, a, cfg, s);
+                              cudaStream_t s, const AdamArgs *adam, bool *fused) {
+  if (dt == kF32) return bwd_dispatch<float>(KP, DEG, packet, a, cfg, s, adam, fused);
+  if (dt == kBF16) return bwd_dispatch<__nv_bfloat16>(KP, DEG, packet, a, cfg, s, adam, fused);
+  if (KP == 8 && DEG == 2) return bwd_one<8, 2, Fp8E4M3>(packet, a, cfg, s, adam, fused);
+  if (KP == 16 && DEG == 3) return bwd_one<16, 3, Fp8E4M3>(packet, a, cfg, s, adam, fused);
   return cudaErrorInvalidValue;
 }
 

@@ -50,8 +50,8 @@ def _check_log(tree, ref, tr, got_leaf, got_chord, got_count, nseg):
     return exempt
 
 
-def _render_and_read(B, tree_d, dr, max_out):
-    out = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=64)
+def _render_and_read(B, tree_d, dr, max_out, log_bytes_per_ray=64):
+    out = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=log_bytes_per_ray)
     B.neuvv_render(tree_d, dr, kernel="packet", out=out)
     log = B.neuvv_log_read(out, dr.n, max_out)
     return out, log
@@ -88,7 +88,8 @@ def test_packet_log_matches_oracle_mixed_trees(B, seed, depth, bricks):
     tree_d = B.Tree(tree, "f32", bricks=bricks)
     dr = B.DeviceRays.from_host(rays)
     mo = 4 * (1 << depth)
-    out, log = _render_and_read(B, tree_d, dr, mo)
+    # incoherent rays shade few lanes per round: a log of 4 KB per ray holds them all
+    out, log = _render_and_read(B, tree_d, dr, mo, log_bytes_per_ray=4096)
     ref = oracle.render(tree, rays)
     tr = oracle.trace(tree, rays, max_out=mo)
     _check_log(tree, ref, tr, log["leaf"].cpu().numpy(), log["chord"].cpu().numpy(), log["count"].cpu().numpy(),
@@ -116,7 +117,7 @@ def test_packet_log_full_size_sampled(B):
     sub = rays.subset(idx)
     src = _rounded(tree, "bf16")
     ref = oracle.render(src, sub)
-    tr = oracle.trace(src, sub, max_out=4096)
+    tr = oracle.trace(src, sub, max_out=512)
     nseg = out["nseg"][it].cpu().numpy()
     keep = nseg <= mo                                   # rays with more segments than max_out: not decoded whole
     assert keep.mean() > 0.999

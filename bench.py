@@ -64,6 +64,8 @@ def parse_args():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the legs of the other workloads (depth-8 and depth-10 training, stereo composition)")
     p.add_argument("--launch", default=None, help="packet launch block,queue,ready (profiling case; default: library's)")
+    p.add_argument("--order", type=int, default=None,
+                   help="packet order of the forward after autotuning (0 as given, 1 by region; default: tuned)")
     p.add_argument("--profile-kernel", choices=["fwd", "bwd", "bwd_adam"], default=None,
                    help="profiling case: launch that kernel twice on the workload and exit (no JSON)")
     return p.parse_args()
@@ -318,9 +320,21 @@ def train_step_leg(B, tree, rays, dtype, steps, seed, gather=True):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # where one step's time goes
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+    ev[1].record()
+    loss.zero_()
+    B.neuvv_mse_grad(out["rgb"], target, scale=1.0 / n, grad=grad_rgb, loss=loss)
+    ev[2].record()
+    B.neuvv_render_backward_adam(tree_d, dr, out, grad_rgb, None, grad, touched, lr=1e-3, step=4 + steps)
+    ev[3].record()
+    torch.cuda.synchronize()
+    parts = {name: ev[i].elapsed_time(ev[i + 1]) for i, name in enumerate(("fwd", "mse", "bwd_adam"))}
     return {"ms_per_step": ms, "msamples_per_s": samples / (ms / 1e3) / 1e6, "rays": n,
             "leaves": tree.n_leaves, "samples_per_step": samples, "storage": dtype, "steps": steps,
-            "adjoint": "leaf-major reduction" if gather else "atomic scatter"}
+            "adjoint": "leaf-major reduction" if gather else "atomic scatter", "parts_ms": parts}
 
 
 def extra_workloads(B, steps, gather=True):
@@ -378,6 +392,8 @@ def profile_case(args, B, tree, dr):
     tree_d = B.Tree(tree, "bf16", with_optimizer=args.profile_kernel == "bwd_adam")
     if args.launch:
         tree_d.set_launch(*[int(x) for x in args.launch.split(",")])
+    if args.order is not None:
+        tree_d.set_packet_order(args.order)
     out = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=64)
     reserve_adjoint(B, tree_d, dr, out, not args.no_gather)
     grad_rgb = torch.randn(dr.n, 3, device=dr.o.device) * 1e-3
@@ -428,8 +444,10 @@ def main():
     tree_d = B.Tree(tree, "bf16", with_optimizer=True)
     if not args.no_autotune:
         B.neuvv_autotune(tree_d, dr)
+    if args.order is not None:
+        tree_d.set_packet_order(args.order)
     launch = {"block": tree_d.info.packet_block, "queue": tree_d.info.packet_queue,
-              "ready": tree_d.info.packet_ready,
+              "ready": tree_d.info.packet_ready, "order": tree_d.info.packet_order,
               "autotuned": not args.no_autotune}
     out = B.alloc_out(n, dev, log_bytes_per_ray=64)
     log_used, log_chunks = reserve_adjoint(B, tree_d, dr, out, not args.no_gather)
@@ -666,6 +684,7 @@ def main():
     if not args.no_fp8:
         tree8 = B.Tree(tree, "fp8", with_optimizer=True)
         tree8.set_launch(launch["block"], launch["queue"], launch["ready"])
+        tree8.set_packet_order(launch["order"])
         reserve_adjoint(B, tree8, dr, out, not args.no_gather)
         rgb8 = B.neuvv_render(tree8, dr, kernel="packet")["rgb"]
         mse8 = float(((rgb8 - rgb32) ** 2).mean().item())

@@ -135,7 +135,18 @@ typedef struct {
   int32_t packet_queue;     /* packet kernels: leaf segments a ray may queue ahead of shading */
   int32_t packet_ready;     /* packet kernels: lanes holding a queued segment that start a
                                shading round (all three set by neuvv_autotune) */
+  int32_t packet_order;     /* packet forward with a segment log: NEUVV_ORDER_* (neuvv_autotune) */
 } neuvv_tree_info;
+
+/* The order in which the packet forward runs its 32-ray packets when the
+ * call has a segment log (the rays themselves, their outputs and the packets'
+ * contents do not change).  AS_GIVEN: in ray order.  BY_REGION: a pre-pass
+ * finds the first leaf each packet reaches and the packets run sorted by
+ * that leaf's region (leaf ids follow the Morton order of the leaves), so
+ * packets of different views that see the same part of the tree run
+ * together and share its records in L2. */
+#define NEUVV_ORDER_AS_GIVEN 0
+#define NEUVV_ORDER_BY_REGION 1
 
 /* Rays, device SoA float32 arrays of length n.  t may be NULL: then the
  * scalar time argument of the call is used for every ray. */
@@ -483,6 +494,10 @@ neuvv_status neuvv_tree_set_limits(neuvv_tree *tree, int32_t step_cap, int32_t w
  * device, caller-owned; asynchronous. */
 neuvv_status neuvv_log_read(const neuvv_out *saved, int64_t n, int32_t max_out, int32_t *leaf, float *chord,
                             int32_t *count, neuvv_stream stream);
+
+/* Sets the packet forward's order (NEUVV_ORDER_*; else INVALID_ARG) instead
+ * of neuvv_autotune.  Host only. */
+neuvv_status neuvv_tree_set_packet_order(neuvv_tree *tree, int32_t order);
 
 /* Sets the packet kernels' launch explicitly instead of neuvv_autotune:
  * block (a multiple of 32 in [32, 256]), queue (a power of two in [1, 32]:

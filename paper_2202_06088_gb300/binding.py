@@ -25,6 +25,7 @@ _lib = None
 F32, BF16, FP8 = 0, 1, 2
 # device status bits (neuvv_tree_status)
 STATUS_SEGMENT_CAP, STATUS_BAD_INDEX, STATUS_TIMEOUT = 0x1, 0x2, 0x4
+ORDER_AS_GIVEN, ORDER_BY_REGION = 0, 1
 _DTYPES = {"f32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16, "fp8": FP8, "fp8_e4m3": FP8}
 _ACT = {"sigmoid": 0, "identity": 1}
 _KERNEL = {"auto": 0, "plain": 1, "packet": 2}
@@ -50,7 +51,7 @@ class TreeInfo(ctypes.Structure):
                 ("rec_stride", ctypes.c_int32), ("rec_stride_f32", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("device", ctypes.c_int32), ("packet_block", ctypes.c_int32), ("packet_queue", ctypes.c_int32),
-                ("packet_ready", ctypes.c_int32)]
+                ("packet_ready", ctypes.c_int32), ("packet_order", ctypes.c_int32)]
 
 
 class RaysC(ctypes.Structure):
@@ -76,7 +77,8 @@ EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv
            "neuvv_tree_set_launch", "neuvv_slice", "neuvv_render_slice", "neuvv_grad_loss",
            "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit",
            "neuvv_camera_rays", "neuvv_render_alpha", "neuvv_tree_reserve_adjoint", "neuvv_tree_set_limits",
-           "neuvv_log_read", "neuvv_tree_set_records", "neuvv_render_backward_adam"]
+           "neuvv_log_read", "neuvv_tree_set_records", "neuvv_render_backward_adam",
+           "neuvv_tree_set_packet_order"]
 
 
 def library_path() -> str:
@@ -122,6 +124,7 @@ def lib(build_if_missing: bool = True):
                 "neuvv_log_read": [p, i64, i32, p, p, p, p],
                 "neuvv_tree_set_records": [p, p, p],
                 "neuvv_render_backward_adam": [p, p, f, p, p, p, p, p, p, f, f, f, f, i32, p],
+                "neuvv_tree_set_packet_order": [p, i32],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -251,6 +254,11 @@ class Tree:
         if records.shape != (self.n_leaves, self.info.rec_stride_f32) or records.dtype != torch.float32:
             raise NeuvvError("records must be float32 [n_leaves, rec_stride_f32]")
         _check(lib().neuvv_tree_set_records(self.handle, _ptr(records.contiguous()), _stream()))
+
+    def set_packet_order(self, order: int) -> None:
+        """ORDER_AS_GIVEN or ORDER_BY_REGION for the packet forward with a log."""
+        _check(lib().neuvv_tree_set_packet_order(self.handle, int(order)))
+        self.refresh_info()
 
     def set_limits(self, step_cap: int = 0, wait_polls: int = 1 << 22) -> None:
         """Walk-step cap per ray (0: the default, which no ray reaches) and

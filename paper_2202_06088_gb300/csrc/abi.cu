@@ -570,6 +570,7 @@ neuvv_status neuvv_tree_get_info(const neuvv_tree *t, neuvv_tree_info *info) {
   info->packet_block = t->packet.block;
   info->packet_queue = t->packet.queue;
   info->packet_ready = t->packet.ready;
+  info->packet_order = t->packet.order;
   return NEUVV_OK;
 }
 
@@ -617,7 +618,7 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   if (rays->n == 0) return NEUVV_OK;
   DeviceGuard g(t->info.device);
   cudaStream_t st = (cudaStream_t)stream;
-  FwdArgs a;
+  FwdArgs a{};
   a.tr = dev_tree(t);
   a.rays = dev_rays(rays, time);
   a.out = DevOut{out->rgb, out->alpha, out->depth, out->tau, out->nseg};
@@ -631,10 +632,17 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   a.slice_stride = 0;
   a.edits = nullptr;
   a.edit_beta = 0.f;
+  a.order = nullptr;
   cudaError_t e;
   if (a.log.n_chunks) {
     e = cudaMemsetAsync(a.log.counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "reset log");
+    if (cfg.order == 1 && a.work) {
+      // persistent warps take the packets in the order of the regions they reach
+      if ((e = launch_packet_order(a.tr, a.rays, a.log, cfg.num_sms, st)) != cudaSuccess)
+        return cuda_fail(e, "packet order");
+      a.order = a.log.order;
+    }
   } else if ((e = clear_log(out, st)) != cudaSuccess) {
     return cuda_fail(e, "clear log");
   }
@@ -652,7 +660,7 @@ neuvv_status neuvv_render_alpha(const neuvv_tree *t, const neuvv_rays *rays, flo
   if (!out || (rays->n > 0 && !out->alpha)) return fail(NEUVV_ERR_INVALID_ARG, "out->alpha is required");
   if (rays->n == 0) return NEUVV_OK;
   DeviceGuard g(t->info.device);
-  FwdArgs a;
+  FwdArgs a{};
   a.tr = dev_tree(t);
   a.rays = dev_rays(rays, time);
   a.out = DevOut{nullptr, out->alpha, out->depth, out->tau, out->nseg};
@@ -706,7 +714,7 @@ neuvv_status neuvv_render_slice(const neuvv_tree *t, const float *slice, int32_t
     return fail(NEUVV_ERR_INVALID_ARG, "slice must be a 16-byte aligned pointer");
   DeviceGuard g(t->info.device);
   cudaStream_t st = (cudaStream_t)stream;
-  FwdArgs a;
+  FwdArgs a{};
   a.tr = dev_tree(t);
   a.rays = dev_rays(rays, 0.f);
   a.out = DevOut{out->rgb, out->alpha, out->depth, out->tau, out->nseg};
@@ -1029,7 +1037,7 @@ neuvv_status neuvv_pick(const neuvv_tree *t, const neuvv_rays *rays, float time,
   if (rays->n == 0) return NEUVV_OK;
   if (!leaf) return fail(NEUVV_ERR_INVALID_ARG, "leaf is NULL");
   DeviceGuard g(t->info.device);
-  FwdArgs a;
+  FwdArgs a{};
   std::memset(&a, 0, sizeof a);
   a.tr = dev_tree(t);
   a.rays = dev_rays(rays, time);
@@ -1068,7 +1076,7 @@ neuvv_status neuvv_render_edit(const neuvv_tree *t, const neuvv_rays *rays, floa
     return fail(NEUVV_ERR_INVALID_ARG, "edits must be a 16-byte aligned pointer");
   DeviceGuard g(t->info.device);
   cudaStream_t st = (cudaStream_t)stream;
-  FwdArgs a;
+  FwdArgs a{};
   std::memset(&a, 0, sizeof a);
   a.tr = dev_tree(t);
   a.rays = dev_rays(rays, time);
@@ -1228,6 +1236,14 @@ neuvv_status neuvv_log_read(const neuvv_out *saved, int64_t n, int32_t max_out, 
   const SampleLog l = log_view(saved->log, saved->log_bytes, n);
   cudaError_t e = launch_log_read(l, (long long)n, saved->nseg, max_out, leaf, chord, count, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "log read launch");
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_tree_set_packet_order(neuvv_tree *t, int32_t order) {
+  if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
+  if (order != NEUVV_ORDER_AS_GIVEN && order != NEUVV_ORDER_BY_REGION)
+    return fail(NEUVV_ERR_INVALID_ARG, "unknown packet order %d", order);
+  t->packet.order = order;
   return NEUVV_OK;
 }
 

@@ -17,6 +17,8 @@ struct LaunchCfg {
   int dynamic_queue;  // compose and the packet forward: 1 = persistent warps pull 32-ray
                       // packets from a counter, 0 = one packet per warp of the grid
   int num_sms;        // multiprocessors of the device
+  int order;          // packet forward with a segment log: 0 = packets in ray order,
+                      // 1 = packets in the order of the region they reach first
 };
 
 // Segment log of the packet forward (device view of neuvv_out.log).  Chunks
@@ -56,6 +58,7 @@ struct FwdArgs {
   int slice_stride;
   const float *edits;        // appearance edits [n_leaves][8]: c_d (3), sigma_d, t_d, 0, 0, 0
   float edit_beta;           // colour blend weight of an active edit
+  const uint32_t *order;     // persistent warps take packets in this order (null: packet index order)
 };
 
 // Workspace of the leaf-major adjoint (owned by the tree; fac, fl and idx
@@ -176,6 +179,12 @@ cudaError_t launch_camera_rays(const CamBatch &cb, float *o, float *d, float *t,
                                cudaStream_t s);
 cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdArgs &a, const LaunchCfg &cfg,
                               cudaStream_t s);
+// Packets in region order for the forward (cfg.order == 1): each packet's key
+// is the first leaf that its first hitting ray (of lanes 0, 8, 16, 24)
+// reaches (leaf ids follow the Morton order of the leaves), counting-sorted
+// into l.order.
+cudaError_t launch_packet_order(const DevTree &tr, const DevRays &rays, const SampleLog &l, int num_sms,
+                                cudaStream_t s);
 // With adam (nullable, adam->on = 1) the per-leaf reduction also applies the
 // Adam step and clears the touched bitmap; *fused tells whether it did (the
 // caller runs the separate Adam step otherwise).

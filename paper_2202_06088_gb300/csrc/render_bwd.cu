@@ -318,6 +318,52 @@ __global__ void __launch_bounds__(kScatterThreads) key_scatter_kernel(const Samp
     if (bin[k] >= 0) l.order[cnt[bin[k]] + rank[k]] = (uint32_t)(first + (long long)k * kScatterThreads + threadIdx.x);
 }
 
+// Region key of each packet for the forward's schedule (see
+// launch_packet_order): the first leaf reached by the first of lanes 0, 8,
+// 16, 24 whose ray enters the tree, kNoKey when none does.
+__global__ void __launch_bounds__(256) packet_key_kernel(const __grid_constant__ DevTree tr, const DevRays rays,
+                                                         const SampleLog l, long long n_packets) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_packets) return;
+  uint32_t key = kNoKey;
+  for (int lane = 0; lane < 32 && key == kNoKey; lane += 8) {
+    const long long i = (p << 5) + lane;
+    if (i >= rays.n) break;
+    float o[3], d[3], t, dn[3];
+    load_ray(rays, i, o, d, t);
+    RayWalk w;
+    uint32_t leaf;
+    float t0, dt;
+    if (walk_init(tr, o, d, w, dn) && walk_next<false>(tr, nullptr, w, leaf, t0, dt)) key = leaf;
+  }
+  l.key[p] = key;
+}
+
+// Counting sort of the packets by their keys into l.order (bins of the
+// leaf id's top bits).
+static cudaError_t sort_packets_by_key(const SampleLog &l, long long n_packets, long long n_leaves, int num_sms,
+                                       cudaStream_t s) {
+  int bits = 0;
+  while (bits < 32 && ((long long)1 << bits) <= n_leaves) ++bits;
+  const int shift = bits > 12 ? bits - 12 : 0;
+  const unsigned g = (unsigned)std::min<long long>((n_packets + 255) / 256, 4LL * num_sms);
+  cudaError_t e = cudaMemsetAsync(l.bins, 0, kSortBins * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  key_hist_kernel<<<g, 256, 0, s>>>(l, n_packets, shift);
+  key_scan_kernel<<<1, 1024, 0, s>>>(l);
+  key_scatter_kernel<<<(unsigned)((n_packets + kScatterPer - 1) / kScatterPer), kScatterThreads, 0, s>>>(l, n_packets,
+                                                                                                       shift);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_packet_order(const DevTree &tr, const DevRays &rays, const SampleLog &l, int num_sms,
+                                cudaStream_t s) {
+  const long long n_packets = (rays.n + 31) >> 5;
+  if (n_packets == 0 || !l.n_chunks) return cudaSuccess;
+  packet_key_kernel<<<(unsigned)((n_packets + 255) / 256), 256, 0, s>>>(tr, rays, l, n_packets);
+  return sort_packets_by_key(l, n_packets, tr.n_leaves, num_sms, s);
+}
+
 // Packet adjoint: replays each packet's shading rounds from the forward's
 // segment log when there is one; otherwise the forward packet kernel's
 // structure (one thread per ray, walk steps and sample rounds decoupled
@@ -577,8 +623,23 @@ __device__ __forceinline__ void leaf_flush(const DevTree &tr, const LeafRecord<K
         }
 }
 
+__device__ __forceinline__ void adam_update(const AdamArgs &ad, float g, float &w, float &m, float &v) {
+  m = ad.b1 * m + (1.f - ad.b1) * g;
+  v = ad.b2 * v + (1.f - ad.b2) * g * g;
+  w -= ad.lr * (m / ad.c1) / (sqrtf(v / ad.c2) + ad.eps);
+}
+
+// With Adam (ad.on, Sec. 4.3 "Optimization"), the block's finished records
+// are not added to the gradient buffer: each warp takes rows of the block in
+// turn, a lane a 4-entry quad of the row, and applies the Adam step to the
+// leaf's FP32 master, m and v and writes its storage record (BF16 rounded,
+// FP8 re-encoded with the row's group scales from warp reductions).  A leaf
+// whose touched bit was set before the call also takes what the atomic
+// scatter left in its gradient row, which is then cleared; the caller clears
+// the touched bitmap afterwards.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant__ BwdArgs a) {
+__global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant__ BwdArgs a,
+                                                          const __grid_constant__ AdamArgs ad) {
   constexpr int NY = (DEG + 1) * (DEG + 1);
   constexpr int LEN = 2 * KP + 3 * n_hh(DEG), PITCH = reduce_pitch<KP, DEG>(), Q4 = (LEN + 3) / 4;
   extern __shared__ float acc_s[];  // [blockDim][PITCH], then one flag per thread
@@ -590,15 +651,17 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
   for (int j = 0; j < LEN; ++j) acc[j] = 0.f;
   uint32_t lo = 0, hi = 0;
   const uint32_t cap = a.gws.cap_chunks * kLogRounds * 32;  // slots of the workspace
+  bool before = false;  // Adam: touched before this kernel (the atomic scatter left a part in the row)
   if (leaf < tr.n_leaves) {
     lo = leaf > 0 ? __ldg(a.gws.off + leaf - 1) : 0u;
     hi = min(__ldg(a.gws.off + leaf), cap);
     lo = min(lo, hi);
+    if (ad.on && a.touched) before = (a.touched[leaf >> 5] >> (leaf & 31)) & 1u;
   }
-  has[threadIdx.x] = lo < hi;
+  has[threadIdx.x] = (lo < hi ? 1 : 0) | (before ? 2 : 0);
   if (lo < hi) {
     LeafRecord<KP, DEG, E> rec;
-    rec.load_sigma_gamma(tr, (uint32_t)leaf);
+    rec.load_gamma(tr, (uint32_t)leaf);
     float F[3 * NY];
 #pragma unroll
     for (int k = 0; k < 3 * NY; ++k) F[k] = 0.f;
@@ -639,220 +702,104 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
     }
     leaf_flush<KP, DEG, E>(tr, rec, u_cur, ps, pg, F, acc);
   }
-  if (a.touched) {
+  if (a.touched && !ad.on) {
     const unsigned bits = __ballot_sync(0xFFFFFFFFu, lo < hi);
     if ((threadIdx.x & 31) == 0 && bits) atomicOr(a.touched + (leaf >> 5), bits);
   }
   __syncthreads();
-  // add the block's records to the gradient buffer, 16 bytes per thread
   const int rows_here = (int)min((long long)blockDim.x, tr.n_leaves - first);
-  for (int q = threadIdx.x; q < rows_here * Q4; q += blockDim.x) {
-    const int r = q / Q4, v = q - r * Q4;
-    if (!has[r]) continue;
-    const float *src = acc_s + r * PITCH + 4 * v;
-    float4 *dst = reinterpret_cast<float4 *>(a.grad + (size_t)(first + r) * a.grad_stride) + v;
-    float4 g = *dst;
-    g.x += src[0];
-    if (4 * v + 1 < LEN) g.y += src[1];
-    if (4 * v + 2 < LEN) g.z += src[2];
-    if (4 * v + 3 < LEN) g.w += src[3];
-    *dst = g;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Per-leaf reduction by teams of four threads, optionally followed by the
-// Adam step of the leaf (K_pad <= 16).  Role 0 of a team owns the leaf's
-// w_sigma and w_gamma entries, role 1 + c the w_HH entries of colour channel
-// c, each as register accumulators (no shared memory).  Every role reads the
-// leaf's samples (the same addresses: one transaction per team); role 0 sums
-// dpre_s and dpre_g, roles 1..3 their channel's F[l,m] = sum dz[c] Y_lm, and
-// when the frame coordinate u changes each role expands its part: role 0
-// acc += dpre_s a(u) | dpre_g b(u), role 1 + c acc[n,l,m] += R_nl(gamma(u)) F.
-// Then, without Adam, each role adds its part to the leaf's gradient record
-// and role 0 sets the touched bit.  With Adam (Sec. 4.3 "Optimization"), the
-// leaf's gradient -- this call's sums plus what the atomic scatter left in
-// its row when its touched bit was already set -- updates the FP32 master,
-// m and v and the storage record in place; the row is cleared, and the
-// caller clears the touched bitmap afterwards.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void adam_update(const AdamArgs &ad, float g, float &w, float &m, float &v) {
-  m = ad.b1 * m + (1.f - ad.b1) * g;
-  v = ad.b2 * v + (1.f - ad.b2) * g * g;
-  w -= ad.lr * (m / ad.c1) / (sqrtf(v / ad.c2) + ad.eps);
-}
-
-template <int KP, int DEG, typename E>
-__device__ __forceinline__ void team_flush(const DevTree &tr, int role, const LeafRecord<KP, DEG, E> &rec, float u,
-                                           float ps, float pg, const float *F, float *acc) {
-  constexpr int NH = n_hh(DEG);
-  const float umax = (float)(tr.T - 1);
-  u = fminf(fmaxf(u, 0.f), umax);
-  const int f0 = min((int)floorf(u), tr.T - 1), f1 = min(f0 + 1, tr.T - 1);
-  const float fr = u - (float)f0;
-  const float *B0 = tr.B + (size_t)f0 * KP, *B1 = tr.B + (size_t)f1 * KP;
-  if (role == 0) {
-    const float *A0 = tr.A + (size_t)f0 * KP, *A1 = tr.A + (size_t)f1 * KP;
-#pragma unroll
-    for (int k = 0; k < KP; ++k) {
-      acc[k] = fmaf(ps, (1.f - fr) * __ldg(A0 + k) + fr * __ldg(A1 + k), acc[k]);
-      acc[KP + k] = fmaf(pg, (1.f - fr) * __ldg(B0 + k) + fr * __ldg(B1 + k), acc[KP + k]);
-    }
-  } else {
-    float q4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < KP; ++k)
-      q4[k & 3] = fmaf((1.f - fr) * __ldg(B0 + k) + fr * __ldg(B1 + k), rec.gam(k), q4[k & 3]);
-    const float pgam = ((q4[0] + q4[1]) + (q4[2] + q4[3])) * rec.scale_gamma();
-    float sg, cg, R[(DEG + 1) * (DEG + 2) / 2];
-    sincospif(sigmoidf_fast(pgam), &sg, &cg);
-    hh_radial<DEG, false>(cg, sg, tr.hh_norm, R, nullptr);
-    int j = 0;
-#pragma unroll
-    for (int n = 0; n <= DEG; ++n)
-#pragma unroll
-      for (int l = 0; l <= n; ++l)
-#pragma unroll
-        for (int m = -l; m <= l; ++m) {
-          acc[j] = fmaf(R[radial_index(n, l)], F[l * l + l + m], acc[j]);
-          ++j;
-        }
-    static_assert(NH <= 2 * KP || NH <= 32, "w_HH of one channel must fit a role's accumulators");
-  }
-}
-
-constexpr int kTeamBlock = 256;
-
-template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(kTeamBlock) leaf_team_kernel(const __grid_constant__ BwdArgs a,
-                                                               const __grid_constant__ AdamArgs ad) {
-  constexpr int NY = (DEG + 1) * (DEG + 1), NH = n_hh(DEG);
-  constexpr int NA = 2 * KP > NH ? 2 * KP : NH;
-  const DevTree &tr = a.tr;
-  const int role = threadIdx.x & 3, lane = threadIdx.x & 31;
-  const long long leaf = ((long long)blockIdx.x * kTeamBlock + threadIdx.x) >> 2;
-  const bool in = leaf < tr.n_leaves;
-  const uint32_t cap = a.gws.cap_chunks * kLogRounds * 32;  // slots of the workspace
-  uint32_t lo = 0, hi = 0;
-  bool before = false;  // touched before this kernel: the atomic scatter left a part in the row
-  if (in) {
-    lo = leaf > 0 ? __ldg(a.gws.off + leaf - 1) : 0u;
-    hi = min(__ldg(a.gws.off + leaf), cap);
-    lo = min(lo, hi);
-    if (ad.on && a.touched) before = (a.touched[leaf >> 5] >> (leaf & 31)) & 1u;
-  }
-  float acc[NA];
-#pragma unroll
-  for (int j = 0; j < NA; ++j) acc[j] = 0.f;
-  if (lo < hi) {
-    LeafRecord<KP, DEG, E> rec;
-    rec.load_gamma(tr, (uint32_t)leaf);
-    float F[NY];
-#pragma unroll
-    for (int k = 0; k < NY; ++k) F[k] = 0.f;
-    float ps = 0.f, pg = 0.f, u_cur = 0.f;
-    float4 n0, n1, n2;  // the record of the sample after the current one
-    {
-      const float4 *f = a.gws.fac + 3 * (size_t)min(__ldg(a.gws.idx + lo), cap - 1);
-      n0 = __ldg(f);
-      n1 = __ldg(f + 1);
-      n2 = __ldg(f + 2);
-    }
-    uint32_t nidx = lo + 1 < hi ? __ldg(a.gws.idx + lo + 1) : 0u;
-    for (uint32_t p = lo; p < hi; ++p) {
-      const float4 f0 = n0, f1 = n1, f2 = n2;
-      if (p + 1 < hi) {
-        const float4 *f = a.gws.fac + 3 * (size_t)min(nidx, cap - 1);
-        n0 = __ldg(f);
-        n1 = __ldg(f + 1);
-        n2 = __ldg(f + 2);
-        if (p + 2 < hi) nidx = __ldg(a.gws.idx + p + 2);
-      }
-      if (p > lo && f1.y != u_cur) {  // a new frame coordinate: expand the finished group
-        team_flush<KP, DEG, E>(tr, role, rec, u_cur, ps, pg, F, acc);
-#pragma unroll
-        for (int k = 0; k < NY; ++k) F[k] = 0.f;
-        ps = pg = 0.f;
-      }
-      u_cur = f1.y;
-      ps += f0.x;
-      pg += f0.y;
-      if (role > 0) {
-        const float dz = role == 1 ? f0.z : (role == 2 ? f0.w : f1.x);
-        const float dn[3] = {f1.z, f1.w, f2.x};
-        float Y[NY];
-        sh_real<DEG>(dn, Y);
-#pragma unroll
-        for (int k = 0; k < NY; ++k) F[k] = fmaf(dz, Y[k], F[k]);
-      }
-    }
-    team_flush<KP, DEG, E>(tr, role, rec, u_cur, ps, pg, F, acc);
-  }
-  // this role's entries of the leaf's record: [first, first + len)
-  const int first = role == 0 ? 0 : 2 * KP + (role - 1) * NH;
-  const int len = role == 0 ? 2 * KP : NH;
-  const size_t row = (size_t)leaf * a.grad_stride + first;
   if (!ad.on) {
-    if (lo < hi) {
-#pragma unroll
-      for (int j = 0; j < NA; ++j)
-        if (j < len) a.grad[row + j] += acc[j];
-    }
-    if (a.touched) {
-      const unsigned bits = __ballot_sync(0xFFFFFFFFu, role == 0 && lo < hi);
-      // the warp's 8 leaves are consecutive and 8-aligned: one byte of a touched word
-      unsigned byte = 0;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) byte |= ((bits >> (4 * k)) & 1u) << k;
-      const long long leaf0 = ((long long)blockIdx.x * kTeamBlock + (threadIdx.x & ~31)) >> 2;
-      if (lane == 0 && byte) atomicOr(a.touched + (leaf0 >> 5), byte << (leaf0 & 31));
+    // add the block's records to the gradient buffer, 16 bytes per thread
+    for (int q = threadIdx.x; q < rows_here * Q4; q += blockDim.x) {
+      const int r = q / Q4, v = q - r * Q4;
+      if (!has[r]) continue;
+      const float *src = acc_s + r * PITCH + 4 * v;
+      float4 *dst = reinterpret_cast<float4 *>(a.grad + (size_t)(first + r) * a.grad_stride) + v;
+      float4 g = *dst;
+      g.x += src[0];
+      if (4 * v + 1 < LEN) g.y += src[1];
+      if (4 * v + 2 < LEN) g.z += src[2];
+      if (4 * v + 3 < LEN) g.w += src[3];
+      *dst = g;
     }
     return;
   }
-  const bool active = in && (lo < hi || before);
-  float mx = 0.f, mx_g = 0.f;  // FP8: largest magnitude of the role's group(s)
-  if (active) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = threadIdx.x >> 5; r < rows_here; r += nw) {
+    const int h = has[r];
+    if (!h) continue;  // the same for the whole warp
+    const size_t row = (size_t)(first + r) * a.grad_stride;
+    float wq[(Q4 + 31) / 32][4];
+    float mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;  // FP8: largest magnitudes of w_sigma, w_gamma, w_hh
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      if (j >= len) continue;
-      float g = acc[j];
-      if (before) {
-        g += a.grad[row + j];
-        a.grad[row + j] = 0.f;
+    for (int k = 0; k < (Q4 + 31) / 32; ++k) {
+      const int q = lane + 32 * k;
+      if (q >= Q4) continue;
+      const float *src = acc_s + r * PITCH + 4 * q;
+      float4 g = make_float4(src[0], 4 * q + 1 < LEN ? src[1] : 0.f, 4 * q + 2 < LEN ? src[2] : 0.f,
+                             4 * q + 3 < LEN ? src[3] : 0.f);
+      float4 *gp = reinterpret_cast<float4 *>(a.grad + row) + q;
+      if (h & 2) {
+        const float4 x = *gp;
+        g.x += x.x;
+        g.y += x.y;
+        g.z += x.z;
+        g.w += x.w;
+        *gp = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      float w = ad.master[row + j], m = ad.m[row + j], v = ad.v[row + j];
-      adam_update(ad, g, w, m, v);
-      ad.master[row + j] = w;
-      ad.m[row + j] = m;
-      ad.v[row + j] = v;
-      acc[j] = w;  // the updated weight, for the storage record
-      if (role == 0 && j >= KP) mx_g = fmaxf(mx_g, fabsf(w));
-      else mx = fmaxf(mx, fabsf(w));
-    }
-    if (ad.dt == kBF16) {
-      unsigned short *st = static_cast<unsigned short *>(ad.storage) + (size_t)leaf * ad.storage_stride + first;
+      float4 w = reinterpret_cast<const float4 *>(ad.master + row)[q];
+      float4 m = reinterpret_cast<const float4 *>(ad.m + row)[q];
+      float4 v = reinterpret_cast<const float4 *>(ad.v + row)[q];
+      float gs[4] = {g.x, g.y, g.z, g.w}, ws[4] = {w.x, w.y, w.z, w.w};
+      float ms[4] = {m.x, m.y, m.z, m.w}, vs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int j = 0; j < NA; ++j)
-        if (j < len) st[j] = f32_to_bf16_rne(acc[j]);
-    }
-  }
-  if (ad.dt == kFP8) {
-    // group scales: w_sigma and w_gamma in role 0, w_HH across roles 1..3
-    float mh = role == 0 ? 0.f : mx;
-    mh = fmaxf(mh, __shfl_xor_sync(0xFFFFFFFFu, mh, 1));
-    mh = fmaxf(mh, __shfl_xor_sync(0xFFFFFFFFu, mh, 2));
-    if (active) {
-      unsigned char *rec = static_cast<unsigned char *>(ad.storage) + (size_t)leaf * ad.storage_stride;
-      const int ps_ = fp8_scale_exp(mx), pg_ = fp8_scale_exp(mx_g), ph_ = fp8_scale_exp(mh);
-      if (role == 0)
-        *reinterpret_cast<uint4 *>(rec) = make_uint4(__float_as_uint(ldexpf(1.f, ps_)),
-                                                     __float_as_uint(ldexpf(1.f, pg_)),
-                                                     __float_as_uint(ldexpf(1.f, ph_)), 0u);
+      for (int c = 0; c < 4; ++c) {
+        const int j = 4 * q + c;
+        if (j >= LEN) continue;  // padding stays zero
+        adam_update(ad, gs[c], ws[c], ms[c], vs[c]);
+        const float aw = fabsf(ws[c]);
+        if (j < KP) mx0 = fmaxf(mx0, aw);
+        else if (j < 2 * KP) mx1 = fmaxf(mx1, aw);
+        else mx2 = fmaxf(mx2, aw);
+      }
+      reinterpret_cast<float4 *>(ad.master + row)[q] = make_float4(ws[0], ws[1], ws[2], ws[3]);
+      reinterpret_cast<float4 *>(ad.m + row)[q] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+      reinterpret_cast<float4 *>(ad.v + row)[q] = make_float4(vs[0], vs[1], vs[2], vs[3]);
 #pragma unroll
-      for (int j = 0; j < NA; ++j) {
-        if (j >= len) continue;
-        const int p = role == 0 ? (j < KP ? ps_ : pg_) : ph_;
-        rec[16 + first + j] = (unsigned char)__nv_cvt_float_to_fp8(ldexpf(acc[j], -p), __NV_SATFINITE, __NV_E4M3);
+      for (int c = 0; c < 4; ++c) wq[k][c] = ws[c];
+      if (ad.dt == kBF16) {
+        unsigned short *st = static_cast<unsigned short *>(ad.storage) + (size_t)(first + r) * ad.storage_stride;
+        const unsigned int lo16 = f32_to_bf16_rne(ws[0]) | ((unsigned int)f32_to_bf16_rne(ws[1]) << 16);
+        const unsigned int hi16 = f32_to_bf16_rne(ws[2]) | ((unsigned int)f32_to_bf16_rne(ws[3]) << 16);
+        *reinterpret_cast<uint2 *>(st + 4 * q) = make_uint2(lo16, hi16);
+      }
+    }
+    if (ad.dt == kFP8) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mx0 = fmaxf(mx0, __shfl_xor_sync(0xFFFFFFFFu, mx0, o));
+        mx1 = fmaxf(mx1, __shfl_xor_sync(0xFFFFFFFFu, mx1, o));
+        mx2 = fmaxf(mx2, __shfl_xor_sync(0xFFFFFFFFu, mx2, o));
+      }
+      const int p[3] = {fp8_scale_exp(mx0), fp8_scale_exp(mx1), fp8_scale_exp(mx2)};
+      unsigned char *rec = static_cast<unsigned char *>(ad.storage) + (size_t)(first + r) * ad.storage_stride;
+      if (lane == 0)
+        *reinterpret_cast<uint4 *>(rec) = make_uint4(__float_as_uint(ldexpf(1.f, p[0])),
+                                                     __float_as_uint(ldexpf(1.f, p[1])),
+                                                     __float_as_uint(ldexpf(1.f, p[2])), 0u);
+#pragma unroll
+      for (int k = 0; k < (Q4 + 31) / 32; ++k) {
+        const int q = lane + 32 * k;
+        if (q >= Q4) continue;
+        unsigned int word = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = 4 * q + c;
+          if (j >= LEN) continue;
+          const int pe = j < KP ? p[0] : (j < 2 * KP ? p[1] : p[2]);
+          word |= (unsigned int)__nv_cvt_float_to_fp8(ldexpf(wq[k][c], -pe), __NV_SATFINITE, __NV_E4M3) << (8 * c);
+        }
+        *reinterpret_cast<unsigned int *>(rec + 16 + 4 * q) = word;
       }
     }
   }
@@ -881,18 +828,8 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
     if (a.log.n_chunks) {
       // packets in key order (a permutation whatever the log holds; the
       // adjoint uses it only when the log belongs to these rays)
-      const long long n_packets = (a.rays.n + 31) >> 5;
-      int bits = 0;
-      while (bits < 32 && ((long long)1 << bits) <= a.tr.n_leaves) ++bits;
-      const int shift = bits > 12 ? bits - 12 : 0;
-      const unsigned g = (unsigned)std::min<long long>((n_packets + 255) / 256, 4LL * cfg.num_sms);
-      cudaError_t e = cudaMemsetAsync(a.log.bins, 0, kSortBins * sizeof(uint32_t), s);
+      cudaError_t e = sort_packets_by_key(a.log, (a.rays.n + 31) >> 5, a.tr.n_leaves, cfg.num_sms, s);
       if (e != cudaSuccess) return e;
-      key_hist_kernel<<<g, 256, 0, s>>>(a.log, n_packets, shift);
-      key_scan_kernel<<<1, 1024, 0, s>>>(a.log);
-      key_scatter_kernel<<<(unsigned)((n_packets + kScatterPer - 1) / kScatterPer), kScatterThreads, 0, s>>>(
-          a.log, n_packets, shift);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const bool gather = a.log.n_chunks && a.gws.cap_chunks;
     const long long nl = a.tr.n_leaves;
@@ -911,21 +848,8 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
       const long long slots = (long long)std::min(a.log.n_chunks, a.gws.cap_chunks) * kLogRounds * 32;
       slot_scatter_kernel<<<(unsigned)std::min<long long>((slots + 255) / 256, 16LL * cfg.num_sms), 256, 0, s>>>(
           a.gws, a.log, nl);
-      if constexpr (KP <= 16) {
-        // teams of four threads per leaf, with the Adam step when asked
-        AdamArgs ad{};
-        if (adam && adam->on) ad = *adam;
-        const long long blocks_t = (nl * 4 + kTeamBlock - 1) / kTeamBlock;
-        leaf_team_kernel<KP, DEG, E><<<(unsigned)blocks_t, kTeamBlock, 0, s>>>(a, ad);
-        if (ad.on) {
-          cudaError_t e = cudaGetLastError();
-          if (e != cudaSuccess) return e;
-          if (a.touched && (e = cudaMemsetAsync(a.touched, 0, (size_t)((nl + 31) / 32) * 4, s)) != cudaSuccess)
-            return e;
-          if (fused) *fused = true;
-        }
-        return cudaGetLastError();
-      }
+      AdamArgs ad{};
+      if (adam && adam->on) ad = *adam;
       constexpr int kReduceBlock = 64;
       const size_t rsm = reduce_smem_bytes<KP, DEG>(kReduceBlock);
       if (rsm > 48 * 1024) {
@@ -933,7 +857,15 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
         if (e != cudaSuccess) return e;
       }
-      leaf_reduce_kernel<KP, DEG, E><<<(unsigned)((nl + kReduceBlock - 1) / kReduceBlock), kReduceBlock, rsm, s>>>(a);
+      leaf_reduce_kernel<KP, DEG, E><<<(unsigned)((nl + kReduceBlock - 1) / kReduceBlock), kReduceBlock, rsm, s>>>(a,
+                                                                                                                 ad);
+      if (ad.on) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (a.touched && (e = cudaMemsetAsync(a.touched, 0, (size_t)((nl + 31) / 32) * 4, s)) != cudaSuccess)
+          return e;
+        if (fused) *fused = true;
+      }
     }
   }
   return cudaGetLastError();

@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_ker
     pk = (long long)__shfl_sync(0xFFFFFFFFu, q, 0);
   }
   while (pk < n_packets) {
+    if (a.order) pk = (long long)min(__ldg(a.order + pk), (uint32_t)(n_packets - 1));
     const long long i = (pk << 5) + lane;
     // lanes past the end sit the packet out; the others stay to its end
     const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);

@@ -136,6 +136,8 @@ typedef struct {
   int32_t packet_ready;     /* packet kernels: lanes holding a queued segment that start a
                                shading round (all three set by neuvv_autotune) */
   int32_t packet_order;     /* packet forward with a segment log: NEUVV_ORDER_* (neuvv_autotune) */
+  int32_t packet_tiles;     /* pixel tile of a 32-ray packet of camera rays, NEUVV_TILES_*
+                               (neuvv_autotune_tiles; default 8x4) */
 } neuvv_tree_info;
 
 /* The order in which the packet forward runs its 32-ray packets when the
@@ -144,9 +146,16 @@ typedef struct {
  * finds the first leaf each packet reaches and the packets run sorted by
  * that leaf's region (leaf ids follow the Morton order of the leaves), so
  * packets of different views that see the same part of the tree run
- * together and share its records in L2. */
+ * together and share its records in L2.  BY_RAY: the packets themselves are
+ * re-formed: the rays are sorted (stable) by a bucket of their direction and
+ * the region of the first leaf they reach, so a batch of rays from many
+ * views and times in any order gets packets of rays that cross the same
+ * cells; outputs stay in the caller's order, and the order is kept in the
+ * log for the adjoint (it needs about 17 bytes per ray of the log as scratch,
+ * else the rays stay as given). */
 #define NEUVV_ORDER_AS_GIVEN 0
 #define NEUVV_ORDER_BY_REGION 1
+#define NEUVV_ORDER_BY_RAY 2
 
 /* Rays, device SoA float32 arrays of length n.  t may be NULL: then the
  * scalar time argument of the call is used for every ray. */
@@ -420,6 +429,12 @@ neuvv_status neuvv_gaussian_blur(const float *in, float *out, int32_t width, int
 neuvv_status neuvv_render_alpha(const neuvv_tree *tree, const neuvv_rays *rays, float t, const neuvv_render_opts *opts,
                                 neuvv_out *out, neuvv_stream stream);
 
+/* Pixel order of neuvv_camera_rays: row-major, or tiles of 32 pixels. */
+#define NEUVV_TILES_NONE 0
+#define NEUVV_TILES_8X4 1
+#define NEUVV_TILES_4X8 2
+#define NEUVV_TILES_16X2 3
+
 /* A pinhole camera (the viewers' and the light's): ray through pixel (px, py)
  * (pixel centres at +0.5) from eye along forward + sx right + sy up,
  * sx = (2 (px+0.5)/width - 1) tan(fov_y/2) width/height,
@@ -436,10 +451,11 @@ typedef neuvv_camera neuvv_light;
  * times: host [n_cams], each in [0, 1].  Camera c owns rays
  * [off_c, off_c + width_c * height_c), off_c the sum of the earlier cameras'
  * pixel counts; n must equal the total.  Ray j of a camera goes through pixel
- * j in row-major order when tiled == 0; when tiled != 0 the pixels are listed
- * by 8x4 tiles (tiles in row-major order, pixels of a tile row-major, the
- * tiles at the right and bottom edges narrower or shorter), so a 32-ray packet
- * covers one tile.  Writes, all device and caller-owned: origins [3][n] (the
+ * j in row-major order when tiled == NEUVV_TILES_NONE; otherwise the pixels
+ * are listed by tiles of 32 pixels, 8x4, 4x8 or 16x2 (NEUVV_TILES_*: tiles in
+ * row-major order, pixels of a tile row-major, the tiles at the right and
+ * bottom edges narrower or shorter), so a 32-ray packet covers one tile; any
+ * other value is INVALID_ARG.  Writes, all device and caller-owned: origins [3][n] (the
  * eye), dirs [3][n] (unit: the direction above divided by its FP32 norm),
  * times_out [n] (times[c]) and, when pixel_of_ray is not NULL, pixel_of_ray
  * [n] (py * width + px of the ray's own camera).  Errors: NULL pointers, a
@@ -505,10 +521,44 @@ neuvv_status neuvv_tree_set_packet_order(neuvv_tree *tree, int32_t order);
  * lanes with a queued segment that start a shading round).  Host only. */
 neuvv_status neuvv_tree_set_launch(neuvv_tree *tree, int32_t block, int32_t queue, int32_t ready);
 
-/* Picks the block size, queue and ready count of the packet kernels by timing candidates on a
- * sample of rays (the first min(n, 2^20)); the choice is stored in the tree.
- * Synchronous.  best_ms (nullable) receives the best forward time. */
+/* Picks the packet kernels' launch -- block size, queue, ready count and the
+ * forward's packet order (NEUVV_ORDER_*) -- by timing candidates with the
+ * packet forward (with a segment log of 64 bytes per ray) on a sample of
+ * rays (the first min(n, 2^20)); the fastest is stored in the tree.  The
+ * choice is kept for the life of the process under the tree's shape (depth,
+ * node and leaf counts, K_pad, degree, storage type, bricks), the device and
+ * its multiprocessor count and the sample size (power of two): a later call
+ * for a tree of the same key reuses it without timing anything.
+ * Synchronous (allocates and frees its sample outputs when it times).
+ * best_ms (nullable) receives the best forward time. */
 neuvv_status neuvv_autotune(neuvv_tree *tree, const neuvv_rays *sample, float t, float *best_ms, neuvv_stream stream);
+
+/* Picks the pixel tile of the camera rays' packets (NEUVV_TILES_8X4, _4X8 or
+ * _16X2) for this tree: generates the rays of the given cameras (host
+ * [n_cams], 1..32, at most 2^31 pixels in all; times host [n_cams] in
+ * [0, 1]) in each tiling with neuvv_camera_rays and times the packet
+ * forward (tree's launch, segment log of 64 bytes per ray) on them; the
+ * fastest is stored in the tree (neuvv_tree_info.packet_tiles) and written
+ * to *best_tiles.  The caller generates its rays with that tiling.
+ * Synchronous; allocates and frees its buffers.  best_ms nullable. */
+neuvv_status neuvv_autotune_tiles(neuvv_tree *tree, const neuvv_camera *cams, const float *times, int32_t n_cams,
+                                  int32_t *best_tiles, float *best_ms, neuvv_stream stream);
+
+/* One candidate of neuvv_autotune and its best time of three. */
+typedef struct {
+  int32_t block, queue, ready, order;
+  float ms;
+} neuvv_tune_entry;
+
+/* The candidates the tree's last neuvv_autotune timed (or the kept table it
+ * reused), in timing order: up to max_entries copied to entries (host),
+ * their number to *n_entries; *from_cache (nullable) is 1 when that call
+ * reused a kept choice.  Host only. */
+neuvv_status neuvv_autotune_report(const neuvv_tree *tree, neuvv_tune_entry *entries, int32_t max_entries,
+                                   int32_t *n_entries, int32_t *from_cache);
+
+/* Forgets every choice neuvv_autotune kept (the next call times again). */
+neuvv_status neuvv_autotune_clear_cache(void);
 
 #ifdef __cplusplus
 }

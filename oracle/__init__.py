@@ -221,17 +221,24 @@ def trace(tree, rays, max_out: int = 64, nthreads: int | None = None, otree: Ora
 
 
 def render_grad(tree, rays, grad_rgb, grad_alpha=None, t_stop: float = 1e-4, act: str = "sigmoid",
-                nthreads: int | None = None, otree: OracleTree | None = None) -> dict:
+                nthreads: int | None = None, otree: OracleTree | None = None, out: dict | None = None) -> dict:
     """Analytic gradient of L(C, alpha) w.r.t. (w_sigma, w_gamma, w_hh), given
-    dL/dC and dL/dalpha per ray (Sec. 4.3 "Optimization").  Planes as inputs."""
+    dL/dC and dL/dalpha per ray (Sec. 4.3 "Optimization").  Planes as inputs.
+    With ``out`` (float64 planes of the returned shapes) the gradient is
+    added to those arrays instead of to fresh zeroed ones."""
     ot = otree or OracleTree(tree)
     o, d, t = _rays64(rays)
     n = t.size
     g = np.ascontiguousarray(grad_rgb, np.float64).reshape(n, 3)
     ga = None if grad_alpha is None else np.ascontiguousarray(grad_alpha, np.float64)
-    gs = np.zeros((ot.K, ot.n_leaves))
-    gg = np.zeros((ot.K, ot.n_leaves))
-    gh = np.zeros((3, ot.N_h, ot.n_leaves))
+    if out is None:
+        gs = np.zeros((ot.K, ot.n_leaves))
+        gg = np.zeros((ot.K, ot.n_leaves))
+        gh = np.zeros((3, ot.N_h, ot.n_leaves))
+    else:
+        gs, gg, gh = out["w_sigma"], out["w_gamma"], out["w_hh"]
+        for a, shape in ((gs, (ot.K, ot.n_leaves)), (gg, (ot.K, ot.n_leaves)), (gh, (3, ot.N_h, ot.n_leaves))):
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == shape
     op = _opts(t_stop, act)
     lib().or_render_grad(ctypes.byref(ot.struct), ctypes.byref(op), n, _ptr(o), _ptr(d), _ptr(t), _ptr(g),
                          None if ga is None else _ptr(ga), _ptr(gs), _ptr(gg), _ptr(gh), nthreads or default_threads())
@@ -348,23 +355,25 @@ def render_edit(tree, rays, edits, beta: float = 1.0, t_stop: float = 1e-4, act:
     return out
 
 
-def camera_rays(cam, t: float, tiled: bool = True) -> dict:
+def camera_rays(cam, t: float, tiled=True) -> dict:
     """Pinhole camera rays through pixel centres (Sec. 4.3 "Rendering": one
     ray per pixel of a view).  cam: eye, orthonormal right/up/forward,
     fov_y_deg, width, height.  Pixel (px, py) looks along
     forward + sx right + sy up with sx = (2 (px + 1/2) / W - 1) tan(fov_y / 2) W / H
     and sy = (1 - 2 (py + 1/2) / H) tan(fov_y / 2), normalised.  The rays list
-    the pixels row-major, or (tiled) tile by tile: 8 x 4 tiles in row-major
-    order of the tiles, the pixels of each tile row-major, the tiles at the
-    right and bottom edges cut to the image.  Returns origins and dirs
-    [3, n], times [n] and the row-major pixel of each ray."""
+    the pixels row-major, or (tiled) tile by tile: tw x th tiles (tiled =
+    True: 8 x 4; or a (tw, th) pair) in row-major order of the tiles, the
+    pixels of each tile row-major, the tiles at the right and bottom edges
+    cut to the image.  Returns origins and dirs [3, n], times [n] and the
+    row-major pixel of each ray."""
     W, H = int(cam.width), int(cam.height)
-    if tiled:
+    if tiled is not False and tiled is not None:
+        tw, th_ = (8, 4) if tiled is True else (int(tiled[0]), int(tiled[1]))
         parts = []
-        for y0 in range(0, H, 4):
-            ys = np.arange(y0, min(y0 + 4, H))
-            for x0 in range(0, W, 8):
-                xs = np.arange(x0, min(x0 + 8, W))
+        for y0 in range(0, H, th_):
+            ys = np.arange(y0, min(y0 + th_, H))
+            for x0 in range(0, W, tw):
+                xs = np.arange(x0, min(x0 + tw, W))
                 parts.append((ys[:, None] * W + xs[None, :]).ravel())
         pix = np.concatenate(parts)
     else:

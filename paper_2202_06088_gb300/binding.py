@@ -26,6 +26,8 @@ F32, BF16, FP8 = 0, 1, 2
 # device status bits (neuvv_tree_status)
 STATUS_SEGMENT_CAP, STATUS_BAD_INDEX, STATUS_TIMEOUT = 0x1, 0x2, 0x4
 ORDER_AS_GIVEN, ORDER_BY_REGION = 0, 1
+TILES_NONE, TILES_8X4, TILES_4X8, TILES_16X2 = 0, 1, 2, 3
+TILE_SHAPES = {TILES_8X4: (8, 4), TILES_4X8: (4, 8), TILES_16X2: (16, 2)}
 _DTYPES = {"f32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16, "fp8": FP8, "fp8_e4m3": FP8}
 _ACT = {"sigmoid": 0, "identity": 1}
 _KERNEL = {"auto": 0, "plain": 1, "packet": 2}
@@ -51,7 +53,8 @@ class TreeInfo(ctypes.Structure):
                 ("rec_stride", ctypes.c_int32), ("rec_stride_f32", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("device", ctypes.c_int32), ("packet_block", ctypes.c_int32), ("packet_queue", ctypes.c_int32),
-                ("packet_ready", ctypes.c_int32), ("packet_order", ctypes.c_int32)]
+                ("packet_ready", ctypes.c_int32), ("packet_order", ctypes.c_int32),
+                ("packet_tiles", ctypes.c_int32)]
 
 
 class RaysC(ctypes.Structure):
@@ -66,6 +69,11 @@ class OutC(ctypes.Structure):
                 ("log_bytes", ctypes.c_int64)]
 
 
+class TuneEntryC(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("queue", ctypes.c_int32), ("ready", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
 class OptsC(ctypes.Structure):
     _fields_ = [("t_stop", ctypes.c_float), ("color_act", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("compose_mode", ctypes.c_int32)]
@@ -78,7 +86,8 @@ EXPORTS = ["neuvv_last_error", "neuvv_tree_create", "neuvv_tree_destroy", "neuvv
            "neuvv_gaussian_blur", "neuvv_spotlight", "neuvv_pick", "neuvv_paint", "neuvv_render_edit",
            "neuvv_camera_rays", "neuvv_render_alpha", "neuvv_tree_reserve_adjoint", "neuvv_tree_set_limits",
            "neuvv_log_read", "neuvv_tree_set_records", "neuvv_render_backward_adam",
-           "neuvv_tree_set_packet_order"]
+           "neuvv_tree_set_packet_order", "neuvv_autotune_report", "neuvv_autotune_clear_cache",
+           "neuvv_autotune_tiles"]
 
 
 def library_path() -> str:
@@ -125,6 +134,9 @@ def lib(build_if_missing: bool = True):
                 "neuvv_tree_set_records": [p, p, p],
                 "neuvv_render_backward_adam": [p, p, f, p, p, p, p, p, p, f, f, f, f, i32, p],
                 "neuvv_tree_set_packet_order": [p, i32],
+                "neuvv_autotune_report": [p, p, i32, p, p],
+                "neuvv_autotune_clear_cache": [],
+                "neuvv_autotune_tiles": [p, p, p, i32, p, p, p],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -427,8 +439,8 @@ def neuvv_camera_rays(cams, times, tiled: bool = True, out: DeviceRays | None = 
                       pixel_of_ray: torch.Tensor | None = None, device="cuda") -> DeviceRays:
     """Rays through the pixel centres of each camera (any objects with eye,
     right, up, forward, fov_y_deg, width, height), generated on the device:
-    camera c's rays follow camera c-1's, in 8x4 tile order when tiled, at time
-    times[c].  out (optional): DeviceRays of the total size to write into;
+    camera c's rays follow camera c-1's, at time times[c]; tiled: False
+    (row-major), True or TILES_8X4, TILES_4X8, TILES_16X2 (tiles of 32 pixels).  out (optional): DeviceRays of the total size to write into;
     pixel_of_ray (optional, int32 [n]) receives each ray's row-major pixel."""
     cams, times = list(cams), [float(x) for x in times]
     if len(cams) != len(times):
@@ -447,7 +459,8 @@ def neuvv_camera_rays(cams, times, tiled: bool = True, out: DeviceRays | None = 
         m = sum(int(c.width) * int(c.height) for c in part)
         o, d, t = out.o[:, done:done + m].contiguous(), out.d[:, done:done + m].contiguous(), out.t[done:done + m]
         pix = None if pixel_of_ray is None else pixel_of_ray[done:done + m]
-        _check(lib().neuvv_camera_rays(arr, ts, len(part), int(bool(tiled)), _ptr(o), _ptr(d), _ptr(t),
+        mode = int(tiled) if not isinstance(tiled, bool) else int(tiled)
+        _check(lib().neuvv_camera_rays(arr, ts, len(part), mode, _ptr(o), _ptr(d), _ptr(t),
                                        None if pix is None else _ptr(pix), m, _stream()))
         if o.data_ptr() != out.o[:, done:done + m].data_ptr():  # a chunk of several: copy the [3][m] block back
             out.o[:, done:done + m].copy_(o)
@@ -598,6 +611,34 @@ def neuvv_autotune(tree: Tree, rays: DeviceRays, t: float = 0.0) -> float:
     _check(lib().neuvv_autotune(tree.handle, ctypes.byref(rc), float(t), ctypes.byref(ms), _stream()))
     tree.refresh_info()
     return float(ms.value)
+
+
+def neuvv_autotune_report(tree: Tree) -> tuple:
+    """(candidates as dicts in timing order, whether the tree's last
+    neuvv_autotune reused a kept choice)."""
+    n, cached = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().neuvv_autotune_report(tree.handle, None, 0, ctypes.byref(n), None))
+    buf = (TuneEntryC * max(n.value, 1))()
+    _check(lib().neuvv_autotune_report(tree.handle, buf, n.value, ctypes.byref(n), ctypes.byref(cached)))
+    rows = [{"block": e.block, "queue": e.queue, "ready": e.ready, "order": e.order, "ms": e.ms}
+            for e in buf[:n.value]]
+    return rows, bool(cached.value)
+
+
+def neuvv_autotune_tiles(tree: Tree, cams, times) -> int:
+    """The fastest pixel tile (TILES_*) of camera packets for this tree, timed
+    on the rays of the given cameras (at most 32); stored in the tree."""
+    cams, times = list(cams), [float(x) for x in times]
+    arr = (LightC * len(cams))(*[light_of(c) for c in cams])
+    ts = (ctypes.c_float * len(cams))(*times)
+    best, ms = ctypes.c_int32(), ctypes.c_float()
+    _check(lib().neuvv_autotune_tiles(tree.handle, arr, ts, len(cams), ctypes.byref(best), ctypes.byref(ms), _stream()))
+    tree.refresh_info()
+    return int(best.value)
+
+
+def neuvv_autotune_clear_cache() -> None:
+    _check(lib().neuvv_autotune_clear_cache())
 
 
 class VOctreeRender(torch.autograd.Function):

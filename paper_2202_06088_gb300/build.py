@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libneuvv.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["abi.cu", "render_fwd.cu", "render_bwd.cu", "compose.cu", "optim.cu", "lighting.cu", "camera.cu"]
+SOURCES = ["abi.cu", "render_fwd.cu", "render_bwd.cu", "compose.cu", "optim.cu", "lighting.cu", "camera.cu",
+           "order.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -95,6 +96,9 @@ struct neuvv_tree {
   LaunchCfg compose{128, 1, 1, 0, 1, 0};
   int step_cap = 0;             // walk steps per ray (0: 3 * 2^depth + 8)
   int wait_polls = 1 << 22;     // polls of a bounded device wait
+  std::vector<neuvv_tune_entry> tune_table;  // candidates of the last neuvv_autotune and their times
+  int tune_cached = 0;                       // 1: that call reused an earlier choice
+  int packet_tiles = NEUVV_TILES_8X4;        // pixel tile of camera packets (neuvv_autotune_tiles)
 };
 
 namespace {
@@ -153,19 +157,24 @@ DevRays dev_rays(const neuvv_rays *r, float t) {
 }
 
 // Device view of a caller's segment log buffer (layout private to the
-// library): 64-byte header, heads, key and order [n_packets], the sort bins,
-// next [n_chunks], then leaf and chord planes of n_chunks x kLogRounds x 32
-// entries.  n_chunks = 0 when the buffer is absent or too small for one chunk.
-SampleLog log_view(void *base, int64_t bytes, int64_t n_rays) {
+// library): 64-byte header, heads, key and order [n_packets], perm [n_rays],
+// the sort bins, next [n_chunks], then leaf and chord planes of n_chunks x
+// kLogRounds x 32 entries.  n_chunks = 0 when the buffer is absent or too
+// small for one chunk.  *chunk_bytes (nullable) receives the bytes from the
+// start of next[] to the end of the buffer (scratch for a ray order before
+// the forward fills the chunks).
+SampleLog log_view(void *base, int64_t bytes, int64_t n_rays, int64_t *chunk_bytes = nullptr) {
   SampleLog l;
   std::memset(&l, 0, sizeof l);
+  if (chunk_bytes) *chunk_bytes = 0;
   if (!base || bytes < 64) return l;
   char *p = static_cast<char *>(base);
   l.counter = reinterpret_cast<unsigned long long *>(p);
   l.header = reinterpret_cast<uint32_t *>(p + 8);
   const int64_t n_packets = (n_rays + 31) / 32;
   const int64_t pk_bytes = (4 * n_packets + 15) / 16 * 16;
-  const int64_t fixed = 64 + 3 * pk_bytes + 4 * kSortBins;
+  const int64_t perm_bytes = (4 * n_rays + 15) / 16 * 16;
+  const int64_t fixed = 64 + 3 * pk_bytes + perm_bytes + 4 * kSortBins;
   const int64_t per_chunk = 4 + (int64_t)kLogRounds * 32 * 8;
   const int64_t avail = bytes - fixed - 16;
   if (avail < per_chunk) return l;
@@ -174,12 +183,14 @@ SampleLog log_view(void *base, int64_t bytes, int64_t n_rays) {
   l.heads = reinterpret_cast<uint32_t *>(p + 64);
   l.key = reinterpret_cast<uint32_t *>(p + 64 + pk_bytes);
   l.order = reinterpret_cast<uint32_t *>(p + 64 + 2 * pk_bytes);
-  l.bins = reinterpret_cast<uint32_t *>(p + 64 + 3 * pk_bytes);
+  l.perm = reinterpret_cast<uint32_t *>(p + 64 + 3 * pk_bytes);
+  l.bins = reinterpret_cast<uint32_t *>(p + 64 + 3 * pk_bytes + perm_bytes);
   l.next = reinterpret_cast<uint32_t *>(p + fixed);
   const int64_t leaf_off = (fixed + 4 * nc + 15) / 16 * 16;
   l.leaf = reinterpret_cast<uint32_t *>(p + leaf_off);
   l.dt = reinterpret_cast<float *>(p + leaf_off + nc * kLogRounds * 32 * 4);
   l.n_chunks = (uint32_t)nc;
+  if (chunk_bytes) *chunk_bytes = bytes - fixed;
   return l;
 }
 
@@ -571,6 +582,7 @@ neuvv_status neuvv_tree_get_info(const neuvv_tree *t, neuvv_tree_info *info) {
   info->packet_queue = t->packet.queue;
   info->packet_ready = t->packet.ready;
   info->packet_order = t->packet.order;
+  info->packet_tiles = t->packet_tiles;
   return NEUVV_OK;
 }
 
@@ -627,7 +639,8 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
   const LaunchCfg &cfg = packet ? t->packet : t->plain;
   a.work = packet && cfg.dynamic_queue ? t->work + 0 : nullptr;
-  a.log = packet ? log_view(out->log, out->log_bytes, rays->n) : log_view(nullptr, 0, 0);
+  int64_t chunk_bytes = 0;
+  a.log = packet ? log_view(out->log, out->log_bytes, rays->n, &chunk_bytes) : log_view(nullptr, 0, 0);
   a.slice = nullptr;
   a.slice_stride = 0;
   a.edits = nullptr;
@@ -642,6 +655,12 @@ neuvv_status neuvv_render(const neuvv_tree *t, const neuvv_rays *rays, float tim
       if ((e = launch_packet_order(a.tr, a.rays, a.log, cfg.num_sms, st)) != cudaSuccess)
         return cuda_fail(e, "packet order");
       a.order = a.log.order;
+    } else if (cfg.order == 2 && (size_t)chunk_bytes >= ray_order_scratch_bytes(rays->n)) {
+      // packets re-formed from the rays sorted by direction and region (the
+      // chunk area is the sort's scratch until the forward writes it)
+      if ((e = launch_ray_order(a.tr, a.rays, a.log.perm, a.log.next, cfg.num_sms, st)) != cudaSuccess)
+        return cuda_fail(e, "ray order");
+      a.perm = a.log.perm;
     }
   } else if ((e = clear_log(out, st)) != cudaSuccess) {
     return cuda_fail(e, "clear log");
@@ -1183,7 +1202,11 @@ neuvv_status neuvv_camera_rays(const neuvv_camera *cams, const float *times, int
   }
   for (int c = n_cams; c <= kMaxCams; ++c) cb.off[c] = total;
   cb.n_cams = n_cams;
-  cb.tiled = tiled != 0;
+  static const int kTiles[4][2] = {{0, 0}, {8, 4}, {4, 8}, {16, 2}};
+  if (tiled < NEUVV_TILES_NONE || tiled > NEUVV_TILES_16X2)
+    return fail(NEUVV_ERR_INVALID_ARG, "unknown tile shape %d", tiled);
+  cb.tile_w = kTiles[tiled][0];
+  cb.tile_h = kTiles[tiled][1];
   if (n != total) return fail(NEUVV_ERR_INVALID_ARG, "n differs from the cameras' total pixel count");
   if (!origins || !dirs || !times_out) return fail(NEUVV_ERR_INVALID_ARG, "origins/dirs/times_out is NULL");
   cudaError_t e = launch_camera_rays(cb, origins, dirs, times_out, pixel_of_ray, (long long)n, (cudaStream_t)stream);
@@ -1241,7 +1264,7 @@ neuvv_status neuvv_log_read(const neuvv_out *saved, int64_t n, int32_t max_out, 
 
 neuvv_status neuvv_tree_set_packet_order(neuvv_tree *t, int32_t order) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
-  if (order != NEUVV_ORDER_AS_GIVEN && order != NEUVV_ORDER_BY_REGION)
+  if (order != NEUVV_ORDER_AS_GIVEN && order != NEUVV_ORDER_BY_REGION && order != NEUVV_ORDER_BY_RAY)
     return fail(NEUVV_ERR_INVALID_ARG, "unknown packet order %d", order);
   t->packet.order = order;
   return NEUVV_OK;
@@ -1260,6 +1283,47 @@ neuvv_status neuvv_tree_set_launch(neuvv_tree *t, int32_t block, int32_t queue, 
   return NEUVV_OK;
 }
 
+namespace {
+
+// Autotuner choices kept for the life of the process, one per tree shape,
+// storage type, device and sample size (see neuvv_autotune).
+struct TuneKey {
+  int device, num_sms, depth, K_pad, degree, dtype, bricks, log2_rays;
+  long long n_nodes, n_leaves;
+  bool operator==(const TuneKey &o) const {
+    return device == o.device && num_sms == o.num_sms && depth == o.depth && K_pad == o.K_pad &&
+           degree == o.degree && dtype == o.dtype && bricks == o.bricks && log2_rays == o.log2_rays &&
+           n_nodes == o.n_nodes && n_leaves == o.n_leaves;
+  }
+};
+struct TuneRecord {
+  TuneKey key;
+  LaunchCfg best;
+  float best_ms;
+  std::vector<neuvv_tune_entry> table;
+};
+std::mutex g_tune_mu;
+std::vector<TuneRecord> g_tune_cache;
+
+TuneKey tune_key(const neuvv_tree *t, long long n_rays) {
+  TuneKey k{};
+  k.device = t->info.device;
+  k.num_sms = t->num_sms;
+  k.depth = t->info.depth;
+  k.K_pad = t->info.K_pad;
+  k.degree = t->info.hh_degree;
+  k.dtype = t->info.dtype;
+  k.bricks = t->coarse ? 2 : (t->bricks ? 1 : 0);
+  int b = 0;
+  while (b < 62 && ((long long)1 << (b + 1)) <= n_rays) ++b;
+  k.log2_rays = b;
+  k.n_nodes = t->info.n_nodes;
+  k.n_leaves = t->info.n_leaves;
+  return k;
+}
+
+}  // namespace
+
 neuvv_status neuvv_autotune(neuvv_tree *t, const neuvv_rays *sample, float time, float *best_ms,
                             neuvv_stream stream) {
   if (!t) return fail(NEUVV_ERR_INVALID_ARG, "tree is NULL");
@@ -1270,49 +1334,162 @@ neuvv_status neuvv_autotune(neuvv_tree *t, const neuvv_rays *sample, float time,
   cudaStream_t st = (cudaStream_t)stream;
   neuvv_rays r = *sample;
   if (r.n > (1 << 20)) r.n = 1 << 20;
+  const TuneKey key = tune_key(t, r.n);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const TuneRecord &rec : g_tune_cache)
+      if (rec.key == key) {  // the same shape was timed before: keep its choice
+        const int sms = t->packet.num_sms;
+        t->packet = rec.best;
+        t->packet.num_sms = sms;
+        t->tune_table = rec.table;
+        t->tune_cached = 1;
+        if (best_ms) *best_ms = rec.best_ms;
+        return NEUVV_OK;
+      }
+  }
+  // outputs and a segment log of 64 bytes per ray, as a training step uses
   float *rgb = nullptr, *alpha = nullptr;
+  void *logbuf = nullptr;
+  const int64_t log_bytes = r.n * 64 + 65536;
   cudaError_t e;
-  if ((e = cudaMalloc(&rgb, r.n * 12)) != cudaSuccess) return cuda_fail(e, "autotune alloc");
-  if ((e = cudaMalloc(&alpha, r.n * 4)) != cudaSuccess) {
+  if ((e = cudaMalloc(&rgb, r.n * 12)) != cudaSuccess || (e = cudaMalloc(&alpha, r.n * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&logbuf, log_bytes)) != cudaSuccess) {
     cudaFree(rgb);
+    cudaFree(alpha);
     return cuda_fail(e, "autotune alloc");
   }
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
   neuvv_render_opts opts{1e-4f, NEUVV_ACT_SIGMOID, NEUVV_KERNEL_PACKET, NEUVV_COMPOSE_SORTED};
-  neuvv_out out{rgb, alpha, nullptr, nullptr, nullptr};
+  neuvv_out out{rgb, alpha, nullptr, nullptr, nullptr, logbuf, log_bytes};
   const LaunchCfg saved = t->packet;
   LaunchCfg best = saved;
   float best_t = 1e30f;
+  std::vector<neuvv_tune_entry> table;
   struct Cand { int block, queue, ready; };
   const Cand cands[] = {{64, 8, 16}, {64, 1, 1}, {64, 4, 8}, {128, 8, 16}, {128, 1, 1}, {32, 8, 16}, {64, 16, 16}};
-  for (const Cand &c : cands) {
-    t->packet = LaunchCfg{c.block, c.queue, c.ready, 0, 1, saved.num_sms};
+  for (int order = NEUVV_ORDER_AS_GIVEN; order <= NEUVV_ORDER_BY_RAY && s == NEUVV_OK; ++order)
+    for (const Cand &c : cands) {
+      t->packet = saved;
+      t->packet.block = c.block;
+      t->packet.queue = c.queue;
+      t->packet.ready = c.ready;
+      t->packet.order = order;
+      t->packet.dynamic_queue = 1;
+      float ms_best = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(ev0, st);
+        s = neuvv_render(t, &r, time, &opts, &out, stream);
+        cudaEventRecord(ev1, st);
+        if (s != NEUVV_OK) break;
+        cudaEventSynchronize(ev1);
+        float ms;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        if (ms < ms_best) ms_best = ms;
+      }
+      if (s != NEUVV_OK) break;
+      table.push_back(neuvv_tune_entry{c.block, c.queue, c.ready, order, ms_best});
+      if (ms_best < best_t) {
+        best_t = ms_best;
+        best = t->packet;
+      }
+    }
+  t->packet = s == NEUVV_OK ? best : saved;
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  cudaStreamSynchronize(st);
+  cudaFree(rgb);
+  cudaFree(alpha);
+  cudaFree(logbuf);
+  if (s != NEUVV_OK) return s;
+  t->tune_table = table;
+  t->tune_cached = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.push_back(TuneRecord{key, best, best_t, table});
+  }
+  if (best_ms) *best_ms = best_t;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_autotune_tiles(neuvv_tree *t, const neuvv_camera *cams, const float *times, int32_t n_cams,
+                                  int32_t *best_tiles, float *best_ms, neuvv_stream stream) {
+  if (!t || !best_tiles) return fail(NEUVV_ERR_INVALID_ARG, "tree/best_tiles is NULL");
+  if (n_cams < 1 || n_cams > kMaxCams || !cams || !times)
+    return fail(NEUVV_ERR_INVALID_ARG, "cams/times must hold 1..32 cameras");
+  long long n = 0;
+  for (int c = 0; c < n_cams; ++c) n += (long long)std::max(cams[c].width, 0) * std::max(cams[c].height, 0);
+  if (n <= 0 || n > ((int64_t)1 << 31)) return fail(NEUVV_ERR_INVALID_ARG, "the cameras' pixel count must be in [1, 2^31]");
+  DeviceGuard g(t->info.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  float *buf = nullptr, *rgb = nullptr, *alpha = nullptr;
+  void *logbuf = nullptr;
+  const int64_t log_bytes = n * 64 + 65536;
+  cudaError_t e;
+  if ((e = cudaMalloc(&buf, (size_t)n * 7 * 4)) != cudaSuccess || (e = cudaMalloc(&rgb, (size_t)n * 12)) != cudaSuccess ||
+      (e = cudaMalloc(&alpha, (size_t)n * 4)) != cudaSuccess || (e = cudaMalloc(&logbuf, log_bytes)) != cudaSuccess) {
+    cudaFree(buf);
+    cudaFree(rgb);
+    cudaFree(alpha);
+    return cuda_fail(e, "tile autotune alloc");
+  }
+  neuvv_rays r{buf, buf + n, buf + 2 * n, buf + 3 * n, buf + 4 * n, buf + 5 * n, buf + 6 * n, n};
+  neuvv_render_opts opts{1e-4f, NEUVV_ACT_SIGMOID, NEUVV_KERNEL_PACKET, NEUVV_COMPOSE_SORTED};
+  neuvv_out out{rgb, alpha, nullptr, nullptr, nullptr, logbuf, log_bytes};
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  neuvv_status s = NEUVV_OK;
+  int best = NEUVV_TILES_8X4;
+  float best_t = 1e30f;
+  for (int mode = NEUVV_TILES_8X4; mode <= NEUVV_TILES_16X2 && s == NEUVV_OK; ++mode) {
+    s = neuvv_camera_rays(cams, times, n_cams, mode, buf, buf + 3 * n, buf + 6 * n, nullptr, n, stream);
     float ms_best = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
+    for (int rep = 0; rep < 3 && s == NEUVV_OK; ++rep) {
       cudaEventRecord(ev0, st);
-      s = neuvv_render(t, &r, time, &opts, &out, stream);
+      s = neuvv_render(t, &r, 0.f, &opts, &out, stream);
       cudaEventRecord(ev1, st);
       if (s != NEUVV_OK) break;
       cudaEventSynchronize(ev1);
       float ms;
       cudaEventElapsedTime(&ms, ev0, ev1);
-      if (ms < ms_best) ms_best = ms;
+      ms_best = std::min(ms_best, ms);
     }
-    if (s != NEUVV_OK) break;
-    if (ms_best < best_t) {
+    if (s == NEUVV_OK && ms_best < best_t) {
       best_t = ms_best;
-      best = t->packet;
+      best = mode;
     }
   }
-  t->packet = s == NEUVV_OK ? best : saved;
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
+  cudaStreamSynchronize(st);
+  cudaFree(buf);
   cudaFree(rgb);
   cudaFree(alpha);
+  cudaFree(logbuf);
   if (s != NEUVV_OK) return s;
+  t->packet_tiles = best;
+  *best_tiles = best;
   if (best_ms) *best_ms = best_t;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_autotune_report(const neuvv_tree *t, neuvv_tune_entry *entries, int32_t max_entries,
+                                   int32_t *n_entries, int32_t *from_cache) {
+  if (!t || !n_entries) return fail(NEUVV_ERR_INVALID_ARG, "tree/n_entries is NULL");
+  if (max_entries < 0 || (max_entries > 0 && !entries)) return fail(NEUVV_ERR_INVALID_ARG, "bad entries buffer");
+  const int n = (int)t->tune_table.size();
+  for (int i = 0; i < n && i < max_entries; ++i) entries[i] = t->tune_table[i];
+  *n_entries = n;
+  if (from_cache) *from_cache = t->tune_cached;
+  return NEUVV_OK;
+}
+
+neuvv_status neuvv_autotune_clear_cache(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.clear();
   return NEUVV_OK;
 }
 

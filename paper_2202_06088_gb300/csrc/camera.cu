@@ -2,22 +2,21 @@
 // of every pixel of each view, written straight into the renderer's ray SoA so
 // that a training step uploads only its target images and camera poses.
 //
-// Order of the rays of one camera: row-major, or by 8x4 pixel tiles (tiles in
-// row-major order, the pixels of a tile row-major, narrower tiles at the right
-// edge and shorter ones at the bottom), so that the 32 rays of a packet cover
-// one compact tile.
+// Order of the rays of one camera: row-major, or by TW x TH pixel tiles of 32
+// pixels (8x4, 4x8 or 16x2; tiles in row-major order, the pixels of a tile
+// row-major, narrower tiles at the right edge and shorter ones at the
+// bottom), so that the 32 rays of a packet cover one compact tile.
 #include "neuvv_kernels.h"
 
 namespace neuvv {
 
 // Pixel (px, py) of the j-th ray of a width x height camera.
-__device__ __forceinline__ void pixel_of_ray(long long j, int width, int height, bool tiled, int &px, int &py) {
-  if (!tiled) {
+__device__ __forceinline__ void pixel_of_ray(long long j, int width, int height, int TW, int TH, int &px, int &py) {
+  if (TW == 0) {
     py = (int)(j / width);
     px = (int)(j - (long long)py * width);
     return;
   }
-  constexpr int TW = kCamTileW, TH = kCamTileH;
   const long long band_pixels = (long long)TH * width;  // a full band of TH rows
   const int band = (int)(j / band_pixels);
   const int y0 = band * TH, h = min(TH, height - y0);
@@ -50,7 +49,7 @@ __global__ void __launch_bounds__(256) camera_rays_kernel(const __grid_constant_
       if (c + step < cb.n_cams && cb.off[c + step] <= i) c += step;
     const LightCam &cam = cb.cam[c];
     int px, py;
-    pixel_of_ray(i - cb.off[c], cam.width, cam.height, cb.tiled != 0, px, py);
+    pixel_of_ray(i - cb.off[c], cam.width, cam.height, cb.tile_w, cb.tile_h, px, py);
     const float sx = (2.f * ((float)px + 0.5f) / (float)cam.width - 1.f) * cb.tan_half[c] * cb.aspect[c];
     const float sy = (1.f - 2.f * ((float)py + 0.5f) / (float)cam.height) * cb.tan_half[c];
     float v[3];

@@ -63,6 +63,31 @@ __device__ __forceinline__ DF df_dot3(const float *mh, const float *ml, const DF
 __device__ __forceinline__ bool walk_init_local(const DevTree &tr, const PrimParam &pp, const float o[3],
                                                 const float d[3], RayWalk &w, float dn[3], float &t_base,
                                                 float &dist_scale) {
+  {
+    // FP32 cull first: most (ray, primitive) pairs miss the primitive's box
+    // (margin for the rounding of this rough ray)
+    const float q0[3] = {o[0] - pp.trans[0], o[1] - pp.trans[1], o[2] - pp.trans[2]};
+    float ro[3], rd[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      ro[r] = pp.minv[3 * r] * q0[0] + pp.minv[3 * r + 1] * q0[1] + pp.minv[3 * r + 2] * q0[2];
+      rd[r] = pp.minv[3 * r] * d[0] + pp.minv[3 * r + 1] * d[1] + pp.minv[3 * r + 2] * d[2];
+    }
+    float sn = -INFINITY, sf = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float ext = 1e-3f * (tr.bmax[a] - tr.bmin[a]);
+      const float lo = tr.bmin[a] - ext, hi = tr.bmax[a] + ext;
+      if (rd[a] == 0.f) {
+        if (ro[a] < lo || ro[a] > hi) return false;
+      } else {
+        const float s0 = (lo - ro[a]) / rd[a], s1 = (hi - ro[a]) / rd[a];
+        sn = fmaxf(sn, fminf(s0, s1));
+        sf = fminf(sf, fmaxf(s0, s1));
+      }
+    }
+    if (!(fmaxf(sn, 0.f) <= sf)) return false;
+  }
   DF q[3], dd[3], ol[3], dl[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {

@@ -18,7 +18,8 @@ struct LaunchCfg {
                       // packets from a counter, 0 = one packet per warp of the grid
   int num_sms;        // multiprocessors of the device
   int order;          // packet forward with a segment log: 0 = packets in ray order,
-                      // 1 = packets in the order of the region they reach first
+                      // 1 = packets in the order of the region they reach first,
+                      // 2 = packets re-formed from the rays sorted by direction and region
 };
 
 // Segment log of the packet forward (device view of neuvv_out.log).  Chunks
@@ -26,12 +27,15 @@ struct LaunchCfg {
 // for a lane that shaded nothing in that round; a packet's chunks are linked
 // from heads[packet] through next[].  heads[packet] = kNoLog: not logged
 // (replay by walking).  Header: chunk counter (u64), then n_chunks, rounds,
-// n_rays (i64) and a valid word, all written by the forward that fills it.
+// n_rays (i64), a valid word and a permuted word, all written by the forward
+// that fills it.  Packets are formed from positions: position p holds ray
+// perm[p] when the permuted word is 1 (a ray order of the library), else ray p.
 constexpr int kLogRounds = 8;
 constexpr uint32_t kNoLog = 0xFFFFFFFFu;
 struct SampleLog {
   unsigned long long *counter;
-  uint32_t *header;   // [0] n_chunks, [1] rounds, [2..3] n_rays, [4] valid
+  uint32_t *header;   // [0] n_chunks, [1] rounds, [2..3] n_rays, [4] valid, [5] permuted
+  uint32_t *perm;     // [n_rays] ray of each position (when permuted)
   uint32_t *heads;    // [n_packets]
   uint32_t *key;      // [n_packets] first leaf the packet shaded (kNoKey: none)
   uint32_t *order;    // [n_packets] packets sorted by key (filled by the adjoint)
@@ -59,6 +63,7 @@ struct FwdArgs {
   const float *edits;        // appearance edits [n_leaves][8]: c_d (3), sigma_d, t_d, 0, 0, 0
   float edit_beta;           // colour blend weight of an active edit
   const uint32_t *order;     // persistent warps take packets in this order (null: packet index order)
+  const uint32_t *perm;      // ray at each position (null: position = ray)
 };
 
 // Workspace of the leaf-major adjoint (owned by the tree; fac, fl and idx
@@ -155,12 +160,12 @@ struct LightCam {
 // owns rays [off[c], off[c + 1]); tan_half = tan(fov_y / 2) and
 // aspect = width / height, both rounded from double on the host.
 constexpr int kMaxCams = 32;
-constexpr int kCamTileW = 8, kCamTileH = 4;
 struct CamBatch {
   LightCam cam[kMaxCams];
   float tan_half[kMaxCams], aspect[kMaxCams], t[kMaxCams];
   long long off[kMaxCams + 1];
-  int n_cams, tiled;
+  int n_cams;
+  int tile_w, tile_h;  // pixel tile of a 32-ray packet (0 x 0: row-major order)
 };
 
 struct SpotArgs {
@@ -179,6 +184,15 @@ cudaError_t launch_camera_rays(const CamBatch &cb, float *o, float *d, float *t,
                                cudaStream_t s);
 cudaError_t launch_render_fwd(int KP, int DEG, DType dt, bool packet, const FwdArgs &a, const LaunchCfg &cfg,
                               cudaStream_t s);
+// Exclusive scan of n uint32 counts in place; v[n] receives the total (v has
+// n + 1 entries; part: kScanParts scratch words; n <= kScanTile * kScanParts).
+cudaError_t launch_exclusive_scan(uint32_t *v, long long n, uint32_t *part, int num_sms, cudaStream_t s);
+// Rays re-formed into packets (cfg.order == 2): perm[position] = ray, sorted
+// by (direction bucket, region of the first leaf), stable; scratch of
+// ray_order_scratch_bytes(n) bytes.
+size_t ray_order_scratch_bytes(long long n);
+cudaError_t launch_ray_order(const DevTree &tr, const DevRays &rays, uint32_t *perm, void *scratch, int num_sms,
+                             cudaStream_t s);
 // Packets in region order for the forward (cfg.order == 1): each packet's key
 // is the first leaf that its first hitting ray (of lanes 0, 8, 16, 24)
 // reaches (leaf ids follow the Morton order of the leaves), counting-sorted

@@ -385,9 +385,11 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
   if (wp >= n_packets) return;
   const bool logged = a.log.n_chunks && log_matches(a.log, a.rays.n);
   const long long pk = logged ? (long long)min(__ldg(a.log.order + wp), (uint32_t)(n_packets - 1)) : wp;
-  const long long i = (pk << 5) + (tid & 31);
-  const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
-  if (i >= a.rays.n) return;
+  const long long pos = (pk << 5) + (tid & 31);  // position; the ray is pos, or perm[pos] in a permuted log
+  const unsigned present = __ballot_sync(0xFFFFFFFFu, pos < a.rays.n);
+  if (pos >= a.rays.n) return;
+  const long long i =
+      logged && __ldg(a.log.header + 5) == 1u ? (long long)min(__ldg(a.log.perm + pos), (uint32_t)(a.rays.n - 1)) : pos;
   RayWalk w;
   AdjState st;
   float dn[3], t;
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
   }
   if (logged) {
     // replay the forward's shading rounds from its log: no walk
-    const uint32_t head = __ldg(a.log.heads + (i >> 5));
+    const uint32_t head = __ldg(a.log.heads + (pos >> 5));
     if (head != kNoLog) {
       const int lane = tid & 31;
       const float u = t * (float)(tr.T - 1);
@@ -474,91 +476,6 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
 // ---------------------------------------------------------------------------
 // Leaf-major reduction of the gradient factors.
 // ---------------------------------------------------------------------------
-
-// Exclusive scan of the per-leaf sample counts, in place, tile by tile: each
-// block scans kScanTile counts (4 per thread) and leaves the tile's total in
-// part[tile].
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(uint32_t *v, long long n, uint32_t *part) {
-  __shared__ uint32_t warp_sum[32];
-  const long long base = (long long)blockIdx.x * kScanTile + 4 * threadIdx.x;
-  uint32_t x[4], sum = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    x[k] = base + k < n ? v[base + k] : 0u;
-    sum += x[k];
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t incl = sum;  // inclusive scan of the threads' sums within the warp
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) warp_sum[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t ws = warp_sum[lane], wi = ws;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-      if (lane >= o) wi += y;
-    }
-    warp_sum[lane] = wi - ws;  // exclusive over warps
-    if (lane == 31) part[blockIdx.x] = wi;
-  }
-  __syncthreads();
-  uint32_t run = warp_sum[wid] + incl - sum;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (base + k < n) v[base + k] = run;
-    run += x[k];
-  }
-}
-
-// Exclusive scan of the tile totals (one block; at most kScanParts tiles);
-// v[n] receives the number of samples.
-__global__ void __launch_bounds__(1024) scan_parts_kernel(uint32_t *part, int n_parts, uint32_t *v, long long n) {
-  __shared__ uint32_t warp_sum[32];
-  uint32_t x[4], sum = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int j = 4 * threadIdx.x + k;
-    x[k] = j < n_parts ? part[j] : 0u;
-    sum += x[k];
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t incl = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) warp_sum[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t ws = warp_sum[lane], wi = ws;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-      if (lane >= o) wi += y;
-    }
-    warp_sum[lane] = wi - ws;
-    if (lane == 31) v[n] = wi;
-  }
-  __syncthreads();
-  uint32_t run = warp_sum[wid] + incl - sum;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int j = 4 * threadIdx.x + k;
-    if (j < n_parts) part[j] = run;
-    run += x[k];
-  }
-}
-
-__global__ void __launch_bounds__(256) scan_add_kernel(uint32_t *v, long long n, const uint32_t *part) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    v[i] += __ldg(part + i / kScanTile);
-}
 
 // Lists each leaf's slots: off[leaf] advances from the leaf's first position
 // to the next leaf's, so afterwards leaf l owns [off[l-1], off[l]) (0 for the
@@ -840,11 +757,8 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
     render_bwd_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
     if (gather && nl > 0) {
       // per-leaf offsets, the slots listed leaf by leaf, then the per-leaf sums
-      const int tiles = (int)((nl + kScanTile - 1) / kScanTile);
-      scan_tiles_kernel<<<tiles, 1024, 0, s>>>(a.gws.off, nl, a.gws.part);
-      scan_parts_kernel<<<1, 1024, 0, s>>>(a.gws.part, tiles, a.gws.off, nl);
-      scan_add_kernel<<<(unsigned)std::min<long long>((nl + 255) / 256, 8LL * cfg.num_sms), 256, 0, s>>>(
-          a.gws.off, nl, a.gws.part);
+      cudaError_t e0 = launch_exclusive_scan(a.gws.off, nl, a.gws.part, cfg.num_sms, s);
+      if (e0 != cudaSuccess) return e0;
       const long long slots = (long long)std::min(a.log.n_chunks, a.gws.cap_chunks) * kLogRounds * 32;
       slot_scatter_kernel<<<(unsigned)std::min<long long>((slots + 255) / 256, 16LL * cfg.num_sms), 256, 0, s>>>(
           a.gws, a.log, nl);

@@ -58,7 +58,8 @@ __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
 // the full render).
 constexpr int kShadeTree = 0, kShadeSlice = 1, kShadeEdit = 2, kShadeAlpha = 3;
 template <int KP, int DEG, typename E, int kShade = kShadeTree>
-__device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, unsigned present, int queue, int ready) {
+__device__ __forceinline__ void packet_forward(const FwdArgs &a, long long pos, long long i, unsigned present,
+                                               int queue, int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
   const int B = blockDim.x, tid = threadIdx.x;
@@ -73,9 +74,10 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
   RayWalk w;
   const bool hit = walk_init(tr, o, d, w, dn);
   if (!hit) write_miss(a.out, i);
+  // i: the ray (its data and outputs); pos: its position (packet pos >> 5, lane)
   if (a.log.n_chunks && (threadIdx.x & 31) == __ffs(present) - 1) {
-    a.log.key[i >> 5] = kNoKey;
-    a.log.heads[i >> 5] = kNoLog;  // until the packet's first chunk
+    a.log.key[pos >> 5] = kNoKey;
+    a.log.heads[pos >> 5] = kNoLog;  // until the packet's first chunk
   }
   if (__ballot_sync(present, hit) == 0) return;  // the whole packet missed the tree
   float Y[(DEG + 1) * (DEG + 1)];
@@ -90,7 +92,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long i, un
   const int qmask = queue - 1;
   // segment log of this packet (warp-uniform state): current chunk and round
   const int lane = threadIdx.x & 31;
-  const long long pk = i >> 5;
+  const long long pk = pos >> 5;
   bool logging = a.log.n_chunks != 0;
   uint32_t chunk = kNoLog;
   int round = kLogRounds;
@@ -226,6 +228,7 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_ker
     a.log.header[2] = (uint32_t)(a.rays.n & 0xFFFFFFFFll);
     a.log.header[3] = (uint32_t)(a.rays.n >> 32);
     a.log.header[4] = 1u;
+    a.log.header[5] = a.perm ? 1u : 0u;
   }
   long long pk = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (a.work) {
@@ -235,10 +238,13 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_packet_ker
   }
   while (pk < n_packets) {
     if (a.order) pk = (long long)min(__ldg(a.order + pk), (uint32_t)(n_packets - 1));
-    const long long i = (pk << 5) + lane;
+    const long long pos = (pk << 5) + lane;
     // lanes past the end sit the packet out; the others stay to its end
-    const unsigned present = __ballot_sync(0xFFFFFFFFu, i < a.rays.n);
-    if (i < a.rays.n) packet_forward<KP, DEG, E, kShade>(a, i, present, queue, ready);
+    const unsigned present = __ballot_sync(0xFFFFFFFFu, pos < a.rays.n);
+    if (pos < a.rays.n) {
+      const long long i = a.perm ? (long long)min(__ldg(a.perm + pos), (uint32_t)(a.rays.n - 1)) : pos;
+      packet_forward<KP, DEG, E, kShade>(a, pos, i, present, queue, ready);
+    }
     __syncwarp();
     if (!a.work) break;
     unsigned long long q = 0;
@@ -727,14 +733,16 @@ cudaError_t launch_render_edit(int KP, int DEG, DType dt, const FwdArgs &a, cons
 // against the log's size.
 __global__ void __launch_bounds__(256) log_read_kernel(const SampleLog l, long long n, const int *nseg, int max_out,
                                                         int *leaf, float *chord, int *count) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= n) return;
   int c = -1;
   const bool valid = l.n_chunks && __ldg(l.header + 4) == 1u && __ldg(l.header) == l.n_chunks &&
                      __ldg(l.header + 1) == (uint32_t)kLogRounds &&
                      __ldg(l.header + 2) == (uint32_t)(n & 0xFFFFFFFFll) && __ldg(l.header + 3) == (uint32_t)(n >> 32);
+  // the ray at this position (its outputs are written at the ray's index)
+  const long long i = valid && __ldg(l.header + 5) == 1u ? (long long)min(__ldg(l.perm + pos), (uint32_t)(n - 1)) : pos;
   if (valid) {
-    uint32_t chunk = __ldg(l.heads + (i >> 5));
+    uint32_t chunk = __ldg(l.heads + (pos >> 5));
     const int want = __ldg(nseg + i);
     if (want == 0) {
       c = 0;
@@ -746,7 +754,7 @@ __global__ void __launch_bounds__(256) log_read_kernel(const SampleLog l, long l
           c = -1;
           break;
         }
-        const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + (i & 31);
+        const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + (pos & 31);
         const uint32_t lf = __ldg(l.leaf + slot);
         if (lf != kEmpty) {
           if (c < max_out) {

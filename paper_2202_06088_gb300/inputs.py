@@ -518,23 +518,22 @@ def config2_rays(width: int = 1920, height: int = 1080, n_views: int = 8) -> tup
 
 def training_rays(seed: int, n_rays: int, n_views: int, n_times: int, width: int, height: int,
                   radius: float = 2.5) -> Rays:
-    """Rays drawn uniformly over (camera, time stamp, pixel)."""
+    """Rays drawn uniformly over (camera, time stamp, pixel), in the order
+    drawn (a training batch as a data loader delivers it)."""
     cams = sphere_cameras(seed, n_views, radius, width, height)
     rng = np.random.default_rng(seed + 1000)
     times = np.linspace(0.0, 1.0, n_times).astype(np.float32)
     view = rng.integers(0, n_views, n_rays)
     tsel = rng.integers(0, n_times, n_rays)
     pix = rng.integers(0, width * height, n_rays)
-    # packets of 32 consecutive rays share a camera: sort by view, then pixel
-    order = np.lexsort((pix, view))
-    view, tsel, pix = view[order], tsel[order], pix[order]
-    parts = []
+    o = np.empty((3, n_rays), np.float32)
+    d = np.empty((3, n_rays), np.float32)
     for v in range(n_views):
-        sel = view == v
+        sel = np.nonzero(view == v)[0]
         r, _ = camera_rays(cams[v], 0.0, pixels=pix[sel])
-        r.times[:] = times[tsel[sel]]
-        parts.append(r)
-    return Rays.concat(parts)
+        o[:, sel] = r.origins
+        d[:, sel] = r.dirs
+    return Rays(o, d, times[tsel].astype(np.float32))
 
 
 def config3_tree() -> VOctree:

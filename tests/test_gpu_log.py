@@ -57,13 +57,20 @@ def _render_and_read(B, tree_d, dr, max_out, log_bytes_per_ray=64):
     return out, log
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_packet_log_matches_oracle_c1(B, dtype):
+@pytest.mark.parametrize("dtype,order", [("f32", None), ("bf16", None), ("f32", 2)])
+def test_packet_log_matches_oracle_c1(B, dtype, order):
+    """The autotuned launch, and the packets re-formed by the library's ray
+    order on the same view's rays shuffled (the log then lists packets of
+    sorted rays; each ray's segments are read back at its own index)."""
     tree = I.config1_tree()
     rays, _ = I.config1_rays()
+    if order is not None:
+        rays = rays.subset(np.random.default_rng(4).permutation(rays.n))
     tree_d = B.Tree(tree, dtype)
     dr = B.DeviceRays.from_host(rays)
     B.neuvv_autotune(tree_d, dr)
+    if order is not None:
+        tree_d.set_packet_order(order)
     mo = 4 * (1 << tree.depth)
     out, log = _render_and_read(B, tree_d, dr, mo)
     src = _rounded(tree, dtype)

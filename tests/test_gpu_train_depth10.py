@@ -117,6 +117,38 @@ def test_training_step_sampled_parity(B, c5):
     assert tree_d.status() == 0
 
 
+def test_ray_order_on_the_training_batch(B, c5):
+    """The batch of rays from 32 views x 32 times in random order, with the
+    library's ray order (packets re-formed from the sorted rays): the same
+    outputs as rays in the given order, the adjoint replayed through the
+    permuted log the same gradient; forward times printed."""
+    tree, rays, _ = c5
+    n = rays.n
+    tree_d = B.Tree(tree, "bf16")
+    dr = B.DeviceRays.from_host(rays)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    res = {}
+    for order in (B.ORDER_AS_GIVEN, B.ORDER_BY_RAY):
+        tree_d.set_packet_order(order)
+        out = B.alloc_out(n, dr.o.device, log_bytes_per_ray=64)
+        B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+        ev[0].record()
+        B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+        ev[1].record()
+        torch.cuda.synchronize()
+        res[order] = (out, ev[0].elapsed_time(ev[1]))
+    a, b = res[B.ORDER_AS_GIVEN][0], res[B.ORDER_BY_RAY][0]
+    for k in ("rgb", "alpha", "depth", "tau", "nseg"):
+        assert torch.equal(a[k], b[k]), k
+    g = torch.randn(n, 3, device="cuda")
+    tree_d.set_packet_order(B.ORDER_AS_GIVEN)
+    ga = B.neuvv_render_backward(tree_d, dr, a, g, kernel="packet")
+    gb = B.neuvv_render_backward(tree_d, dr, b, g, kernel="packet")
+    assert (ga - gb).abs().max().item() <= 1e-5 * ga.abs().max().item()
+    print(f"depth-10 batch forward: rays as given {res[0][1]:.3f} ms, ray order {res[2][1]:.3f} ms")
+    assert tree_d.status() == 0
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
 def test_training_step_time(B, c5, dtype):
     """Forward + MSE + adjoint + Adam over the 1,048,576 rays (times printed)."""

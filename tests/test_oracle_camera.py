@@ -22,19 +22,20 @@ def _cam(W, H, fov=40.0, eye=(0.5, 0.5, 3.0), seed=0):
 
 
 @pytest.mark.parametrize("W,H", [(53, 37), (8, 4), (1, 1), (40, 1), (1, 40), (33, 9), (64, 48)])
-@pytest.mark.parametrize("tiled", [True, False])
+@pytest.mark.parametrize("tiled", [True, False, (4, 8), (16, 2)])
 def test_pixel_order(W, H, tiled):
     r = oracle.camera_rays(_cam(W, H), 0.3, tiled)
     pix = r["pixel"]
     assert sorted(pix.tolist()) == list(range(W * H))          # every pixel once
-    ref = I.tile_order(W, H) if tiled else np.arange(W * H)   # built by sorting keys, not by loops
+    tw, th = (8, 4) if tiled is True else (tiled if tiled else (0, 0))
+    ref = I.tile_order(W, H, tw, th) if tiled else np.arange(W * H)   # built by sorting keys, not by loops
     np.testing.assert_array_equal(pix, ref)
-    if tiled and H >= 4:
-        # the first band's full 8x4 tiles: 32 consecutive rays fill each one
+    if tiled and H >= th:
+        # the first band's full tiles: 32 consecutive rays fill each one
         py, px = np.divmod(pix, W)
-        for k in range(W // 8):
+        for k in range(W // tw):
             sl = slice(32 * k, 32 * k + 32)
-            assert (px[sl].min(), px[sl].max(), py[sl].min(), py[sl].max()) == (8 * k, 8 * k + 7, 0, 3)
+            assert (px[sl].min(), px[sl].max(), py[sl].min(), py[sl].max()) == (tw * k, tw * k + tw - 1, 0, th - 1)
 
 
 @pytest.mark.parametrize("fov", [20.0, 40.0, 90.0])

@@ -27,7 +27,7 @@ MUTANTS = {
                                    "math.radians(float(cam.fov_y_deg))"),
     "camera_tile_column_major": ("camera", "(ys[:, None] * W + xs[None, :]).ravel()",
                                  "(ys[None, :] * W + xs[:, None]).ravel()"),
-    "camera_tiles_8_wide_4_high_swapped": ("camera", "for x0 in range(0, W, 8):", "for x0 in range(0, W, 4):"),
+    "camera_tiles_width_and_height_swapped": ("camera", "tw, th_ = (8, 4) if tiled is True", "tw, th_ = (4, 8) if tiled is True"),
     "gradloss_first_pixel_sign": ("gradloss", "np.add.at(dE, ra, -2.0 * D)", "np.add.at(dE, ra, 2.0 * D)"),
     "gradloss_no_vertical_pairs": ("gradloss",
                                    "for a, b in ((m[:, :, :-1], m[:, :, 1:]), (m[:, :-1, :], m[:, 1:, :])):",

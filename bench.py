@@ -212,9 +212,17 @@ def cpu_baseline(tree, rays, target_seconds, seed=99):
     t0 = time.perf_counter()
     oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores, out=planes)
     dt = time.perf_counter() - t0
+    # the same on one core, on a sample of about 3 s
+    n1 = int(max(1024, min(n, 3.0 / (per_ray * cores))))
+    sub1 = sub.subset(np.arange(n1))
+    s1 = int(fwd["nseg"][:n1].sum())
+    t0 = time.perf_counter()
+    oracle.render_grad(tree, sub1, g[:n1], otree=ot, nthreads=1, out=planes)
+    dt1 = time.perf_counter() - t0
     return {"value": samples / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} seeded random rays of the same 16.6M-ray workload ({samples} samples), "
-                      f"FP64 forward+adjoint into gradient planes allocated once, {dt:.1f} s"}
+                      f"FP64 forward+adjoint into gradient planes allocated once, {dt:.1f} s",
+            "single_core": {"value": s1 / dt1 / 1e6, "unit": UNIT, "rays": n1, "seconds": dt1}}
 
 
 def run_reference(args):
@@ -292,7 +300,7 @@ def reserve_adjoint(B, tree_d, dr, out, enable=True):
     return used, n_chunks
 
 
-def train_step_leg(B, tree, rays, dtype, steps, seed, gather=True):
+def train_step_leg(B, tree, rays, dtype, steps, seed, gather=True, force_gather=False):
     """ms per training step (fwd + MSE + adjoint + Adam) and samples/s on one
     workload, targets rendered from perturbed coefficients."""
     import torch
@@ -306,7 +314,7 @@ def train_step_leg(B, tree, rays, dtype, steps, seed, gather=True):
     B.neuvv_autotune(tree_d, dr)
     out = B.alloc_out(n, dr.o.device, log_bytes_per_ray=64)
     # the per-leaf pass pays per leaf: worth it with at least a sample per leaf
-    gather = gather and n >= tree.n_leaves
+    gather = gather and (n >= tree.n_leaves or force_gather)
     reserve_adjoint(B, tree_d, dr, out, gather)
     grad_rgb = torch.empty(n, 3, device=dr.o.device)
     grad = tree_d.new_grad()
@@ -393,6 +401,9 @@ def extra_workloads(B, steps, gather=True):
     rays5 = I.config5_rays()
     res["depth10_train_1m_rays"] = train_step_leg(B, tree5, rays5, "bf16", steps, 1005, gather)
     res["depth10_train_1m_rays_fp8"] = train_step_leg(B, tree5, rays5, "fp8", steps, 1005, gather)
+    # the same step with the leaf-major adjoint (Adam fused into the per-leaf pass) for comparison
+    res["depth10_train_1m_rays_leaf_major"] = train_step_leg(B, tree5, rays5, "bf16", steps, 1005, gather,
+                                                             force_gather=True)
     return res
 
 
@@ -443,22 +454,26 @@ def main():
     rays, view_pixels, view_cams, view_times = I.config2_rays(n_views=args.views)
     n = rays.n
     dev = torch.device("cuda", local)
-    dr = B.DeviceRays.from_host(rays, device=dev)
     if args.profile_kernel:
-        profile_case(args, B, tree, dr)
+        profile_case(args, B, tree, B.DeviceRays.from_host(rays, device=dev))
         return
+    tree_d = B.Tree(tree, "bf16", with_optimizer=True)
+    # the pixel tile of the views' packets, then the rays generated on the
+    # device in that tiling (the same rays as the generator's, in tile order)
+    tiles = B.neuvv_autotune_tiles(tree_d, view_cams, view_times) if not args.no_autotune else B.TILES_8X4
+    pix = torch.empty(n, dtype=torch.int32, device=dev)
+    dr = B.neuvv_camera_rays(view_cams, view_times, tiled=tiles, pixel_of_ray=pix, device=dev)
     # fixed target images: the same views rendered from perturbed coefficients
     tgt_tree = B.Tree(I.perturbed(tree, seed=1000), "f32")
     target = B.neuvv_render(tgt_tree, dr, kernel="packet")["rgb"].clone()
     del tgt_tree
-    tree_d = B.Tree(tree, "bf16", with_optimizer=True)
     if not args.no_autotune:
         B.neuvv_autotune(tree_d, dr)
     if args.order is not None:
         tree_d.set_packet_order(args.order)
     launch = {"block": tree_d.info.packet_block, "queue": tree_d.info.packet_queue,
               "ready": tree_d.info.packet_ready, "order": tree_d.info.packet_order,
-              "autotuned": not args.no_autotune}
+              "tiles": {1: "8x4", 2: "4x8", 3: "16x2"}[tiles], "autotuned": not args.no_autotune}
     out = B.alloc_out(n, dev, log_bytes_per_ray=64)
     log_used, log_chunks = reserve_adjoint(B, tree_d, dr, out, not args.no_gather)
     grad_rgb = torch.empty(n, 3, device=dev)
@@ -469,11 +484,11 @@ def main():
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     # the image-gradient regulariser needs each view's pixel -> ray map
     W_img, H_img = 1920, 1080
-    pix_map = np.empty((args.views, H_img * W_img), np.int32)
-    for v, pv in enumerate(view_pixels):
-        pix_map[v, pv] = v * H_img * W_img + np.arange(H_img * W_img, dtype=np.int32)
-    ray_of_pixel = torch.from_numpy(pix_map.reshape(args.views, H_img, W_img)).to(dev)
-    del pix_map
+    view_of_ray = torch.arange(n, device=dev, dtype=torch.int64) // (H_img * W_img)
+    ray_of_pixel = torch.empty(args.views * H_img * W_img, dtype=torch.int32, device=dev)
+    ray_of_pixel[view_of_ray * (H_img * W_img) + pix.long()] = torch.arange(n, device=dev, dtype=torch.int32)
+    ray_of_pixel = ray_of_pixel.view(args.views, H_img, W_img)
+    del view_of_ray, pix
 
     def step(k, evs=None):
         if evs:
@@ -797,7 +812,7 @@ def main():
 
     def e2e_step(j, k):
         b = j % 2
-        B.neuvv_camera_rays(view_cams, view_times, tiled=True, out=dr_e2e)
+        B.neuvv_camera_rays(view_cams, view_times, tiled=tiles, out=dr_e2e)
         B.neuvv_render(tree_d, dr_e2e, kernel="packet", out=out)
         stream.wait_event(copied[b])
         loss.zero_()

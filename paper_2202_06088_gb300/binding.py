@@ -25,7 +25,7 @@ _lib = None
 F32, BF16, FP8 = 0, 1, 2
 # device status bits (neuvv_tree_status)
 STATUS_SEGMENT_CAP, STATUS_BAD_INDEX, STATUS_TIMEOUT = 0x1, 0x2, 0x4
-ORDER_AS_GIVEN, ORDER_BY_REGION = 0, 1
+ORDER_AS_GIVEN, ORDER_BY_REGION, ORDER_BY_RAY = 0, 1, 2
 TILES_NONE, TILES_8X4, TILES_4X8, TILES_16X2 = 0, 1, 2, 3
 TILE_SHAPES = {TILES_8X4: (8, 4), TILES_4X8: (4, 8), TILES_16X2: (16, 2)}
 _DTYPES = {"f32": F32, "float32": F32, "bf16": BF16, "bfloat16": BF16, "fp8": FP8, "fp8_e4m3": FP8}

@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(kGradTileW *kGradTileH)
 }
 
 
-// One thread per (leaf, 4-float quad of the record).
+// One warp per word of the touched bitmap (32 leaves): an empty word is
+// skipped at once, and each set bit's leaf is updated by the warp, one
+// 4-float quad of its record per lane, so a row is one coalesced access.
 __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ master, float *__restrict__ m,
                                                    float *__restrict__ v, void *__restrict__ storage, int dt,
                                                    int storage_stride, float *__restrict__ grad,
@@ -127,35 +129,40 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ master, f
                                                    int stride_f32, int rec_len, float lr, float b1, float b2,
                                                    float eps, float c1, float c2) {
   const int quads = (rec_len + 3) / 4;  // quads past the record's entries are padding and stay zero
-  const long long total = n_leaves * quads;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long leaf = idx / quads;
-    const int q = (int)(idx - leaf * quads);
-    if (!((__ldg(touched + (leaf >> 5)) >> (leaf & 31)) & 1u)) continue;
-    const size_t off = (size_t)leaf * stride_f32 + 4 * q;
-    float4 g = *reinterpret_cast<const float4 *>(grad + off);
-    float4 w = *reinterpret_cast<const float4 *>(master + off);
-    float4 mm = *reinterpret_cast<const float4 *>(m + off);
-    float4 vv = *reinterpret_cast<const float4 *>(v + off);
-    float gs[4] = {g.x, g.y, g.z, g.w}, ws[4] = {w.x, w.y, w.z, w.w};
-    float ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+  const int lane = threadIdx.x & 31;
+  const long long n_words = (n_leaves + 31) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long wd = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wd < n_words; wd += nwarps) {
+    unsigned int bits = __ldg(touched + wd);  // the same for the whole warp
+    while (bits) {
+      const long long leaf = (wd << 5) + (__ffs(bits) - 1);
+      bits &= bits - 1u;
+      for (int q = lane; q < quads; q += 32) {
+        const size_t off = (size_t)leaf * stride_f32 + 4 * q;
+        float4 g = *reinterpret_cast<const float4 *>(grad + off);
+        float4 w = *reinterpret_cast<const float4 *>(master + off);
+        float4 mm = *reinterpret_cast<const float4 *>(m + off);
+        float4 vv = *reinterpret_cast<const float4 *>(v + off);
+        float gs[4] = {g.x, g.y, g.z, g.w}, ws[4] = {w.x, w.y, w.z, w.w};
+        float ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (4 * q + k >= rec_len) continue;  // padding stays zero
-      ms[k] = b1 * ms[k] + (1.f - b1) * gs[k];
-      vs[k] = b2 * vs[k] + (1.f - b2) * gs[k] * gs[k];
-      ws[k] -= lr * (ms[k] / c1) / (sqrtf(vs[k] / c2) + eps);
-    }
-    *reinterpret_cast<float4 *>(master + off) = make_float4(ws[0], ws[1], ws[2], ws[3]);
-    *reinterpret_cast<float4 *>(m + off) = make_float4(ms[0], ms[1], ms[2], ms[3]);
-    *reinterpret_cast<float4 *>(v + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
-    *reinterpret_cast<float4 *>(grad + off) = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (dt == kBF16) {
-      unsigned short *st = static_cast<unsigned short *>(storage) + (size_t)leaf * storage_stride + 4 * q;
-      const unsigned int lo = f32_to_bf16_rne(ws[0]) | ((unsigned int)f32_to_bf16_rne(ws[1]) << 16);
-      const unsigned int hi = f32_to_bf16_rne(ws[2]) | ((unsigned int)f32_to_bf16_rne(ws[3]) << 16);
-      *reinterpret_cast<uint2 *>(st) = make_uint2(lo, hi);
+        for (int k = 0; k < 4; ++k) {
+          if (4 * q + k >= rec_len) continue;  // padding stays zero
+          ms[k] = b1 * ms[k] + (1.f - b1) * gs[k];
+          vs[k] = b2 * vs[k] + (1.f - b2) * gs[k] * gs[k];
+          ws[k] -= lr * (ms[k] / c1) / (sqrtf(vs[k] / c2) + eps);
+        }
+        *reinterpret_cast<float4 *>(master + off) = make_float4(ws[0], ws[1], ws[2], ws[3]);
+        *reinterpret_cast<float4 *>(m + off) = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        *reinterpret_cast<float4 *>(v + off) = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        *reinterpret_cast<float4 *>(grad + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (dt == kBF16) {
+          unsigned short *st = static_cast<unsigned short *>(storage) + (size_t)leaf * storage_stride + 4 * q;
+          const unsigned int lo = f32_to_bf16_rne(ws[0]) | ((unsigned int)f32_to_bf16_rne(ws[1]) << 16);
+          const unsigned int hi = f32_to_bf16_rne(ws[2]) | ((unsigned int)f32_to_bf16_rne(ws[3]) << 16);
+          *reinterpret_cast<uint2 *>(st) = make_uint2(lo, hi);
+        }
+      }
     }
   }
 }
@@ -174,8 +181,11 @@ __global__ void __launch_bounds__(256) adam_fp8_kernel(float *__restrict__ maste
   const int lane = threadIdx.x & 31;
   const int quads = stride_f32 / 4;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long leaf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < n_leaves; leaf += nwarps) {
-    if (!((__ldg(touched + (leaf >> 5)) >> (leaf & 31)) & 1u)) continue;  // the same for the whole warp
+  const long long n_words = (n_leaves + 31) >> 5;
+  // one warp per word of the touched bitmap: empty words are skipped at once
+  for (long long wd = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wd < n_words; wd += nwarps)
+  for (unsigned int bits = __ldg(touched + wd); bits; bits &= bits - 1u) {
+    const long long leaf = (wd << 5) + (__ffs(bits) - 1);
     float ws[kMaxRounds][4];
     float mx[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -315,14 +325,13 @@ cudaError_t launch_adam(float *master, float *m, float *v, void *storage, DType 
   if (n_leaves == 0) return cudaSuccess;
   if (dt == kFP8) {
     if (stride_f32 > 256 || !storage) return cudaErrorInvalidValue;
-    const long long want = (n_leaves * 32 + 255) / 256;
+    const long long want = ((n_leaves + 31) / 32 * 32 + 255) / 256;
     const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
     adam_fp8_kernel<<<blocks, 256, 0, s>>>(master, m, v, static_cast<unsigned char *>(storage), storage_stride, grad,
                                            touched, n_leaves, stride_f32, rec_len, kp, lr, b1, b2, eps, c1, c2);
     return cudaGetLastError();
   }
-  const long long total = n_leaves * (stride_f32 / 4);
-  const long long want = (total + 255) / 256;
+  const long long want = ((n_leaves + 31) / 32 * 32 + 255) / 256;  // one warp per bitmap word
   const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
   adam_kernel<<<blocks, 256, 0, s>>>(master, m, v, storage, (int)dt, storage_stride, grad, touched, n_leaves,
                                      stride_f32, rec_len, lr, b1, b2, eps, c1, c2);

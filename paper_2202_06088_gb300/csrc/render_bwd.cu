@@ -565,7 +565,6 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
   const long long first = (long long)blockIdx.x * blockDim.x;
   const long long leaf = first + threadIdx.x;
   float *acc = acc_s + threadIdx.x * PITCH;
-  for (int j = 0; j < LEN; ++j) acc[j] = 0.f;
   uint32_t lo = 0, hi = 0;
   const uint32_t cap = a.gws.cap_chunks * kLogRounds * 32;  // slots of the workspace
   bool before = false;  // Adam: touched before this kernel (the atomic scatter left a part in the row)
@@ -576,6 +575,8 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
     if (ad.on && a.touched) before = (a.touched[leaf >> 5] >> (leaf & 31)) & 1u;
   }
   has[threadIdx.x] = (lo < hi ? 1 : 0) | (before ? 2 : 0);
+  if (lo < hi || before)  // only rows the epilogue reads
+    for (int j = 0; j < LEN; ++j) acc[j] = 0.f;
   if (lo < hi) {
     LeafRecord<KP, DEG, E> rec;
     rec.load_gamma(tr, (uint32_t)leaf);

@@ -149,7 +149,7 @@ def test_log_read_marks_rays_without_a_log(B):
     B.neuvv_render(tree_d, dr, kernel="packet", out=out)
     sub = B.neuvv_log_read(out, dr.n - 32, 8)                    # a log written for other rays
     assert (sub["count"] == -1).all().item()
-    tiny = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=4)   # room for few packets: the rest walk
+    tiny = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=8)   # room for few packets: the rest walk
     B.neuvv_render(tree_d, dr, kernel="packet", out=tiny)
     t = B.neuvv_log_read(tiny, dr.n, 64)
     c, ns = t["count"], tiny["nseg"]

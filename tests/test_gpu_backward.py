@@ -144,7 +144,8 @@ def test_autograd_function_matches_direct_calls(B):
     loss.backward()
     out = B.neuvv_render(tree_d, dr)
     direct = B.neuvv_render_backward(tree_d, dr, out, torch.from_numpy(g).cuda(), torch.from_numpy(ga).cuda())
-    assert torch.allclose(coeffs.grad, direct, rtol=1e-5, atol=1e-7)
+    # the same adjoint; FP32 atomic sums in another order: within 1e-5 of the largest entry
+    assert (coeffs.grad - direct).abs().max().item() <= 1e-5 * direct.abs().max().item()
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])

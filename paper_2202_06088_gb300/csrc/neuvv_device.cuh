@@ -796,6 +796,18 @@ __device__ __forceinline__ void ray_const_basis(const DevTree &tr, float u, RayC
 
 __device__ __forceinline__ float sigmoidf_fast(float x) { return 1.f / (1.f + __expf(-x)); }
 
+// One Adam step of one entry (Sec. 4.3 "Optimization"): moments
+// m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2, then
+// w <- w - lr m_hat / (sqrt(v_hat) + eps) with m_hat = m / c1 and
+// v_hat = v / c2 (bias corrections c = 1 - b^step), taken as
+// (lr / c1) m / (sqrt(v (1 / c2)) + eps) with one fast division.
+__device__ __forceinline__ void adam_entry(float g, float b1, float b2, float lr_c1, float inv_c2, float eps, float &w,
+                                           float &m, float &v) {
+  m = fmaf(b1, m, (1.f - b1) * g);
+  v = fmaf(b2, v, (1.f - b2) * g * g);
+  w -= __fdividef(lr_c1 * m, sqrtf(v * inv_c2) + eps);
+}
+
 // float -> bfloat16 bits, round to nearest even (a NaN stays a quiet NaN).
 __device__ __forceinline__ unsigned short f32_to_bf16_rne(float f) {
   unsigned int u = __float_as_uint(f);

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ master, f
                                                    float eps, float c1, float c2) {
   const int quads = (rec_len + 3) / 4;  // quads past the record's entries are padding and stay zero
   const int lane = threadIdx.x & 31;
+  const float lr_c1 = lr / c1, inv_c2 = 1.f / c2;
   const long long n_words = (n_leaves + 31) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long wd = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wd < n_words; wd += nwarps) {
@@ -148,9 +149,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ master, f
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (4 * q + k >= rec_len) continue;  // padding stays zero
-          ms[k] = b1 * ms[k] + (1.f - b1) * gs[k];
-          vs[k] = b2 * vs[k] + (1.f - b2) * gs[k] * gs[k];
-          ws[k] -= lr * (ms[k] / c1) / (sqrtf(vs[k] / c2) + eps);
+          adam_entry(gs[k], b1, b2, lr_c1, inv_c2, eps, ws[k], ms[k], vs[k]);
         }
         *reinterpret_cast<float4 *>(master + off) = make_float4(ws[0], ws[1], ws[2], ws[3]);
         *reinterpret_cast<float4 *>(m + off) = make_float4(ms[0], ms[1], ms[2], ms[3]);
@@ -179,6 +178,7 @@ __global__ void __launch_bounds__(256) adam_fp8_kernel(float *__restrict__ maste
                                                        float b2, float eps, float c1, float c2) {
   constexpr int kMaxRounds = 2;  // stride_f32 <= 256 floats (64 quads) per leaf
   const int lane = threadIdx.x & 31;
+  const float lr_c1 = lr / c1, inv_c2 = 1.f / c2;
   const int quads = stride_f32 / 4;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long n_words = (n_leaves + 31) >> 5;
@@ -206,9 +206,7 @@ __global__ void __launch_bounds__(256) adam_fp8_kernel(float *__restrict__ maste
       for (int k = 0; k < 4; ++k) {
         const int j = 4 * q + k;
         if (j >= rec_len) continue;  // padding stays zero
-        ms[k] = b1 * ms[k] + (1.f - b1) * gs[k];
-        vs[k] = b2 * vs[k] + (1.f - b2) * gs[k] * gs[k];
-        ws[r][k] -= lr * (ms[k] / c1) / (sqrtf(vs[k] / c2) + eps);
+        adam_entry(gs[k], b1, b2, lr_c1, inv_c2, eps, ws[r][k], ms[k], vs[k]);
         const int grp = j < kp ? 0 : (j < 2 * kp ? 1 : 2);
         mx[grp] = fmaxf(mx[grp], fabsf(ws[r][k]));
       }

@@ -540,11 +540,6 @@ __device__ __forceinline__ void leaf_flush(const DevTree &tr, const LeafRecord<K
         }
 }
 
-__device__ __forceinline__ void adam_update(const AdamArgs &ad, float g, float &w, float &m, float &v) {
-  m = ad.b1 * m + (1.f - ad.b1) * g;
-  v = ad.b2 * v + (1.f - ad.b2) * g * g;
-  w -= ad.lr * (m / ad.c1) / (sqrtf(v / ad.c2) + ad.eps);
-}
 
 // With Adam (ad.on, Sec. 4.3 "Optimization"), the block's finished records
 // are not added to the gradient buffer: each warp takes rows of the block in
@@ -642,82 +637,107 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
     }
     return;
   }
+  // each warp takes rows r and r + nw of the block together (their loads in
+  // flight at once), a lane one 4-entry quad of each
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = threadIdx.x >> 5; r < rows_here; r += nw) {
-    const int h = has[r];
-    if (!h) continue;  // the same for the whole warp
-    const size_t row = (size_t)(first + r) * a.grad_stride;
-    float wq[(Q4 + 31) / 32][4];
-    float mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;  // FP8: largest magnitudes of w_sigma, w_gamma, w_hh
+  const float lr_c1 = ad.lr / ad.c1, inv_c2 = 1.f / ad.c2;
+  float *__restrict__ mst = ad.master;
+  float *__restrict__ mom = ad.m;
+  float *__restrict__ vel = ad.v;
+  constexpr int QR = (Q4 + 31) / 32;  // quads of a row per lane
+  for (int r0 = threadIdx.x >> 5; r0 < rows_here; r0 += 2 * nw) {
+    int rr[2] = {r0, r0 + nw};
+    int h[2];
 #pragma unroll
-    for (int k = 0; k < (Q4 + 31) / 32; ++k) {
-      const int q = lane + 32 * k;
-      if (q >= Q4) continue;
-      const float *src = acc_s + r * PITCH + 4 * q;
-      float4 g = make_float4(src[0], 4 * q + 1 < LEN ? src[1] : 0.f, 4 * q + 2 < LEN ? src[2] : 0.f,
-                             4 * q + 3 < LEN ? src[3] : 0.f);
-      float4 *gp = reinterpret_cast<float4 *>(a.grad + row) + q;
-      if (h & 2) {
-        const float4 x = *gp;
-        g.x += x.x;
-        g.y += x.y;
-        g.z += x.z;
-        g.w += x.w;
-        *gp = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = 0; e < 2; ++e) h[e] = rr[e] < rows_here ? has[rr[e]] : 0;
+    if (!(h[0] | h[1])) continue;  // the same for the whole warp
+    float4 g[2][QR], w[2][QR], m[2][QR], v[2][QR];
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+      for (int k = 0; k < QR; ++k) {
+        const int q = lane + 32 * k;
+        if (!h[e] || q >= Q4) continue;
+        const size_t row = (size_t)(first + rr[e]) * a.grad_stride;
+        const float *src = acc_s + rr[e] * PITCH + 4 * q;
+        g[e][k] = make_float4(src[0], 4 * q + 1 < LEN ? src[1] : 0.f, 4 * q + 2 < LEN ? src[2] : 0.f,
+                              4 * q + 3 < LEN ? src[3] : 0.f);
+        if (h[e] & 2) {
+          float4 *gp = reinterpret_cast<float4 *>(a.grad + row) + q;
+          const float4 x = *gp;
+          g[e][k].x += x.x;
+          g[e][k].y += x.y;
+          g[e][k].z += x.z;
+          g[e][k].w += x.w;
+          *gp = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        w[e][k] = reinterpret_cast<const float4 *>(mst + row)[q];
+        m[e][k] = reinterpret_cast<const float4 *>(mom + row)[q];
+        v[e][k] = reinterpret_cast<const float4 *>(vel + row)[q];
       }
-      float4 w = reinterpret_cast<const float4 *>(ad.master + row)[q];
-      float4 m = reinterpret_cast<const float4 *>(ad.m + row)[q];
-      float4 v = reinterpret_cast<const float4 *>(ad.v + row)[q];
-      float gs[4] = {g.x, g.y, g.z, g.w}, ws[4] = {w.x, w.y, w.z, w.w};
-      float ms[4] = {m.x, m.y, m.z, m.w}, vs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int j = 4 * q + c;
-        if (j >= LEN) continue;  // padding stays zero
-        adam_update(ad, gs[c], ws[c], ms[c], vs[c]);
-        const float aw = fabsf(ws[c]);
-        if (j < KP) mx0 = fmaxf(mx0, aw);
-        else if (j < 2 * KP) mx1 = fmaxf(mx1, aw);
-        else mx2 = fmaxf(mx2, aw);
-      }
-      reinterpret_cast<float4 *>(ad.master + row)[q] = make_float4(ws[0], ws[1], ws[2], ws[3]);
-      reinterpret_cast<float4 *>(ad.m + row)[q] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-      reinterpret_cast<float4 *>(ad.v + row)[q] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    for (int e = 0; e < 2; ++e) {
+      if (!h[e]) continue;
+      const size_t row = (size_t)(first + rr[e]) * a.grad_stride;
+      float mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;  // FP8: largest magnitudes of w_sigma, w_gamma, w_hh
+      float wq[QR][4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) wq[k][c] = ws[c];
-      if (ad.dt == kBF16) {
-        unsigned short *st = static_cast<unsigned short *>(ad.storage) + (size_t)(first + r) * ad.storage_stride;
-        const unsigned int lo16 = f32_to_bf16_rne(ws[0]) | ((unsigned int)f32_to_bf16_rne(ws[1]) << 16);
-        const unsigned int hi16 = f32_to_bf16_rne(ws[2]) | ((unsigned int)f32_to_bf16_rne(ws[3]) << 16);
-        *reinterpret_cast<uint2 *>(st + 4 * q) = make_uint2(lo16, hi16);
-      }
-    }
-    if (ad.dt == kFP8) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        mx0 = fmaxf(mx0, __shfl_xor_sync(0xFFFFFFFFu, mx0, o));
-        mx1 = fmaxf(mx1, __shfl_xor_sync(0xFFFFFFFFu, mx1, o));
-        mx2 = fmaxf(mx2, __shfl_xor_sync(0xFFFFFFFFu, mx2, o));
-      }
-      const int p[3] = {fp8_scale_exp(mx0), fp8_scale_exp(mx1), fp8_scale_exp(mx2)};
-      unsigned char *rec = static_cast<unsigned char *>(ad.storage) + (size_t)(first + r) * ad.storage_stride;
-      if (lane == 0)
-        *reinterpret_cast<uint4 *>(rec) = make_uint4(__float_as_uint(ldexpf(1.f, p[0])),
-                                                     __float_as_uint(ldexpf(1.f, p[1])),
-                                                     __float_as_uint(ldexpf(1.f, p[2])), 0u);
-#pragma unroll
-      for (int k = 0; k < (Q4 + 31) / 32; ++k) {
+      for (int k = 0; k < QR; ++k) {
         const int q = lane + 32 * k;
         if (q >= Q4) continue;
-        unsigned int word = 0;
+        float gs[4] = {g[e][k].x, g[e][k].y, g[e][k].z, g[e][k].w};
+        float ws[4] = {w[e][k].x, w[e][k].y, w[e][k].z, w[e][k].w};
+        float ms[4] = {m[e][k].x, m[e][k].y, m[e][k].z, m[e][k].w};
+        float vs[4] = {v[e][k].x, v[e][k].y, v[e][k].z, v[e][k].w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int j = 4 * q + c;
-          if (j >= LEN) continue;
-          const int pe = j < KP ? p[0] : (j < 2 * KP ? p[1] : p[2]);
-          word |= (unsigned int)__nv_cvt_float_to_fp8(ldexpf(wq[k][c], -pe), __NV_SATFINITE, __NV_E4M3) << (8 * c);
+          if (j >= LEN) continue;  // padding stays zero
+          adam_entry(gs[c], ad.b1, ad.b2, lr_c1, inv_c2, ad.eps, ws[c], ms[c], vs[c]);
+          const float aw = fabsf(ws[c]);
+          if (j < KP) mx0 = fmaxf(mx0, aw);
+          else if (j < 2 * KP) mx1 = fmaxf(mx1, aw);
+          else mx2 = fmaxf(mx2, aw);
         }
-        *reinterpret_cast<unsigned int *>(rec + 16 + 4 * q) = word;
+        reinterpret_cast<float4 *>(mst + row)[q] = make_float4(ws[0], ws[1], ws[2], ws[3]);
+        reinterpret_cast<float4 *>(mom + row)[q] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        reinterpret_cast<float4 *>(vel + row)[q] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) wq[k][c] = ws[c];
+        if (ad.dt == kBF16) {
+          unsigned short *st = static_cast<unsigned short *>(ad.storage) + (size_t)(first + rr[e]) * ad.storage_stride;
+          const unsigned int lo16 = f32_to_bf16_rne(ws[0]) | ((unsigned int)f32_to_bf16_rne(ws[1]) << 16);
+          const unsigned int hi16 = f32_to_bf16_rne(ws[2]) | ((unsigned int)f32_to_bf16_rne(ws[3]) << 16);
+          *reinterpret_cast<uint2 *>(st + 4 * q) = make_uint2(lo16, hi16);
+        }
+      }
+      if (ad.dt == kFP8) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          mx0 = fmaxf(mx0, __shfl_xor_sync(0xFFFFFFFFu, mx0, o));
+          mx1 = fmaxf(mx1, __shfl_xor_sync(0xFFFFFFFFu, mx1, o));
+          mx2 = fmaxf(mx2, __shfl_xor_sync(0xFFFFFFFFu, mx2, o));
+        }
+        const int p[3] = {fp8_scale_exp(mx0), fp8_scale_exp(mx1), fp8_scale_exp(mx2)};
+        unsigned char *rec = static_cast<unsigned char *>(ad.storage) + (size_t)(first + rr[e]) * ad.storage_stride;
+        if (lane == 0)
+          *reinterpret_cast<uint4 *>(rec) = make_uint4(__float_as_uint(ldexpf(1.f, p[0])),
+                                                       __float_as_uint(ldexpf(1.f, p[1])),
+                                                       __float_as_uint(ldexpf(1.f, p[2])), 0u);
+#pragma unroll
+        for (int k = 0; k < QR; ++k) {
+          const int q = lane + 32 * k;
+          if (q >= Q4) continue;
+          unsigned int word = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int j = 4 * q + c;
+            if (j >= LEN) continue;
+            const int pe = j < KP ? p[0] : (j < 2 * KP ? p[1] : p[2]);
+            word |= (unsigned int)__nv_cvt_float_to_fp8(ldexpf(wq[k][c], -pe), __NV_SATFINITE, __NV_E4M3) << (8 * c);
+          }
+          *reinterpret_cast<unsigned int *>(rec + 16 + 4 * q) = word;
+        }
       }
     }
   }

@@ -131,3 +131,32 @@ def test_camera_rays_arguments_are_checked_on_the_host(L):
 def test_reserve_adjoint_arguments_are_checked_on_the_host(L):
     assert L.neuvv_tree_reserve_adjoint(None, 0) == 1
     assert b"NULL" in L.neuvv_last_error()
+
+
+def test_new_entry_points_check_their_arguments_on_the_host(L):
+    """Null trees, negative limits, unknown orders and tile shapes, missing
+    buffers: rejected before any device work."""
+    from paper_2202_06088_gb300 import binding as B
+    assert L.neuvv_tree_set_limits(None, 0, 0) == 1
+    assert L.neuvv_tree_set_packet_order(None, 0) == 1
+    assert L.neuvv_tree_set_records(None, None, None) == 1
+    n = ctypes.c_int32()
+    assert L.neuvv_autotune_report(None, None, 0, ctypes.byref(n), None) == 1
+    assert L.neuvv_autotune_clear_cache() == 0
+    assert L.neuvv_log_read(None, 4, 8, None, None, None, None) == 1
+    assert b"nseg" in L.neuvv_last_error()
+    assert L.neuvv_render_backward_adam(None, None, 0.0, None, None, None, None, None, None, 1e-3, 0.9, 0.999,
+                                        1e-8, 1, None) == 1
+    cam = B.LightC()
+    cam.fov_y_deg, cam.width, cam.height = 40.0, 8, 4
+    for k in range(3):
+        cam.right[k], cam.up[k], cam.forward[k] = float(k == 0), float(k == 1), float(k == 2)
+    arr = (B.LightC * 1)(cam)
+    ts = (ctypes.c_float * 1)(0.5)
+    buf = np.zeros(7 * 32, np.float32)
+    p = buf.ctypes.data
+    # tile shapes 0..3 are known; 4 is rejected before the launch
+    assert L.neuvv_camera_rays(arr, ts, 1, 4, p, p, p, None, 32, None) == 1
+    assert b"tile" in L.neuvv_last_error()
+    best = ctypes.c_int32()
+    assert L.neuvv_autotune_tiles(None, arr, ts, 1, ctypes.byref(best), None, None) == 1

@@ -68,6 +68,9 @@ def parse_args():
                    help="packet order of the forward after autotuning (0 as given, 1 by region; default: tuned)")
     p.add_argument("--profile-kernel", choices=["fwd", "bwd", "bwd_adam"], default=None,
                    help="profiling case: launch that kernel twice on the workload and exit (no JSON)")
+    p.add_argument("--profile-workload", choices=["views", "depth8_train"], default="views",
+                   help="profiling case's input: the --views 1080p views of the depth-9 tree, or the depth-8 "
+                        "training batch (262,144 rays over 1.28 M leaves: fewer samples than leaves)")
     return p.parse_args()
 
 
@@ -451,10 +454,13 @@ def main():
     from paper_2202_06088_gb300 import inputs as I
     B.lib()
 
+    dev = torch.device("cuda", local)
+    if args.profile_kernel and args.profile_workload == "depth8_train":
+        profile_case(args, B, I.config3_tree(), B.DeviceRays.from_host(I.config3_rays(), device=dev))
+        return
     tree = I.config2_tree()
     rays, view_pixels, view_cams, view_times = I.config2_rays(n_views=args.views)
     n = rays.n
-    dev = torch.device("cuda", local)
     if args.profile_kernel:
         profile_case(args, B, tree, B.DeviceRays.from_host(rays, device=dev))
         return

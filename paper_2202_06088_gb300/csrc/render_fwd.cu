@@ -80,11 +80,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long pos, 
     a.log.heads[pos >> 5] = kNoLog;  // until the packet's first chunk
   }
   if (__ballot_sync(present, hit) == 0) return;  // the whole packet missed the tree
-  float Y[(DEG + 1) * (DEG + 1)];
-  if (hit) {
-    if (kShade != kShadeSlice) rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
-    if (kShade != kShadeAlpha) sh_real<DEG>(dn, Y);
-  }
+  if (hit && kShade != kShadeSlice) rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f, dnum = 0.f, tau = 0.f;
   int nseg = 0;
   bool walking = hit && w.alive;
@@ -154,6 +150,10 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long pos, 
       qh = (qh + 1) & qmask;
       --qn;
       float sigma, col[3];
+      // the harmonics of the ray's direction, formed per round rather than
+      // held through the walk (16 registers fewer across the loop)
+      float Y[(DEG + 1) * (DEG + 1)];
+      if (kShade != kShadeAlpha) sh_real<DEG>(dn, Y);
       if constexpr (kShade == kShadeSlice) {
         shade_slice<DEG>(a.slice, a.slice_stride, leaf, Y, a.act, sigma, col);
       } else if constexpr (kShade == kShadeAlpha) {

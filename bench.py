@@ -290,15 +290,25 @@ def job_msamples_per_s(samples_per_rank, ms_step, world):
 
 
 def reserve_adjoint(B, tree_d, dr, out, enable=True):
-    """Reserves the leaf-major adjoint's workspace for the log chunks one
-    forward over these rays hands out (plus a quarter).  Returns the chunks
-    used and the chunks the log holds."""
+    """Sizes the segment log so that it holds every packet of a forward over
+    these rays (grown from its given size when the forward ran out of chunks:
+    the adjoint walks a packet the log does not hold again, which is slow for
+    long incoherent rays), then reserves the leaf-major adjoint's workspace
+    for the chunks used (plus a quarter).  Returns the chunks used and the
+    chunks the log holds."""
     import numpy as np
     import torch
-    B.neuvv_render(tree_d, dr, kernel="packet", out=out)
-    torch.cuda.synchronize()
-    head = out["log"][:3].cpu().numpy().astype(np.int64)
-    used, n_chunks = int(head[0]), int(head[2])
+    for _ in range(4):
+        B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+        torch.cuda.synchronize()
+        head = out["log"][:3].cpu().numpy().astype(np.int64)
+        used, n_chunks = int(head[0]), int(head[2])
+        if used <= n_chunks:
+            break
+        log = out["log"]
+        out["log"] = torch.empty(int(log.numel() * 1.25 * used / max(n_chunks, 1)) + 1024, dtype=log.dtype,
+                                 device=log.device)
+        del log
     if enable:
         tree_d.reserve_adjoint(min(n_chunks, used + used // 4 + 1) * 256)
     return used, n_chunks
@@ -875,7 +885,7 @@ def main():
         "time_slice_and_lighting": time_slice,
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": (8 if args.no_gather else 12) * args.steps,
+        "gpu_launches": (9 if args.no_gather else 13) * args.steps,
         "clocks": clk,
     }
     if not args.no_extra:

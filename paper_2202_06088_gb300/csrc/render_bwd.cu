@@ -364,13 +364,14 @@ cudaError_t launch_packet_order(const DevTree &tr, const DevRays &rays, const Sa
   return sort_packets_by_key(l, n_packets, tr.n_leaves, num_sms, s);
 }
 
-// Packet adjoint: replays each packet's shading rounds from the forward's
-// segment log when there is one; otherwise the forward packet kernel's
-// structure (one thread per ray, walk steps and sample rounds decoupled
-// through a per-lane queue), the walk stopped at the forward's segment count.
+// Walking adjoint of one packet (ray i of this lane) that the segment log
+// does not hold: the forward packet kernel's structure (walk steps and sample
+// rounds decoupled through a per-lane queue), the walk stopped at the
+// forward's segment count.  Not inlined: its state does not add to the
+// registers of the replay, which most packets take.
 template <int KP, int DEG, typename E>
-__global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a, int queue,
-                                                                int ready) {
+__device__ __noinline__ void adjoint_walk_packet(const BwdArgs &a, long long i, unsigned present, int queue,
+                                                 int ready) {
   extern __shared__ __align__(16) uint32_t smem[];
   const DevTree &tr = a.tr;
   const int B = blockDim.x, tid = threadIdx.x;
@@ -379,64 +380,12 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
   uint32_t *q_leaf = smem + (2 * KP + 16) * B + tid;
   float *q_dt = reinterpret_cast<float *>(q_leaf + queue * B);
   const SmemRows<KP> rows{my_rows, B};
-  // warp w adjoins packet w, or with a valid log the w-th packet in key order
-  const long long n_packets = (a.rays.n + 31) >> 5;
-  const long long wp = ((long long)blockIdx.x * B + tid) >> 5;
-  if (wp >= n_packets) return;
-  const bool logged = a.log.n_chunks && log_matches(a.log, a.rays.n);
-  const long long pk = logged ? (long long)min(__ldg(a.log.order + wp), (uint32_t)(n_packets - 1)) : wp;
-  const long long pos = (pk << 5) + (tid & 31);  // position; the ray is pos, or perm[pos] in a permuted log
-  const unsigned present = __ballot_sync(0xFFFFFFFFu, pos < a.rays.n);
-  if (pos >= a.rays.n) return;
-  const long long i =
-      logged && __ldg(a.log.header + 5) == 1u ? (long long)min(__ldg(a.log.perm + pos), (uint32_t)(a.rays.n - 1)) : pos;
   RayWalk w;
   AdjState st;
   float dn[3], t;
   const bool live = adjoint_setup(a, i, w, dn, t, st);
   if (__ballot_sync(present, live) == 0) return;
-  float Y[(DEG + 1) * (DEG + 1)];
-  if (live) {
-    rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
-    sh_real<DEG>(dn, Y);
-  }
-  if (logged) {
-    // replay the forward's shading rounds from its log: no walk
-    const uint32_t head = __ldg(a.log.heads + (pos >> 5));
-    if (head != kNoLog) {
-      const int lane = tid & 31;
-      const float u = t * (float)(tr.T - 1);
-      uint32_t chunk = head;
-      int round = 0;
-      while (__ballot_sync(present, live && st.count < st.target)) {
-        if (chunk >= a.log.n_chunks) {  // a log that does not belong to these rays
-          raise_status(tr, kStatusBadIndex);
-          return;
-        }
-        uint32_t leaf = kEmpty;
-        float dt = 0.f;
-        bool has = false;
-        const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
-        if (live && st.count < st.target) {
-          leaf = __ldg(a.log.leaf + slot);
-          if (leaf != kEmpty) {
-            ++st.count;
-            has = leaf < (uint32_t)tr.n_leaves;
-            if (has) dt = __ldg(a.log.dt + slot);
-            else raise_status(tr, kStatusBadIndex);
-          }
-        }
-        // chunks with room in the workspace: factors to the slot; others: atomics
-        if (chunk < a.gws.cap_chunks) adjoint_round_gather<KP, DEG, E>(a, rows, Y, leaf, dt, u, dn, has, st, slot);
-        else adjoint_round<KP, DEG, E>(a, rows, Y, leaf, dt, t, has, present, st);
-        if (++round == kLogRounds) {
-          round = 0;
-          chunk = __ldg(a.log.next + chunk);
-        }
-      }
-      return;
-    }
-  }
+  if (live) rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
   int walked = 0;  // segments found so far (the walk stops at the forward's count)
   bool walking = live && w.alive;
   int qh = 0, qn = 0;
@@ -469,7 +418,78 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
       --qn;
       ++st.count;
     }
+    float Y[(DEG + 1) * (DEG + 1)];
+    sh_real<DEG>(dn, Y);
     adjoint_round<KP, DEG, E>(a, rows, Y, leaf, dt, t, has, present, st);
+  }
+}
+
+// Packet adjoint: replays each packet's shading rounds from the forward's
+// segment log when the log holds the packet (no walk); other packets (all of
+// them without a log for these rays) take adjoint_walk_packet.
+template <int KP, int DEG, typename E>
+__global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet_kernel(const __grid_constant__ BwdArgs a, int queue,
+                                                                int ready) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const DevTree &tr = a.tr;
+  const int B = blockDim.x, tid = threadIdx.x;
+  float *my_rows = reinterpret_cast<float *>(smem) + tid;
+  const SmemRows<KP> rows{my_rows, B};
+  // warp w adjoins packet w, or with a valid log the w-th packet in key order
+  const long long n_packets = (a.rays.n + 31) >> 5;
+  const long long wp = ((long long)blockIdx.x * B + tid) >> 5;
+  if (wp >= n_packets) return;
+  const bool logged = a.log.n_chunks && log_matches(a.log, a.rays.n);
+  const long long pk = logged ? (long long)min(__ldg(a.log.order + wp), (uint32_t)(n_packets - 1)) : wp;
+  const long long pos = (pk << 5) + (tid & 31);  // position; the ray is pos, or perm[pos] in a permuted log
+  const unsigned present = __ballot_sync(0xFFFFFFFFu, pos < a.rays.n);
+  if (pos >= a.rays.n) return;
+  const long long i =
+      logged && __ldg(a.log.header + 5) == 1u ? (long long)min(__ldg(a.log.perm + pos), (uint32_t)(a.rays.n - 1)) : pos;
+  const uint32_t head = logged ? __ldg(a.log.heads + pk) : kNoLog;  // warp-uniform
+  if (head == kNoLog) {
+    adjoint_walk_packet<KP, DEG, E>(a, i, present, queue, ready);
+    return;
+  }
+  RayWalk w;
+  AdjState st;
+  float dn[3], t;
+  const bool live = adjoint_setup(a, i, w, dn, t, st);
+  if (__ballot_sync(present, live) == 0) return;
+  if (live) rows_to_smem<KP>(tr, t * (float)(tr.T - 1), my_rows, B);
+  // replay the forward's shading rounds from its log: no walk
+  const int lane = tid & 31;
+  const float u = t * (float)(tr.T - 1);
+  uint32_t chunk = head;
+  int round = 0;
+  while (__ballot_sync(present, live && st.count < st.target)) {
+    if (chunk >= a.log.n_chunks) {  // a log that does not belong to these rays
+      raise_status(tr, kStatusBadIndex);
+      return;
+    }
+    uint32_t leaf = kEmpty;
+    float dt = 0.f;
+    bool has = false;
+    const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
+    if (live && st.count < st.target) {
+      leaf = __ldg(a.log.leaf + slot);
+      if (leaf != kEmpty) {
+        ++st.count;
+        has = leaf < (uint32_t)tr.n_leaves;
+        if (has) dt = __ldg(a.log.dt + slot);
+        else raise_status(tr, kStatusBadIndex);
+      }
+    }
+    // the harmonics of the ray's direction, per round rather than held
+    float Y[(DEG + 1) * (DEG + 1)];
+    sh_real<DEG>(dn, Y);
+    // chunks with room in the workspace: factors to the slot; others: atomics
+    if (chunk < a.gws.cap_chunks) adjoint_round_gather<KP, DEG, E>(a, rows, Y, leaf, dt, u, dn, has, st, slot);
+    else adjoint_round<KP, DEG, E>(a, rows, Y, leaf, dt, t, has, present, st);
+    if (++round == kLogRounds) {
+      round = 0;
+      chunk = __ldg(a.log.next + chunk);
+    }
   }
 }
 

@@ -252,8 +252,11 @@ def test_adjoint_from_the_segment_log_matches_the_walk(B):
     walk = B.neuvv_render_backward(tree_d, dr, B.neuvv_render(tree_d, dr, kernel="packet"), g, kernel="packet")
     ref = walk.cpu().numpy().astype(np.float64)
     scale = np.abs(ref).max()
-    for per_ray in (64, 2):          # ample, then room for a few chunks only
+    for per_ray in (64, 24, 2):      # ample, room for a few packets only (the others are walked), none
         out = B.neuvv_render(tree_d, dr, kernel="packet", out=B.alloc_out(rays.n, log_bytes_per_ray=per_ray))
+        if per_ray == 24:
+            held = B.neuvv_log_read(out, rays.n, 8)["count"] >= 0
+            assert held.any().item() and (~held & (out["nseg"] > 0)).any().item()
         got = B.neuvv_render_backward(tree_d, dr, out, g, kernel="packet").cpu().numpy()
         assert np.abs(got - ref).max() <= 1e-5 * scale, per_ray
         assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)

@@ -885,7 +885,7 @@ def main():
         "time_slice_and_lighting": time_slice,
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": (9 if args.no_gather else 13) * args.steps,
+        "gpu_launches": (8 if args.no_gather else 12) * args.steps,
         "clocks": clk,
     }
     if not args.no_extra:

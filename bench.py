@@ -189,52 +189,78 @@ def grad_planes(ot):
             "w_hh": np.full((3, ot.N_h, ot.n_leaves), 0.0)}
 
 
+ORACLE_SPAN = 4096   # consecutive rays of the workload (a band of 128 pixel tiles of one view)
+
+
+ORACLE_SPANS_PER_CORE = 32   # spans per thread in one timed call (equal contiguous shares per thread)
+
+
+def oracle_sample(rng, n_rays, n_spans):
+    """Ray indices of n_spans seeded random distinct spans of ORACLE_SPAN
+    consecutive rays, the spans in random order.  The oracle's samples keep
+    the workload's neighbourhoods (a span's rays meet the same records, as
+    the GPU's packets do), and with many spans per thread each thread's share
+    mixes costly and cheap parts of the views."""
+    total = n_rays // ORACLE_SPAN
+    pick = rng.choice(total, size=min(max(n_spans, 1), total), replace=False)
+    return (pick[:, None] * ORACLE_SPAN + np.arange(ORACLE_SPAN)[None, :]).ravel()
+
+
+def oracle_step(tree, rays, ot, planes, rng, cores):
+    """One timed oracle call as both oracle arms make it: forward and adjoint
+    of ORACLE_SPANS_PER_CORE random spans per thread, accumulated into the
+    FP64 planes.  Returns (samples, seconds, the sample's rays, their dL/dC,
+    their segment counts)."""
+    import oracle
+    sub = rays.subset(oracle_sample(rng, rays.n, ORACLE_SPANS_PER_CORE * cores))
+    g = rng.standard_normal((sub.n, 3))
+    nseg = oracle.render(tree, sub, otree=ot, nthreads=cores)["nseg"]
+    t0 = time.perf_counter()
+    oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores, out=planes)
+    return int(nseg.sum()), time.perf_counter() - t0, sub, g, nseg
+
+
 def cpu_baseline(tree, rays, target_seconds, seed=99):
-    """FP64 oracle forward+adjoint on a seeded random sample of the same rays,
-    on all host cores, accumulated into FP64 gradient planes allocated once;
-    sized to about target_seconds of CPU work."""
+    """The FP64 oracle's forward+adjoint on the host cores, timed as the
+    reference arm times it (`oracle_step`), calls repeated until about
+    target_seconds; then part of one call's sample on one core."""
     import oracle
     rng = np.random.default_rng(seed)
     ot = oracle.OracleTree(tree)
     cores = oracle.default_threads()
     planes = grad_planes(ot)
-    # a probe fixes the sample size that takes about target_seconds
-    n_try = 2048 * cores
-    idx = np.sort(rng.choice(rays.n, size=n_try, replace=False))
-    sub = rays.subset(idx)
-    g = rng.standard_normal((sub.n, 3))
+    oracle_step(tree, rays, ot, planes, rng, cores)   # warm-up
+    samples, dt, calls = 0, 0.0, 0
+    while dt < target_seconds and calls < 64:
+        s_, t_, sub, g, nseg = oracle_step(tree, rays, ot, planes, rng, cores)
+        samples, dt, calls = samples + s_, dt + t_, calls + 1
+    # on one core: seeded spans of the last call's sample (about 3 s; one with samples at least)
+    per_span_seg = nseg.reshape(-1, ORACLE_SPAN).sum(1)
+    per_span = t_ * cores / per_span_seg.size
+    k1 = int(max(1, min(per_span_seg.size, 3.0 / per_span)))
+    spans1 = rng.choice(per_span_seg.size, size=k1, replace=False)
+    if per_span_seg[spans1].sum() == 0:
+        spans1[0] = rng.choice(np.nonzero(per_span_seg > 0)[0])
+    pick = (spans1[:, None] * ORACLE_SPAN + np.arange(ORACLE_SPAN)[None, :]).ravel()
+    s1 = int(nseg[pick].sum())
     t0 = time.perf_counter()
-    oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores, out=planes)
-    per_ray = max((time.perf_counter() - t0) / n_try, 1e-9)
-    n = int(min(rays.n, max(n_try, target_seconds / per_ray)))
-    idx = np.sort(rng.choice(rays.n, size=n, replace=False))
-    sub = rays.subset(idx)
-    g = rng.standard_normal((sub.n, 3))
-    fwd = oracle.render(tree, sub, otree=ot, nthreads=cores)
-    samples = int(fwd["nseg"].sum())
-    t0 = time.perf_counter()
-    oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores, out=planes)
-    dt = time.perf_counter() - t0
-    # the same on one core, on a seeded part of the sample of about 3 s
-    n1 = int(max(1024, min(n, 3.0 / (per_ray * cores))))
-    pick = np.sort(rng.choice(n, size=n1, replace=False))
-    sub1 = sub.subset(pick)
-    s1 = int(fwd["nseg"][pick].sum())
-    t0 = time.perf_counter()
-    oracle.render_grad(tree, sub1, g[pick], otree=ot, nthreads=1, out=planes)
+    oracle.render_grad(tree, sub.subset(pick), g[pick], otree=ot, nthreads=1, out=planes)
     dt1 = time.perf_counter() - t0
+    per_call = ORACLE_SPAN * ORACLE_SPANS_PER_CORE * cores
     return {"value": samples / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} seeded random rays of the same 16.6M-ray workload ({samples} samples), "
-                      f"FP64 forward+adjoint into gradient planes allocated once, {dt:.1f} s",
-            "single_core": {"value": s1 / dt1 / 1e6, "unit": UNIT, "rays": n1, "seconds": dt1}}
+            "sample": f"{calls} calls of {per_call} rays, each in {ORACLE_SPANS_PER_CORE * cores} seeded random spans "
+                      f"of {ORACLE_SPAN} consecutive rays of the same 16.6M-ray workload ({samples} samples in "
+                      f"all), FP64 forward+adjoint into gradient planes allocated once, {dt:.1f} s",
+            "single_core": {"value": s1 / dt1 / 1e6, "unit": UNIT, "rays": int(pick.size), "seconds": dt1}}
 
 
 def run_reference(args):
     """The reference arm: the FP64 oracle (the only reference this method has)
     timed on bounded samples of the same workload on the host cores.  Each
-    step is the forward and adjoint of a seeded sample of the rays,
-    accumulated into FP64 gradient planes allocated once, outside the timed
-    region (as the GPU's adjoint accumulates into its gradient buffer)."""
+    step is one call as `cpu_baseline` makes them (`oracle_step`: the
+    forward and adjoint of seeded random spans of the rays, accumulated into
+    FP64 gradient planes allocated once, outside the timed region, as the
+    GPU's adjoint accumulates into its gradient buffer)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -246,17 +272,11 @@ def run_reference(args):
     ot = oracle.OracleTree(tree)
     cores = oracle.default_threads()
     rng = np.random.default_rng(5)
-    per_step = 4096 * cores
+    per_step = ORACLE_SPAN * ORACLE_SPANS_PER_CORE * cores   # one call of cpu_baseline per step
     planes = grad_planes(ot)
     times, samples = [], []
     for s in range(args.warmup + args.steps):
-        idx = np.sort(rng.choice(rays.n, size=per_step, replace=False))
-        sub = rays.subset(idx)
-        g = rng.standard_normal((sub.n, 3))
-        nseg = int(oracle.render(tree, sub, otree=ot, nthreads=cores)["nseg"].sum())
-        t0 = time.perf_counter()
-        oracle.render_grad(tree, sub, g, otree=ot, nthreads=cores, out=planes)
-        dt = time.perf_counter() - t0
+        nseg, dt = oracle_step(tree, rays, ot, planes, rng, cores)[:2]
         if s >= args.warmup:
             times.append(dt)
             samples.append(nseg)
@@ -266,8 +286,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "per_step_sample_rays": per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} seeded random rays of the workload per step, FP64 fwd+adjoint "
-                                       "into gradient planes allocated once"},
+                             "sample": f"{per_step} rays per step in {ORACLE_SPANS_PER_CORE * cores} seeded random "
+                                       f"spans of {ORACLE_SPAN} "
+                                       "consecutive rays of the workload, FP64 fwd+adjoint into gradient planes "
+                                       "allocated once"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -812,21 +812,27 @@ def main():
                      + touched_leaves * info.rec_len * 10),
         "mse": (n * 36, 0),
     }
+    def roofline_of(part):
+        bytes_, flops_ = traffic[part]
+        t_s = kern[part] / 1e3
+        if flops_ / (fp32_tflops * 1e12) > bytes_ / (hbm_gbs * 1e9):
+            r = {"bound": "alu", "achieved": flops_ / t_s / 1e12, "peak": fp32_tflops, "unit": "TFLOP/s",
+                 "peak_kind": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"}
+        else:
+            r = {"bound": "hbm", "achieved": bytes_ / t_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                 "peak_kind": f"{peak_kind} (copy bandwidth)"}
+        r["frac"] = r["achieved"] / r["peak"]
+        r["kernel"] = part
+        # DRAM bytes per launch from one ncu capture of this workload (null once the kernel changed)
+        r["traffic"] = measured_traffic(part) if args.views == 8 else None
+        r["algorithmic_bytes"] = bytes_
+        r["algorithmic_flops"] = flops_
+        return r
+
     dom = max(("fwd", "mse", "bwd_adam"), key=kern.get)
-    bytes_, flops_ = traffic[dom]
-    t_s = kern[dom] / 1e3
-    if flops_ / (fp32_tflops * 1e12) > bytes_ / (hbm_gbs * 1e9):
-        roof = {"bound": "alu", "achieved": flops_ / t_s / 1e12, "peak": fp32_tflops, "unit": "TFLOP/s",
-                "peak_kind": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"}
-    else:
-        roof = {"bound": "hbm", "achieved": bytes_ / t_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
-                "peak_kind": f"{peak_kind} (copy bandwidth)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom
-    # DRAM bytes per launch from one ncu capture of this workload (null once the kernel changed)
-    roof["traffic"] = measured_traffic(dom) if args.views == 8 else None
-    roof["algorithmic_bytes"] = bytes_
-    roof["algorithmic_flops"] = flops_
+    roof = roofline_of(dom)
+    # the other large step part against its own roof
+    roof_other = {p: roofline_of(p) for p in ("fwd", "bwd_adam") if p != dom}
 
     # -- end to end through the C ABI with host buffers.  Every step copies its
     # inputs in from pinned host memory -- the target images and the views'
@@ -906,6 +912,7 @@ def main():
         "fp8_ablation": fp8,
         "time_slice_and_lighting": time_slice,
         "roofline": roof,
+        "roofline_other_parts": roof_other,
         "e2e": e2e,
         "gpu_launches": (8 if args.no_gather else 12) * args.steps,
         "clocks": clk,

@@ -269,6 +269,75 @@ void fill_coarse(const uint32_t *child, uint32_t node, int level, int Lb, int ox
   }
 }
 
+// Empty boxes of the brick map's empty cells.  Each starts as the cube of
+// radius k-1 around the cell (k its Chebyshev distance to the nearest
+// occupied cell) and grows, face by face (+x, -x, +y, -y, +z, -z, in two
+// rounds, the first capped at the cube's size), as far as it stays empty; a
+// box-emptiness test is O(1) on a prefix sum of the occupancy.  The word of
+// an empty cell is then (kCoarseEmpty << 28) | (s << 24) | the six extents
+// (cells below and above the cell on x, y, z, 4 bits each, in units of 2^s,
+// rounded down): s is the smallest shift that fits the largest extent.
+void coarse_empty_boxes(const std::vector<uint8_t> &occ, const std::vector<int32_t> &dist, int n,
+                        std::vector<uint32_t> &map) {
+  const size_t m = (size_t)n + 1;
+  std::vector<int32_t> P(m * m * m, 0);
+  auto pa = [m](int x, int y, int z) { return ((size_t)x * m + y) * m + z; };
+  for (int x = 0; x < n; ++x)
+    for (int y = 0; y < n; ++y)
+      for (int z = 0; z < n; ++z)
+        P[pa(x + 1, y + 1, z + 1)] = occ[((size_t)x * n + y) * n + z] + P[pa(x, y + 1, z + 1)] +
+                                     P[pa(x + 1, y, z + 1)] + P[pa(x + 1, y + 1, z)] - P[pa(x, y, z + 1)] -
+                                     P[pa(x, y + 1, z)] - P[pa(x + 1, y, z)] + P[pa(x, y, z)];
+  // occupied cells in [lo, hi] (inclusive) per axis
+  auto count = [&](const int lo[3], const int hi[3]) {
+    const int x0 = lo[0], y0 = lo[1], z0 = lo[2], x1 = hi[0] + 1, y1 = hi[1] + 1, z1 = hi[2] + 1;
+    return P[pa(x1, y1, z1)] - P[pa(x0, y1, z1)] - P[pa(x1, y0, z1)] - P[pa(x1, y1, z0)] + P[pa(x0, y0, z1)] +
+           P[pa(x0, y1, z0)] + P[pa(x1, y0, z0)] - P[pa(x0, y0, z0)];
+  };
+  for (int x = 0; x < n; ++x)
+    for (int y = 0; y < n; ++y)
+      for (int z = 0; z < n; ++z) {
+        const size_t q = ((size_t)x * n + y) * n + z;
+        if (occ[q]) continue;
+        const int c[3] = {x, y, z}, r = std::max(dist[q] - 1, 0);
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = std::max(c[a] - r, 0);
+          hi[a] = std::min(c[a] + r, n - 1);
+        }
+        for (int round = 0; round < 2; ++round)
+          for (int f = 0; f < 6; ++f) {
+            const int a = f >> 1;
+            const bool up = (f & 1) == 0;
+            const int room = up ? n - 1 - hi[a] : lo[a];
+            int best = 0, top = round == 0 ? std::min(room, 2 * r + 1) : room;
+            // largest extension g <= top whose slab keeps the box empty (monotone in g)
+            int l = 1, h = top;
+            while (l <= h) {
+              const int g = (l + h) / 2;
+              int slo[3] = {lo[0], lo[1], lo[2]}, shi[3] = {hi[0], hi[1], hi[2]};
+              if (up) { slo[a] = hi[a] + 1; shi[a] = hi[a] + g; }
+              else { slo[a] = lo[a] - g; shi[a] = lo[a] - 1; }
+              if (count(slo, shi) == 0) { best = g; l = g + 1; }
+              else h = g - 1;
+            }
+            if (up) hi[a] += best;
+            else lo[a] -= best;
+          }
+        int e[6], emax = 0;
+        for (int a = 0; a < 3; ++a) {
+          e[2 * a] = c[a] - lo[a];
+          e[2 * a + 1] = hi[a] - c[a];
+          emax = std::max(emax, std::max(e[2 * a], e[2 * a + 1]));
+        }
+        uint32_t sh = 0;
+        while ((emax >> sh) > 15) ++sh;
+        uint32_t w = (kCoarseEmpty << 28) | (sh << 24);
+        for (int i = 0; i < 6; ++i) w |= (uint32_t)(e[i] >> sh) << (4 * i);
+        map[q] = w;
+      }
+}
+
 // Chebyshev (L-infinity) distance from every cell of an n^3 grid to the
 // nearest occupied cell (0 for occupied cells; `far` when there is none):
 // the one-dimensional distance along z, then two passes of
@@ -506,8 +575,7 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
         std::vector<uint8_t> occ(n3);
         for (size_t q = 0; q < n3; ++q) occ[q] = (map[q] >> 28) != kCoarseEmpty;
         const std::vector<int32_t> dist = chebyshev_distance(occ, nc, nc);
-        for (size_t q = 0; q < n3; ++q)
-          if (!occ[q]) map[q] = (kCoarseEmpty << 28) | (uint32_t)dist[q];
+        coarse_empty_boxes(occ, dist, nc, map);
         NEUVV_TRY(cudaMalloc(&t->coarse, n3 * 4), "cudaMalloc(brick map)");
         NEUVV_TRY(cudaMemcpy(t->coarse, map.data(), n3 * 4, cudaMemcpyHostToDevice), "copy brick map");
       }

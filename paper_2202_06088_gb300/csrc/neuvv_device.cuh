@@ -53,9 +53,10 @@ struct DevTree {
   // Brick map: a dense grid over the cells of level brick_level, one word per
   // cell: (0 << 28) | brick index (the cell is an internal node with a brick),
   // (L << 28) | leaf id (the cell lies in a leaf of level L <= brick_level), or
-  // (kCoarseEmpty << 28) | k for an empty cell whose Chebyshev distance to the
-  // nearest non-empty cell is k >= 1 (the box of radius k-1 around it is
-  // empty).  Null when the tree has none; the walk then descends the octree.
+  // (kCoarseEmpty << 28) | (s << 24) | six 4-bit extents for an empty cell:
+  // the box from (cell - below * 2^s) to (cell + above * 2^s) per axis, x in
+  // bits 0-7, y 8-15, z 16-23 (below in the low nibble), holds no non-empty
+  // cell.  Null when the tree has none; the walk then descends the octree.
   const uint32_t *coarse;
   // Limits: walk steps per ray (0: 3 * 2^depth + 8, enough for any ray) and
   // polls of a bounded wait before it gives up and flags kStatusTimeout.
@@ -345,13 +346,15 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
     }
     const uint32_t cw = w.c_word, kind = cw >> 28;
     if (kind == kCoarseEmpty) {
-      // empty box of radius k-1 brick-map cells around this one
-      const int r = (int)(cw & 0x0FFFFFFFu) - 1, Nc = 1 << Lc;
+      // the empty box around this brick-map cell: extents below and above
+      // it per axis, 4 bits each in units of 2^s cells
+      const int s = (int)((cw >> 24) & 15u), Nc = 1 << Lc;
       const int cc[3] = {cx, cy, cz};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        lo[a] = max(cc[a] - r, 0) << cs;
-        hi[a] = min(cc[a] + r + 1, Nc) << cs;
+        const int below = (int)((cw >> (8 * a)) & 15u) << s, above = (int)((cw >> (8 * a + 4)) & 15u) << s;
+        lo[a] = max(cc[a] - below, 0) << cs;
+        hi[a] = min(cc[a] + above + 1, Nc) << cs;
       }
       e = kEmpty;
     } else {

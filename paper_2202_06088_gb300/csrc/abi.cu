@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/neuvv.h"
@@ -338,6 +339,107 @@ void coarse_empty_boxes(const std::vector<uint8_t> &occ, const std::vector<int32
       }
 }
 
+// Empty boxes inside bricks.  For each empty finest cell of a brick the box
+// starts as the empty octree node holding it (aligned, from the entry's
+// level) and grows face by face (+x, -x, +y, -y, +z, -z, one binary search
+// each) as far as it stays empty within the 3x3x3 brick-map neighbourhood of
+// the brick (24^3 finest cells, occupancy from the neighbours' bricks and
+// leaves, cells outside the root box counted as occupied).  Its extents below
+// and above the cell (at most 15 per side) go into the entry as
+// kBrickBoxBase | extents (4 bits each: x in bits 0-7, y 8-15, z 16-23, below
+// in the low nibble); the level bits stay.  Bricks are split over host
+// threads; `in` is only read and `out` only written.
+void brick_empty_boxes(const std::vector<uint32_t> &in, std::vector<uint32_t> &out, const std::vector<uint32_t> &map,
+                       int nc, int depth) {
+  constexpr int W = 24, M = W + 1;
+  const int64_t n_bricks = (int64_t)(in.size() / 512);
+  // brick index -> its brick-map cell
+  std::vector<int32_t> cell_of_brick(n_bricks, -1);
+  for (size_t q = 0; q < map.size(); ++q)
+    if ((map[q] >> 28) == 0 && (int64_t)(map[q] & 0x0FFFFFFFu) < n_bricks) cell_of_brick[map[q] & 0x0FFFFFFFu] = (int32_t)q;
+  auto work = [&](int64_t b0, int64_t b1) {
+    std::vector<uint8_t> occ(W * W * W);
+    std::vector<int32_t> P(M * M * M);
+    auto pa = [&](int x, int y, int z) { return (x * M + y) * M + z; };
+    auto count = [&](const int lo[3], const int hi[3]) {
+      const int x0 = lo[0], y0 = lo[1], z0 = lo[2], x1 = hi[0] + 1, y1 = hi[1] + 1, z1 = hi[2] + 1;
+      return P[pa(x1, y1, z1)] - P[pa(x0, y1, z1)] - P[pa(x1, y0, z1)] - P[pa(x1, y1, z0)] + P[pa(x0, y0, z1)] +
+             P[pa(x0, y1, z0)] + P[pa(x1, y0, z0)] - P[pa(x0, y0, z0)];
+    };
+    for (int64_t b = b0; b < b1; ++b) {
+      const int32_t q = cell_of_brick[b];
+      if (q < 0) continue;
+      const int cx = q / (nc * nc), cy = (q / nc) % nc, cz = q % nc;
+      // occupancy of the window: finest cells of the 27 brick-map cells around
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            const int ux = cx + dx, uy = cy + dy, uz = cz + dz;
+            const bool inside = ux >= 0 && uy >= 0 && uz >= 0 && ux < nc && uy < nc && uz < nc;
+            const uint32_t w = inside ? map[((size_t)ux * nc + uy) * nc + uz] : 0u;
+            const uint32_t kind = w >> 28;
+            const uint32_t *nb = inside && kind == 0 ? in.data() + (size_t)(w & 0x0FFFFFFFu) * 512 : nullptr;
+            for (int x = 0; x < 8; ++x)
+              for (int y = 0; y < 8; ++y)
+                for (int z = 0; z < 8; ++z) {
+                  uint8_t o;
+                  if (!inside) o = 1;
+                  else if (kind == kCoarseEmpty) o = 0;
+                  else if (kind != 0) o = 1;
+                  else o = (nb[(x << 6) | (y << 3) | z] & 0x0FFFFFFFu) < kBrickBoxBase;
+                  occ[((dx + 1) * 8 + x) * W * W + ((dy + 1) * 8 + y) * W + (dz + 1) * 8 + z] = o;
+                }
+          }
+      for (int x = 0; x < W; ++x)
+        for (int y = 0; y < W; ++y)
+          for (int z = 0; z < W; ++z)
+            P[pa(x + 1, y + 1, z + 1)] = occ[(x * W + y) * W + z] + P[pa(x, y + 1, z + 1)] + P[pa(x + 1, y, z + 1)] +
+                                         P[pa(x + 1, y + 1, z)] - P[pa(x, y, z + 1)] - P[pa(x, y + 1, z)] -
+                                         P[pa(x + 1, y, z)] + P[pa(x, y, z)];
+      for (int x = 0; x < 8; ++x)
+        for (int y = 0; y < 8; ++y)
+          for (int z = 0; z < 8; ++z) {
+            const size_t k = (size_t)b * 512 + ((x << 6) | (y << 3) | z);
+            const uint32_t v = in[k];
+            if ((v & 0x0FFFFFFFu) != kBrickEmpty) continue;
+            // the empty node holding the cell (aligned, from its level)
+            const int size = 1 << std::max(0, depth - (int)(v >> 28));
+            const int c[3] = {8 + x, 8 + y, 8 + z};
+            int lo[3], hi[3];
+            for (int a = 0; a < 3; ++a) {
+              lo[a] = 8 + ((c[a] - 8) & -size);
+              hi[a] = lo[a] + size - 1;
+            }
+            for (int f = 0; f < 6; ++f) {
+              const int a = f >> 1;
+              const bool up = (f & 1) == 0;
+              int best = 0, l = 1, h = up ? W - 1 - hi[a] : lo[a];
+              while (l <= h) {
+                const int g = (l + h) / 2;
+                int slo[3] = {lo[0], lo[1], lo[2]}, shi[3] = {hi[0], hi[1], hi[2]};
+                if (up) { slo[a] = hi[a] + 1; shi[a] = hi[a] + g; }
+                else { slo[a] = lo[a] - g; shi[a] = lo[a] - 1; }
+                if (count(slo, shi) == 0) { best = g; l = g + 1; }
+                else h = g - 1;
+              }
+              if (up) hi[a] += best;
+              else lo[a] -= best;
+            }
+            uint32_t ext = 0;
+            for (int a = 0; a < 3; ++a) {
+              ext |= (uint32_t)std::min(c[a] - lo[a], 15) << (8 * a);
+              ext |= (uint32_t)std::min(hi[a] - c[a], 15) << (8 * a + 4);
+            }
+            out[k] = (v & 0xF0000000u) | kBrickBoxBase | ext;
+          }
+    }
+  };
+  const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (int i = 0; i < nt; ++i) th.emplace_back(work, n_bricks * i / nt, n_bricks * (i + 1) / nt);
+  for (auto &x : th) x.join();
+}
+
 // Chebyshev (L-infinity) distance from every cell of an n^3 grid to the
 // nearest occupied cell (0 for occupied cells; `far` when there is none):
 // the one-dimensional distance along z, then two passes of
@@ -546,7 +648,7 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
   }
   // -- bricks at level depth-3 (8^3 finest cells per internal node there),
   //    when those nodes form one contiguous index range and leaf ids fit
-  if (!(d.flags & NEUVV_TREE_NO_BRICKS) && d.depth >= 3 && d.n_leaves < (int64_t)kBrickEmpty) {
+  if (!(d.flags & NEUVV_TREE_NO_BRICKS) && d.depth >= 3 && d.n_leaves < (int64_t)kBrickBoxBase) {
     const int Lb = d.depth - 3, sh = 3;
     int64_t first = -1, last = -1;
     bool contiguous = true;
@@ -561,12 +663,11 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
       std::vector<uint32_t> br((size_t)count * 512, 0);
       for (int64_t n = first; n <= last; ++n)
         fill_brick(d.child, (uint32_t)n, Lb, d.depth, sh, 0, 0, 0, br.data() + (size_t)(n - first) * 512);
-      NEUVV_TRY(cudaMalloc(&t->bricks, br.size() * 4), "cudaMalloc(bricks)");
-      NEUVV_TRY(cudaMemcpy(t->bricks, br.data(), br.size() * 4, cudaMemcpyHostToDevice), "copy bricks");
       t->brick_level = Lb;
       t->brick_first = (int)first;
       t->brick_count = (int)count;
-      // brick map over the level-Lb cells (kept to 128^3 cells, 8 MB)
+      // brick map over the level-Lb cells (kept to 128^3 cells, 8 MB), and
+      // with it the empty boxes inside the bricks
       if (Lb >= 1 && Lb <= 7) {
         const int nc = 1 << Lb;
         const size_t n3 = (size_t)nc * nc * nc;
@@ -575,10 +676,15 @@ neuvv_status neuvv_tree_create(const neuvv_tree_desc *desc, neuvv_tree **out) {
         std::vector<uint8_t> occ(n3);
         for (size_t q = 0; q < n3; ++q) occ[q] = (map[q] >> 28) != kCoarseEmpty;
         const std::vector<int32_t> dist = chebyshev_distance(occ, nc, nc);
+        std::vector<uint32_t> boxed(br);
+        brick_empty_boxes(br, boxed, map, nc, d.depth);
+        br.swap(boxed);
         coarse_empty_boxes(occ, dist, nc, map);
         NEUVV_TRY(cudaMalloc(&t->coarse, n3 * 4), "cudaMalloc(brick map)");
         NEUVV_TRY(cudaMemcpy(t->coarse, map.data(), n3 * 4, cudaMemcpyHostToDevice), "copy brick map");
       }
+      NEUVV_TRY(cudaMalloc(&t->bricks, br.size() * 4), "cudaMalloc(bricks)");
+      NEUVV_TRY(cudaMemcpy(t->bricks, br.data(), br.size() * 4, cudaMemcpyHostToDevice), "copy bricks");
     }
   }
 #undef NEUVV_TRY

@@ -45,9 +45,10 @@ struct DevTree {
   int depth, T, K, rec_stride, smem_nodes;
   // Bricks: for each internal node at brick_level (nodes brick_first ..
   // brick_first + brick_count - 1), a dense table over its finest cells of
-  // (level << 28 | leaf id), 0x0FFFFFFF as id for empty: the node that holds
-  // each cell, so the descent below brick_level is one load.  Null when the
-  // tree has none.
+  // (level << 28 | leaf id), an id from kBrickBoxBase up for empty: the node
+  // that holds each cell, so the descent below brick_level is one load (and
+  // for an empty cell, when the id says so, an empty box around it larger
+  // than its node).  Null when the tree has none.
   const uint32_t *bricks;
   int brick_level, brick_first, brick_count;
   // Brick map: a dense grid over the cells of level brick_level, one word per
@@ -66,6 +67,11 @@ struct DevTree {
 constexpr uint32_t kCoarseEmpty = 15u;
 
 constexpr uint32_t kBrickEmpty = 0x0FFFFFFFu;
+// Brick entries with an id from kBrickBoxBase up are empty: kBrickEmpty, or
+// kBrickBoxBase | the extents of an empty box around the cell (4 bits each,
+// cells below and above it on x in bits 0-7, y 8-15, z 16-23, below in the
+// low nibble).  Leaf ids stay below kBrickBoxBase.
+constexpr uint32_t kBrickBoxBase = 0x0F000000u;
 
 __device__ __forceinline__ void raise_status(const DevTree &tr, uint32_t bit) {
   if (tr.status) atomicOr(tr.status, bit);
@@ -289,7 +295,7 @@ __device__ __forceinline__ uint32_t descend(const DevTree &tr, const uint32_t *s
       const uint32_t v = __ldg(tr.bricks + ((size_t)b << (3 * sh)) + idx);
       level = (int)(v >> 28);
       const uint32_t id = v & kBrickEmpty;
-      return id == kBrickEmpty ? kEmpty : (kLeafBit | id);
+      return id >= kBrickBoxBase ? kEmpty : (kLeafBit | id);
     }
     const int bit = D - 1 - L;
     const int slot = (((cell[0] >> bit) & 1) << 2) | (((cell[1] >> bit) & 1) << 1) | ((cell[2] >> bit) & 1);
@@ -359,6 +365,7 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
       e = kEmpty;
     } else {
       int level;
+      uint32_t box = 0u;  // an empty box's code from the brick (0: none)
       if (kind == 0) {
         const uint32_t b = cw & 0x0FFFFFFFu;
         if (b >= (uint32_t)tr.brick_count) {
@@ -371,7 +378,8 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
         const uint32_t v = __ldg(tr.bricks + ((size_t)b << (3 * cs)) + idx);
         level = (int)(v >> 28);
         const uint32_t id = v & kBrickEmpty;
-        e = id == kBrickEmpty ? kEmpty : (kLeafBit | id);
+        e = id >= kBrickBoxBase ? kEmpty : (kLeafBit | id);
+        if (id >= kBrickBoxBase && id != kBrickEmpty) box = id;  // an empty box around the cell
       } else {
         level = (int)kind;
         e = kLeafBit | (cw & 0x0FFFFFFFu);
@@ -380,12 +388,22 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
         raise_status(tr, kStatusBadIndex);
         e = kEmpty;
       }
-      const int size = 1 << (tr.depth - level);
-      fine = size == 1;
+      if (box) {
+        // extents below and above the cell per axis, 4 bits each
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        lo[a] = w.cell[a] & -size;
-        hi[a] = lo[a] + size;
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = w.cell[a] - (int)((box >> (8 * a)) & 15u);
+          hi[a] = w.cell[a] + (int)((box >> (8 * a + 4)) & 15u) + 1;
+        }
+        fine = (box & 0x00FFFFFFu) == 0u;
+      } else {
+        const int size = 1 << (tr.depth - level);
+        fine = size == 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = w.cell[a] & -size;
+          hi[a] = lo[a] + size;
+        }
       }
     }
   } else {

@@ -267,11 +267,12 @@ neuvv_status neuvv_render_slice(const neuvv_tree *tree, const float *slice, int3
 /* Reserves device memory for the leaf-major adjoint (synchronous; frees an
  * earlier reservation; n_slots = 0 only frees).  A slot is one lane of one
  * shading round of a segment log (a log of B bytes holds fewer than B / 8);
- * the reservation takes 56 B per slot plus 4 B per leaf.  With it,
+ * the reservation takes 32 B per slot plus 8 B per leaf.  With it,
  * neuvv_render_backward (packet kernel, with a log from the forward over the
- * same rays) leaves each logged sample's gradient factors in its slot, lists
- * each leaf's samples by a counting sort, and sums them one leaf per thread
- * into the leaf's gradient record: no gradient atomics for those samples.
+ * same rays) counts each leaf's logged samples, writes each replayed
+ * sample's gradient factors at the next position of its leaf's run (leaf
+ * order), and sums each run one leaf per thread into the leaf's gradient
+ * record: no gradient atomics for those samples.
  * Samples in chunks beyond the reservation, and packets the log could not
  * hold, use the atomic scatter.  The result equals the atomic path's up to
  * FP32 summation order.  It pays when a call has many samples per leaf (8

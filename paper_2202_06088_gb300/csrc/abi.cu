@@ -106,9 +106,8 @@ namespace {
 
 void free_gather(neuvv_tree *t) {
   cudaFree(t->gws.fac);
-  cudaFree(t->gws.fl);
-  cudaFree(t->gws.idx);
   cudaFree(t->gws.off);
+  cudaFree(t->gws.cur);
   cudaFree(t->gws.part);
   t->gws = GatherWs{};
 }
@@ -138,6 +137,7 @@ DevTree dev_tree(const neuvv_tree *t) {
   d.brick_first = t->brick_first;
   d.brick_count = t->brick_count;
   d.coarse = t->coarse;
+  d.path_words = t->coarse ? 0 : kPathWords;
   d.step_cap = t->step_cap;
   d.wait_polls = t->wait_polls;
   return d;
@@ -727,10 +727,9 @@ neuvv_status neuvv_tree_reserve_adjoint(neuvv_tree *t, int64_t n_slots) {
   if (chunks == 0) return NEUVV_OK;
   const size_t slots = (size_t)chunks * kLogRounds * 32;
   GatherWs w{};
-  if (cudaMalloc(&w.fac, slots * 3 * sizeof(float4)) != cudaSuccess ||
-      cudaMalloc(&w.fl, slots * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMalloc(&w.idx, slots * sizeof(uint32_t)) != cudaSuccess ||
+  if (cudaMalloc(&w.fac, slots * 2 * sizeof(float4)) != cudaSuccess ||
       cudaMalloc(&w.off, (size_t)(nl + 1) * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&w.cur, (size_t)(nl + 1) * sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&w.part, kScanParts * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
     t->gws = w;
@@ -738,13 +737,6 @@ neuvv_status neuvv_tree_reserve_adjoint(neuvv_tree *t, int64_t n_slots) {
     return fail(NEUVV_ERR_OOM, "cudaMalloc of the adjoint workspace (%zu slots)", slots);
   }
   w.cap_chunks = (uint32_t)chunks;
-  if ((e = cudaMemset(w.fl, 0xFF, slots * sizeof(uint32_t))) != cudaSuccess ||  // all kEmpty
-      (e = cudaMemset(w.idx, 0, slots * sizeof(uint32_t))) != cudaSuccess ||
-      (e = cudaDeviceSynchronize()) != cudaSuccess) {
-    t->gws = w;
-    free_gather(t);
-    return cuda_fail(e, "initialise the adjoint workspace");
-  }
   t->gws = w;
   return NEUVV_OK;
 }

@@ -62,6 +62,9 @@ struct DevTree {
   // Limits: walk steps per ray (0: 3 * 2^depth + 8, enough for any ray) and
   // polls of a bounded wait before it gives up and flags kStatusTimeout.
   int step_cap, wait_polls;
+  // Words of the per-thread descent path in a packet kernel's shared memory
+  // (0 with a brick map, whose walk never descends the child table).
+  int path_words;
 };
 
 constexpr uint32_t kCoarseEmpty = 15u;
@@ -996,14 +999,16 @@ struct DevRays {
   float t_scalar;
 };
 
+// Rays are read once per launch: loads with the evict-first (streaming)
+// policy leave L2 to the records and the walk's tables.
 __device__ __forceinline__ void load_ray(const DevRays &r, long long i, float o[3], float d[3], float &t) {
-  o[0] = __ldg(r.ox + i);
-  o[1] = __ldg(r.oy + i);
-  o[2] = __ldg(r.oz + i);
-  d[0] = __ldg(r.dx + i);
-  d[1] = __ldg(r.dy + i);
-  d[2] = __ldg(r.dz + i);
-  t = r.t ? __ldg(r.t + i) : r.t_scalar;
+  o[0] = __ldcs(r.ox + i);
+  o[1] = __ldcs(r.oy + i);
+  o[2] = __ldcs(r.oz + i);
+  d[0] = __ldcs(r.dx + i);
+  d[1] = __ldcs(r.dy + i);
+  d[2] = __ldcs(r.dz + i);
+  t = r.t ? __ldcs(r.t + i) : r.t_scalar;
   t = fminf(fmaxf(t, 0.f), 1.f);
 }
 

@@ -66,19 +66,23 @@ struct FwdArgs {
   const uint32_t *perm;      // ray at each position (null: position = ray)
 };
 
-// Workspace of the leaf-major adjoint (owned by the tree; fac, fl and idx
-// have one entry per slot of the first cap_chunks chunks of a segment log).
-// A replayed sample leaves its gradient factors in its slot; a counting sort
-// lists each leaf's slots; one thread per leaf then sums them into its
-// gradient record.  fl is all kEmpty between launches.
+// Workspace of the leaf-major adjoint (owned by the tree; fac has one
+// 32-byte record per slot of the first cap_chunks chunks of a segment log).
+// A count over the log gives each leaf's samples and, scanned, the first
+// position of its run in leaf order; the replay takes each sample's position
+// from cur (a warp-aggregated atomic per leaf and round) and writes the
+// sample's gradient factors there; one thread per leaf then reads its run
+// [off[leaf], cur[leaf]) front to back.
 struct GatherWs {
-  float4 *fac;           // [slots][3]: dpre_s, dpre_g, dz0, dz1 | dz2, u, dn0, dn1 | dn2, 0, 0, 0
-  uint32_t *fl;          // [slots] leaf of the slot's sample, kEmpty for none
-  uint32_t *off;         // [n_leaves + 1] samples per leaf, then their offsets
-  uint32_t *idx;         // [slots] slots listed leaf by leaf
+  float4 *fac;           // [slots][2]: dpre_s, dpre_g, dz0, dz1 | dz2, u, e0, e1 ((e0, e1): octahedral
+                         // code of the unit direction; e0 = kNoFactor: a sample of zero density)
+  uint32_t *off;         // [n_leaves + 1] samples per leaf, then the first position of each leaf's run
+  uint32_t *cur;         // [n_leaves + 1] next free position of each leaf's run
   uint32_t *part;        // [kScanParts] block sums of the offsets' scan
   uint32_t cap_chunks;   // 0: no workspace (the atomic scatter only)
 };
+// Marks a factor record without a contribution (octahedral codes lie in [-1, 1]).
+constexpr float kNoFactor = 4.f;
 // Offsets are scanned in tiles of kScanTile leaves, at most kScanParts tiles.
 constexpr int kScanTile = 4096, kScanParts = 4096;
 
@@ -236,10 +240,13 @@ cudaError_t launch_grad_loss(const float *rgb, const float *target, const int *m
                              long long n_views, long long n_rays, float lam, float *grad, float *loss, cudaStream_t s);
 
 // Dynamic shared memory of the packet kernels: per thread the basis rows
-// (2 K_pad floats), the descent path (16 levels) and the segment queue
-// (queue x {leaf, t0, t1}).
-inline size_t smem_bytes(int block, int KP, int queue) {
-  return (size_t)block * (2 * KP + 16 + 3 * queue) * sizeof(float);
+// (2 K_pad floats), the descent path (kPathWords levels; none for a tree with
+// a brick map, whose walk never descends the child table) and the segment
+// queue (queue x {leaf, t0, t1}).
+constexpr int kPathWords = 16;
+__host__ __device__ inline int path_words(const DevTree &tr) { return tr.path_words; }
+inline size_t smem_bytes(int block, int KP, int queue, const DevTree &tr) {
+  return (size_t)block * (2 * KP + path_words(tr) + 3 * queue) * sizeof(float);
 }
 constexpr int kMaxQueue = 32;
 // Packet kernels are latency bound: two 256-thread blocks per SM (128

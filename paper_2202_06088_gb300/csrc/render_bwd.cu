@@ -176,24 +176,73 @@ __device__ __forceinline__ void adjoint_round(const BwdArgs &a, const Rows &rows
   if (leader) scatter_gradient<KP, DEG, Rows>(a, rows, leaf, s.R, F, dpre_s, dpre_g);
 }
 
-// Adjoint of one shading round for the leaf-major reduction: a lane with a
-// contributing sample leaves its gradient factors (dpre_s, dpre_g, dz) and
-// its ray's frame coordinate u and unit direction in the sample's log slot,
-// notes the leaf in fl and counts the sample for its leaf.  No gradient
+// Octahedral code of a unit direction (the direction divided by its L1 norm,
+// the lower hemisphere folded over the diagonals of the square): two floats
+// instead of three, exact to a few FP32 ulps of the direction (the decoder
+// normalises, so the fast reciprocal's error of an ulp or two only scales
+// the code).
+__device__ __forceinline__ void oct_encode(const float d[3], float &e0, float &e1) {
+  const float s = __fdividef(1.f, fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2]));
+  const float p = d[0] * s, q = d[1] * s;
+  if (d[2] < 0.f) {
+    e0 = copysignf(1.f - fabsf(q), p);
+    e1 = copysignf(1.f - fabsf(p), q);
+  } else {
+    e0 = p;
+    e1 = q;
+  }
+}
+__device__ __forceinline__ void oct_decode(float e0, float e1, float d[3]) {
+  const float z = 1.f - fabsf(e0) - fabsf(e1);
+  float x = e0, y = e1;
+  if (z < 0.f) {
+    x = copysignf(1.f - fabsf(e1), e0);
+    y = copysignf(1.f - fabsf(e0), e1);
+  }
+  const float il = 1.f / sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
+  d[0] = x * il;
+  d[1] = y * il;
+  d[2] = z * il;
+}
+
+// Adjoint of one shading round for the leaf-major reduction, called by every
+// present lane; `has` marks the lanes that hold a sample.  Each sample takes
+// the next position of its leaf's run (lanes of the round that share a leaf
+// take consecutive positions with one atomic), reserved before the sample is
+// evaluated so that the atomic's round trip overlaps the evaluation, and
+// leaves its gradient factors (dpre_s, dpre_g, dz), its ray's frame
+// coordinate u and the octahedral code of its unit direction there.  A
+// sample of zero density leaves a record marked kNoFactor.  No gradient
 // atomics; the per-leaf sums are formed by leaf_reduce_kernel.
 template <int KP, int DEG, typename E, typename Rows>
 __device__ __forceinline__ void adjoint_round_gather(const BwdArgs &a, const Rows &rows, const float *Y, uint32_t leaf,
-                                                     float dt, float u, const float dn[3], bool has, AdjState &st,
-                                                     size_t slot) {
+                                                     float dt, float u, const float dn[3], bool has, unsigned present,
+                                                     AdjState &st) {
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0u;
+  {
+    const unsigned grp = __match_any_sync(present, has ? leaf : kEmpty);
+    if (has && lane == __ffs(grp) - 1) base = atomicAdd(a.gws.cur + leaf, (uint32_t)__popc(grp));
+  }
   Sample<DEG> s;
   float dz[3] = {0.f, 0.f, 0.f}, dpre_s = 0.f, dpre_g = 0.f;
-  if (!(has && sample_factors<KP, DEG, E, Rows>(a, rows, Y, leaf, dt, st, s, dz, dpre_s, dpre_g))) return;
-  float4 *f = a.gws.fac + 3 * slot;
-  f[0] = make_float4(dpre_s, dpre_g, dz[0], dz[1]);
-  f[1] = make_float4(dz[2], u, dn[0], dn[1]);
-  f[2] = make_float4(dn[2], 0.f, 0.f, 0.f);
-  a.gws.fl[slot] = leaf;
-  atomicAdd(a.gws.off + leaf, 1u);
+  const bool contrib = has && sample_factors<KP, DEG, E, Rows>(a, rows, Y, leaf, dt, st, s, dz, dpre_s, dpre_g);
+  // the group again (recomputed rather than held through the evaluation)
+  const unsigned grp = __match_any_sync(present, has ? leaf : kEmpty);
+  base = __shfl_sync(present, base, __ffs(grp) - 1);
+  if (!has) return;
+  const uint32_t p = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+  // the count over the log bounds every run; this keeps a write inside the
+  // workspace even if the log changed between the count and the replay
+  if (p >= a.gws.cap_chunks * (uint32_t)(kLogRounds * 32)) {
+    raise_status(a.tr, kStatusBadIndex);
+    return;
+  }
+  float e0 = kNoFactor, e1 = 0.f;
+  if (contrib) oct_encode(dn, e0, e1);
+  float4 *f = a.gws.fac + 2 * (size_t)p;
+  __stcs(f, make_float4(dpre_s, dpre_g, dz[0], dz[1]));
+  __stcs(f + 1, make_float4(dz[2], u, e0, e1));
 }
 
 // Whether a segment log was written by a forward over these rays.
@@ -205,7 +254,7 @@ __device__ __forceinline__ bool log_matches(const SampleLog &l, long long n) {
 // Sets up the replay of ray i; false when the ray has nothing to replay.
 __device__ __forceinline__ bool adjoint_setup(const BwdArgs &a, long long i, RayWalk &w, float dn[3], float &t,
                                               AdjState &st) {
-  st.target = a.nseg[i];
+  st.target = __ldcs(a.nseg + i);
   if (st.target <= 0) return false;
   float o[3], d[3];
   load_ray(a.rays, i, o, d, t);
@@ -215,11 +264,11 @@ __device__ __forceinline__ bool adjoint_setup(const BwdArgs &a, long long i, Ray
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) {
     st.acc[ch] = 0.f;
-    st.C[ch] = a.rgb[3 * i + ch];
-    st.g[ch] = a.grad_rgb[3 * i + ch];
+    st.C[ch] = __ldcs(a.rgb + 3 * i + ch);
+    st.g[ch] = __ldcs(a.grad_rgb + 3 * i + ch);
   }
-  st.gA = a.grad_alpha ? a.grad_alpha[i] : 0.f;
-  st.T_final = __expf(-a.tau[i]);
+  st.gA = a.grad_alpha ? __ldcs(a.grad_alpha + i) : 0.f;
+  st.T_final = __expf(-__ldcs(a.tau + i));
   return true;
 }
 
@@ -377,7 +426,7 @@ __device__ __noinline__ void adjoint_walk_packet(const BwdArgs &a, long long i, 
   const int B = blockDim.x, tid = threadIdx.x;
   float *my_rows = reinterpret_cast<float *>(smem) + tid;
   const PathRef pr{smem + 2 * KP * B + tid, B};
-  uint32_t *q_leaf = smem + (2 * KP + 16) * B + tid;
+  uint32_t *q_leaf = smem + (2 * KP + path_words(tr)) * B + tid;
   float *q_dt = reinterpret_cast<float *>(q_leaf + queue * B);
   const SmemRows<KP> rows{my_rows, B};
   RayWalk w;
@@ -472,19 +521,19 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
     bool has = false;
     const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
     if (live && st.count < st.target) {
-      leaf = __ldg(a.log.leaf + slot);
+      leaf = __ldcs(a.log.leaf + slot);
       if (leaf != kEmpty) {
         ++st.count;
         has = leaf < (uint32_t)tr.n_leaves;
-        if (has) dt = __ldg(a.log.dt + slot);
+        if (has) dt = __ldcs(a.log.dt + slot);
         else raise_status(tr, kStatusBadIndex);
       }
     }
     // the harmonics of the ray's direction, per round rather than held
     float Y[(DEG + 1) * (DEG + 1)];
     sh_real<DEG>(dn, Y);
-    // chunks with room in the workspace: factors to the slot; others: atomics
-    if (chunk < a.gws.cap_chunks) adjoint_round_gather<KP, DEG, E>(a, rows, Y, leaf, dt, u, dn, has, st, slot);
+    // chunks with room in the workspace: factors to the leaf's run; others: atomics
+    if (chunk < a.gws.cap_chunks) adjoint_round_gather<KP, DEG, E>(a, rows, Y, leaf, dt, u, dn, has, present, st);
     else adjoint_round<KP, DEG, E>(a, rows, Y, leaf, dt, t, has, present, st);
     if (++round == kLogRounds) {
       round = 0;
@@ -497,25 +546,31 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
 // Leaf-major reduction of the gradient factors.
 // ---------------------------------------------------------------------------
 
-// Lists each leaf's slots: off[leaf] advances from the leaf's first position
-// to the next leaf's, so afterwards leaf l owns [off[l-1], off[l]) (0 for the
-// first).  Resets fl to kEmpty for the next launch.
-__global__ void __launch_bounds__(256) slot_scatter_kernel(const GatherWs g, const SampleLog l, long long n_leaves) {
-  const unsigned long long used = *l.counter;  // chunks the forward handed out
-  const long long chunks = (long long)min(used, (unsigned long long)min(l.n_chunks, g.cap_chunks));
+// Counts, per leaf, the samples that the replay will leave in the workspace:
+// every slot of the chunks below the workspace's capacity, read in order (the
+// forward leaves kEmpty in slots without a segment), when the log was written
+// by a forward over these rays.  The 32 slots of a warp are one shading
+// round of one packet: lanes that share a leaf add to its count with one
+// atomic.  A packet whose log ran out of chunks is walked by the replay, so
+// its counted samples only leave unused room at the end of their runs.
+__global__ void __launch_bounds__(256) leaf_count_kernel(const __grid_constant__ BwdArgs a) {
+  if (!log_matches(a.log, a.rays.n)) return;
+  const unsigned long long used = *a.log.counter;  // chunks the forward handed out
+  const long long chunks = (long long)min(used, (unsigned long long)min(a.log.n_chunks, a.gws.cap_chunks));
   const long long n_slots = chunks * kLogRounds * 32;
-  for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < n_slots;
-       sl += (long long)gridDim.x * blockDim.x) {
-    const uint32_t leaf = g.fl[sl];
-    if (leaf == kEmpty) continue;
-    g.fl[sl] = kEmpty;
-    if (leaf >= (uint32_t)n_leaves) continue;
-    const uint32_t pos = atomicAdd(g.off + leaf, 1u);
-    if (pos < (uint32_t)(g.cap_chunks * kLogRounds * 32)) g.idx[pos] = (uint32_t)sl;
+  const uint32_t n_leaves = (uint32_t)a.tr.n_leaves;
+  const int lane = threadIdx.x & 31;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < n_slots; w += warps) {
+    const uint32_t leaf = __ldcs(a.log.leaf + w * 32 + lane);
+    const bool has = leaf < n_leaves;
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, has ? leaf : kEmpty);
+    if (has && lane == __ffs(grp) - 1) atomicAdd(a.gws.off + leaf, (uint32_t)__popc(grp));
   }
 }
 
-// One thread per leaf: sums the factors of the leaf's samples.  Samples of
+// One thread per leaf: sums the factors of the leaf's samples, whose records
+// lie one after another in the leaf's run.  Samples of
 // one frame coordinate u share the basis rows a(u), b(u) and the radial
 // factors R_nl(gamma(u)), so they are summed first (dpre_s, dpre_g and
 // F[ch][l,m] = sum dz[ch] Y_lm) and expanded into the record when u changes:
@@ -581,17 +636,16 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
   const long long leaf = first + threadIdx.x;
   float *acc = acc_s + threadIdx.x * PITCH;
   uint32_t lo = 0, hi = 0;
-  const uint32_t cap = a.gws.cap_chunks * kLogRounds * 32;  // slots of the workspace
   bool before = false;  // Adam: touched before this kernel (the atomic scatter left a part in the row)
   if (leaf < tr.n_leaves) {
-    lo = leaf > 0 ? __ldg(a.gws.off + leaf - 1) : 0u;
-    hi = min(__ldg(a.gws.off + leaf), cap);
+    lo = __ldg(a.gws.off + leaf);
+    hi = min(__ldg(a.gws.cur + leaf), __ldg(a.gws.off + leaf + 1));
     lo = min(lo, hi);
     if (ad.on && a.touched) before = (a.touched[leaf >> 5] >> (leaf & 31)) & 1u;
   }
-  has[threadIdx.x] = (lo < hi ? 1 : 0) | (before ? 2 : 0);
-  if (lo < hi || before)  // only rows the epilogue reads
+  if (lo < hi || before)  // only rows the epilogue may read
     for (int j = 0; j < LEN; ++j) acc[j] = 0.f;
+  bool got = false;  // a sample of nonzero density reached the leaf
   if (lo < hi) {
     LeafRecord<KP, DEG, E> rec;
     rec.load_gamma(tr, (uint32_t)leaf);
@@ -599,33 +653,29 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
 #pragma unroll
     for (int k = 0; k < 3 * NY; ++k) F[k] = 0.f;
     float ps = 0.f, pg = 0.f, u_cur = 0.f;
-    float4 n0, n1, n2;  // the record of the sample after the current one
-    {
-      const float4 *f = a.gws.fac + 3 * (size_t)min(__ldg(a.gws.idx + lo), cap - 1);
-      n0 = __ldg(f);
-      n1 = __ldg(f + 1);
-      n2 = __ldg(f + 2);
-    }
-    uint32_t nidx = lo + 1 < hi ? __ldg(a.gws.idx + lo + 1) : 0u;
+    const float4 *f = a.gws.fac + 2 * (size_t)lo;
+    float4 n0 = __ldg(f), n1 = __ldg(f + 1);  // the record after the current one
     for (uint32_t p = lo; p < hi; ++p) {
-      const float4 f0 = n0, f1 = n1, f2 = n2;
+      const float4 f0 = n0, f1 = n1;
+      f += 2;
       if (p + 1 < hi) {
-        const float4 *f = a.gws.fac + 3 * (size_t)min(nidx, cap - 1);
         n0 = __ldg(f);
         n1 = __ldg(f + 1);
-        n2 = __ldg(f + 2);
-        if (p + 2 < hi) nidx = __ldg(a.gws.idx + p + 2);
       }
-      if (p > lo && f1.y != u_cur) {  // a new frame coordinate: expand the finished group
+      if (f1.z == kNoFactor) continue;  // zero density: no path to the loss
+      if (got && f1.y != u_cur) {  // a new frame coordinate: expand the finished group
         leaf_flush<KP, DEG, E>(tr, rec, u_cur, ps, pg, F, acc);
 #pragma unroll
         for (int k = 0; k < 3 * NY; ++k) F[k] = 0.f;
         ps = pg = 0.f;
       }
+      got = true;
       u_cur = f1.y;
       ps += f0.x;
       pg += f0.y;
-      const float dn[3] = {f1.z, f1.w, f2.x}, dz[3] = {f0.z, f0.w, f1.x};
+      const float dz[3] = {f0.z, f0.w, f1.x};
+      float dn[3];
+      oct_decode(f1.z, f1.w, dn);
       float Y[NY];
       sh_real<DEG>(dn, Y);
 #pragma unroll
@@ -633,10 +683,11 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
 #pragma unroll
         for (int k = 0; k < NY; ++k) F[ch * NY + k] = fmaf(dz[ch], Y[k], F[ch * NY + k]);
     }
-    leaf_flush<KP, DEG, E>(tr, rec, u_cur, ps, pg, F, acc);
+    if (got) leaf_flush<KP, DEG, E>(tr, rec, u_cur, ps, pg, F, acc);
   }
+  has[threadIdx.x] = (got ? 1 : 0) | (before ? 2 : 0);
   if (a.touched && !ad.on) {
-    const unsigned bits = __ballot_sync(0xFFFFFFFFu, lo < hi);
+    const unsigned bits = __ballot_sync(0xFFFFFFFFu, got);
     if ((threadIdx.x & 31) == 0 && bits) atomicOr(a.touched + (leaf >> 5), bits);
   }
   __syncthreads();
@@ -657,23 +708,27 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
     }
     return;
   }
-  // each warp takes rows r and r + nw of the block together (their loads in
-  // flight at once), a lane one 4-entry quad of each
+  // each warp takes kER rows of the block together (r, r + nw, ...: their
+  // loads in flight at once), a lane one 4-entry quad of each
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const float lr_c1 = ad.lr / ad.c1, inv_c2 = 1.f / ad.c2;
   float *__restrict__ mst = ad.master;
   float *__restrict__ mom = ad.m;
   float *__restrict__ vel = ad.v;
   constexpr int QR = (Q4 + 31) / 32;  // quads of a row per lane
-  for (int r0 = threadIdx.x >> 5; r0 < rows_here; r0 += 2 * nw) {
-    int rr[2] = {r0, r0 + nw};
-    int h[2];
+  constexpr int kER = 4;
+  for (int r0 = threadIdx.x >> 5; r0 < rows_here; r0 += kER * nw) {
+    int rr[kER], h[kER], any = 0;
 #pragma unroll
-    for (int e = 0; e < 2; ++e) h[e] = rr[e] < rows_here ? has[rr[e]] : 0;
-    if (!(h[0] | h[1])) continue;  // the same for the whole warp
-    float4 g[2][QR], w[2][QR], m[2][QR], v[2][QR];
+    for (int e = 0; e < kER; ++e) {
+      rr[e] = r0 + e * nw;
+      h[e] = rr[e] < rows_here ? has[rr[e]] : 0;
+      any |= h[e];
+    }
+    if (!any) continue;  // the same for the whole warp
+    float4 g[kER][QR], w[kER][QR], m[kER][QR], v[kER][QR];
 #pragma unroll
-    for (int e = 0; e < 2; ++e)
+    for (int e = 0; e < kER; ++e)
 #pragma unroll
       for (int k = 0; k < QR; ++k) {
         const int q = lane + 32 * k;
@@ -691,12 +746,12 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
           g[e][k].w += x.w;
           *gp = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        w[e][k] = reinterpret_cast<const float4 *>(mst + row)[q];
-        m[e][k] = reinterpret_cast<const float4 *>(mom + row)[q];
-        v[e][k] = reinterpret_cast<const float4 *>(vel + row)[q];
+        w[e][k] = __ldcs(reinterpret_cast<const float4 *>(mst + row) + q);
+        m[e][k] = __ldcs(reinterpret_cast<const float4 *>(mom + row) + q);
+        v[e][k] = __ldcs(reinterpret_cast<const float4 *>(vel + row) + q);
       }
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
+    for (int e = 0; e < kER; ++e) {
       if (!h[e]) continue;
       const size_t row = (size_t)(first + rr[e]) * a.grad_stride;
       float mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;  // FP8: largest magnitudes of w_sigma, w_gamma, w_hh
@@ -719,16 +774,16 @@ __global__ void __launch_bounds__(128) leaf_reduce_kernel(const __grid_constant_
           else if (j < 2 * KP) mx1 = fmaxf(mx1, aw);
           else mx2 = fmaxf(mx2, aw);
         }
-        reinterpret_cast<float4 *>(mst + row)[q] = make_float4(ws[0], ws[1], ws[2], ws[3]);
-        reinterpret_cast<float4 *>(mom + row)[q] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-        reinterpret_cast<float4 *>(vel + row)[q] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        __stcs(reinterpret_cast<float4 *>(mst + row) + q, make_float4(ws[0], ws[1], ws[2], ws[3]));
+        __stcs(reinterpret_cast<float4 *>(mom + row) + q, make_float4(ms[0], ms[1], ms[2], ms[3]));
+        __stcs(reinterpret_cast<float4 *>(vel + row) + q, make_float4(vs[0], vs[1], vs[2], vs[3]));
 #pragma unroll
         for (int c = 0; c < 4; ++c) wq[k][c] = ws[c];
         if (ad.dt == kBF16) {
           unsigned short *st = static_cast<unsigned short *>(ad.storage) + (size_t)(first + rr[e]) * ad.storage_stride;
           const unsigned int lo16 = f32_to_bf16_rne(ws[0]) | ((unsigned int)f32_to_bf16_rne(ws[1]) << 16);
           const unsigned int hi16 = f32_to_bf16_rne(ws[2]) | ((unsigned int)f32_to_bf16_rne(ws[3]) << 16);
-          *reinterpret_cast<uint2 *>(st + 4 * q) = make_uint2(lo16, hi16);
+          __stcs(reinterpret_cast<uint2 *>(st + 4 * q), make_uint2(lo16, hi16));
         }
       }
       if (ad.dt == kFP8) {
@@ -777,7 +832,7 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
   if (!packet) {
     render_bwd_plain_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, 0, s>>>(a);
   } else {
-    const size_t sm = smem_bytes(cfg.block, KP, cfg.queue);
+    const size_t sm = smem_bytes(cfg.block, KP, cfg.queue, a.tr);
     if (sm > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(render_bwd_packet_kernel<KP, DEG, E>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -789,20 +844,21 @@ static cudaError_t bwd_one(bool packet, const BwdArgs &a, const LaunchCfg &cfg, 
       cudaError_t e = sort_packets_by_key(a.log, (a.rays.n + 31) >> 5, a.tr.n_leaves, cfg.num_sms, s);
       if (e != cudaSuccess) return e;
     }
-    const bool gather = a.log.n_chunks && a.gws.cap_chunks;
     const long long nl = a.tr.n_leaves;
+    const bool gather = a.log.n_chunks && a.gws.cap_chunks && nl > 0;
     if (gather) {
+      // samples per leaf counted over the log, scanned into the first
+      // position of each leaf's run; the replay advances a copy of them
       cudaError_t e = cudaMemsetAsync(a.gws.off, 0, (size_t)(nl + 1) * sizeof(uint32_t), s);
+      if (e != cudaSuccess) return e;
+      leaf_count_kernel<<<(unsigned)(16 * cfg.num_sms), 256, 0, s>>>(a);
+      if ((e = launch_exclusive_scan(a.gws.off, nl, a.gws.part, cfg.num_sms, s)) != cudaSuccess) return e;
+      e = cudaMemcpyAsync(a.gws.cur, a.gws.off, (size_t)(nl + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
       if (e != cudaSuccess) return e;
     }
     render_bwd_packet_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, sm, s>>>(a, cfg.queue, cfg.ready);
-    if (gather && nl > 0) {
-      // per-leaf offsets, the slots listed leaf by leaf, then the per-leaf sums
-      cudaError_t e0 = launch_exclusive_scan(a.gws.off, nl, a.gws.part, cfg.num_sms, s);
-      if (e0 != cudaSuccess) return e0;
-      const long long slots = (long long)std::min(a.log.n_chunks, a.gws.cap_chunks) * kLogRounds * 32;
-      slot_scatter_kernel<<<(unsigned)std::min<long long>((slots + 255) / 256, 16LL * cfg.num_sms), 256, 0, s>>>(
-          a.gws, a.log, nl);
+    if (gather) {
+      // the per-leaf sums over each leaf's run
       AdamArgs ad{};
       if (adam && adam->on) ad = *adam;
       constexpr int kReduceBlock = 64;

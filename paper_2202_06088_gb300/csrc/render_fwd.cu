@@ -28,16 +28,18 @@ __global__ void __launch_bounds__(256) render_plain_kernel(const __grid_constant
   if (a.out.nseg) a.out.nseg[i] = r.nseg;
 }
 
+// Outputs and the segment log are written once and read by later launches:
+// stores with the evict-first (streaming) policy.
 __device__ __forceinline__ void write_miss(const DevOut &out, long long i) {
   if (out.rgb) {
-    out.rgb[3 * i + 0] = 0.f;
-    out.rgb[3 * i + 1] = 0.f;
-    out.rgb[3 * i + 2] = 0.f;
+    __stcs(out.rgb + 3 * i + 0, 0.f);
+    __stcs(out.rgb + 3 * i + 1, 0.f);
+    __stcs(out.rgb + 3 * i + 2, 0.f);
   }
-  out.alpha[i] = 0.f;
-  if (out.depth) out.depth[i] = INFINITY;
-  if (out.tau) out.tau[i] = 0.f;
-  if (out.nseg) out.nseg[i] = 0;
+  __stcs(out.alpha + i, 0.f);
+  if (out.depth) __stcs(out.depth + i, INFINITY);
+  if (out.tau) __stcs(out.tau + i, 0.f);
+  if (out.nseg) __stcs(out.nseg + i, 0);
 }
 
 // Packet forward kernel: one thread per ray, so each warp is a packet of 32
@@ -65,7 +67,7 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long pos, 
   const int B = blockDim.x, tid = threadIdx.x;
   float *my_rows = reinterpret_cast<float *>(smem) + tid;
   const PathRef pr{smem + 2 * KP * B + tid, B};
-  uint32_t *q_leaf = smem + (2 * KP + 16) * B + tid;
+  uint32_t *q_leaf = smem + (2 * KP + path_words(tr)) * B + tid;
   float *q_t0 = reinterpret_cast<float *>(q_leaf + queue * B);
   float *q_dt = q_t0 + queue * B;
   const SmemRows<KP> rows{my_rows, B};
@@ -139,8 +141,8 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long pos, 
       }
       if (logging) {
         const size_t slot = ((size_t)chunk * kLogRounds + round) * 32 + lane;
-        a.log.leaf[slot] = qn > 0 ? q_leaf[qh * B] : kEmpty;
-        a.log.dt[slot] = qn > 0 ? q_dt[qh * B] : 0.f;
+        __stcs(a.log.leaf + slot, qn > 0 ? q_leaf[qh * B] : kEmpty);
+        __stcs(a.log.dt + slot, qn > 0 ? q_dt[qh * B] : 0.f);
         ++round;
       }
     }
@@ -201,16 +203,32 @@ __device__ __forceinline__ void packet_forward(const FwdArgs &a, long long pos, 
       }
     }
   }
+  if (logging) {
+    // slots that hold no segment read kEmpty, so that the log can be read
+    // slot by slot: the rounds of the last chunk that the packet did not
+    // reach, and in the packet past the last ray, the slots of its absent
+    // lanes in every chunk
+    for (int r = round; r < kLogRounds; ++r) a.log.leaf[((size_t)chunk * kLogRounds + r) * 32 + lane] = kEmpty;
+    if (present != 0xFFFFFFFFu && lane == __ffs(present) - 1) {
+      uint32_t c = a.log.heads[pk];
+      for (uint32_t k = 0; k < a.log.n_chunks && c < a.log.n_chunks; ++k) {
+        for (int j = 0; j < kLogRounds * 32; ++j)
+          if (!((present >> (j & 31)) & 1u)) a.log.leaf[(size_t)c * kLogRounds * 32 + j] = kEmpty;
+        if (c == chunk) break;
+        c = a.log.next[c];
+      }
+    }
+  }
   if (!hit) return;
   if (kShade != kShadeAlpha) {
-    a.out.rgb[3 * i + 0] = C0;
-    a.out.rgb[3 * i + 1] = C1;
-    a.out.rgb[3 * i + 2] = C2;
+    __stcs(a.out.rgb + 3 * i + 0, C0);
+    __stcs(a.out.rgb + 3 * i + 1, C1);
+    __stcs(a.out.rgb + 3 * i + 2, C2);
   }
-  a.out.alpha[i] = A;
-  if (a.out.depth) a.out.depth[i] = A >= 1e-4f ? dnum / A : INFINITY;
-  if (a.out.tau) a.out.tau[i] = tau;
-  if (a.out.nseg) a.out.nseg[i] = nseg;
+  __stcs(a.out.alpha + i, A);
+  if (a.out.depth) __stcs(a.out.depth + i, A >= 1e-4f ? dnum / A : INFINITY);
+  if (a.out.tau) __stcs(a.out.tau + i, tau);
+  if (a.out.nseg) __stcs(a.out.nseg + i, nseg);
 }
 
 // Packet forward kernel.  With a work counter the grid is persistent: each
@@ -288,7 +306,7 @@ static cudaError_t fwd_one(bool packet, const FwdArgs &a, const LaunchCfg &cfg, 
   if (!packet) {
     render_plain_kernel<KP, DEG, E><<<(unsigned)blocks, cfg.block, 0, s>>>(a);
   } else {
-    const size_t sm = smem_bytes(cfg.block, KP, cfg.queue);
+    const size_t sm = smem_bytes(cfg.block, KP, cfg.queue, a.tr);
     if (sm > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(render_packet_kernel<KP, DEG, E>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -538,7 +556,7 @@ static cudaError_t render_slice_one(const FwdArgs &a, const LaunchCfg &cfg, cuda
   const bool persistent = a.work != nullptr;
   cudaError_t e;
   if (persistent && (e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-  const size_t sm = smem_bytes(cfg.block, 8, cfg.queue);
+  const size_t sm = smem_bytes(cfg.block, 8, cfg.queue, a.tr);
   if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(render_packet_kernel<8, DEG, __nv_bfloat16, kShadeSlice>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
     return e;
@@ -663,7 +681,7 @@ template <int KP, int DEG, typename E>
 static cudaError_t edit_one(const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
   if (a.rays.n == 0) return cudaSuccess;
   const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
-  const size_t sm = smem_bytes(cfg.block, KP, cfg.queue);
+  const size_t sm = smem_bytes(cfg.block, KP, cfg.queue, a.tr);
   cudaError_t e;
   if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(render_packet_kernel<KP, DEG, E, kShadeEdit>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
@@ -690,7 +708,7 @@ template <int KP, int DEG, typename E>
 static cudaError_t alpha_one(const FwdArgs &a, const LaunchCfg &cfg, cudaStream_t s) {
   if (a.rays.n == 0) return cudaSuccess;
   const long long blocks = (a.rays.n + cfg.block - 1) / cfg.block;
-  const size_t sm = smem_bytes(cfg.block, KP, cfg.queue);
+  const size_t sm = smem_bytes(cfg.block, KP, cfg.queue, a.tr);
   cudaError_t e;
   if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(render_packet_kernel<KP, DEG, E, kShadeAlpha>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)

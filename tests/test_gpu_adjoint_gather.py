@@ -1,13 +1,13 @@
-"""GPU parity of the leaf-major adjoint (neuvv_tree_reserve_adjoint): the
-replayed samples leave their gradient factors in their log slots, a counting
-sort lists each leaf's samples, and one thread per leaf sums them into its
-gradient record.  Checked against the FP64 oracle's analytic gradient at the
+"""GPU parity of the leaf-major adjoint (neuvv_tree_reserve_adjoint): a count
+over the segment log gives each leaf's samples, the replayed samples leave
+their gradient factors at the next position of their leaf's run, and one
+thread per leaf sums its run into its gradient record.  Checked against the FP64 oracle's analytic gradient at the
 adjoint's bar (per leaf record, relative 1e-4 plus 1e-6 of the largest), and
 against the atomic scatter on the same inputs: every gradient entry within
 1e-5 of its plane's largest entry (FP32 summation order is all that differs),
 the touched bitmap identical.  Covers FP32, BF16 and FP8 storage, both record
 shapes, a reservation smaller than the log (chunks past it take the atomic
-path), repeated calls (the workspace's slot marks are reset by each call) and
+path), repeated calls (each call counts and lays out the runs afresh) and
 the full-size training workload."""
 import numpy as np
 import pytest

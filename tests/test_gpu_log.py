@@ -156,3 +156,49 @@ def test_log_read_marks_rays_without_a_log(B):
     logged = c >= 0
     assert torch.equal(c[logged], ns[logged])
     assert ((c == -1) | logged).all().item() and (~logged).any().item() and logged.any().item()
+
+
+def _log_leaf_slots(log, n_rays):
+    """The leaf entries of the chunks the forward handed out, from the log's
+    layout (64-byte header; heads, keys and order per packet, the ray
+    permutation, the sort bins, next links; then leaf and chord per slot)."""
+    words = log.cpu().numpy().view(np.uint32)
+    used = int(words[0]) | (int(words[1]) << 32)
+    n_chunks = int(words[2])
+    n_packets = (n_rays + 31) // 32
+    pk_bytes = (4 * n_packets + 15) // 16 * 16
+    perm_bytes = (4 * n_rays + 15) // 16 * 16
+    fixed = 64 + 3 * pk_bytes + perm_bytes + 4 * 4096
+    leaf_off = (fixed + 4 * n_chunks + 15) // 16 * 16
+    chunks = min(used, n_chunks)
+    return words[leaf_off // 4: leaf_off // 4 + chunks * 8 * 32], words[16: 16 + n_packets]
+
+
+@pytest.mark.parametrize("n", [4096 + 3, 32 * 40])
+def test_log_slots_without_a_segment_read_empty(B, n):
+    """Every slot of a chunk the forward handed out holds a segment or kEmpty,
+    so that the adjoint can count each leaf's samples slot by slot: the rounds
+    of a packet's last chunk after its end and the lanes past the last ray are
+    written empty.  The log starts out as zeros (leaf 0, a real leaf), so a
+    slot left unwritten would add samples of leaf 0."""
+    tree = I.config1_tree()
+    rays, _ = I.config1_rays()
+    rays = rays.subset(np.arange(n) + 6000)             # rows through the middle of the view
+    tree_d = B.Tree(tree, "bf16")
+    dr = B.DeviceRays.from_host(rays)
+    # every ray of these rows crosses the object: 4 KB per ray holds every packet
+    out = B.alloc_out(dr.n, dr.o.device, log_bytes_per_ray=4096)
+    out["log"].zero_()
+    B.neuvv_render(tree_d, dr, kernel="packet", out=out)
+    torch.cuda.synchronize()
+    leaf, heads = _log_leaf_slots(out["log"], dr.n)
+    nseg = out["nseg"].cpu().numpy()
+    logged = np.repeat(heads != 0xFFFFFFFF, 32)[:dr.n]
+    assert logged.any()
+    assert (nseg[~logged] == 0).all(), np.nonzero(nseg[~logged])[0][:8]   # packets without a chunk shaded nothing
+    full = int((leaf != 0xFFFFFFFF).sum())
+    assert full == int(nseg.sum()), (full, int(nseg.sum()), leaf.size)
+    dec = B.neuvv_log_read(out, dr.n, 256)
+    assert torch.equal(dec["count"], out["nseg"])
+    assert int((leaf == 0).sum()) == int(np.count_nonzero(dec["leaf"].cpu().numpy() == 0))
+    assert tree_d.status() == 0

@@ -453,13 +453,19 @@ __device__ __forceinline__ bool walk_step(const DevTree &tr, const uint32_t *s_c
       w.t_lo = x_lo;
     }
     // on the other axes the neighbour of a finest cell across the exit face
-    // has the same coordinates; a larger box needs the exit point's cell
+    // has the same coordinates; a larger box needs the exit point's cell.
+    // The ray's coordinates move one way only, so a cell behind the current
+    // one on such an axis is the exit point's rounding (at an edge the ray
+    // crosses, the exit plane of one axis and a cell boundary of another at
+    // one distance) and is not taken: otherwise two boxes meeting at that
+    // edge could hand the walk back and forth without progress.
     if (!fine) {
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         if (b != ax) {
           const float p = fmaf(w.t_cur, w.gd[b], w.go[b]);
-          w.cell[b] = min(max(cell_of(p, w.gd[b], N), lo[b]), hi[b] - 1);
+          const int c = min(max(cell_of(p, w.gd[b], N), lo[b]), hi[b] - 1);
+          w.cell[b] = w.gd[b] > 0.f ? max(c, w.cell[b]) : (w.gd[b] < 0.f ? min(c, w.cell[b]) : c);
         }
       }
     }

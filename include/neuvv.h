@@ -276,10 +276,10 @@ neuvv_status neuvv_render_slice(const neuvv_tree *tree, const float *slice, int3
  * Samples in chunks beyond the reservation, and packets the log could not
  * hold, use the atomic scatter.  The result equals the atomic path's up to
  * FP32 summation order.  It pays when a call has many samples per leaf (8
- * views at 1080p over 2 M leaves, 17 samples per leaf: adjoint 6.9 against
- * 7.5 ms); with fewer samples than leaves its per-leaf pass costs more than
- * the atomics it saves (1 M rays over 8 M leaves: training step 8.5 against
- * 7.6 ms).  Trees of more than 2^24 leaves: NEUVV_ERR_UNSUPPORTED;
+ * views at 1080p over 2 M leaves, 17 samples per leaf: adjoint with Adam 6.5
+ * against 7.4 ms); with fewer samples than leaves its per-leaf pass costs
+ * more than the atomics it saves (1 M rays over 8 M leaves: training step
+ * 5.8 against 4.8 ms).  Trees of more than 2^24 leaves: NEUVV_ERR_UNSUPPORTED;
  * n_slots outside [0, 2^32 - 256]: NEUVV_ERR_INVALID_ARG; allocation failure:
  * NEUVV_ERR_OOM (the tree keeps no reservation). */
 neuvv_status neuvv_tree_reserve_adjoint(neuvv_tree *tree, int64_t n_slots);

@@ -914,7 +914,7 @@ def main():
         "roofline": roof,
         "roofline_other_parts": roof_other,
         "e2e": e2e,
-        "gpu_launches": (8 if args.no_gather else 12) * args.steps,
+        "gpu_launches": (8 if args.no_gather else 9) * args.steps,
         "clocks": clk,
     }
     if not args.no_extra:

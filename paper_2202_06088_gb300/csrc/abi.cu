@@ -950,6 +950,7 @@ neuvv_status prepare_backward(const neuvv_tree *t, const neuvv_rays *rays, float
   a.act = opts->color_act;
   a.log = log_view(saved->log, saved->log_bytes, rays->n);
   const bool packet = opts->kernel != NEUVV_KERNEL_PLAIN;
+  a.key_order = 1;
   a.gws = packet && a.log.n_chunks ? t->gws : GatherWs{};
   return NEUVV_OK;
 }

@@ -101,6 +101,7 @@ struct BwdArgs {
   float t_stop;
   int act;
   SampleLog log;          // the forward's segment log (n_chunks == 0: walk every packet)
+  int key_order;          // the replay takes the logged packets in key order (1) or in ray order (0)
 };
 
 // Adam step applied by the per-leaf reduction of the adjoint (the fused

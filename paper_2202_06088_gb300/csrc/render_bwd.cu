@@ -484,7 +484,8 @@ __global__ void __launch_bounds__(256, packet_min_blocks<E>()) render_bwd_packet
   const int B = blockDim.x, tid = threadIdx.x;
   float *my_rows = reinterpret_cast<float *>(smem) + tid;
   const SmemRows<KP> rows{my_rows, B};
-  // warp w adjoins packet w, or with a valid log the w-th packet in key order
+  // warp w adjoins packet w, or with a valid log in key order (the atomic
+  // scatter) the w-th packet of that order
   const long long n_packets = (a.rays.n + 31) >> 5;
   const long long wp = ((long long)blockIdx.x * B + tid) >> 5;
   if (wp >= n_packets) return;

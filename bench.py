@@ -9,9 +9,9 @@ resident in HBM.  Coefficients are stored in BF16 with an FP32 master copy.
 One step = forward render (packet kernel) -> loss gradient against fixed
 target images (Eq. rgb-loss plus 0.1 x the image-gradient regulariser of
 Sec. 4.3) -> fused adjoint and sparse Adam on the touched leaves in one call
-(gradient sums formed per leaf after a counting sort of the samples, where a
-step has at least one ray per leaf, and the Adam update applied by the same
-per-leaf pass).  The
+(gradient sums formed per leaf from each leaf's run of samples, laid out by
+a count over the segment log, where a step has at least one ray per leaf,
+and the Adam update applied by the same per-leaf pass).  The
 headline metric is leaf-segment samples per second of the forward+backward
 pair (a sample is one leaf segment evaluated by the forward and re-evaluated
 by the adjoint, counted once).
